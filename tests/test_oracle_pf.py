@@ -1,0 +1,151 @@
+"""Pins of the oracle's particle filter (Sec. II-A; one tracker per agent per
+target, Sec. III-A.2) against closed forms, brute-force Bayes, exact-rational
+systematic resampling and textbook least-squares trilateration."""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from synth import preset
+
+
+def _env(n_envs=2, seed=0, **kw):
+    p = preset("fleet5", n_envs=n_envs).replace(**kw)
+    e = oracle.OracleEnv(p, seed)
+    e.reset(0)
+    return e
+
+
+def test_predict_closed_form_without_noise_or_measurements():
+    """sigma_a = 0 and nothing heard: p_T = p_0 + T dt v, velocities unchanged."""
+    e = _env(n_envs=2, n_particles=64, pf_accel_sigma=0.0, det_radius=0.0)
+    rng = np.random.default_rng(1)
+    vx = rng.uniform(-1, 1, e.F * 64)
+    vy = rng.uniform(-1, 1, e.F * 64)
+    e.set_arrays(pvx=vx, pvy=vy)
+    px0, py0 = e.arr["px"].copy(), e.arr["py"].copy()
+    for _ in range(7):
+        o = e.step(np.full(e.NA, 3, np.int32), want=("idx",))
+        assert np.all(o["idx"].reshape(e.F, 64) == np.arange(64))
+    np.testing.assert_allclose(e.arr["px"], px0 + 7 * 30 * vx, atol=1e-9)
+    np.testing.assert_allclose(e.arr["py"], py0 + 7 * 30 * vy, atol=1e-9)
+
+
+def test_velocity_cap():
+    e = _env(n_envs=1, n_particles=8, pf_accel_sigma=0.0, det_radius=0.0)
+    e.set_arrays(pvx=np.full(e.F * 8, 3.0), pvy=np.full(e.F * 8, 4.0))
+    e.step(np.full(e.NA, 3, np.int32))
+    np.testing.assert_allclose(np.hypot(e.arr["pvx"], e.arr["pvy"]), 1.2 * 1.5, rtol=1e-14)
+    np.testing.assert_allclose(e.arr["pvy"] / e.arr["pvx"], 4.0 / 3.0, rtol=1e-14)
+
+
+def test_weights_brute_force_bayes_p4():
+    """Posterior of 4 particles = normalised product of Gaussian range pdfs."""
+    e = _env(n_envs=1, n_particles=4, pf_accel_sigma=0.0, range_sigma=3.0, target_depth_max=30.0)
+    rng = np.random.default_rng(5)
+    e.set_arrays(px=e.arr["px"] + rng.normal(0, 5, e.F * 4), pvx=np.zeros(e.F * 4), pvy=np.zeros(e.F * 4))
+    o = e.step(np.full(e.NA, 3, np.int32), want=("pred_px", "weight", "meas", "meas_n"))
+    for f in range(e.F):
+        k = f % 5
+        n = o["meas_n"][f]
+        assert n > 0
+        post = np.ones(4)
+        for m in o["meas"][f, :n]:
+            dist = np.sqrt((o["pred_px"][f * 4:f * 4 + 4] - m[0]) ** 2 + (o["pred_py"][f * 4:f * 4 + 4] - m[1]) ** 2
+                           + (e.arr["tz"][k] - m[2]) ** 2)
+            post *= stats.norm.pdf(m[3], loc=dist, scale=3.0)
+        w = o["weight"][f * 4:f * 4 + 4]
+        assert w.sum() == pytest.approx(1.0, abs=1e-14)
+        if post.sum() > 1e-250:
+            np.testing.assert_allclose(w, post / post.sum(), rtol=1e-9, atol=1e-15)
+
+
+def test_single_measurement_argmax_is_nearest_to_range_circle():
+    e = _env(n_envs=1, n_particles=256, max_agents=1, max_targets=1, pf_accel_sigma=0.0)
+    rng = np.random.default_rng(2)
+    e.set_arrays(px=e.arr["tx"][0] + rng.uniform(-300, 300, 256), py=e.arr["ty"][0] + rng.uniform(-300, 300, 256),
+                 pvx=np.zeros(256), pvy=np.zeros(256))
+    o = e.step(np.zeros(1, np.int32), want=("pred_px", "weight", "meas", "meas_n"))
+    assert o["meas_n"][0] == 1
+    qx, qy, _, r = o["meas"][0, 0]
+    gap = np.abs(np.hypot(o["pred_px"] - qx, o["pred_py"] - qy) - r)
+    assert np.argmax(o["weight"]) == np.argmin(gap)
+
+
+def _brute_resample(wmax, u64):
+    """Systematic resampling by its definition in exact rationals: weights
+    quantised to q_i = floor(w_i 2^38), C_i = Q_i / W, u0 = floor(u64 W / 2^64) / W,
+    u_j = (j + u0) / P, idx_j = min{i : C_i > u_j}."""
+    P = len(wmax)
+    q = [int(math.floor(Fraction(w) * 2 ** 38)) for w in wmax]
+    Q = np.cumsum(q).tolist()
+    W = Q[-1]
+    u0 = Fraction((u64 * W) >> 64, W)
+    out = []
+    for j in range(P):
+        u = (j + u0) / P
+        out.append(next(i for i in range(P) if Fraction(Q[i], W) > u))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("P", [1, 2, 3, 5, 8, 13, 16])
+def test_resample_brute_force_small(P):
+    rng = np.random.default_rng(P)
+    for trial in range(40):
+        if trial % 3 == 0:   # dyadic weights: exact in any summation order
+            w = rng.integers(0, 9, P) / 8.0
+        elif trial % 3 == 1:  # heavy-tailed
+            w = np.exp(-rng.exponential(8.0, P))
+        else:
+            w = rng.uniform(0, 1, P)
+        w[rng.integers(0, P)] = 1.0  # max-normalised
+        u64 = int(rng.integers(0, 2 ** 63)) * 2 + int(rng.integers(0, 2))
+        np.testing.assert_array_equal(oracle.systematic_resample(w, u64), _brute_resample(w, u64))
+
+
+def test_resample_structure():
+    rng = np.random.default_rng(9)
+    P = 1000
+    # uniform weights give the identity map
+    np.testing.assert_array_equal(oracle.systematic_resample(np.ones(P), int(rng.integers(0, 2 ** 63))),
+                                  np.arange(P))
+    for _ in range(20):
+        w = np.exp(-rng.exponential(2.0, P))
+        w /= w.max()
+        idx = oracle.systematic_resample(w, int(rng.integers(0, 2 ** 63)))
+        assert np.all(np.diff(idx) >= 0)
+        counts = np.bincount(idx, minlength=P)
+        q = np.floor(w * 2 ** 38)
+        expect = P * q / q.sum()
+        assert np.all(counts >= np.floor(expect) - 1e-9) and np.all(counts <= np.ceil(expect) + 1e-9)
+
+
+def _ls_trilateration(q, r):
+    """Textbook linearised least squares: subtract the first circle equation."""
+    A = 2 * (q[1:] - q[0])
+    b = (r[0] ** 2 - r[1:] ** 2) + (q[1:] ** 2).sum(1) - (q[0] ** 2).sum()
+    return np.linalg.lstsq(A, b, rcond=None)[0]
+
+
+def test_static_target_trilateration_convergence():
+    """Static target, three non-collinear agents circling, small range noise:
+    the filter estimate converges to the truth and to the LS fix."""
+    e = _env(n_envs=1, n_particles=2000, max_agents=3, max_targets=1, target_speed_min=0.0,
+             target_speed_max=0.0, range_sigma=0.2, pf_accel_sigma=0.02, pf_vcap=0.05, heading_noise=0.0,
+             target_drift_sigma=0.0)
+    pooled = [[] for _ in range(3)]
+    for t in range(40):
+        o = e.step(np.array([6, 0, 5], np.int32), want=("meas", "meas_n"))
+        for a in range(3):
+            pooled[a].extend(o["meas"][a, :o["meas_n"][a]])
+    truth = np.array([e.arr["tx"][0], e.arr["ty"][0]])
+    for a in range(3):
+        est = np.array([e.arr["estx"][a], e.arr["esty"][a]])
+        assert np.linalg.norm(est - truth) < 1.0
+        m = np.array(pooled[a])  # static target: every step's pings constrain the same point
+        ls = _ls_trilateration(m[:, :2], m[:, 3])
+        assert np.linalg.norm(ls - truth) < 1.0
+        assert np.linalg.norm(est - ls) < 1.5
