@@ -1,0 +1,271 @@
+/*
+ * utrack.h — C ABI of the GB300 batched underwater-tracking environment.
+ *
+ * The library advances thousands of independent range-only tracking episodes
+ * at once on one GPU: LRAUV heading kinematics, target motion, noisy
+ * range-only pings, inter-agent communication, one particle filter per
+ * (agent, target), observation tokens and reward, the transformer agent that
+ * picks the next actions, and an optional learned range-only estimator.
+ *
+ * Paper: Gallici, Masmitja, Martin, "Scaling Multi-Agent Reinforcement
+ * Learning for Underwater Acoustic Tracking via Autonomous Vehicles"
+ * (arXiv 2505.08222).  Section references below are to that paper.
+ *
+ * Conventions for every entry point:
+ *   - Return value: UT_OK or an error code; nothing throws across the ABI.
+ *     env_last_error() describes the most recent error of a handle.
+ *   - Asynchrony: every call is enqueued on the handle's CUDA stream and
+ *     returns without waiting, except the ones documented as synchronising.
+ *   - Pointers named *_dev are device pointers; *_host are host pointers.
+ *     Device pointers returned by the library are borrowed: they stay valid
+ *     until env_destroy() and their contents change with the next mutating
+ *     call.  Caller-owned pointers are only read or written during the call
+ *     (or, for device pointers, by the work the call enqueues).
+ *   - Layouts: struct-of-arrays, float32 unless stated.  Agents, targets and
+ *     filters of all environments are concatenated in environment order
+ *     (CSR offsets from the per-environment counts).  Filter f of
+ *     environment e, observer agent a, target k is
+ *     f = filter_off[e] + a * T_e + k; particle i of filter f sits at
+ *     f * n_particles + i (64-bit index).
+ *   - A handle is not thread-safe.
+ */
+#ifndef UTRACK_H
+#define UTRACK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define UT_ABI_VERSION 1u
+#define UT_MAX_AGENTS 8      /* per environment */
+#define UT_MAX_TARGETS 8     /* per environment */
+#define UT_MAX_PARTICLES 4096
+#define UT_TOKEN_FEATURES 8  /* observation token width */
+#define UT_EST_RING 16       /* pings kept per filter for the learned estimator */
+#define UT_EST_FEATURES 96   /* estimator input width (80 used, 16 zero) */
+
+typedef enum {
+  UT_OK = 0,
+  UT_ERR_INVALID = 1,     /* bad argument or configuration */
+  UT_ERR_NOMEM = 2,       /* allocation failed */
+  UT_ERR_CUDA = 3,        /* CUDA runtime error (message in env_last_error) */
+  UT_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+  UT_ERR_STATE = 5,       /* call not valid in the handle's current state */
+  UT_ERR_UNSUPPORTED = 6  /* feature not available in this build/config */
+} ut_status;
+
+/* Caller-supplied device allocator.  alloc(bytes, stream, ctx) returns a
+ * device pointer aligned to at least 256 bytes or NULL; free(ptr, stream,
+ * ctx) releases it.  NULL allocator: the library uses cudaMallocAsync /
+ * cudaFreeAsync on the handle's stream. */
+typedef struct ut_allocator {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, void* stream, void* ctx);
+  void* ctx;
+} ut_allocator;
+
+/* Flags of ut_config.flags. */
+#define UT_FLAG_DEBUG 1u       /* keep per-step intermediates (ut_debug_view) */
+#define UT_FLAG_RING 2u        /* maintain the estimator ping ring every step */
+
+/* Environment configuration (plain data, read at env_create only).
+ * Constants of Sec. III-A.2 / III-A.3; the readings for what the paper leaves
+ * open are the defaults documented per field. */
+typedef struct ut_config {
+  uint32_t abi_version;        /* must be UT_ABI_VERSION */
+  uint32_t flags;              /* UT_FLAG_* */
+  int32_t n_envs;              /* E >= 1 */
+  int32_t max_agents;          /* 1..UT_MAX_AGENTS */
+  int32_t max_targets;         /* 1..UT_MAX_TARGETS */
+  int32_t n_particles;         /* P, 1..UT_MAX_PARTICLES, per filter */
+  int32_t horizon;             /* episode length in steps (Termination paragraph) */
+  const int32_t* agents_per_env_host;   /* [E] in 1..max_agents, or NULL: all max_agents */
+  const int32_t* targets_per_env_host;  /* [E] in 1..max_targets, or NULL: all max_targets */
+  float dt;                    /* step length, s (30 s, Sec. III-A.2) */
+  float agent_speed;           /* m/s (1.0, Actions Space paragraph) */
+  float heading_noise;         /* std of Gaussian heading noise, rad (0.02, Sec. III-A.3) */
+  int32_t action_mode;         /* 0: {-turn, 0, +turn}; 1: equidistant rudder angles */
+  int32_t n_actions;           /* 3 for mode 0; 2..8 for mode 1 (7 default) */
+  float turn_angle;            /* mode 0 heading change, rad */
+  float rudder_max;            /* mode 1: rudder in [-rudder_max, rudder_max] (0.24 rad) */
+  float rudder_gain;           /* mode 1: heading change = gain * rudder (1.45/0.24) */
+  int32_t target_model;        /* 0: heading redrawn uniformly each step; 1: Gaussian drift */
+  float target_speed_min, target_speed_max;  /* per-target speed drawn at reset, m/s */
+  float target_drift_sigma;    /* model 1 heading increment std, rad */
+  float target_depth_max;      /* target depth drawn in [0, max), m (0: surface) */
+  float range_sigma;           /* range noise std, m */
+  float det_radius;            /* pings heard iff 3-D distance <= det_radius, m */
+  float comm_radius;           /* messages received iff distance <= comm_radius, m */
+  float comm_drop;             /* probability that a message is dropped */
+  float pf_accel_sigma;        /* particle velocity random-walk std per step, m/s */
+  float pf_vcap;               /* particle speed cap, m/s */
+  int32_t reward_type;         /* 0: tracking reward Eq. (1); 1: follow reward Eq. (2) */
+  float eps_min, eps_max;      /* Eq. (1) errors, m (10, 50) */
+  float follow_dmin;           /* Eq. (2) distance, m (50; 100 for fast targets) */
+  float d_safe;                /* crash distance between agents, m */
+  float spawn_min;             /* minimum spawn distance between entities, m (50) */
+  float spawn_radius;          /* spawn disk radius, m (100 = half the 200 m maximum) */
+  int32_t spawn_tries;         /* rejection-sampling tries per entity (64) */
+  float feature_scale;         /* S: metres per unit in tokens and estimator features */
+  int32_t d_model;             /* transformer agent width; 0 = no policy */
+  int32_t n_layers;            /* transformer blocks */
+  int32_t n_heads;             /* attention heads (d_model % n_heads == 0) */
+} ut_config;
+
+typedef struct ut_env ut_env;
+
+/* Borrowed device views of one step's outputs. */
+typedef struct ut_step_out {
+  const float* reward;       /* [E] shared reward (Eq. 1 or 2, normalised, -1 on crash) */
+  const int32_t* done;       /* [E] 1 when the episode reached the horizon */
+  const uint16_t* obs;       /* [NA][A_max+T_max][8] bf16 bit patterns */
+  const float* estx;         /* [F] tracker estimate x */
+  const float* esty;         /* [F] tracker estimate y */
+  const float* err;          /* [F] 2-D tracking error of the estimate */
+  const int32_t* actions;    /* [NA] actions applied this step */
+  const float* logits;       /* [NA][n_actions] policy logits (NULL without policy) */
+} ut_step_out;
+
+/* Device views of the full environment state (struct of arrays). */
+typedef struct ut_state_view {
+  float *ax, *ay, *apsi;              /* agents [NA]; depth 0 */
+  float *tx, *ty, *tz, *tpsi, *tspeed;/* targets [NT] */
+  float *px, *py, *pvx, *pvy;         /* particles [F * P] */
+  float *lpx, *lpy;                   /* last received pose of teammate b at agent a [NA * A_max] */
+  int32_t* lpage;                     /* steps since that reception [NA * A_max] */
+  float *estx, *esty;                 /* tracker estimates [F] */
+  float* ring;                        /* estimator ring [F][16][4] (qx, qy, r, step) */
+  int32_t *ring_head, *ring_count;    /* [F] */
+  uint16_t* h;                        /* recurrent token bf16 [NA][d_model] (NULL without policy) */
+  uint32_t step;                      /* global step counter g (random-stream position) */
+  int32_t t_ep;                       /* steps since the last reset */
+  int64_t n_agents, n_targets, n_filters; /* sizes, filled by env_get_state */
+} ut_state_view;
+
+/* Borrowed device views of per-step intermediates (UT_FLAG_DEBUG only). */
+typedef struct ut_debug_view {
+  float* range;        /* [F] noisy range heard by agent a of target k (0 if not heard) */
+  int32_t* valid;      /* [F] detection bit */
+  int32_t* recv;       /* [NA * A_max] agent a received agent b */
+  float* meas;         /* [F][A_max][4] (qx, qy, qz, r) measurement list of each filter */
+  int32_t* meas_n;     /* [F] */
+  float *pred_px, *pred_py, *pred_pvx, *pred_pvy; /* [F * P] particles after predict */
+  float* weight;       /* [F * P] normalised weights */
+  float* wmax;         /* [F * P] exp(l_i - max l) */
+  int32_t* idx;        /* [F * P] resample indices (identity without measurements) */
+} ut_debug_view;
+
+/* Statistics accumulated on the device since the last env_reset /
+ * env_metrics_reset. */
+typedef struct ut_rollout_stats {
+  double sum_sq_err;       /* sum of squared 2-D tracking errors over filters and steps */
+  int64_t n_err;           /* number of terms in sum_sq_err */
+  double rmse;             /* sqrt(sum_sq_err / n_err) */
+  double reward_sum;       /* sum over envs and steps */
+  int64_t crash_count;     /* env-steps with a crash */
+  int64_t agent_steps;     /* sum over steps of the number of agents */
+  int64_t steps;           /* environment steps */
+  int32_t device_status;   /* device error word (0 = none) */
+  int64_t kernel_launches; /* kernels the library enqueued since the metrics were cleared */
+} ut_rollout_stats;
+
+/* Creates a handle and allocates every state buffer through `allocator`
+ * (NULL: cudaMallocAsync).  `cuda_stream` (cudaStream_t, NULL = legacy
+ * default stream) orders all later work of the handle.  Validates sizes:
+ * counts within the maxima, 1 <= P <= UT_MAX_PARTICLES, d_model % n_heads.
+ * Errors: UT_ERR_INVALID, UT_ERR_NOMEM, UT_ERR_CUDA.  On error *out is NULL. */
+ut_status env_create(const ut_config* cfg, const ut_allocator* allocator, void* cuda_stream, ut_env** out);
+
+/* Releases every buffer of the handle (after the stream's pending work). */
+void env_destroy(ut_env* env);
+
+/* Message of the most recent error of the handle ("" if none). */
+const char* env_last_error(const ut_env* env);
+
+/* Starts new episodes in every environment (Sec. III-A.2): agents on the
+ * surface and targets spawned in a disk with pairwise separation >=
+ * spawn_min (bounded rejection), first pings, each filter's particles
+ * initialised around its agent at the heard range (uniform in the detection
+ * disk if nothing was heard), recurrent tokens zeroed, observation tokens
+ * of the reset state built, device metrics cleared.  The global step
+ * counter becomes 0: every random draw is a function of (seed, step, ids). */
+ut_status env_reset(ut_env* env, uint64_t seed);
+
+/* One environment step, in order: actions -> agent kinematics
+ * (Sec. III-A.3) -> target motion -> pings -> communication (Sec. III-A.2)
+ * -> particle filter predict / weight / estimate / systematic resample
+ * (Sec. II-A) -> observation tokens -> reward (Eq. 1 / Eq. 2).
+ * actions_dev: [NA] int32 in [0, n_actions), or NULL: the transformer agent's
+ * Gumbel-max sample when a policy is set, else uniform random actions.
+ * out (optional): borrowed device views of this step's outputs. */
+ut_status env_step(ut_env* env, const int32_t* actions_dev, ut_step_out* out);
+
+/* T steps with policy (or random) actions, replayed from a captured CUDA
+ * graph.  Clears the device metrics first; synchronises and fills `stats`
+ * (host struct) with the metrics of these T steps.  T >= 1. */
+ut_status rollout(ut_env* env, int32_t T, ut_rollout_stats* stats);
+
+/* Captures and instantiates (and uploads) the T-step rollout graph without
+ * running it, so that a later rollout(T) starts executing at once.  Not
+ * synchronising. */
+ut_status rollout_prepare(ut_env* env, int32_t T);
+
+/* Stage timing.  When enabled, every step records a pair of CUDA timing
+ * events on the launching stream around the tracker stage (the particle
+ * filter, or the learned estimator in its place) — inside captured rollout
+ * graphs too.  env_stage_time synchronises and returns the summed device time
+ * (ms) and the number of timed stage launches since the previous read. */
+ut_status env_profile(ut_env* env, int32_t enable);
+ut_status env_stage_time(ut_env* env, double* total_ms, int64_t* launches);
+
+/* Launch variants of the particle-filter step (threads per filter x
+ * particles per thread).  Variant v is usable for P particles iff
+ * pf_variant_usable(v, P); the handle starts with the default for its P and
+ * the autotuner (bench / tests) may switch it.  Names are static strings. */
+int32_t pf_variant_count(void);
+int32_t pf_variant_usable(int32_t variant, int32_t P);
+const char* pf_variant_label(int32_t variant);
+ut_status env_set_pf_variant(ut_env* env, int32_t variant);
+ut_status env_get_pf_variant(const ut_env* env, int32_t* variant);
+
+/* Device views of the state buffers (borrowed).  Synchronises to read the
+ * step counters. */
+ut_status env_get_state(const ut_env* env, ut_state_view* out);
+
+/* Copies state in from device pointers laid out as in ut_state_view; NULL
+ * fields are left unchanged; step and t_ep are always taken. */
+ut_status env_set_state(ut_env* env, const ut_state_view* in);
+
+/* Device views of the last step's intermediates; UT_ERR_STATE unless the
+ * handle was created with UT_FLAG_DEBUG. */
+ut_status env_debug(const ut_env* env, ut_debug_view* out);
+
+/* Synchronises and reads the device metrics (see ut_rollout_stats). */
+ut_status env_metrics(ut_env* env, ut_rollout_stats* out);
+ut_status env_metrics_reset(ut_env* env);
+
+/* ---------------------------------------------------------------------- */
+/* Stand-alone operations (the same device code the step uses).            */
+/* ---------------------------------------------------------------------- */
+
+/* Philox4x32-10 of n counters: ctr_dev [n][4] uint32, key = seed (low word
+ * first), out_dev [n][4].  Errors: UT_ERR_INVALID (n < 0), UT_ERR_CUDA. */
+ut_status ut_philox(const uint32_t* ctr_dev, uint64_t seed, uint32_t* out_dev, int64_t n, void* cuda_stream);
+
+/* Systematic resampling (Sec. II-A; readings C4, C5) of n_filters filters of
+ * P particles: wmax_dev [n_filters][P] holds exp(l_i - max l) in [0, 1] with
+ * at least one entry equal to 1; u64_dev [n_filters] the random offset bits.
+ * With q_i = floor(w_i 2^38), Q the inclusive sum, W = Q[P-1] and
+ * U0 = floor(u64 W / 2^64): idx[j] = min{ i : P Q_i > j W + U0 }.
+ * Writes idx_dev [n_filters][P] int32.  Errors: UT_ERR_INVALID, UT_ERR_CUDA. */
+ut_status pf_resample(const float* wmax_dev, const uint64_t* u64_dev, int64_t n_filters, int32_t P,
+                      int32_t* idx_dev, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UTRACK_H */

@@ -77,6 +77,8 @@ class OcConfig(ctypes.Structure):
         ("spawn_min", ctypes.c_double), ("spawn_radius", ctypes.c_double), ("spawn_tries", ctypes.c_int32),
         ("feature_scale", ctypes.c_double),
         ("seed", ctypes.c_uint64),
+        ("env0", ctypes.c_int32), ("agent0", ctypes.c_int32), ("target0", ctypes.c_int32),
+        ("filter0", ctypes.c_int32),
     ]
 
 
@@ -178,7 +180,7 @@ def uniform_normal(seed, id0, id1, step, tag):
 class OracleEnv:
     """Batched environment state in float64 plus the stage functions."""
 
-    def __init__(self, params, seed: int):
+    def __init__(self, params, seed: int, id_base=(0, 0, 0, 0)):
         self.p = params
         a, t = params.counts()
         self.n_agents_env, self.n_targets_env = a, t
@@ -202,6 +204,7 @@ class OracleEnv:
                      "follow_dmin", "d_safe", "spawn_min", "spawn_radius", "spawn_tries", "feature_scale"):
             setattr(c, name, getattr(params, name))
         c.seed = seed
+        c.env0, c.agent0, c.target0, c.filter0 = (int(v) for v in id_base)
         self.seed = seed
         AM = params.max_agents
         self.arr = {

@@ -84,6 +84,10 @@ typedef struct {
   int32_t spawn_tries;
   double feature_scale;
   uint64_t seed;
+  /* Global index of this batch's first env / agent / target / filter in a
+   * larger batch: random draws are keyed by global ids, so a sub-batch of
+   * independent environments replays exactly the draws of the full batch. */
+  int32_t env0, agent0, target0, filter0;
 } oc_config;
 
 typedef struct {
@@ -207,7 +211,7 @@ static void spawn_env(const oc_config* c, int e, uint32_t g, double* ex, double*
     int64_t cx = 0, cy = 0; /* last candidate inside the disk (origin if none) */
     for (int t = 0; t < c->spawn_tries; ++t) {
       uint32_t x[4];
-      draw(c->seed, (uint32_t)e, (uint32_t)(n * 64 + t), g, OC_TAG_SPAWN, x);
+      draw(c->seed, (uint32_t)(c->env0 + e), (uint32_t)(n * 64 + t), g, OC_TAG_SPAWN, x);
       int64_t ux = (int64_t)(x[0] >> 8) - 8388608;
       int64_t uy = (int64_t)(x[1] >> 8) - 8388608;
       if (ux * ux + uy * uy > r_int * r_int) continue;
@@ -244,14 +248,14 @@ void oc_reset(const oc_config* c, oc_state* s, uint32_t g) {
     spawn_env(c, e, g, ex, ey);
     for (int a = 0; a < A; ++a) {
       uint32_t x[4];
-      draw(c->seed, (uint32_t)(a0 + a), 0, g, OC_TAG_AGENT_INIT, x);
+      draw(c->seed, (uint32_t)(c->agent0 + a0 + a), 0, g, OC_TAG_AGENT_INIT, x);
       s->ax[a0 + a] = ex[a];
       s->ay[a0 + a] = ey[a];
       s->apsi[a0 + a] = M_PI * (2.0 * u01(x[0]) - 1.0);
     }
     for (int k = 0; k < T; ++k) {
       uint32_t x[4];
-      draw(c->seed, (uint32_t)(t0 + k), 0, g, OC_TAG_TARGET_INIT, x);
+      draw(c->seed, (uint32_t)(c->target0 + t0 + k), 0, g, OC_TAG_TARGET_INIT, x);
       s->tx[t0 + k] = ex[A + k];
       s->ty[t0 + k] = ey[A + k];
       s->tpsi[t0 + k] = M_PI * (2.0 * u01(x[0]) - 1.0);
@@ -274,7 +278,7 @@ void oc_reset(const oc_config* c, oc_state* s, uint32_t g) {
         double d = true_range(s, ia, it);
         int valid = d <= c->det_radius;
         uint32_t xp[4];
-        draw(c->seed, (uint32_t)f, 0, g, OC_TAG_RESET_PING, xp);
+        draw(c->seed, (uint32_t)(c->filter0 + f), 0, g, OC_TAG_RESET_PING, xp);
         double n0, n1;
         normal_pair(xp[0], xp[1], &n0, &n1);
         double r0 = d + c->range_sigma * n0;
@@ -283,8 +287,8 @@ void oc_reset(const oc_config* c, oc_state* s, uint32_t g) {
         double sx = 0.0, sy = 0.0;
         for (int i = 0; i < P; ++i) {
           uint32_t x[4], y[4];
-          draw(c->seed, (uint32_t)f, (uint32_t)i, g, OC_TAG_PF_INIT, x);
-          draw(c->seed, (uint32_t)f, (uint32_t)i, g, OC_TAG_PF_INIT2, y);
+          draw(c->seed, (uint32_t)(c->filter0 + f), (uint32_t)i, g, OC_TAG_PF_INIT, x);
+          draw(c->seed, (uint32_t)(c->filter0 + f), (uint32_t)i, g, OC_TAG_PF_INIT2, y);
           double rho, m0, m1;
           if (valid) {
             normal_pair(x[0], x[1], &m0, &m1);
@@ -321,7 +325,7 @@ void oc_reset(const oc_config* c, oc_state* s, uint32_t g) {
 void oc_random_actions(const oc_config* c, uint32_t g, int32_t n_agents, int32_t* act) {
   for (int i = 0; i < n_agents; ++i) {
     uint32_t x[4];
-    draw(c->seed, (uint32_t)i, 0, g, OC_TAG_ACTION, x);
+    draw(c->seed, (uint32_t)(c->agent0 + i), 0, g, OC_TAG_ACTION, x);
     act[i] = (int32_t)(((uint64_t)x[0] * (uint64_t)c->n_actions) >> 32);
   }
 }
@@ -353,7 +357,7 @@ void oc_move_agents(const oc_config* c, oc_state* s, const int32_t* act, uint32_
   int NA = c->agent_off[c->n_envs];
   for (int i = 0; i < NA; ++i) {
     uint32_t x[4];
-    draw(c->seed, (uint32_t)i, 0, g, OC_TAG_AGENT_NOISE, x);
+    draw(c->seed, (uint32_t)(c->agent0 + i), 0, g, OC_TAG_AGENT_NOISE, x);
     double n0, n1;
     normal_pair(x[0], x[1], &n0, &n1);
     double psi = wrap_angle(s->apsi[i] + action_dpsi(c, act[i]) + c->heading_noise * n0);
@@ -370,7 +374,7 @@ void oc_move_targets(const oc_config* c, oc_state* s, uint32_t g) {
   int NT = c->target_off[c->n_envs];
   for (int j = 0; j < NT; ++j) {
     uint32_t x[4];
-    draw(c->seed, (uint32_t)j, 0, g, OC_TAG_TARGET_MOVE, x);
+    draw(c->seed, (uint32_t)(c->target0 + j), 0, g, OC_TAG_TARGET_MOVE, x);
     double psi;
     if (c->target_model == 0) {
       psi = wrap_angle(2.0 * M_PI * u01(x[0]));
@@ -396,7 +400,7 @@ void oc_pings(const oc_config* c, const oc_state* s, uint32_t g, double* range, 
         int f = filter_index(c, e, a, k);
         double d = true_range(s, c->agent_off[e] + a, c->target_off[e] + k);
         uint32_t x[4];
-        draw(c->seed, (uint32_t)f, 0, g, OC_TAG_PING, x);
+        draw(c->seed, (uint32_t)(c->filter0 + f), 0, g, OC_TAG_PING, x);
         double n0, n1;
         normal_pair(x[0], x[1], &n0, &n1);
         valid[f] = d <= c->det_radius;
@@ -426,7 +430,7 @@ void oc_comms(const oc_config* c, oc_state* s, uint32_t g, const double* range, 
           } else {
             double dx = s->ax[ia] - s->ax[ib], dy = s->ay[ia] - s->ay[ib];
             uint32_t x[4];
-            draw(c->seed, (uint32_t)ia, (uint32_t)b, g, OC_TAG_COMM, x);
+            draw(c->seed, (uint32_t)(c->agent0 + ia), (uint32_t)b, g, OC_TAG_COMM, x);
             r = sqrt(dx * dx + dy * dy) <= c->comm_radius && !(u01(x[0]) < c->comm_drop);
           }
           if (b != a) {
@@ -526,7 +530,7 @@ void oc_pf_update(const oc_config* c, oc_state* s, uint32_t g, const double* mea
     /* predict */
     for (int i = 0; i < P; ++i) {
       uint32_t r[4];
-      draw(c->seed, (uint32_t)f, (uint32_t)(i / 2), g, OC_TAG_PF_PREDICT, r);
+      draw(c->seed, (uint32_t)(c->filter0 + f), (uint32_t)(i / 2), g, OC_TAG_PF_PREDICT, r);
       double n0, n1;
       if (i % 2 == 0) normal_pair(r[0], r[1], &n0, &n1);
       else normal_pair(r[2], r[3], &n0, &n1);
@@ -584,7 +588,7 @@ void oc_pf_update(const oc_config* c, oc_state* s, uint32_t g, const double* mea
     /* resample */
     if (nm > 0) {
       uint32_t r[4];
-      draw(c->seed, (uint32_t)f, 0, g, OC_TAG_RESAMPLE, r);
+      draw(c->seed, (uint32_t)(c->filter0 + f), 0, g, OC_TAG_RESAMPLE, r);
       uint64_t u64 = (uint64_t)r[0] | ((uint64_t)r[1] << 32);
       oc_systematic_resample(P, w, u64, idx);
       for (int j = 0; j < P; ++j) {

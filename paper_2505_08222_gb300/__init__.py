@@ -1,0 +1,286 @@
+"""GB300-native batched underwater-tracking environment (arXiv 2505.08222).
+
+A thin Python binding over the C ABI of ``_build/libutrack.so`` (declared in
+``include/utrack.h``).  Every step of the environment runs in the library's
+CUDA kernels; this module only marshals arguments.  PyTorch provides device
+memory (its caching allocator is handed to the library as the allocator) and
+streams, and wraps the library's borrowed device buffers as tensors.
+
+There is no CPU or Python fallback: importing the binding without the built
+library raises ImportError.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _abi
+
+__all__ = ["Env", "UtError", "philox", "pf_resample", "lib"]
+
+lib = _abi.load()
+
+
+class UtError(RuntimeError):
+    pass
+
+
+def _check(rc: int, handle=None, what: str = ""):
+    if rc != 0:
+        msg = ""
+        if handle:
+            raw = lib.env_last_error(handle)
+            msg = raw.decode() if raw else ""
+        raise UtError(f"{what}: {_abi.STATUS.get(rc, rc)} {msg}".strip())
+
+
+class _DevArray:
+    """Exposes a borrowed device pointer through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(int(s) for s in shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+_TYPESTR = {torch.float32: "<f4", torch.int32: "<i4", torch.int16: "<i2", torch.uint8: "|u1",
+            torch.float64: "<f8", torch.int64: "<i8"}
+
+
+def device_view(ptr: int, shape, dtype=torch.float32) -> Optional[torch.Tensor]:
+    """Zero-copy tensor over a borrowed device buffer of the library."""
+    if not ptr:
+        return None
+    n = int(np.prod(shape)) if len(shape) else 1
+    if n == 0:
+        return torch.empty(shape, dtype=dtype, device="cuda")
+    return torch.as_tensor(_DevArray(ptr, shape, _TYPESTR[dtype]), device="cuda")
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class _TorchAllocator:
+    """Routes the library's allocations through PyTorch's caching allocator."""
+
+    def __init__(self):
+        dev = torch.cuda.current_device()
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(stream or 0))
+            except Exception:
+                return None
+
+        def _free(ptr, stream, ctx):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self._a = _abi.ALLOC_FN(_alloc)
+        self._f = _abi.FREE_FN(_free)
+        self.struct = _abi.Allocator(self._a, self._f, None)
+
+
+def make_config(params, flags: int = 0):
+    """ut_config from an object carrying the EnvParams fields."""
+    cfg = _abi.Config()
+    cfg.abi_version = _abi.UT_ABI_VERSION
+    cfg.flags = flags
+    keep = []
+    for name, _ in _abi.CONFIG_FIELDS:
+        if name in ("abi_version", "flags"):
+            continue
+        if name in ("agents_per_env_host", "targets_per_env_host"):
+            src = getattr(params, name.replace("_host", ""), None)
+            if src is None:
+                setattr(cfg, name, None)
+            else:
+                arr = np.ascontiguousarray(src, np.int32)
+                keep.append(arr)
+                setattr(cfg, name, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+            continue
+        setattr(cfg, name, getattr(params, name))
+    return cfg, keep
+
+
+class Env:
+    """One batch of independent tracking environments on the current GPU."""
+
+    def __init__(self, params, debug: bool = False, ring: bool = False, stream=None,
+                 use_torch_allocator: bool = True):
+        self.params = params
+        flags = (_abi.UT_FLAG_DEBUG if debug else 0) | (_abi.UT_FLAG_RING if ring else 0)
+        self._cfg, self._keep = make_config(params, flags)
+        self._stream = _stream_ptr(stream)
+        self._alloc = _TorchAllocator() if use_torch_allocator else None
+        h = ctypes.c_void_p()
+        rc = lib.env_create(ctypes.byref(self._cfg),
+                            ctypes.byref(self._alloc.struct) if self._alloc else None,
+                            ctypes.c_void_p(self._stream), ctypes.byref(h))
+        _check(rc, None, "env_create")
+        self.h = h
+        st = self._state_view()
+        self.NA, self.NT, self.F = st.n_agents, st.n_targets, st.n_filters
+        self.P = params.n_particles
+        self.AM = params.max_agents
+        self.NS = params.max_agents + params.max_targets
+        self.E = params.n_envs
+
+    # ------------------------------------------------------------ lifecycle
+    def close(self):
+        if getattr(self, "h", None):
+            lib.env_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, seed: int):
+        _check(lib.env_reset(self.h, ctypes.c_uint64(seed)), self.h, "env_reset")
+
+    def step(self, actions: Optional[torch.Tensor] = None) -> dict:
+        ptr = None
+        if actions is not None:
+            assert actions.is_cuda and actions.dtype == torch.int32 and actions.is_contiguous()
+            assert actions.numel() == self.NA
+            ptr = ctypes.c_void_p(actions.data_ptr())
+        out = _abi.StepOut()
+        _check(lib.env_step(self.h, ptr, ctypes.byref(out)), self.h, "env_step")
+        return self._step_views(out)
+
+    def _step_views(self, out) -> dict:
+        return {
+            "reward": device_view(out.reward, (self.E,)),
+            "done": device_view(out.done, (self.E,), torch.int32),
+            "obs": device_view(out.obs, (self.NA, self.NS, 8), torch.int16),
+            "estx": device_view(out.estx, (self.F,)),
+            "esty": device_view(out.esty, (self.F,)),
+            "err": device_view(out.err, (self.F,)),
+            "actions": device_view(out.actions, (self.NA,), torch.int32),
+            "logits": device_view(out.logits, (self.NA, self.params.n_actions)),
+        }
+
+    def rollout(self, T: int) -> dict:
+        s = _abi.RolloutStats()
+        _check(lib.rollout(self.h, T, ctypes.byref(s)), self.h, "rollout")
+        return {k: getattr(s, k) for k, _ in _abi.RolloutStats._fields_}
+
+    def rollout_prepare(self, T: int):
+        _check(lib.rollout_prepare(self.h, T), self.h, "rollout_prepare")
+
+    def profile(self, enable: bool = True):
+        _check(lib.env_profile(self.h, 1 if enable else 0), self.h, "env_profile")
+
+    def stage_time(self):
+        """(total ms, launches) of the tracker stage since the last read."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(lib.env_stage_time(self.h, ctypes.byref(ms), ctypes.byref(n)), self.h, "env_stage_time")
+        return ms.value, n.value
+
+    def pf_variants(self):
+        """Usable particle-filter launch variants for this handle's P."""
+        return [v for v in range(lib.pf_variant_count()) if lib.pf_variant_usable(v, self.P)]
+
+    def set_pf_variant(self, v: int):
+        _check(lib.env_set_pf_variant(self.h, v), self.h, "env_set_pf_variant")
+
+    def pf_variant(self) -> int:
+        v = ctypes.c_int32()
+        _check(lib.env_get_pf_variant(self.h, ctypes.byref(v)), self.h, "env_get_pf_variant")
+        return v.value
+
+    def pf_variant_name(self) -> str:
+        return lib.pf_variant_label(self.pf_variant()).decode()
+
+    def metrics(self) -> dict:
+        s = _abi.RolloutStats()
+        _check(lib.env_metrics(self.h, ctypes.byref(s)), self.h, "env_metrics")
+        return {k: getattr(s, k) for k, _ in _abi.RolloutStats._fields_}
+
+    def metrics_reset(self):
+        _check(lib.env_metrics_reset(self.h), self.h, "env_metrics_reset")
+
+    # ------------------------------------------------------------ state
+    def _state_view(self):
+        v = _abi.StateView()
+        _check(lib.env_get_state(self.h, ctypes.byref(v)), self.h, "env_get_state")
+        return v
+
+    def state(self) -> dict:
+        """Borrowed device views of every state buffer plus the counters."""
+        v = self._state_view()
+        NA, NT, FP, F, AM = self.NA, self.NT, self.F * self.P, self.F, self.AM
+        shapes = {"ax": (NA,), "ay": (NA,), "apsi": (NA,), "tx": (NT,), "ty": (NT,), "tz": (NT,),
+                  "tpsi": (NT,), "tspeed": (NT,), "px": (FP,), "py": (FP,), "pvx": (FP,), "pvy": (FP,),
+                  "lpx": (NA * AM,), "lpy": (NA * AM,), "lpage": (NA * AM,), "estx": (F,), "esty": (F,),
+                  "ring": (F, 16, 4), "ring_head": (F,), "ring_count": (F,)}
+        out = {}
+        for k, shp in shapes.items():
+            dt = torch.int32 if k in ("lpage", "ring_head", "ring_count") else torch.float32
+            out[k] = device_view(getattr(v, k), shp, dt)
+        d = getattr(self.params, "d_model", 0)
+        out["h"] = device_view(v.h, (NA, d), torch.int16) if d else None
+        out["step"] = v.step
+        out["t_ep"] = v.t_ep
+        return out
+
+    def set_state(self, step: int, t_ep: int = 0, **tensors):
+        """Copies the given device tensors (float32 / int32, contiguous) in."""
+        v = _abi.StateView()
+        keep = []
+        for k, t in tensors.items():
+            if t is None:
+                continue
+            t = t.contiguous()
+            keep.append(t)
+            setattr(v, k, t.data_ptr())
+        v.step = step
+        v.t_ep = t_ep
+        _check(lib.env_set_state(self.h, ctypes.byref(v)), self.h, "env_set_state")
+        torch.cuda.synchronize()
+
+    def debug(self) -> dict:
+        v = _abi.DebugView()
+        _check(lib.env_debug(self.h, ctypes.byref(v)), self.h, "env_debug")
+        F, FP, NA, AM = self.F, self.F * self.P, self.NA, self.AM
+        return {
+            "range": device_view(v.range, (F,)), "valid": device_view(v.valid, (F,), torch.int32),
+            "recv": device_view(v.recv, (NA * AM,), torch.int32), "meas": device_view(v.meas, (F, AM, 4)),
+            "meas_n": device_view(v.meas_n, (F,), torch.int32),
+            "pred_px": device_view(v.pred_px, (FP,)), "pred_py": device_view(v.pred_py, (FP,)),
+            "pred_pvx": device_view(v.pred_pvx, (FP,)), "pred_pvy": device_view(v.pred_pvy, (FP,)),
+            "weight": device_view(v.weight, (FP,)), "wmax": device_view(v.wmax, (FP,)),
+            "idx": device_view(v.idx, (FP,), torch.int32),
+        }
+
+
+# ---------------------------------------------------------------- stand-alone ops
+def philox(ctr: torch.Tensor, seed: int) -> torch.Tensor:
+    """Philox4x32-10 of counters ctr [n, 4] (int32 bit patterns on the GPU)."""
+    assert ctr.is_cuda and ctr.dtype == torch.int32 and ctr.shape[-1] == 4
+    ctr = ctr.contiguous()
+    out = torch.empty_like(ctr)
+    _check(lib.ut_philox(ctypes.c_void_p(ctr.data_ptr()), ctypes.c_uint64(seed), ctypes.c_void_p(out.data_ptr()),
+                         ctr.shape[0], ctypes.c_void_p(_stream_ptr(None))), None, "ut_philox")
+    return out
+
+
+def pf_resample(wmax: torch.Tensor, u64: torch.Tensor) -> torch.Tensor:
+    """Systematic resample map of wmax [n_filters, P] (float32) with offsets
+    u64 [n_filters] (int64 bit patterns)."""
+    assert wmax.is_cuda and wmax.dtype == torch.float32 and u64.dtype == torch.int64
+    wmax = wmax.contiguous()
+    u64 = u64.contiguous()
+    F, P = wmax.shape
+    idx = torch.empty((F, P), dtype=torch.int32, device=wmax.device)
+    _check(lib.pf_resample(ctypes.c_void_p(wmax.data_ptr()), ctypes.c_void_p(u64.data_ptr()), F, P,
+                           ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(_stream_ptr(None))), None, "pf_resample")
+    return idx

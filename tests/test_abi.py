@@ -1,0 +1,91 @@
+"""The C-ABI library loads and exports every entry point include/*.h declares;
+host-side validation rejects bad configurations (no GPU needed: validation
+happens before any CUDA call)."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        text = re.sub(r"typedef\s+struct\s+\w*\s*\{.*?\}\s*\w+\s*;", "", text, flags=re.S)
+        text = re.sub(r"typedef\s+enum\s*\{.*?\}\s*\w+\s*;", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b([A-Za-z_]\w*)\s*\([^;{}]*\)\s*;", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2505_08222_gb300.build as b
+    path = b.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("env_create", "env_reset", "env_step", "rollout", "env_get_state", "env_set_state",
+                     "env_destroy", "env_last_error", "pf_resample", "ut_philox"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    path = lib._name
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = _declared_functions() - exported
+    assert not missing, f"declared but not exported: {sorted(missing)}"
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2505_08222_gb300 import _abi
+    assert _declared_functions() <= set(_abi.SIGNATURES)
+
+
+def _cfg(**kw):
+    from paper_2505_08222_gb300 import make_config
+    from synth import preset
+    p = preset("fleet5", n_envs=4)
+    cfg, keep = make_config(p.replace(**kw))
+    return cfg, keep
+
+
+@pytest.mark.parametrize("kw", [
+    {"n_envs": 0}, {"max_agents": 9}, {"max_targets": 0}, {"n_particles": 0}, {"n_particles": 4097},
+    {"range_sigma": 0.0}, {"n_heads": 3}, {"n_actions": 9}, {"reward_type": 2}, {"spawn_tries": 65},
+])
+def test_create_rejects_invalid_config(lib, kw):
+    from paper_2505_08222_gb300 import _abi
+    import paper_2505_08222_gb300 as ut
+    cfg, keep = _cfg(**kw)
+    h = ctypes.c_void_p()
+    rc = ut.lib.env_create(ctypes.byref(cfg), None, None, ctypes.byref(h))
+    assert rc == 1 and not h.value
+
+
+def test_create_rejects_bad_ragged_counts_and_abi(lib):
+    import numpy as np
+    import paper_2505_08222_gb300 as ut
+    cfg, keep = _cfg(agents_per_env=np.array([1, 2, 9, 1], np.int32))
+    h = ctypes.c_void_p()
+    assert ut.lib.env_create(ctypes.byref(cfg), None, None, ctypes.byref(h)) == 1
+    cfg, keep = _cfg()
+    cfg.abi_version = 99
+    assert ut.lib.env_create(ctypes.byref(cfg), None, None, ctypes.byref(h)) == 1
+
+
+def test_standalone_ops_validate_arguments(lib):
+    import paper_2505_08222_gb300 as ut
+    assert ut.lib.pf_resample(None, None, -1, 16, None, None) == 1
+    assert ut.lib.pf_resample(None, None, 4, 0, None, None) == 1
+    assert ut.lib.ut_philox(None, 0, None, -3, None) == 1
