@@ -213,11 +213,12 @@ ut_status rollout(ut_env* env, int32_t T, ut_rollout_stats* stats);
  * synchronising. */
 ut_status rollout_prepare(ut_env* env, int32_t T);
 
-/* Stage timing.  When enabled, every step records a pair of CUDA timing
- * events on the launching stream around the tracker stage (the particle
- * filter, or the learned estimator in its place) — inside captured rollout
- * graphs too.  env_stage_time synchronises and returns the summed device time
- * (ms) and the number of timed stage launches since the previous read. */
+/* Stage timing.  When enabled, every eager env_step records a pair of CUDA
+ * timing events on the launching stream around the tracker stage (the
+ * particle filter, or the learned estimator in its place); graph rollouts
+ * are not timed per stage (CUDA cannot time events recorded by graph nodes).
+ * env_stage_time synchronises and returns the summed device time (ms) and the
+ * number of timed stage launches since the previous read. */
 ut_status env_profile(ut_env* env, int32_t enable);
 ut_status env_stage_time(ut_env* env, double* total_ms, int64_t* launches);
 

@@ -327,7 +327,6 @@ void env_destroy(ut_env* h) {
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (cudaEvent_t ev : h->eager_ev) cudaEventDestroy(ev);
-  for (cudaEvent_t ev : h->graph_ev) cudaEventDestroy(ev);
   extension_destroy(h);
   env_free_all(h);
   cudaStreamSynchronize(h->stream);
@@ -353,13 +352,8 @@ namespace ut {
 // Timing-event pair for the tracker stage of this step (nullptr: off).
 static cudaError_t stage_events(ut_env* h, cudaEvent_t* ev0, cudaEvent_t* ev1) {
   *ev0 = *ev1 = nullptr;
-  if (!h->prof_on) return cudaSuccess;
-  if (h->capture_pair >= 0) {  // inside rollout capture: pool pre-sized
-    *ev0 = h->graph_ev[2 * h->capture_pair];
-    *ev1 = h->graph_ev[2 * h->capture_pair + 1];
-    h->capture_pair++;
-    return cudaSuccess;
-  }
+  // CUDA cannot time events recorded by graph nodes: eager steps only
+  if (!h->prof_on || h->capturing) return cudaSuccess;
   if (2 * (h->eager_used + 1) > h->eager_ev.size()) {
     for (int i = 0; i < 2; ++i) {
       cudaEvent_t ev;
@@ -464,27 +458,19 @@ static ut_status graph_ensure(ut_env* h, int32_t T) {
     UT_CUDA(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   }
   const int key = T * 4 + (h->policy_ready ? 1 : 0) + (h->est_mode ? 2 : 0);
-  if (!h->graph_exec || h->graph_key != key || h->graph_variant != h->pf_variant || h->graph_prof != h->prof_on) {
+  if (!h->graph_exec || h->graph_key != key || h->graph_variant != h->pf_variant) {
     if (h->graph_exec) {
       cudaGraphExecDestroy(h->graph_exec);
       h->graph_exec = nullptr;
     }
     cudaGraph_t graph = nullptr;
-    if (h->prof_on) {
-      while (h->graph_ev.size() < (size_t)(2 * T)) {
-        cudaEvent_t ev;
-        UT_CUDA(h, cudaEventCreate(&ev));
-        h->graph_ev.push_back(ev);
-      }
-      h->capture_pair = 0;
-    }
     const int64_t launches_before = h->launches;
+    h->capturing = true;
     UT_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int t = 0; t < T && e == cudaSuccess; ++t) e = enqueue_step(h, nullptr, h->cap_stream);
     cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &graph);
-    h->graph_prof_pairs = h->prof_on ? h->capture_pair : 0;
-    h->capture_pair = -1;
+    h->capturing = false;
     h->launches_per_graph = (int)(h->launches - launches_before);
     h->launches = launches_before;
     if (e != cudaSuccess) {
@@ -497,7 +483,6 @@ static ut_status graph_ensure(ut_env* h, int32_t T) {
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
     h->graph_key = key;
     h->graph_variant = h->pf_variant;
-    h->graph_prof = h->prof_on;
     UT_CUDA(h, cudaGraphUpload(h->graph_exec, h->cap_stream));
   }
   return UT_OK;
@@ -516,7 +501,6 @@ ut_status rollout(ut_env* h, int32_t T, ut_rollout_stats* stats) {
   if (st != UT_OK) return st;
   UT_CUDA(h, env_metrics_reset(h) == UT_OK ? cudaSuccess : cudaErrorUnknown);
   h->launches += h->launches_per_graph;
-  if (h->graph_prof_pairs) h->graph_runs_pending++;
   UT_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
   UT_CUDA(h, cudaStreamWaitEvent(h->cap_stream, h->ev_fork, 0));
   UT_CUDA(h, cudaGraphLaunch(h->graph_exec, h->cap_stream));
@@ -547,7 +531,6 @@ ut_status env_profile(ut_env* h, int32_t enable) {
   if (!h) return UT_ERR_INVALID;
   h->prof_on = enable != 0;
   h->eager_used = 0;
-  h->graph_runs_pending = 0;
   return UT_OK;
 }
 
@@ -563,17 +546,7 @@ ut_status env_stage_time(ut_env* h, double* total_ms, int64_t* launches) {
     sum += ms;
     ++n;
   }
-  // a graph's event nodes hold the times of its latest launch only
-  if (h->graph_runs_pending > 0) {
-    for (int k = 0; k < h->graph_prof_pairs; ++k) {
-      float ms = 0.0f;
-      UT_CUDA(h, cudaEventElapsedTime(&ms, h->graph_ev[2 * k], h->graph_ev[2 * k + 1]));
-      sum += ms * h->graph_runs_pending;
-      n += h->graph_runs_pending;
-    }
-  }
   h->eager_used = 0;
-  h->graph_runs_pending = 0;
   *total_ms = sum;
   *launches = n;
   return UT_OK;

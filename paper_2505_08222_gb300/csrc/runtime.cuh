@@ -32,7 +32,6 @@ struct ut_env {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   int graph_key = -1, graph_variant = -1;
-  bool graph_prof = false;
   // host count of kernels enqueued since the metrics were cleared
   int64_t launches = 0;
   int launches_per_graph = 0;
@@ -40,10 +39,7 @@ struct ut_env {
   bool prof_on = false;
   std::vector<cudaEvent_t> eager_ev;   // pairs for eager steps
   size_t eager_used = 0;               // pairs recorded since the last read
-  std::vector<cudaEvent_t> graph_ev;   // pairs captured in the rollout graph
-  int graph_prof_pairs = 0;            // pairs inside the current graph
-  int graph_runs_pending = 0;          // graph launches since the last read
-  int capture_pair = -1;               // next graph pair during capture (-1: eager)
+  bool capturing = false;              // inside rollout graph capture
   // transformer agent and learned estimator
   bool policy_ready = false;
   PolicyState* policy = nullptr;

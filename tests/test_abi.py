@@ -27,8 +27,8 @@ def _declared_functions():
 
 @pytest.fixture(scope="module")
 def lib():
-    import paper_2505_08222_gb300.build as b
-    path = b.build()
+    import __graft_entry__
+    path = __graft_entry__._build_module().build()
     return ctypes.CDLL(path)
 
 
