@@ -104,9 +104,12 @@ def _dist_env():
     return world, rank, local
 
 
+_ENVS = None
+
+
 def _workload(name: str):
     from synth import preset
-    return preset(name)
+    return preset(name, n_envs=_ENVS)
 
 
 def cpu_baseline(workload: str, budget_s: float = 12.0, n_envs: int = 64):
@@ -117,7 +120,8 @@ def cpu_baseline(workload: str, budget_s: float = 12.0, n_envs: int = 64):
 
     import oracle
     import synth
-    p = _workload(workload).replace(n_envs=n_envs)
+    from synth import preset
+    p = preset(workload, n_envs=n_envs)
     o = oracle.OracleEnv(p, 0)
     o.reset(0)
     cores = os.cpu_count() or 1
@@ -317,7 +321,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="fleet5")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--envs", type=int, default=None, help="override the env count (profiling cases)")
     args = ap.parse_args()
+    global _ENVS
+    _ENVS = args.envs
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
