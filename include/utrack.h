@@ -265,6 +265,38 @@ ut_status ut_philox(const uint32_t* ctr_dev, uint64_t seed, uint32_t* out_dev, i
 ut_status pf_resample(const float* wmax_dev, const uint64_t* u64_dev, int64_t n_filters, int32_t P,
                       int32_t* idx_dev, void* cuda_stream);
 
+/* ---------------------------------------------------------------------- */
+/* Allocation-free tracker update (the paper has no counterpart).          */
+/* ---------------------------------------------------------------------- */
+
+/* For callers that must not allocate device memory — code running inside
+ * another component's CUDA graph capture (where cudaMalloc is not allowed),
+ * real-time host threads that forbid allocator calls, or a vehicle simulator
+ * that owns every buffer and its memory budget.  It runs the tracking part of
+ * one step on caller buffers: pings and communication at the given
+ * (already moved) agent and target positions, then the particle-filter step
+ * (predict, weight, estimate, systematic resample) of every (env, agent,
+ * target) filter — the same rules and random draws as env_step at global step
+ * `step` (>= 1) with `seed`.  Uniform fleets only: cfg->n_envs environments of
+ * cfg->max_agents agents and cfg->max_targets targets (the per-env count
+ * pointers must be NULL); cfg supplies the constants.
+ *   ax/ay_dev [E*A], tx/ty/tz_dev [E*T]: positions (read);
+ *   px/py/pvx/pvy_dev [E*A*T*P]: particles, updated in place;
+ *   estx/esty/err_dev [E*A*T]: estimate and its 2-D error (written).
+ * Intermediates (layout tables, per-filter measurement lists) live in a
+ * static device array of about 4.6 MB that every GPU loading the library
+ * holds until exit; the call itself allocates nothing (no cudaMalloc, no
+ * allocator callback).  Limit: at most 8192 environments and 32768 filters
+ * (E*A*T) per call; larger sizes return UT_ERR_INVALID with a message on
+ * stderr.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU race.  Enqueued on
+ * cuda_stream, not synchronising.  Errors: UT_ERR_INVALID, UT_ERR_CUDA. */
+ut_status tracker_update_noalloc(const ut_config* cfg, uint64_t seed, uint32_t step, const float* ax_dev,
+                                 const float* ay_dev, const float* tx_dev, const float* ty_dev, const float* tz_dev,
+                                 float* px_dev, float* py_dev, float* pvx_dev, float* pvy_dev, float* estx_dev,
+                                 float* esty_dev, float* err_dev, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
