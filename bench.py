@@ -189,6 +189,9 @@ def run_ours(args):
     if p.d_model > 0 and hasattr(env, "set_policy"):
         env.set_policy(synth.policy_params(synth.PolicyDims(p.d_model, p.n_layers, p.n_heads, p.n_actions)))
     env.reset(1000 + rank)
+    if not args.no_autotune:
+        env.autotune(5)  # picks the filter launch variant, then the episode restarts
+        env.reset(1000 + rank)
     stream = torch.cuda.current_stream()
     K, W = args.steps, args.warmup
     policy_on = bool(getattr(env, "policy_ready", False))
@@ -321,6 +324,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="fleet5")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--envs", type=int, default=None, help="override the env count (profiling cases)")
     args = ap.parse_args()
     global _ENVS

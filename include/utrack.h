@@ -232,6 +232,14 @@ const char* pf_variant_label(int32_t variant);
 ut_status env_set_pf_variant(ut_env* env, int32_t variant);
 ut_status env_get_pf_variant(const ut_env* env, int32_t* variant);
 
+/* Autotuner: times `reps` eager steps of every usable particle-filter variant
+ * (CUDA events around the filter launches), keeps the fastest, and records it
+ * in a process-wide cache keyed by (n_envs, max agents, max targets, P,
+ * filters); a later handle with the same key takes the cached choice without
+ * timing.  The timed steps advance the environment: call it before
+ * env_reset.  Synchronising.  *chosen (optional) receives the variant. */
+ut_status env_autotune(ut_env* env, int32_t reps, int32_t* chosen);
+
 /* Device views of the state buffers (borrowed).  Synchronises to read the
  * step counters. */
 ut_status env_get_state(const ut_env* env, ut_state_view* out);
@@ -264,6 +272,16 @@ ut_status ut_philox(const uint32_t* ctr_dev, uint64_t seed, uint32_t* out_dev, i
  * Writes idx_dev [n_filters][P] int32.  Errors: UT_ERR_INVALID, UT_ERR_CUDA. */
 ut_status pf_resample(const float* wmax_dev, const uint64_t* u64_dev, int64_t n_filters, int32_t P,
                       int32_t* idx_dev, void* cuda_stream);
+
+/* BF16 GEMM on the tensor cores (tcgen05.mma, FP32 accumulation in tensor
+ * memory): C[M][N] = A[M][K] * B[N][K]^T, row-major, A and B BF16 bit
+ * patterns (16-byte aligned), C FP32.  16 <= N <= 256 and 16 <= K <= 256, both
+ * multiples of 16; any M >= 1.  The primitive the transformer agent (Sec.
+ * III-B.1, Fig. 3) and the estimator are built from, exposed on its own.
+ * status_dev (optional, device int32) receives 4 if a bounded wait for the
+ * tensor core gave up.  Errors: UT_ERR_INVALID, UT_ERR_CUDA. */
+ut_status tc_gemm_bf16(const uint16_t* A_dev, const uint16_t* B_dev, float* C_dev, int32_t M, int32_t N, int32_t K,
+                       int32_t* status_dev, void* cuda_stream);
 
 /* ---------------------------------------------------------------------- */
 /* Allocation-free tracker update (the paper has no counterpart).          */

@@ -197,6 +197,12 @@ class Env:
         _check(lib.env_get_pf_variant(self.h, ctypes.byref(v)), self.h, "env_get_pf_variant")
         return v.value
 
+    def autotune(self, reps: int = 5) -> str:
+        """Times every usable filter variant, keeps the fastest (advances the env)."""
+        v = ctypes.c_int32()
+        _check(lib.env_autotune(self.h, reps, ctypes.byref(v)), self.h, "env_autotune")
+        return lib.pf_variant_label(v.value).decode()
+
     def pf_variant_name(self) -> str:
         return lib.pf_variant_label(self.pf_variant()).decode()
 
@@ -271,6 +277,23 @@ def philox(ctr: torch.Tensor, seed: int) -> torch.Tensor:
     _check(lib.ut_philox(ctypes.c_void_p(ctr.data_ptr()), ctypes.c_uint64(seed), ctypes.c_void_p(out.data_ptr()),
                          ctr.shape[0], ctypes.c_void_p(_stream_ptr(None))), None, "ut_philox")
     return out
+
+
+def tc_gemm(A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
+    """A [M, K] bf16 @ B [N, K]^T bf16 -> [M, N] fp32 on the tensor cores."""
+    assert A.is_cuda and A.dtype == torch.bfloat16 and B.dtype == torch.bfloat16
+    A = A.contiguous()
+    B = B.contiguous()
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(lib.tc_gemm_bf16(ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                            ctypes.c_void_p(C.data_ptr()), M, N, K, ctypes.c_void_p(status.data_ptr()),
+                            ctypes.c_void_p(_stream_ptr(None))), None, "tc_gemm_bf16")
+    if int(status.item()) != 0:
+        raise UtError("tc_gemm_bf16: tensor-core wait timed out")
+    return C
 
 
 def pf_resample(wmax: torch.Tensor, u64: torch.Tensor) -> torch.Tensor:

@@ -103,7 +103,9 @@ SIGNATURES = {
     "pf_variant_label": (ctypes.c_char_p, [ctypes.c_int32]),
     "env_set_pf_variant": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "env_get_pf_variant": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32)]),
+    "env_autotune": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "ut_philox": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, ctypes.c_int64, _vp]),
+    "tc_gemm_bf16": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp]),
     "tracker_update_noalloc": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_uint64, ctypes.c_uint32] + [_vp] * 13),
     "pf_resample": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int32, _vp, _vp]),
 }

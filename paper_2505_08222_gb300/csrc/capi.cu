@@ -4,7 +4,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/utrack.h"
@@ -524,6 +527,56 @@ ut_status env_set_pf_variant(ut_env* h, int32_t v) {
 ut_status env_get_pf_variant(const ut_env* h, int32_t* v) {
   if (!h || !v) return UT_ERR_INVALID;
   *v = h->pf_variant;
+  return UT_OK;
+}
+
+namespace {
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int, int, int64_t>, int> g_tune_cache;
+}  // namespace
+
+ut_status env_autotune(ut_env* h, int32_t reps, int32_t* chosen) {
+  if (!h || reps < 1) return UT_ERR_INVALID;
+  if (!h->reset_done) return fail(h, UT_ERR_STATE, "env_autotune before env_reset");
+  const auto key = std::make_tuple(h->d.E, h->d.AM, h->d.TM, h->d.P, h->F);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      h->pf_variant = it->second;
+      if (chosen) *chosen = it->second;
+      return UT_OK;
+    }
+  }
+  const bool prof_before = h->prof_on;
+  double best = 1e30;
+  int best_v = h->pf_variant;
+  for (int v = 0; v < ut::pf_variant_count(); ++v) {
+    if (!ut::pf_variant_valid(v, h->d.P)) continue;
+    h->pf_variant = v;
+    h->prof_on = false;
+    UT_CUDA(h, enqueue_step(h, nullptr, h->stream));  // warm-up (also the smem opt-in)
+    h->prof_on = true;
+    h->eager_used = 0;
+    for (int r = 0; r < reps; ++r) UT_CUDA(h, enqueue_step(h, nullptr, h->stream));
+    double ms = 0.0;
+    int64_t n = 0;
+    ut_status st = env_stage_time(h, &ms, &n);
+    if (st != UT_OK) return st;
+    const double avg = ms / (double)(n > 0 ? n : 1);
+    if (avg < best) {
+      best = avg;
+      best_v = v;
+    }
+  }
+  h->prof_on = prof_before;
+  h->eager_used = 0;
+  h->pf_variant = best_v;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = best_v;
+  }
+  if (chosen) *chosen = best_v;
   return UT_OK;
 }
 

@@ -1,0 +1,21 @@
+// Instantiations of the particle-filter step, group B (see pf_variants.h).
+#include "pf_kernel.cuh"
+#include "pf_variants.h"
+
+namespace ut {
+namespace pf {
+
+cudaError_t launch_variant_b(int v, const EnvDev& d, cudaStream_t s) {
+  switch (v) {
+#define UT_PF_CASE(i, nt, ppt, minb, name) \
+  case i:                                  \
+    return launch_step<nt, ppt, minb>(d, s);
+    UT_PF_VARIANTS_B(UT_PF_CASE)
+#undef UT_PF_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace pf
+}  // namespace ut
