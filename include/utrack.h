@@ -256,6 +256,30 @@ ut_status env_debug(const ut_env* env, ut_debug_view* out);
 ut_status env_metrics(ut_env* env, ut_rollout_stats* out);
 ut_status env_metrics_reset(ut_env* env);
 
+/* Transformer agent weights (Sec. III-B.1, Fig. 3; readings C16).  params_host
+ * holds n_params floats in the canonical order: W_emb[d][8], b_emb[d]; per
+ * block: ln1_g[d], ln1_b[d], Wqkv[3d][d], bqkv[3d], Wo[d][d], bo[d], ln2_g[d],
+ * ln2_b[d], W1[4d][d], b1[4d], W2[d][4d], b2[d]; then lnf_g[d], lnf_b[d],
+ * Wh[n_actions][d], bh[n_actions] (row-major, out x in).  Matrices are rounded
+ * to BF16 (round to nearest even) and packed into tensor-core operand images;
+ * vectors stay FP32.  Copied in (synchronising).  From then on env_step with
+ * actions_dev == NULL and rollout() draw actions by the Gumbel-max rule from
+ * the agent's logits on the previous observation.  Built for d_model 64 and
+ * 128 with 16-wide heads (else UT_ERR_UNSUPPORTED); UT_ERR_STATE if the
+ * handle was created with d_model == 0; UT_ERR_INVALID on a count mismatch. */
+ut_status env_set_policy(ut_env* env, const float* params_host, int64_t n_params);
+
+/* Transformer agent forward on caller buffers with the handle's weights:
+ * tokens_dev [n_agents][n_slots][8] BF16 (16-byte aligned), n_ent_dev
+ * [n_agents] entity tokens in use (<= n_slots), h_dev [n_agents][d_model]
+ * BF16 recurrent embedding, read and replaced by the block output at the
+ * recurrent token; logits_dev [n_agents][n_actions] FP32 written;
+ * actions_dev [n_agents] (optional) receives Gumbel-max samples drawn at
+ * global step `step`.  Errors: UT_ERR_STATE (no weights), UT_ERR_INVALID. */
+ut_status policy_forward(ut_env* env, const uint16_t* tokens_dev, const int32_t* n_ent_dev, uint16_t* h_dev,
+                         float* logits_dev, int32_t* actions_dev, int64_t n_agents, int32_t n_slots, uint32_t step,
+                         void* cuda_stream);
+
 /* ---------------------------------------------------------------------- */
 /* Stand-alone operations (the same device code the step uses).            */
 /* ---------------------------------------------------------------------- */

@@ -117,6 +117,7 @@ def _declare(L):
     L.oc_systematic_resample.argtypes = [ctypes.c_int32, _dp, ctypes.c_uint64, _ip]
     L.oc_tracking_reward.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.oc_tracking_reward.restype = ctypes.c_double
+    L.oc_obs.argtypes = [ctypes.POINTER(OcConfig), ctypes.POINTER(OcState), _dp]
     L.oc_est_features.argtypes = [ctypes.POINTER(OcConfig), ctypes.POINTER(OcState), ctypes.c_uint32, _dp, _dp]
     L.oc_policy_param_count.argtypes = [ctypes.POINTER(OcPolicyDims)]
     L.oc_policy_param_count.restype = ctypes.c_int64
@@ -273,6 +274,13 @@ class OracleEnv:
         if "meas" in out:
             out["meas"] = out["meas"].reshape(self.F, AM, 4)
         return out
+
+    def obs(self) -> np.ndarray:
+        """Observation tokens of the current state [NA, A_max + T_max, 8]."""
+        NS = self.p.max_agents + self.p.max_targets
+        tok = np.zeros(self.NA * NS * 8)
+        lib().oc_obs(ctypes.byref(self.cfg), ctypes.byref(self.st), _p(tok))
+        return tok.reshape(self.NA, NS, 8)
 
     def est_features(self, g: Optional[int] = None):
         feat = np.zeros((self.F, FEAT))

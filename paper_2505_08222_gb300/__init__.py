@@ -172,6 +172,32 @@ class Env:
         _check(lib.rollout(self.h, T, ctypes.byref(s)), self.h, "rollout")
         return {k: getattr(s, k) for k, _ in _abi.RolloutStats._fields_}
 
+    @property
+    def policy_ready(self) -> bool:
+        return getattr(self, "_policy_ready", False)
+
+    def set_policy(self, params: np.ndarray):
+        """Canonical float32 parameter blob of the transformer agent."""
+        prm = np.ascontiguousarray(params, np.float32)
+        _check(lib.env_set_policy(self.h, prm.ctypes.data_as(ctypes.c_void_p), prm.size), self.h, "env_set_policy")
+        self._policy_ready = True
+
+    def policy_forward(self, tokens: torch.Tensor, n_ent: torch.Tensor, h: torch.Tensor, step: int = 1,
+                       sample: bool = False):
+        """Forward of the agent on caller tensors: tokens [n, S, 8] bf16,
+        n_ent [n] int32, h [n, d] bf16 (updated in place).  Returns logits
+        (and actions if sample)."""
+        assert tokens.dtype == torch.bfloat16 and h.dtype == torch.bfloat16 and n_ent.dtype == torch.int32
+        tokens = tokens.contiguous()
+        n, S, _ = tokens.shape
+        logits = torch.empty((n, self.params.n_actions), dtype=torch.float32, device="cuda")
+        act = torch.empty(n, dtype=torch.int32, device="cuda") if sample else None
+        _check(lib.policy_forward(self.h, ctypes.c_void_p(tokens.data_ptr()), ctypes.c_void_p(n_ent.data_ptr()),
+                                  ctypes.c_void_p(h.data_ptr()), ctypes.c_void_p(logits.data_ptr()),
+                                  ctypes.c_void_p(act.data_ptr()) if act is not None else None, n, S, step,
+                                  ctypes.c_void_p(_stream_ptr(None))), self.h, "policy_forward")
+        return (logits, act) if sample else logits
+
     def rollout_prepare(self, T: int):
         _check(lib.rollout_prepare(self.h, T), self.h, "rollout_prepare")
 

@@ -104,6 +104,9 @@ SIGNATURES = {
     "env_set_pf_variant": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "env_get_pf_variant": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32)]),
     "env_autotune": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "env_set_policy": (ctypes.c_int, [_vp, _vp, ctypes.c_int64]),
+    "policy_forward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32,
+                                      _vp]),
     "ut_philox": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, ctypes.c_int64, _vp]),
     "tc_gemm_bf16": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp]),
     "tracker_update_noalloc": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_uint64, ctypes.c_uint32] + [_vp] * 13),

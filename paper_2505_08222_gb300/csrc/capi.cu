@@ -182,6 +182,7 @@ ut_status env_create(const ut_config* cfg, const ut_allocator* allocator, void* 
   h->NT = L.NT;
   h->F = L.F;
   h->agents_per_env = L.a;
+  h->targets_per_env = L.t;
 
   EnvDev& d = h->d;
   std::memset(&d, 0, sizeof(d));

@@ -24,7 +24,7 @@ struct ut_env {
   ut::EnvDev d{};
   std::string err;
   int64_t NA = 0, NT = 0, F = 0;
-  std::vector<int32_t> agents_per_env;
+  std::vector<int32_t> agents_per_env, targets_per_env;
   int pf_variant = 0;
   bool reset_done = false;
   // graph-captured rollout

@@ -1,0 +1,120 @@
+"""Transformer agent (Sec. III-B.1, Fig. 3) on the tensor cores against the
+FP64 oracle on the same BF16-representable weights and inputs.
+
+Tolerance: activations are rounded to BF16 before every matrix product
+(relative error 2^-9 per operand), accumulations are FP32; over L pre-LN
+blocks the logits (magnitude ~1) differ from the FP64 oracle by a few 1e-3
+typically and stay below 3e-2 + 2e-2 |logit|, which the test uses."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from synth import preset
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2505_08222_gb300 as ut  # noqa: E402
+
+ATOL, RTOL = 3e-2, 2e-2
+
+
+def _env(name, **kw):
+    p = preset(name, n_envs=4).replace(**kw)
+    env = ut.Env(p)
+    dims = synth.PolicyDims(p.d_model, p.n_layers, p.n_heads, p.n_actions)
+    params = synth.policy_params(dims, seed=17)
+    env.set_policy(params)
+    return env, p, params
+
+
+def _bf16(x):
+    return torch.from_numpy(synth.bf16_bits(x).view(np.int16)).view(torch.bfloat16)
+
+
+@pytest.mark.parametrize("name,n_agents", [("fleet5", 300), ("large", 150), ("fleet5", 1)])
+def test_policy_logits_match_oracle(name, n_agents):
+    env, p, params = _env(name)
+    NS = p.max_agents + p.max_targets
+    rng = np.random.default_rng(n_agents)
+    n_ent = rng.integers(1, NS + 1, n_agents).astype(np.int32)
+    n_ent[:3] = NS
+    tok = synth.random_tokens(n_agents, NS, n_ent, seed=5)
+    h = synth.round_bf16(0.5 * rng.standard_normal((n_agents, p.d_model)).astype(np.float32))
+    h_dev = _bf16(h).cuda()
+    logits = env.policy_forward(_bf16(tok).cuda(), torch.from_numpy(n_ent).cuda(), h_dev)
+    ref, ref_h = oracle.policy_forward(params, p.d_model, p.n_layers, p.n_heads, tok, n_ent, h, p.n_actions)
+    got = logits.cpu().numpy()
+    err = np.abs(got - ref)
+    assert np.all(err <= ATOL + RTOL * np.abs(ref)), float(err.max())
+    got_h = h_dev.float().cpu().numpy()
+    assert np.all(np.abs(got_h - ref_h) <= ATOL + RTOL * np.abs(ref_h)), float(np.abs(got_h - ref_h).max())
+    print(f"{name}: max |dlogit| {err.max():.2e}, mean {err.mean():.2e}")
+
+
+def test_policy_entity_permutation_invariance_on_gpu():
+    env, p, params = _env("fleet5")
+    NS = 10
+    n = 64
+    n_ent = np.full(n, NS, np.int32)
+    tok = synth.random_tokens(n, NS, n_ent, seed=9)
+    h = synth.round_bf16(np.random.default_rng(1).standard_normal((n, p.d_model)).astype(np.float32))
+    a = env.policy_forward(_bf16(tok).cuda(), torch.from_numpy(n_ent).cuda(), _bf16(h).cuda()).cpu().numpy()
+    perm = np.random.default_rng(2).permutation(NS)
+    b = env.policy_forward(_bf16(tok[:, perm]).cuda(), torch.from_numpy(n_ent).cuda(), _bf16(h).cuda()).cpu().numpy()
+    np.testing.assert_allclose(a, b, atol=1e-4)
+
+
+def test_gumbel_actions_are_argmax_of_noisy_logits():
+    env, p, params = _env("fleet5")
+    n, NS = 200, 10
+    n_ent = np.full(n, NS, np.int32)
+    tok = synth.random_tokens(n, NS, n_ent, seed=3)
+    h = np.zeros((n, p.d_model), np.float32)
+    logits, act = env.policy_forward(_bf16(tok).cuda(), torch.from_numpy(n_ent).cuda(), _bf16(h).cuda(), step=7,
+                                     sample=True)
+    lg = logits.cpu().numpy().astype(np.float64)
+    # the handle was never reset: its seed is 0
+    _, gum = oracle.gumbel_actions(0, 7, lg)
+    a = act.cpu().numpy()
+    noisy = lg + gum
+    assert np.all(noisy[np.arange(n), a] >= noisy.max(1) - 1e-5)
+
+
+def test_env_step_uses_policy_on_reset_observation():
+    p = preset("fleet5", n_envs=6).replace(n_particles=128)
+    env = ut.Env(p)
+    dims = synth.PolicyDims(p.d_model, p.n_layers, p.n_heads, p.n_actions)
+    params = synth.policy_params(dims, seed=3)
+    env.set_policy(params)
+    env.reset(21)
+    out = env.step()
+    o = oracle.OracleEnv(p, 21)
+    o.reset(0)
+    tok = o.obs()
+    ref, _ = oracle.policy_forward(params, p.d_model, p.n_layers, p.n_heads, tok, o.n_entities(),
+                                   np.zeros((o.NA, p.d_model)), p.n_actions)
+    got = out["logits"].cpu().numpy()
+    assert np.all(np.abs(got - ref) <= ATOL + RTOL * np.abs(ref)), float(np.abs(got - ref).max())
+    _, gum = oracle.gumbel_actions(21, 1, got.astype(np.float64))
+    a = out["actions"].cpu().numpy()
+    noisy = got + gum
+    assert np.all(noisy[np.arange(o.NA), a] >= noisy.max(1) - 1e-5)
+    # the whole step ran with those actions: positions follow from them
+    o.step(a)
+    st = env.state()
+    assert np.allclose(st["ax"].cpu().numpy(), o.arr["ax"], rtol=0, atol=1e-3)
+
+
+def test_rollout_with_policy_runs_in_a_graph():
+    p = preset("fleet5", n_envs=32).replace(n_particles=256)
+    env = ut.Env(p)
+    env.set_policy(synth.policy_params(synth.PolicyDims(64, 2, 4), seed=1))
+    env.reset(4)
+    s = env.rollout(12)
+    assert s["steps"] == 12 and s["kernel_launches"] == 12 * 5 and s["device_status"] == 0
+    assert np.isfinite(s["rmse"])
