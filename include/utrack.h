@@ -281,6 +281,64 @@ ut_status policy_forward(ut_env* env, const uint16_t* tokens_dev, const int32_t*
                          void* cuda_stream);
 
 /* ---------------------------------------------------------------------- */
+/* Learned range-only estimator (no counterpart in the paper, whose tracker */
+/* is the particle filter of Sec. II-A; readings C18).                     */
+/* MLP 96 -> 256 -> 256 -> 256 -> 2, erf-GELU.  Features of a filter: its 16 */
+/* most recent received pings, newest first, each [(qx - ax)/S, (qy - ay)/S, */
+/* r/S, (g - g_m)/16, 1], zero padded to 96 (FP32).  Output: target position */
+/* relative to the observer agent, in units of S.  Parameters in canonical  */
+/* order W1[256][96], b1, W2[256][256], b2, W3[256][256], b3, W4[2][256], b4 */
+/* (156,930 floats).  Hidden layers run on the tensor cores (BF16 operands,  */
+/* FP32 accumulation; the first layer multiplies the features' BF16 high and */
+/* low parts), FP32 master weights.                                          */
+/* ---------------------------------------------------------------------- */
+#define UT_EST_PARAMS 156930
+
+typedef struct ut_est_train_config {
+  int32_t steps;      /* Adam steps */
+  int32_t batch;      /* rows per step, drawn uniformly with replacement
+                         (batch == n_rows: the whole dataset in order) */
+  float lr;           /* peak learning rate */
+  int32_t cosine;     /* 1: cosine decay of lr to 0 over the steps */
+  float beta1, beta2, eps;
+  uint64_t seed;      /* batch sampling stream */
+} ut_est_train_config;
+
+typedef struct ut_est_train_stats {
+  double loss_first;  /* loss L of the first batch (definition at est_loss_grad) */
+  double loss_last;   /* loss L of the last batch */
+  double ms;          /* device time of the run */
+  int64_t rows_seen;
+} ut_est_train_stats;
+
+/* Sets the FP32 weights (host, canonical order) and clears Adam's moments.
+ * Synchronising.  Errors: UT_ERR_INVALID (count), UT_ERR_NOMEM, UT_ERR_CUDA. */
+ut_status est_set_weights(ut_env* env, const float* params_host, int64_t n_params);
+/* Copies the FP32 master weights out (synchronising). */
+ut_status est_get_weights(ut_env* env, float* params_host, int64_t n_params);
+/* 0: particle filter (default); 1: the learned estimator replaces the filter
+ * stage of every step (needs weights and a handle created with UT_FLAG_RING). */
+ut_status est_set_mode(ut_env* env, int32_t mode);
+/* Raw network outputs out_dev [n_rows][2] of features X_dev [n_rows][96]. */
+ut_status est_forward(ut_env* env, const float* X_dev, float* out_dev, int64_t n_rows);
+/* Features [F][96] and labels [F][2] = (target - observer)/S of every filter
+ * in the current state (after a step); needs UT_FLAG_RING. */
+ut_status est_record(ut_env* env, float* feat_dev, float* label_dev);
+/* Loss L = (1/(2B)) sum over rows and both outputs of (out - y)^2 on rows
+ * 0..B-1 and its gradient grad_dev [156930] (device, canonical order).
+ * Synchronising; *loss_host (optional) receives L. */
+ut_status est_loss_grad(ut_env* env, const float* X_dev, const float* Y_dev, int32_t B, float* grad_dev,
+                        double* loss_host);
+/* Adam (bias-corrected) over cfg->steps batches of X_dev / Y_dev
+ * ([n_rows][96], [n_rows][2], device).  Synchronising; stats optional. */
+ut_status est_train(ut_env* env, const float* X_dev, const float* Y_dev, int64_t n_rows,
+                    const ut_est_train_config* cfg, ut_est_train_stats* stats);
+/* Raw little-endian file: 4 uint32 header (magic, version, count, Adam step),
+ * then FP32 master weights, first and second moments. */
+ut_status est_save(ut_env* env, const char* path);
+ut_status est_load(ut_env* env, const char* path);
+
+/* ---------------------------------------------------------------------- */
 /* Stand-alone operations (the same device code the step uses).            */
 /* ---------------------------------------------------------------------- */
 

@@ -198,6 +198,54 @@ class Env:
                                   ctypes.c_void_p(_stream_ptr(None))), self.h, "policy_forward")
         return (logits, act) if sample else logits
 
+    # ------------------------------------------------------------ estimator
+    def est_set_weights(self, params: np.ndarray):
+        prm = np.ascontiguousarray(params, np.float32)
+        _check(lib.est_set_weights(self.h, prm.ctypes.data_as(ctypes.c_void_p), prm.size), self.h, "est_set_weights")
+
+    def est_get_weights(self) -> np.ndarray:
+        out = np.zeros(156930, np.float32)
+        _check(lib.est_get_weights(self.h, out.ctypes.data_as(ctypes.c_void_p), out.size), self.h, "est_get_weights")
+        return out
+
+    def est_set_mode(self, learned: bool):
+        _check(lib.est_set_mode(self.h, 1 if learned else 0), self.h, "est_set_mode")
+
+    def est_forward(self, X: torch.Tensor) -> torch.Tensor:
+        assert X.is_cuda and X.dtype == torch.float32 and X.shape[-1] == 96
+        X = X.contiguous()
+        out = torch.empty((X.shape[0], 2), dtype=torch.float32, device="cuda")
+        _check(lib.est_forward(self.h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(out.data_ptr()), X.shape[0]),
+               self.h, "est_forward")
+        return out
+
+    def est_record(self, feat: torch.Tensor, label: torch.Tensor):
+        """Writes the current features [F, 96] and labels [F, 2] into the given tensors."""
+        assert feat.is_contiguous() and label.is_contiguous()
+        _check(lib.est_record(self.h, ctypes.c_void_p(feat.data_ptr()), ctypes.c_void_p(label.data_ptr())), self.h,
+               "est_record")
+
+    def est_loss_grad(self, X: torch.Tensor, Y: torch.Tensor):
+        grad = torch.empty(156930, dtype=torch.float32, device="cuda")
+        loss = ctypes.c_double()
+        _check(lib.est_loss_grad(self.h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()), X.shape[0],
+                                 ctypes.c_void_p(grad.data_ptr()), ctypes.byref(loss)), self.h, "est_loss_grad")
+        return loss.value, grad
+
+    def est_train(self, X: torch.Tensor, Y: torch.Tensor, steps: int, batch: int, lr: float = 1e-3,
+                  cosine: bool = True, seed: int = 0, beta1=0.9, beta2=0.999, eps=1e-8) -> dict:
+        cfg = _abi.EstTrainConfig(steps, batch, lr, 1 if cosine else 0, beta1, beta2, eps, seed)
+        st = _abi.EstTrainStats()
+        _check(lib.est_train(self.h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()), X.shape[0],
+                             ctypes.byref(cfg), ctypes.byref(st)), self.h, "est_train")
+        return {k: getattr(st, k) for k, _ in _abi.EstTrainStats._fields_}
+
+    def est_save(self, path: str):
+        _check(lib.est_save(self.h, path.encode()), self.h, "est_save")
+
+    def est_load(self, path: str):
+        _check(lib.est_load(self.h, path.encode()), self.h, "est_load")
+
     def rollout_prepare(self, T: int):
         _check(lib.rollout_prepare(self.h, T), self.h, "rollout_prepare")
 

@@ -75,6 +75,17 @@ class DebugView(ctypes.Structure):
     _fields_ = [(n, _vp) for n in DEBUG_PTRS]
 
 
+class EstTrainConfig(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("cosine", ctypes.c_int32), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+class EstTrainStats(ctypes.Structure):
+    _fields_ = [("loss_first", ctypes.c_double), ("loss_last", ctypes.c_double), ("ms", ctypes.c_double),
+                ("rows_seen", ctypes.c_int64)]
+
+
 class RolloutStats(ctypes.Structure):
     _fields_ = [("sum_sq_err", ctypes.c_double), ("n_err", ctypes.c_int64), ("rmse", ctypes.c_double),
                 ("reward_sum", ctypes.c_double), ("crash_count", ctypes.c_int64),
@@ -107,6 +118,16 @@ SIGNATURES = {
     "env_set_policy": (ctypes.c_int, [_vp, _vp, ctypes.c_int64]),
     "policy_forward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32,
                                       _vp]),
+    "est_set_weights": (ctypes.c_int, [_vp, _vp, ctypes.c_int64]),
+    "est_get_weights": (ctypes.c_int, [_vp, _vp, ctypes.c_int64]),
+    "est_set_mode": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "est_forward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64]),
+    "est_record": (ctypes.c_int, [_vp, _vp, _vp]),
+    "est_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _vp, ctypes.POINTER(ctypes.c_double)]),
+    "est_train": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, ctypes.POINTER(EstTrainConfig),
+                                 ctypes.POINTER(EstTrainStats)]),
+    "est_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),
+    "est_load": (ctypes.c_int, [_vp, ctypes.c_char_p]),
     "ut_philox": (ctypes.c_int, [_vp, ctypes.c_uint64, _vp, ctypes.c_int64, _vp]),
     "tc_gemm_bf16": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp]),
     "tracker_update_noalloc": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_uint64, ctypes.c_uint32] + [_vp] * 13),

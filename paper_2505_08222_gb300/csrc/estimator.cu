@@ -1,0 +1,559 @@
+// Learned range-only estimator kernels: forward (inference and training),
+// input-gradient pass, weight-gradient pass, Adam, feature recording.
+//
+// All three hidden layers run on the tensor cores (tcgen05.mma, BF16 x BF16 ->
+// FP32 in TMEM) with 128 rows per CTA and one thread per row in the
+// epilogues.  The first layer's inputs are FP32 features split into a BF16
+// high part and a BF16 remainder that are multiplied by the same weights and
+// accumulated together: ranges of hundreds of metres keep ~1e-5 relative
+// precision instead of BF16's 4e-3, which matters for metre-level tracking.
+// The 2-wide output layer runs on CUDA cores.
+#include "estimator.cuh"
+#include "tc.cuh"
+
+#include <cmath>
+#include <cstring>
+
+namespace ut {
+namespace est {
+namespace {
+
+constexpr int kT = 128;
+constexpr uint32_t TAG_BATCH = 14;
+constexpr size_t kFwdSmem = 65536 + 65536;
+constexpr size_t kWgradSmem = 32768 + 65536;
+
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x) {
+  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+}
+
+__device__ __forceinline__ void store8(unsigned char* img, int row, int k0, int rows, const float* v) {
+  uint4 p;
+  p.x = (uint32_t)f2bf_bits(v[0]) | ((uint32_t)f2bf_bits(v[1]) << 16);
+  p.y = (uint32_t)f2bf_bits(v[2]) | ((uint32_t)f2bf_bits(v[3]) << 16);
+  p.z = (uint32_t)f2bf_bits(v[4]) | ((uint32_t)f2bf_bits(v[5]) << 16);
+  p.w = (uint32_t)f2bf_bits(v[6]) | ((uint32_t)f2bf_bits(v[7]) << 16);
+  *reinterpret_cast<uint4*>(img + tc::kmajor_offset(row, k0, rows)) = p;
+}
+
+__device__ __forceinline__ void copy_img(unsigned char* dst, const unsigned char* __restrict__ src, size_t bytes) {
+  const uint4* s = reinterpret_cast<const uint4*>(src);
+  uint4* t = reinterpret_cast<uint4*>(dst);
+  for (size_t i = threadIdx.x; i < bytes / 16; i += kT) t[i] = __ldg(s + i);
+}
+
+// Estimator features of filter f at step g from its ping ring (reading C18):
+// 16 slots newest first, [(qx - ax)/S, (qy - ay)/S, r/S, (g - g_m)/16, 1].
+__device__ __forceinline__ void ring_features(const EnvDev& d, int f, uint32_t g, float (&x)[IN]) {
+  const int ia = d.filt_agent[f];
+  const float ax = d.ax[ia], ay = d.ay[ia];
+  const int head = d.ring_head[f], cnt = d.ring_count[f];
+  const float4* ring = reinterpret_cast<const float4*>(d.ring) + (long long)f * kRing;
+#pragma unroll
+  for (int s = 0; s < kRing; ++s) {
+    float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool on = s < cnt;
+    if (on) e = ring[(head - 1 - s) & (kRing - 1)];
+    x[5 * s + 0] = on ? (e.x - ax) / d.S : 0.0f;
+    x[5 * s + 1] = on ? (e.y - ay) / d.S : 0.0f;
+    x[5 * s + 2] = on ? e.z / d.S : 0.0f;
+    x[5 * s + 3] = on ? ((float)g - e.w) / 16.0f : 0.0f;
+    x[5 * s + 4] = on ? 1.0f : 0.0f;
+  }
+#pragma unroll
+  for (int i = 5 * kRing; i < IN; ++i) x[i] = 0.0f;
+}
+
+struct FwdArgs {
+  Net net;
+  const float* X;
+  const int32_t* rows;
+  int B;
+  float* out;
+  float* z;     // training: [3][B][256], else NULL
+  uint16_t* a;  // training: [3][B][256], else NULL
+  EnvDev d;     // env mode
+  int* status;
+};
+
+template <bool ENV>
+__global__ void __launch_bounds__(kT, 1) fwd_kernel(FwdArgs p) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sA = smem;          // features hi | lo, then hidden activations [128 x 256]
+  unsigned char* sB = smem + 65536;  // one weight chunk [128 x K]
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tbase;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const long long b = (long long)blockIdx.x * kT + tid;
+  const long long n = ENV ? (long long)p.d.F : (long long)p.B;
+  const bool valid = b < n;
+
+  if (warp == 0) {
+    tc::tmem_alloc(&tbase, 256);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+
+  float x[IN];
+  if (ENV) {
+    if (valid) ring_features(p.d, (int)b, p.d.counters[0] + 1u, x);
+    else
+#pragma unroll
+      for (int i = 0; i < IN; ++i) x[i] = 0.0f;
+  } else {
+    const long long src = valid ? (p.rows ? (long long)p.rows[b] : b) : 0;
+#pragma unroll
+    for (int i = 0; i < IN; i += 4) {
+      float4 v = valid ? __ldg(reinterpret_cast<const float4*>(p.X + src * IN + i)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      x[i] = v.x; x[i + 1] = v.y; x[i + 2] = v.z; x[i + 3] = v.w;
+    }
+  }
+#pragma unroll
+  for (int c0 = 0; c0 < IN; c0 += 8) {
+    float hi[8], lo[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      hi[i] = bf_bits2f(f2bf_bits(x[c0 + i]));
+      lo[i] = x[c0 + i] - hi[i];
+    }
+    store8(sA, tid, c0, 128, hi);
+    store8(sA + 128 * IN * 2, tid, c0, 128, lo);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tbase;
+  const uint32_t lane = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t aA = tc::smem_addr(sA), aB = tc::smem_addr(sB);
+  uint32_t phase = 0;
+  bool ok = true;
+  const float* mst = p.net.master;
+
+  // layer 1: K = 96, both halves of the features, two N-halves of 128
+  {
+    const uint32_t a2[2] = {aA, aA + 128 * IN * 2};
+    for (int h = 0; h < 2; ++h) {
+      copy_img(sB, p.net.img + IMG_W1_OFF + (size_t)h * 128 * IN * 2, (size_t)128 * IN * 2);
+      ok &= tc::mma_group(tmem + 128 * h, a2, 2, aB, 128, IN, false, &mbar, phase);
+    }
+  }
+  float o0 = 0.0f, o1 = 0.0f;
+  for (int l = 0; l < 3; ++l) {
+    // epilogue of hidden layer l: z = acc + b, a = GELU(z) -> next A operand
+    const float* bias = mst + (l == 0 ? B1_OFF : (l == 1 ? B2_OFF : B3_OFF));
+#pragma unroll 1
+    for (int c0 = 0; c0 < HID; c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(lane + c0, v);
+      float av[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        v[i] += __ldg(bias + c0 + i);
+        av[i] = gelu(v[i]);
+      }
+      if (p.z && valid) {
+        float* zr = p.z + ((long long)l * p.B + b) * HID + c0;
+        uint16_t* ar = p.a + ((long long)l * p.B + b) * HID + c0;
+#pragma unroll
+        for (int i = 0; i < 16; i += 4) *reinterpret_cast<float4*>(zr + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+#pragma unroll
+        for (int i = 0; i < 16; i += 2)
+          *reinterpret_cast<uint32_t*>(ar + i) = (uint32_t)f2bf_bits(av[i]) | ((uint32_t)f2bf_bits(av[i + 1]) << 16);
+      }
+      if (l < 2) {
+        store8(sA, tid, c0, 128, av);
+        store8(sA, tid, c0 + 8, 128, av + 8);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          o0 = fmaf(__ldg(mst + W4_OFF + c0 + i), av[i], o0);
+          o1 = fmaf(__ldg(mst + W4_OFF + HID + c0 + i), av[i], o1);
+        }
+      }
+    }
+    if (l < 2) {
+      const size_t base = l == 0 ? IMG_W2_OFF : IMG_W3_OFF;
+      for (int h = 0; h < 2; ++h) {
+        copy_img(sB, p.net.img + base + (size_t)h * 128 * HID * 2, (size_t)128 * HID * 2);
+        ok &= tc::mma_group(tmem + 128 * h, &aA, 1, aB, 128, HID, false, &mbar, phase);
+      }
+    }
+  }
+  o0 += __ldg(mst + B4_OFF);
+  o1 += __ldg(mst + B4_OFF + 1);
+  if (valid && ok) {
+    if (ENV) {
+      const int f = (int)b;
+      const int ia = p.d.filt_agent[f], it = p.d.filt_target[f];
+      const float ex = p.d.ax[ia] + p.d.S * o0, ey = p.d.ay[ia] + p.d.S * o1;
+      p.d.estx[f] = ex;
+      p.d.esty[f] = ey;
+      const float dx = ex - p.d.tx[it], dy = ey - p.d.ty[it];
+      p.d.err[f] = sqrtf(dx * dx + dy * dy);
+    } else {
+      p.out[b * OUT] = o0;
+      p.out[b * OUT + 1] = o1;
+    }
+  }
+  if (!ok && tid == 0) raise_status(p.status, 2);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+// ---------------------------------------------------------------------------
+// Input-gradient pass: dz3, dz2, dz1 (BF16, for the weight gradients), bias
+// gradients and the output layer's gradients; loss.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kT, 1) bwd_kernel(Net net, TrainBufs t, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + 65536;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tbase;
+  __shared__ float s_red[2 * HID + 3 * HID + 2];  // dW4, db3, db2, db1, db4
+  __shared__ double s_loss;
+  const int tid = threadIdx.x, warp = tid >> 5, lanei = tid & 31;
+  const long long b = (long long)blockIdx.x * kT + tid;
+  const bool valid = b < t.B;
+  const long long row = valid ? (t.rows ? (long long)t.rows[b] : b) : 0;
+  const float* mst = net.master;
+
+  if (warp == 0) {
+    tc::tmem_alloc(&tbase, 256);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&mbar, 1);
+    s_loss = 0.0;
+  }
+  for (int i = tid; i < 5 * HID + 2; i += kT) s_red[i] = 0.0f;
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tbase;
+  const uint32_t lane = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t aA = tc::smem_addr(sA), aB = tc::smem_addr(sB);
+  uint32_t phase = 0;
+  bool ok = true;
+  float* s_dW4 = s_red;
+  float* s_db3 = s_red + 2 * HID;
+  float* s_db2 = s_db3 + HID;
+  float* s_db1 = s_db2 + HID;
+  float* s_db4 = s_db1 + HID;
+
+  // output layer: dL/dout = (out - y) / B
+  float d0 = 0.0f, d1 = 0.0f;
+  double se = 0.0;
+  if (valid) {
+    const float e0 = t.out[b * OUT] - t.Y[row * OUT], e1 = t.out[b * OUT + 1] - t.Y[row * OUT + 1];
+    d0 = e0 / (float)t.B;
+    d1 = e1 / (float)t.B;
+    se = (double)e0 * e0 + (double)e1 * e1;
+  }
+  se = warp_sum_d(se);
+  if (lanei == 0) atomicAdd(&s_loss, se);
+  {
+    const float r0 = warp_sum(d0), r1 = warp_sum(d1);
+    if (lanei == 0) {
+      atomicAdd(&s_db4[0], r0);
+      atomicAdd(&s_db4[1], r1);
+    }
+  }
+  // dz3 = (W4^T dout) * GELU'(z3); dW4 += dout a3^T
+#pragma unroll 1
+  for (int c0 = 0; c0 < HID; c0 += 16) {
+    float dz[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int k = c0 + i;
+      const float z = valid ? t.z[((long long)2 * t.B + b) * HID + k] : 0.0f;
+      const float a = valid ? gelu(z) : 0.0f;
+      const float w0 = warp_sum(d0 * a), w1 = warp_sum(d1 * a);
+      if (lanei == 0) {
+        atomicAdd(&s_dW4[k], w0);
+        atomicAdd(&s_dW4[HID + k], w1);
+      }
+      const float da = d0 * __ldg(mst + W4_OFF + k) + d1 * __ldg(mst + W4_OFF + HID + k);
+      dz[i] = valid ? da * gelu_grad(z) : 0.0f;
+      const float sdz = warp_sum(dz[i]);
+      if (lanei == 0) atomicAdd(&s_db3[k], sdz);
+    }
+    if (valid) {
+      uint16_t* dr = t.dz + ((long long)2 * t.B + b) * HID + c0;
+#pragma unroll
+      for (int i = 0; i < 16; i += 2)
+        *reinterpret_cast<uint32_t*>(dr + i) = (uint32_t)f2bf_bits(dz[i]) | ((uint32_t)f2bf_bits(dz[i + 1]) << 16);
+    }
+    store8(sA, tid, c0, 128, dz);
+    store8(sA, tid, c0 + 8, 128, dz + 8);
+  }
+  // dz2, dz1 through the transposed weights on the tensor cores
+  for (int l = 1; l >= 0; --l) {
+    const size_t base = l == 1 ? IMG_W3T_OFF : IMG_W2T_OFF;
+    for (int h = 0; h < 2; ++h) {
+      copy_img(sB, net.img + base + (size_t)h * 128 * HID * 2, (size_t)128 * HID * 2);
+      ok &= tc::mma_group(tmem + 128 * h, &aA, 1, aB, 128, HID, false, &mbar, phase);
+    }
+    float* s_db = l == 1 ? s_db2 : s_db1;
+#pragma unroll 1
+    for (int c0 = 0; c0 < HID; c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(lane + c0, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const float z = valid ? t.z[((long long)l * t.B + b) * HID + c0 + i] : 0.0f;
+        v[i] = valid ? v[i] * gelu_grad(z) : 0.0f;
+        const float s = warp_sum(v[i]);
+        if (lanei == 0) atomicAdd(&s_db[c0 + i], s);
+      }
+      if (valid) {
+        uint16_t* dr = t.dz + ((long long)l * t.B + b) * HID + c0;
+#pragma unroll
+        for (int i = 0; i < 16; i += 2)
+          *reinterpret_cast<uint32_t*>(dr + i) = (uint32_t)f2bf_bits(v[i]) | ((uint32_t)f2bf_bits(v[i + 1]) << 16);
+      }
+      if (l == 1) {
+        store8(sA, tid, c0, 128, v);
+        store8(sA, tid, c0 + 8, 128, v + 8);
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  for (int i = tid; i < 2 * HID; i += kT) atomicAdd(&t.grad[W4_OFF + i], s_dW4[i]);
+  for (int i = tid; i < HID; i += kT) {
+    atomicAdd(&t.grad[B3_OFF + i], s_db3[i]);
+    atomicAdd(&t.grad[B2_OFF + i], s_db2[i]);
+    atomicAdd(&t.grad[B1_OFF + i], s_db1[i]);
+  }
+  if (tid < 2) atomicAdd(&t.grad[B4_OFF + tid], s_db4[tid]);
+  if (tid == 0) atomicAdd(t.loss, s_loss / (2.0 * t.B));
+  if (!ok && tid == 0) raise_status(status, 2);
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradients dW_l = dz_l^T a_{l-1} summed over the batch, on the tensor
+// cores: M = 128 output features (one half), N = input features, K = 128
+// batch rows per MMA group, accumulated in TMEM over the CTA's batch range.
+// The transposed operands are written element-wise into K-major images.
+// grid = (batch splits, output half, layer).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kT, 2) wgrad_kernel(TrainBufs t, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sA = smem;          // dz^T [128 x 128]
+  unsigned char* sB = smem + 32768;  // a^T [N_in x 128]
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tbase;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int layer = blockIdx.z, half = blockIdx.y;
+  const int n_in = layer == 0 ? IN : HID;
+  const int n_chunks = (t.B + kT - 1) / kT;
+  const int per = (n_chunks + gridDim.x - 1) / gridDim.x;
+  const int c_begin = blockIdx.x * per, c_end = min(n_chunks, c_begin + per);
+
+  if (warp == 0) {
+    tc::tmem_alloc(&tbase, 256);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tbase;
+  const uint32_t aA = tc::smem_addr(sA), aB = tc::smem_addr(sB);
+  uint32_t phase = 0;
+  bool ok = true;
+  uint16_t* sAh = reinterpret_cast<uint16_t*>(sA);
+  uint16_t* sBh = reinterpret_cast<uint16_t*>(sB);
+  for (int c = c_begin; c < c_end; ++c) {
+    const long long b = (long long)c * kT + tid;
+    const bool valid = b < t.B;
+    // dz^T: element (o, b) of the [128 x 128] operand
+    const uint16_t* dzr = t.dz + ((long long)layer * t.B + b) * HID + half * 128;
+#pragma unroll 4
+    for (int o = 0; o < 128; o += 8) {
+      uint4 v = valid ? *reinterpret_cast<const uint4*>(dzr + o) : make_uint4(0, 0, 0, 0);
+      const uint16_t* e = reinterpret_cast<const uint16_t*>(&v);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) sAh[tc::kmajor_offset(o + i, tid, 128) / 2] = e[i];
+    }
+    // a^T: element (i, b) of the [n_in x 128] operand (layer 0: the features)
+    if (layer == 0) {
+      const long long row = valid ? (t.rows ? (long long)t.rows[b] : b) : 0;
+      for (int i = 0; i < IN; ++i)
+        sBh[tc::kmajor_offset(i, tid, IN) / 2] = valid ? f2bf_bits(t.X[row * IN + i]) : (uint16_t)0;
+    } else {
+      const uint16_t* ar = t.a + ((long long)(layer - 1) * t.B + b) * HID;
+#pragma unroll 4
+      for (int i = 0; i < HID; i += 8) {
+        uint4 v = valid ? *reinterpret_cast<const uint4*>(ar + i) : make_uint4(0, 0, 0, 0);
+        const uint16_t* e = reinterpret_cast<const uint16_t*>(&v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) sBh[tc::kmajor_offset(i + j, tid, HID) / 2] = e[j];
+      }
+    }
+    ok &= tc::mma_group(tmem, &aA, 1, aB, n_in, kT, c > c_begin, &mbar, phase);
+  }
+  if (c_end > c_begin && ok) {
+    const int o = warp * 32 + (tid & 31);
+    const long long w_off = layer == 0 ? W1_OFF : (layer == 1 ? W2_OFF : W3_OFF);
+    const uint32_t lane = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c0 = 0; c0 < n_in; c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(lane + c0, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) atomicAdd(&t.grad[w_off + (long long)(half * 128 + o) * n_in + c0 + i], v[i]);
+    }
+  }
+  if (!ok && tid == 0) raise_status(status, 2);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+// Image position of weight element (layer, out, in) in the forward operand
+// (chunks of 128 output rows) and, for layers 2 and 3, in the transposed one.
+__device__ __forceinline__ void write_images(unsigned char* img, long long i, float w) {
+  const uint16_t bits = f2bf_bits(w);
+  if (i >= W1_OFF && i < B1_OFF) {
+    const int o = (int)((i - W1_OFF) / IN), in = (int)((i - W1_OFF) % IN);
+    *reinterpret_cast<uint16_t*>(img + IMG_W1_OFF + (size_t)(o / 128) * 128 * IN * 2 +
+                                 tc::kmajor_offset(o % 128, in, 128)) = bits;
+  } else if ((i >= W2_OFF && i < B2_OFF) || (i >= W3_OFF && i < B3_OFF)) {
+    const bool l2 = i < B2_OFF;
+    const long long r = i - (l2 ? W2_OFF : W3_OFF);
+    const int o = (int)(r / HID), in = (int)(r % HID);
+    const size_t fw = l2 ? IMG_W2_OFF : IMG_W3_OFF, bw = l2 ? IMG_W2T_OFF : IMG_W3T_OFF;
+    *reinterpret_cast<uint16_t*>(img + fw + (size_t)(o / 128) * 128 * HID * 2 + tc::kmajor_offset(o % 128, in, 128)) =
+        bits;
+    *reinterpret_cast<uint16_t*>(img + bw + (size_t)(in / 128) * 128 * HID * 2 + tc::kmajor_offset(in % 128, o, 128)) =
+        bits;
+  }
+}
+
+__global__ void adam_kernel(float* master, float* m, float* v, const float* grad, float lr, float beta1, float beta2,
+                            float eps, float c1, float c2, unsigned char* img) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NPARAM) return;
+  const float g = grad[i];
+  const float mi = beta1 * m[i] + (1.0f - beta1) * g;
+  const float vi = beta2 * v[i] + (1.0f - beta2) * g * g;
+  const float th = master[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  m[i] = mi;
+  v[i] = vi;
+  master[i] = th;
+  write_images(img, i, th);
+}
+
+__global__ void pack_kernel(const float* master, unsigned char* img) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < NPARAM) write_images(img, i, master[i]);
+}
+
+__global__ void batch_rows_kernel(int32_t* rows, int B, uint32_t n_rows, uint64_t seed, uint32_t step) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  Rand4 r = philox((uint32_t)b, step, 0u, TAG_BATCH, seed);
+  rows[b] = (int32_t)__umulhi(r.x[0], n_rows);
+}
+
+__global__ void record_kernel(EnvDev d, float* feat, float* label) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= d.F) return;
+  float x[IN];
+  ring_features(d, f, d.counters[0], x);
+#pragma unroll
+  for (int i = 0; i < IN; i += 4)
+    *reinterpret_cast<float4*>(feat + (long long)f * IN + i) = make_float4(x[i], x[i + 1], x[i + 2], x[i + 3]);
+  const int ia = d.filt_agent[f], it = d.filt_target[f];
+  label[(long long)f * 2] = (d.tx[it] - d.ax[ia]) / d.S;
+  label[(long long)f * 2 + 1] = (d.ty[it] - d.ay[ia]) / d.S;
+}
+
+template <typename K>
+cudaError_t smem_optin(K k, size_t bytes, int& done) {
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done = 1;
+  return e;
+}
+
+}  // namespace
+
+cudaError_t launch_forward(const Net& net, const float* X, const int32_t* rows, int B, float* out, float* z,
+                           uint16_t* a, cudaStream_t s) {
+  static int ready = 0;
+  cudaError_t e = smem_optin(fwd_kernel<false>, kFwdSmem, ready);
+  if (e != cudaSuccess) return e;
+  if (B <= 0) return cudaSuccess;
+  FwdArgs p;
+  memset(&p, 0, sizeof(p));
+  p.net = net;
+  p.X = X;
+  p.rows = rows;
+  p.B = B;
+  p.out = out;
+  p.z = z;
+  p.a = a;
+  fwd_kernel<false><<<(B + kT - 1) / kT, kT, kFwdSmem, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_forward_env(const Net& net, const EnvDev& d, cudaStream_t s) {
+  static int ready = 0;
+  cudaError_t e = smem_optin(fwd_kernel<true>, kFwdSmem, ready);
+  if (e != cudaSuccess) return e;
+  if (d.F <= 0) return cudaSuccess;
+  FwdArgs p;
+  memset(&p, 0, sizeof(p));
+  p.net = net;
+  p.d = d;
+  p.status = d.status;
+  fwd_kernel<true><<<(d.F + kT - 1) / kT, kT, kFwdSmem, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_record(const EnvDev& d, float* feat, float* label, cudaStream_t s) {
+  if (d.F <= 0) return cudaSuccess;
+  record_kernel<<<(d.F + 127) / 128, 128, 0, s>>>(d, feat, label);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward(const Net& net, const TrainBufs& t, cudaStream_t s) {
+  static int ready_b = 0, ready_w = 0;
+  cudaError_t e = smem_optin(bwd_kernel, kFwdSmem, ready_b);
+  if (e == cudaSuccess) e = smem_optin(wgrad_kernel, kWgradSmem, ready_w);
+  if (e != cudaSuccess) return e;
+  if (t.B <= 0) return cudaSuccess;
+  bwd_kernel<<<(t.B + kT - 1) / kT, kT, kFwdSmem, s>>>(net, t, nullptr);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int n_chunks = (t.B + kT - 1) / kT;
+  const int splits = n_chunks < 24 ? n_chunks : 24;
+  wgrad_kernel<<<dim3(splits, 2, 3), kT, kWgradSmem, s>>>(t, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* master, float* m, float* v, const float* grad, int step, float lr, float beta1,
+                        float beta2, float eps, unsigned char* img, cudaStream_t s) {
+  const double c1 = 1.0 - std::pow((double)beta1, step), c2 = 1.0 - std::pow((double)beta2, step);
+  adam_kernel<<<(unsigned)((NPARAM + 255) / 256), 256, 0, s>>>(master, m, v, grad, lr, beta1, beta2, eps, (float)c1,
+                                                              (float)c2, img);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const float* master, unsigned char* img, cudaStream_t s) {
+  pack_kernel<<<(unsigned)((NPARAM + 255) / 256), 256, 0, s>>>(master, img);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_rows(int32_t* rows, int B, int64_t n_rows, uint64_t seed, uint32_t step, cudaStream_t s) {
+  batch_rows_kernel<<<(B + 255) / 256, 256, 0, s>>>(rows, B, (uint32_t)n_rows, seed, step);
+  return cudaGetLastError();
+}
+
+}  // namespace est
+}  // namespace ut

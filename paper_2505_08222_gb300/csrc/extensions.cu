@@ -1,11 +1,33 @@
 // Hooks through which the transformer agent (and the learned estimator) plug
 // into the environment step, and their C-ABI entry points.
+#include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "../../include/utrack.h"
+#include "estimator.cuh"
 #include "policy.cuh"
 #include "runtime.cuh"
+
+struct EstimatorState {
+  bool weights_set = false;
+  float* master = nullptr;  // [NPARAM]
+  float* m = nullptr;
+  float* v = nullptr;
+  float* grad = nullptr;
+  unsigned char* img = nullptr;
+  int adam_t = 0;
+  // training buffers (sized for batch_cap rows)
+  int batch_cap = 0;
+  float* z = nullptr;
+  uint16_t* a = nullptr;
+  uint16_t* dz = nullptr;
+  float* out = nullptr;
+  int32_t* rows = nullptr;
+  double* loss = nullptr;
+};
 
 struct PolicyState {
   int d = 0, L = 0, H = 0, n_act = 0;
@@ -83,6 +105,8 @@ ut_status extension_create(ut_env* h) {
 void extension_destroy(ut_env* h) {
   delete h->policy;
   h->policy = nullptr;
+  delete h->est;
+  h->est = nullptr;
 }
 
 cudaError_t extension_reset(ut_env* h, cudaStream_t s) {
@@ -96,7 +120,8 @@ cudaError_t extension_policy_actions(ut_env* h, cudaStream_t s) {
 }
 
 int extension_policy_kernels(ut_env*) { return 1; }
-cudaError_t extension_estimate(ut_env*, cudaStream_t) { return cudaErrorNotReady; }
+cudaError_t extension_estimate_impl(ut_env* h, cudaStream_t s);
+cudaError_t extension_estimate(ut_env* h, cudaStream_t s) { return extension_estimate_impl(h, s); }
 const float* extension_logits(ut_env* h) { return h->policy ? h->policy->logits : nullptr; }
 uint16_t* extension_h(ut_env* h) { return h->policy ? h->policy->h : nullptr; }
 
@@ -180,5 +205,255 @@ extern "C" ut_status policy_forward(ut_env* h, const uint16_t* tokens_dev, const
     h->err = std::string("policy_forward: ") + cudaGetErrorString(e);
     return UT_ERR_CUDA;
   }
+  return UT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Learned range-only estimator
+// ---------------------------------------------------------------------------
+
+
+
+namespace {
+
+EstimatorState* est_state(ut_env* h) {
+  if (!h->est) h->est = new EstimatorState();
+  return h->est;
+}
+
+ut_status est_fail(ut_env* h, ut_status st, const char* msg) {
+  h->err = msg;
+  return st;
+}
+
+ut_status est_alloc_weights(ut_env* h) {
+  EstimatorState* es = est_state(h);
+  if (es->master) return UT_OK;
+  es->master = (float*)env_alloc(h, est::NPARAM * 4);
+  es->m = (float*)env_alloc(h, est::NPARAM * 4);
+  es->v = (float*)env_alloc(h, est::NPARAM * 4);
+  es->grad = (float*)env_alloc(h, est::NPARAM * 4);
+  es->img = (unsigned char*)env_alloc(h, est::IMG_BYTES);
+  es->loss = (double*)env_alloc(h, 8);
+  if (!es->master || !es->m || !es->v || !es->grad || !es->img || !es->loss)
+    return est_fail(h, UT_ERR_NOMEM, "estimator: allocation failed");
+  return UT_OK;
+}
+
+ut_status est_alloc_batch(ut_env* h, int B) {
+  EstimatorState* es = est_state(h);
+  if (es->batch_cap >= B) return UT_OK;
+  // earlier (smaller) buffers stay owned by the handle until destroy
+  es->z = (float*)env_alloc(h, (size_t)3 * B * est::HID * 4);
+  es->a = (uint16_t*)env_alloc(h, (size_t)3 * B * est::HID * 2);
+  es->dz = (uint16_t*)env_alloc(h, (size_t)3 * B * est::HID * 2);
+  es->out = (float*)env_alloc(h, (size_t)B * 2 * 4);
+  es->rows = (int32_t*)env_alloc(h, (size_t)B * 4);
+  if (!es->z || !es->a || !es->dz || !es->out || !es->rows)
+    return est_fail(h, UT_ERR_NOMEM, "estimator: batch allocation failed");
+  es->batch_cap = B;
+  return UT_OK;
+}
+
+est::Net est_net(ut_env* h) {
+  est::Net n;
+  n.img = h->est->img;
+  n.master = h->est->master;
+  return n;
+}
+
+// Forward + backward of one batch into es->grad (cleared first) and es->loss.
+cudaError_t est_grad_batch(ut_env* h, const float* X, const float* Y, const int32_t* rows, int B) {
+  EstimatorState* es = h->est;
+  cudaStream_t s = h->stream;
+  cudaError_t e = cudaMemsetAsync(es->grad, 0, est::NPARAM * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(es->loss, 0, 8, s);
+  if (e == cudaSuccess) e = est::launch_forward(est_net(h), X, rows, B, es->out, es->z, es->a, s);
+  if (e != cudaSuccess) return e;
+  est::TrainBufs t;
+  t.X = X;
+  t.Y = Y;
+  t.rows = rows;
+  t.z = es->z;
+  t.a = es->a;
+  t.out = es->out;
+  t.dz = es->dz;
+  t.grad = es->grad;
+  t.loss = es->loss;
+  t.B = B;
+  return est::launch_backward(est_net(h), t, s);
+}
+
+}  // namespace
+
+namespace ut {
+cudaError_t extension_estimate_impl(ut_env* h, cudaStream_t s) {
+  if (h->est_mode != 1 || !h->est || !h->est->weights_set) return cudaErrorNotReady;
+  return est::launch_forward_env(est_net(h), h->d, s);
+}
+}  // namespace ut
+
+extern "C" ut_status est_set_weights(ut_env* h, const float* params_host, int64_t n_params) {
+  if (!h || !params_host) return UT_ERR_INVALID;
+  if (n_params != est::NPARAM) return est_fail(h, UT_ERR_INVALID, "est_set_weights: parameter count mismatch");
+  ut_status st = est_alloc_weights(h);
+  if (st != UT_OK) return st;
+  EstimatorState* es = h->est;
+  cudaError_t e = cudaMemcpyAsync(es->master, params_host, est::NPARAM * 4, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(es->m, 0, est::NPARAM * 4, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(es->v, 0, est::NPARAM * 4, h->stream);
+  if (e == cudaSuccess) e = est::launch_pack(es->master, es->img, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return est_fail(h, UT_ERR_CUDA, cudaGetErrorString(e));
+  es->adam_t = 0;
+  es->weights_set = true;
+  return UT_OK;
+}
+
+extern "C" ut_status est_get_weights(ut_env* h, float* params_host, int64_t n_params) {
+  if (!h || !params_host) return UT_ERR_INVALID;
+  if (!h->est || !h->est->weights_set) return est_fail(h, UT_ERR_STATE, "est_get_weights: no weights");
+  if (n_params != est::NPARAM) return est_fail(h, UT_ERR_INVALID, "est_get_weights: parameter count mismatch");
+  cudaError_t e = cudaMemcpyAsync(params_host, h->est->master, est::NPARAM * 4, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? UT_OK : est_fail(h, UT_ERR_CUDA, cudaGetErrorString(e));
+}
+
+extern "C" ut_status est_set_mode(ut_env* h, int32_t mode) {
+  if (!h || (mode != 0 && mode != 1)) return UT_ERR_INVALID;
+  if (mode == 1) {
+    if (!h->est || !h->est->weights_set) return est_fail(h, UT_ERR_STATE, "est_set_mode: no estimator weights");
+    if (!h->d.ring_on) return est_fail(h, UT_ERR_STATE, "est_set_mode: handle created without UT_FLAG_RING");
+  }
+  h->est_mode = mode;
+  return UT_OK;
+}
+
+extern "C" ut_status est_forward(ut_env* h, const float* X_dev, float* out_dev, int64_t n_rows) {
+  if (!h || n_rows < 0 || n_rows > 0x7fffffff || (n_rows && (!X_dev || !out_dev))) return UT_ERR_INVALID;
+  if (!h->est || !h->est->weights_set) return est_fail(h, UT_ERR_STATE, "est_forward: no weights");
+  if (reinterpret_cast<uintptr_t>(X_dev) & 15) return est_fail(h, UT_ERR_INVALID, "est_forward: X not 16-byte aligned");
+  cudaError_t e = est::launch_forward(est_net(h), X_dev, nullptr, (int)n_rows, out_dev, nullptr, nullptr, h->stream);
+  return e == cudaSuccess ? UT_OK : est_fail(h, UT_ERR_CUDA, cudaGetErrorString(e));
+}
+
+extern "C" ut_status est_record(ut_env* h, float* feat_dev, float* label_dev) {
+  if (!h || !feat_dev || !label_dev) return UT_ERR_INVALID;
+  if (!h->d.ring_on) return est_fail(h, UT_ERR_STATE, "est_record: handle created without UT_FLAG_RING");
+  if (reinterpret_cast<uintptr_t>(feat_dev) & 15) return est_fail(h, UT_ERR_INVALID, "est_record: misaligned");
+  cudaError_t e = est::launch_record(h->d, feat_dev, label_dev, h->stream);
+  return e == cudaSuccess ? UT_OK : est_fail(h, UT_ERR_CUDA, cudaGetErrorString(e));
+}
+
+extern "C" ut_status est_loss_grad(ut_env* h, const float* X_dev, const float* Y_dev, int32_t B, float* grad_dev,
+                                   double* loss_host) {
+  if (!h || !X_dev || !Y_dev || B < 1 || !grad_dev) return UT_ERR_INVALID;
+  if (!h->est || !h->est->weights_set) return est_fail(h, UT_ERR_STATE, "est_loss_grad: no weights");
+  ut_status st = est_alloc_batch(h, B);
+  if (st != UT_OK) return st;
+  cudaError_t e = est_grad_batch(h, X_dev, Y_dev, nullptr, B);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(grad_dev, h->est->grad, est::NPARAM * 4, cudaMemcpyDeviceToDevice, h->stream);
+  double loss = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&loss, h->est->loss, 8, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return est_fail(h, UT_ERR_CUDA, cudaGetErrorString(e));
+  if (loss_host) *loss_host = loss;
+  return UT_OK;
+}
+
+extern "C" ut_status est_train(ut_env* h, const float* X_dev, const float* Y_dev, int64_t n_rows,
+                               const ut_est_train_config* cfg, ut_est_train_stats* out) {
+  if (!h || !X_dev || !Y_dev || !cfg || n_rows < 1 || n_rows >= (1ll << 32)) return UT_ERR_INVALID;
+  if (cfg->steps < 1 || cfg->batch < 1 || cfg->batch > (1 << 22) || !(cfg->lr > 0.0f)) return UT_ERR_INVALID;
+  if (!h->est || !h->est->weights_set) return est_fail(h, UT_ERR_STATE, "est_train: no initial weights");
+  const int B = cfg->batch;
+  ut_status st = est_alloc_batch(h, B);
+  if (st != UT_OK) return st;
+  EstimatorState* es = h->est;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, h->stream);
+  double first = -1.0, last = 0.0;
+  const bool full = (B == n_rows);  // the whole dataset as one batch, in order
+  cudaError_t e = cudaSuccess;
+  for (int s = 0; s < cfg->steps && e == cudaSuccess; ++s) {
+    const int32_t* rows = nullptr;
+    if (!full) {
+      e = est::launch_batch_rows(es->rows, B, n_rows, cfg->seed, (uint32_t)s, h->stream);
+      rows = es->rows;
+    }
+    if (e == cudaSuccess) e = est_grad_batch(h, X_dev, Y_dev, rows, B);
+    // cosine decay of the learning rate over the run (reading C18)
+    const double frac = cfg->steps > 1 ? (double)s / (double)(cfg->steps - 1) : 0.0;
+    const float lr = cfg->cosine ? (float)(cfg->lr * 0.5 * (1.0 + std::cos(3.14159265358979 * frac))) : cfg->lr;
+    es->adam_t += 1;
+    if (e == cudaSuccess)
+      e = est::launch_adam(es->master, es->m, es->v, es->grad, es->adam_t, lr, cfg->beta1, cfg->beta2, cfg->eps,
+                           es->img, h->stream);
+    if (e == cudaSuccess && (s == 0 || s == cfg->steps - 1)) {
+      double l = 0.0;
+      e = cudaMemcpyAsync(&l, es->loss, 8, cudaMemcpyDeviceToHost, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      if (s == 0) first = l;
+      last = l;
+    }
+  }
+  cudaEventRecord(e1, h->stream);
+  cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return est_fail(h, UT_ERR_CUDA, cudaGetErrorString(e));
+  if (out) {
+    out->loss_first = first;
+    out->loss_last = last;
+    out->ms = ms;
+    out->rows_seen = (int64_t)cfg->steps * B;
+  }
+  return UT_OK;
+}
+
+extern "C" ut_status est_save(ut_env* h, const char* path) {
+  if (!h || !path) return UT_ERR_INVALID;
+  if (!h->est || !h->est->weights_set) return est_fail(h, UT_ERR_STATE, "est_save: no weights");
+  std::vector<float> buf(3 * est::NPARAM);
+  EstimatorState* es = h->est;
+  cudaError_t e = cudaMemcpyAsync(buf.data(), es->master, est::NPARAM * 4, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(buf.data() + est::NPARAM, es->m, est::NPARAM * 4, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(buf.data() + 2 * est::NPARAM, es->v, est::NPARAM * 4, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return est_fail(h, UT_ERR_CUDA, cudaGetErrorString(e));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return est_fail(h, UT_ERR_INVALID, "est_save: cannot open file");
+  const uint32_t hdr[4] = {0x55545245u /* "UTRE" */, 1u, (uint32_t)est::NPARAM, (uint32_t)es->adam_t};
+  bool ok = std::fwrite(hdr, 4, 4, f) == 4 && std::fwrite(buf.data(), 4, buf.size(), f) == buf.size();
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? UT_OK : est_fail(h, UT_ERR_INVALID, "est_save: write failed");
+}
+
+extern "C" ut_status est_load(ut_env* h, const char* path) {
+  if (!h || !path) return UT_ERR_INVALID;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return est_fail(h, UT_ERR_INVALID, "est_load: cannot open file");
+  uint32_t hdr[4] = {0, 0, 0, 0};
+  std::vector<float> buf(3 * est::NPARAM);
+  bool ok = std::fread(hdr, 4, 4, f) == 4 && hdr[0] == 0x55545245u && hdr[1] == 1u && hdr[2] == (uint32_t)est::NPARAM &&
+            std::fread(buf.data(), 4, buf.size(), f) == buf.size();
+  std::fclose(f);
+  if (!ok) return est_fail(h, UT_ERR_INVALID, "est_load: not an estimator file of this layout");
+  ut_status st = est_set_weights(h, buf.data(), est::NPARAM);
+  if (st != UT_OK) return st;
+  EstimatorState* es = h->est;
+  cudaError_t e = cudaMemcpyAsync(es->m, buf.data() + est::NPARAM, est::NPARAM * 4, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(es->v, buf.data() + 2 * est::NPARAM, est::NPARAM * 4, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return est_fail(h, UT_ERR_CUDA, cudaGetErrorString(e));
+  es->adam_t = (int)hdr[3];
   return UT_OK;
 }

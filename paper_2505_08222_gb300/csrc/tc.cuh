@@ -133,3 +133,38 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 
 }  // namespace tc
 }  // namespace ut
+
+namespace ut {
+namespace tc {
+
+// One accumulation group issued by thread 0 of the CTA: for each of
+// `n_a` A operands (e.g. the high and low BF16 halves of the same values),
+// acc[128 x N] (+)= A[128 x K] * B[N x K]^T, then a commit to `mbar` and a
+// bounded wait by every thread.  All threads must call it (it contains a
+// block barrier); their shared-memory operand writes are published first.
+__device__ __forceinline__ bool mma_group(uint32_t tmem, const uint32_t* a_addr, int n_a, uint32_t b_addr, int N,
+                                          int K, bool accumulate, uint64_t* mbar, uint32_t& phase) {
+  fence_async_smem();
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  if (threadIdx.x == 0) {
+    const uint32_t idesc = idesc_bf16(128, (uint32_t)N);
+    bool acc = accumulate;
+    for (int j = 0; j < n_a; ++j)
+      for (int k = 0; k < K / 16; ++k) {
+        const uint64_t ad = smem_desc(a_addr[j] + k * 2 * 128 * 16, 128 * 16, 128);
+        const uint64_t bd = smem_desc(b_addr + k * 2 * N * 16, N * 16, 128);
+        mma_bf16(tmem, ad, bd, idesc, acc ? 1u : 0u);
+        acc = true;
+      }
+    mma_commit(mbar);
+  }
+  const bool ok = mbar_wait(mbar, phase, 1u << 22);
+  phase ^= 1u;
+  fence_after_sync();
+  return ok;
+}
+
+}  // namespace tc
+}  // namespace ut

@@ -1,0 +1,172 @@
+"""Learned range-only estimator on the GPU against the FP64 oracle.
+
+Forward / gradient tolerance: hidden activations and weights are BF16
+operands (relative rounding 2^-9) with FP32 accumulation; outputs of
+magnitude ~0.3 land within 2e-2 of the FP64 network, gradients within 5 %
+(relative L2 norm per tensor).  Features are FP32 (the first layer splits
+them into BF16 high and low parts), so they match the oracle's to 1e-6."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from synth import preset
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2505_08222_gb300 as ut  # noqa: E402
+
+NP = 156930
+
+
+def _features(n, seed):
+    """Ring-like FP32 features: relative sender positions and ranges of a few
+    hundred metres (in units of 1 km), ages, valid flags; later slots empty."""
+    rng = np.random.default_rng(seed)
+    x = np.zeros((n, 96), np.float32)
+    cnt = rng.integers(1, 17, n)
+    for s in range(16):
+        on = s < cnt
+        x[on, 5 * s:5 * s + 2] = rng.uniform(-0.3, 0.3, (on.sum(), 2))
+        x[on, 5 * s + 2] = rng.uniform(0.02, 0.6, on.sum())
+        x[on, 5 * s + 3] = (s // 5) / 16.0
+        x[on, 5 * s + 4] = 1.0
+    return x
+
+
+def _env(n_envs=4, **kw):
+    p = preset("fleet5", n_envs=n_envs).replace(d_model=0, **kw)
+    return ut.Env(p, ring=True), p
+
+
+def test_est_forward_matches_oracle():
+    env, _ = _env()
+    params = synth.mlp_params(seed=3, bias_scale=0.1)
+    env.est_set_weights(params)
+    X = _features(1000, 1)
+    got = env.est_forward(torch.from_numpy(X).cuda()).cpu().numpy()
+    ref = oracle.mlp_forward(params, X)
+    err = np.abs(got - ref)
+    assert np.all(err <= 2e-2 + 2e-2 * np.abs(ref)), float(err.max())
+    print(f"est forward: max |d| {err.max():.2e} mean {err.mean():.2e}")
+
+
+def test_est_gradients_match_oracle():
+    env, _ = _env()
+    params = synth.mlp_params(seed=5, bias_scale=0.1)
+    env.est_set_weights(params)
+    X = _features(700, 2)
+    Y = (np.random.default_rng(3).standard_normal((700, 2)) * 0.2).astype(np.float32)
+    loss, grad = env.est_loss_grad(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda())
+    ref_loss, ref_grad = oracle.mlp_loss_grad(params, X, Y)
+    assert abs(loss - ref_loss) <= 2e-2 * ref_loss
+    g = grad.cpu().numpy().astype(np.float64)
+    off = 0
+    for name, shape, _ in synth.mlp_shapes():
+        n = int(np.prod(shape))
+        a, b = g[off:off + n], ref_grad[off:off + n]
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        print(f"grad {name}: relative error {rel:.2e}")
+        assert rel < 5e-2, (name, rel)
+        off += n
+
+
+def test_record_features_match_oracle():
+    env, p = _env(n_envs=6, comm_drop=0.2)
+    env.reset(8)
+    o = oracle.OracleEnv(p, 8)
+    o.reset(0)
+    F = env.F
+    feat = torch.empty((F, 96), device="cuda")
+    lab = torch.empty((F, 2), device="cuda")
+    for t in range(1, 7):
+        act = np.random.default_rng(t).integers(0, 7, o.NA).astype(np.int32)
+        env.step(torch.from_numpy(act).cuda())
+        o.step(act)
+        env.est_record(feat, lab)
+        rf, rl = o.est_features(t)
+        np.testing.assert_allclose(feat.cpu().numpy(), rf, atol=2e-6, rtol=1e-5)
+        np.testing.assert_allclose(lab.cpu().numpy(), rl, atol=2e-6, rtol=1e-5)
+
+
+def test_adam_step_matches_oracle():
+    env, _ = _env()
+    params = synth.mlp_params(seed=7, bias_scale=0.1)
+    env.est_set_weights(params)
+    X = _features(512, 4)
+    Y = (np.random.default_rng(5).standard_normal((512, 2)) * 0.2).astype(np.float32)
+    lr = 1e-3
+    env.est_train(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), steps=1, batch=512, lr=lr, cosine=False)
+    got = env.est_get_weights().astype(np.float64)
+    _, g = oracle.mlp_loss_grad(params, X, Y)
+    want, _, _ = oracle.adam(params, np.zeros(NP), np.zeros(NP), g, 1, lr=lr)
+    step_g, step_o = got - params, want - params
+    # first Adam step moves every weight by ~lr * sign(g): compare where the
+    # gradient is clearly non-zero, and bound the rest by lr
+    big = np.abs(g) > 1e-3 * np.abs(g).max()
+    assert np.mean(np.sign(step_g[big]) == np.sign(step_o[big])) > 0.99
+    assert np.all(np.abs(step_g) <= lr * 1.001 + 1e-7)
+
+
+def _naive_last_ping(X):
+    """Target on the newest ping's range circle, at the point nearest the observer."""
+    d = X[:, 0:2].astype(np.float64)
+    r = X[:, 2:3].astype(np.float64)
+    n = np.linalg.norm(d, axis=1, keepdims=True)
+    est = np.where(n > 1e-9, d * (1 - r / np.maximum(n, 1e-9)), np.concatenate([r, 0 * r], 1))
+    return est
+
+
+def test_training_beats_untrained_and_naive():
+    env, p = _env(n_envs=128)
+    env.reset(1)
+    F = env.F
+    rows = []
+    for t in range(64):
+        env.step()
+        feat = torch.empty((F, 96), device="cuda")
+        lab = torch.empty((F, 2), device="cuda")
+        env.est_record(feat, lab)
+        if t >= 4:
+            rows.append((feat, lab))
+    X = torch.cat([r[0] for r in rows])
+    Y = torch.cat([r[1] for r in rows])
+    n = X.shape[0]
+    held = n // 8
+    Xtr, Ytr, Xte, Yte = X[held:].contiguous(), Y[held:].contiguous(), X[:held].contiguous(), Y[:held].contiguous()
+    env.est_set_weights(synth.mlp_params(seed=11))
+    untrained = float(((env.est_forward(Xte) - Yte) ** 2).sum(1).mean().sqrt())
+    st = env.est_train(Xtr, Ytr, steps=2000, batch=4096, lr=2e-3, seed=3)
+    trained = float(((env.est_forward(Xte) - Yte) ** 2).sum(1).mean().sqrt())
+    naive = float(np.sqrt(((_naive_last_ping(Xte.cpu().numpy()) - Yte.cpu().numpy()) ** 2).sum(1).mean()))
+    print(f"held-out RMSE (km): untrained {untrained:.4f} naive {naive:.4f} trained {trained:.4f}; "
+          f"loss {st['loss_first']:.4e} -> {st['loss_last']:.4e} in {st['ms']:.1f} ms")
+    assert st["loss_last"] < 0.2 * st["loss_first"]
+    assert trained < 0.6 * untrained and trained < naive
+
+
+def test_learned_mode_step_uses_network():
+    env, p = _env(n_envs=8)
+    params = synth.mlp_params(seed=13, bias_scale=0.1)
+    env.est_set_weights(params)
+    env.reset(2)
+    env.step()
+    env.est_set_mode(True)
+    F = env.F
+    feat = torch.empty((F, 96), device="cuda")
+    lab = torch.empty((F, 2), device="cuda")
+    out = env.step()
+    env.est_record(feat, lab)
+    st = env.state()
+    pred = env.est_forward(feat)
+    # estimate = observer + S * network(features); error against the truth
+    ax = st["ax"].cpu().numpy()
+    fa = np.repeat(np.arange(env.NA), 5)
+    est = np.stack([out["estx"].cpu().numpy(), out["esty"].cpu().numpy()], 1)
+    want = np.stack([ax[fa], st["ay"].cpu().numpy()[fa]], 1) + 1000.0 * pred.cpu().numpy()
+    np.testing.assert_allclose(est, want, atol=2e-3)
+    env.est_set_mode(False)
