@@ -153,6 +153,99 @@ def cpu_baseline(workload: str, budget_s: float = 12.0, n_envs: int = 64):
             "sample": f"{n_envs} envs of the {workload} workload x {steps} steps ({dt:.1f} s, FP64, OpenMP)"}
 
 
+def learned_form(args, p, K, W, rank):
+    """The learned-estimator form of the same workload: record ~10M
+    (feature, label) transitions from filter-form rollouts, train the MLP with
+    the library's kernels, then time a learned-form rollout and compare mean
+    tracking RMSE against the filter form on held-out seeds."""
+    import torch
+
+    import paper_2505_08222_gb300 as ut
+    import synth
+
+    pol = synth.policy_params(synth.PolicyDims(p.d_model, p.n_layers, p.n_heads, p.n_actions)) if p.d_model else None
+    env = ut.Env(p, ring=True)
+    if pol is not None:
+        env.set_policy(pol)
+    F = env.F
+    steps_rec = max(1, args.train_rows // F)
+    X = torch.empty((steps_rec * F, 96), dtype=torch.float32, device="cuda")
+    Y = torch.empty((steps_rec * F, 2), dtype=torch.float32, device="cuda")
+
+    def record(t0_step, n_steps, seed, learned):
+        env.est_set_mode(learned)
+        env.reset(seed)
+        for t in range(t0_step, t0_step + n_steps):
+            env.step()
+            env.est_record(X[t * F:(t + 1) * F], Y[t * F:(t + 1) * F])
+        env.est_set_mode(False)
+
+    # DAgger-style schedule: half the rows from filter-driven rollouts (the
+    # filter's estimates as the update's inputs), then two rounds of rows from
+    # rollouts driven by the network itself, retraining after each round.
+    t0 = time.perf_counter()
+    half = steps_rec // 2
+    quarter = (steps_rec - half) // 2
+    record(0, half, 7000 + rank, False)
+    env.est_set_weights(synth.mlp_params(seed=4321))
+    rounds = [(0, half)]
+    tr = env.est_train(X[:half * F], Y[:half * F], steps=args.train_steps, batch=16384, lr=1e-3, seed=rank,
+                       huber=1.0)
+    losses = [tr["loss_last"]]
+    train_ms = tr["ms"]
+    for r, (a, n) in enumerate([(half, quarter), (half + quarter, steps_rec - half - quarter)]):
+        record(a, n, 7100 + 10 * r + rank, True)
+        upto = (a + n) * F
+        tr = env.est_train(X[:upto], Y[:upto], steps=args.train_steps // 2, batch=16384, lr=5e-4, seed=rank + r + 1,
+                           huber=1.0)
+        losses.append(tr["loss_last"])
+        train_ms += tr["ms"]
+    torch.cuda.synchronize()
+    rec_s = time.perf_counter() - t0
+    del X, Y
+    torch.cuda.empty_cache()
+
+    def eval_rmse(learned: bool, seed: int, T: int) -> float:
+        env.est_set_mode(learned)
+        env.reset(seed)
+        return env.rollout(T)["rmse"]
+
+    T_eval = args.eval_steps
+    seeds = [9000 + rank, 9100 + rank]
+    pf_rmse = [eval_rmse(False, s, T_eval) for s in seeds]
+    le_rmse = [eval_rmse(True, s, T_eval) for s in seeds]
+    # timed learned-form rollout
+    env.est_set_mode(True)
+    env.reset(1000 + rank)
+    for _ in range(W):
+        env.step()
+    env.rollout_prepare(K)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    ev0.record(stream)
+    st = env.rollout(K)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    env.profile(True)
+    for _ in range(K):
+        env.step()
+    est_ms, est_n = env.stage_time()
+    env.profile(False)
+    env.close()
+    pf_mean = sum(pf_rmse) / len(pf_rmse)
+    le_mean = sum(le_rmse) / len(le_rmse)
+    return {"value": st["agent_steps"] / (ms / 1e3), "unit": "agent-steps/s", "ms_per_step": ms / K,
+            "estimator_kernel_ms": est_ms / max(est_n, 1),
+            "rmse_m": le_mean, "pf_rmse_m": pf_mean, "rmse_ratio": le_mean / pf_mean,
+            "eval": f"{len(seeds)} held-out seeds x {T_eval} steps each form, pooled RMSE per run, mean over seeds",
+            "train": {"rows": steps_rec * F, "wall_s": rec_s, "steps": 2 * args.train_steps, "batch": 16384,
+                      "schedule": "50% filter-driven rows, then 2 x 25% network-driven rows (retrain each)",
+                      "loss_last_per_round": losses, "train_ms": train_ms, "loss": "Huber, delta = 1 L"}}
+
+
 def run_reference(args):
     world, rank, _ = _dist_env()
     if rank != 0:
@@ -305,6 +398,8 @@ def run_ours(args):
             "clocks": clock_info,
             "rmse_m": stats["rmse"],
         }
+        if not args.no_learned:
+            line["learned"] = learned_form(args, p, K, W, rank)
         if world == 1 and not args.no_cpu_baseline:
             os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
             line["cpu_baseline"] = cpu_baseline(args.workload)
@@ -325,6 +420,10 @@ def main():
     ap.add_argument("--workload", default="fleet5")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-estimator form")
+    ap.add_argument("--train-rows", type=int, default=10_000_000)
+    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--eval-steps", type=int, default=100)
     ap.add_argument("--envs", type=int, default=None, help="override the env count (profiling cases)")
     args = ap.parse_args()
     global _ENVS

@@ -109,7 +109,8 @@ typedef struct ut_config {
   float spawn_min;             /* minimum spawn distance between entities, m (50) */
   float spawn_radius;          /* spawn disk radius, m (100 = half the 200 m maximum) */
   int32_t spawn_tries;         /* rejection-sampling tries per entity (64) */
-  float feature_scale;         /* S: metres per unit in tokens and estimator features */
+  float feature_scale;         /* S: metres per unit in observation tokens */
+  float est_scale;             /* L: metres per unit of the learned estimator's local frame (100) */
   int32_t d_model;             /* transformer agent width; 0 = no policy */
   int32_t n_layers;            /* transformer blocks */
   int32_t n_heads;             /* attention heads (d_model % n_heads == 0) */
@@ -137,6 +138,8 @@ typedef struct ut_state_view {
   float *lpx, *lpy;                   /* last received pose of teammate b at agent a [NA * A_max] */
   int32_t* lpage;                     /* steps since that reception [NA * A_max] */
   float *estx, *esty;                 /* tracker estimates [F] */
+  float *prev_estx, *prev_esty;       /* estimate before the last update [F] */
+  float *prev2_estx, *prev2_esty;     /* estimate before that [F] */
   float* ring;                        /* estimator ring [F][16][4] (qx, qy, r, step) */
   int32_t *ring_head, *ring_count;    /* [F] */
   uint16_t* h;                        /* recurrent token bf16 [NA][d_model] (NULL without policy) */
@@ -283,12 +286,16 @@ ut_status policy_forward(ut_env* env, const uint16_t* tokens_dev, const int32_t*
 /* ---------------------------------------------------------------------- */
 /* Learned range-only estimator (no counterpart in the paper, whose tracker */
 /* is the particle filter of Sec. II-A; readings C18).                     */
-/* MLP 96 -> 256 -> 256 -> 256 -> 2, erf-GELU.  Features of a filter: its 16 */
-/* most recent received pings, newest first, each [(qx - ax)/S, (qy - ay)/S, */
-/* r/S, (g - g_m)/16, 1], zero padded to 96 (FP32).  Output: target position */
-/* relative to the observer agent, in units of S.  Parameters in canonical  */
+/* MLP 96 -> 256 -> 256 -> 256 -> 2, erf-GELU, a learned update of the      */
+/* filter's estimate e1.  Features of a filter, in e1's local frame (units   */
+/* of L = est_scale): its 16 most recent received pings, newest first, each */
+/* [(q - e1)/L, (r - |q - e1|_3D)/L, (g - g_m)/16, 1], then the estimate's  */
+/* last motion (e1 - e2)/L, zero padded to 96 (FP32).  Output: the          */
+/* correction (x - e1)/L; the new estimate is e1 + L * output, each output   */
+/* clamped to +-3 in the step (+-v_cap dt / L when no ping arrived this     */
+/* step).  Canonical                                                         */
 /* order W1[256][96], b1, W2[256][256], b2, W3[256][256], b3, W4[2][256], b4 */
-/* (156,930 floats).  Hidden layers run on the tensor cores (BF16 operands,  */
+/* parameter order (156,930 floats).  Hidden layers on the tensor cores (BF16 */
 /* FP32 accumulation; the first layer multiplies the features' BF16 high and */
 /* low parts), FP32 master weights.                                          */
 /* ---------------------------------------------------------------------- */
@@ -302,6 +309,7 @@ typedef struct ut_est_train_config {
   int32_t cosine;     /* 1: cosine decay of lr to 0 over the steps */
   float beta1, beta2, eps;
   uint64_t seed;      /* batch sampling stream */
+  float huber_delta;  /* 0: squared-error loss; > 0: Huber loss with this threshold (label units) */
 } ut_est_train_config;
 
 typedef struct ut_est_train_stats {
@@ -321,10 +329,11 @@ ut_status est_get_weights(ut_env* env, float* params_host, int64_t n_params);
 ut_status est_set_mode(ut_env* env, int32_t mode);
 /* Raw network outputs out_dev [n_rows][2] of features X_dev [n_rows][96]. */
 ut_status est_forward(ut_env* env, const float* X_dev, float* out_dev, int64_t n_rows);
-/* Features [F][96] and labels [F][2] = (target - observer)/S of every filter
- * in the current state (after a step); needs UT_FLAG_RING. */
+/* Features [F][96] and labels [F][2] = (target - e1)/L of every filter's
+ * last update (call after a step; e1, e2 = the estimates before it); needs
+ * UT_FLAG_RING. */
 ut_status est_record(ut_env* env, float* feat_dev, float* label_dev);
-/* Loss L = (1/(2B)) sum over rows and both outputs of (out - y)^2 on rows
+/* Loss = (1/(2B)) sum over rows and both outputs of (out - y)^2 on rows
  * 0..B-1 and its gradient grad_dev [156930] (device, canonical order).
  * Synchronising; *loss_host (optional) receives L. */
 ut_status est_loss_grad(ut_env* env, const float* X_dev, const float* Y_dev, int32_t B, float* grad_dev,

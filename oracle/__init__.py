@@ -78,14 +78,15 @@ class OcConfig(ctypes.Structure):
         ("feature_scale", ctypes.c_double),
         ("seed", ctypes.c_uint64),
         ("env0", ctypes.c_int32), ("agent0", ctypes.c_int32), ("target0", ctypes.c_int32),
-        ("filter0", ctypes.c_int32),
+        ("filter0", ctypes.c_int32), ("est_scale", ctypes.c_double),
     ]
 
 
 class OcState(ctypes.Structure):
     _fields_ = [(n, _dp) for n in ("ax", "ay", "apsi", "tx", "ty", "tz", "tpsi", "tspeed",
                                    "px", "py", "pvx", "pvy", "lpx", "lpy")] + [
-        ("lpage", _ip), ("estx", _dp), ("esty", _dp), ("ring", _dp), ("ring_head", _ip),
+        ("lpage", _ip), ("estx", _dp), ("esty", _dp), ("prev_estx", _dp), ("prev_esty", _dp),
+        ("prev2_estx", _dp), ("prev2_esty", _dp), ("ring", _dp), ("ring_head", _ip),
         ("ring_count", _ip), ("step", ctypes.c_uint32), ("t_ep", ctypes.c_int32)]
 
 
@@ -202,7 +203,8 @@ class OracleEnv:
                      "rudder_max", "rudder_gain", "target_model", "target_speed_min", "target_speed_max",
                      "target_drift_sigma", "target_depth_max", "range_sigma", "det_radius", "comm_radius",
                      "comm_drop", "pf_accel_sigma", "pf_vcap", "reward_type", "eps_min", "eps_max",
-                     "follow_dmin", "d_safe", "spawn_min", "spawn_radius", "spawn_tries", "feature_scale"):
+                     "follow_dmin", "d_safe", "spawn_min", "spawn_radius", "spawn_tries", "feature_scale",
+                     "est_scale"):
             setattr(c, name, getattr(params, name))
         c.seed = seed
         c.env0, c.agent0, c.target0, c.filter0 = (int(v) for v in id_base)
@@ -217,6 +219,8 @@ class OracleEnv:
             "lpx": np.zeros(self.NA * AM), "lpy": np.zeros(self.NA * AM),
             "lpage": np.zeros(self.NA * AM, np.int32),
             "estx": np.zeros(self.F), "esty": np.zeros(self.F),
+            "prev_estx": np.zeros(self.F), "prev_esty": np.zeros(self.F),
+            "prev2_estx": np.zeros(self.F), "prev2_esty": np.zeros(self.F),
             "ring": np.zeros(self.F * RING * 4), "ring_head": np.zeros(self.F, np.int32),
             "ring_count": np.zeros(self.F, np.int32),
         }

@@ -88,6 +88,7 @@ typedef struct {
    * larger batch: random draws are keyed by global ids, so a sub-batch of
    * independent environments replays exactly the draws of the full batch. */
   int32_t env0, agent0, target0, filter0;
+  double est_scale; /* L: local frame of the learned estimator's features */
 } oc_config;
 
 typedef struct {
@@ -97,6 +98,8 @@ typedef struct {
   double *lpx, *lpy;                        /* last received teammate pose [NA*A_max] */
   int32_t *lpage;                           /* steps since last reception [NA*A_max] */
   double *estx, *esty;                      /* tracker estimate [F] */
+  double *prev_estx, *prev_esty;            /* estimate before the last update [F] */
+  double *prev2_estx, *prev2_esty;          /* estimate before that [F] */
   double *ring;                             /* [F*16*4]: qx, qy, r, step */
   int32_t *ring_head, *ring_count;          /* [F] */
   uint32_t step;                            /* global step counter g */
@@ -309,6 +312,8 @@ void oc_reset(const oc_config* c, oc_state* s, uint32_t g) {
         }
         s->estx[f] = sx / P;
         s->esty[f] = sy / P;
+        s->prev_estx[f] = s->prev2_estx[f] = s->estx[f];
+        s->prev_esty[f] = s->prev2_esty[f] = s->esty[f];
         s->ring_head[f] = 0;
         s->ring_count[f] = 0;
         for (int j = 0; j < OC_RING * 4; ++j) s->ring[(int64_t)f * OC_RING * 4 + j] = 0.0;
@@ -569,6 +574,10 @@ void oc_pf_update(const oc_config* c, oc_state* s, uint32_t g, const double* mea
       ex += (w[i] / W) * x[i];
       ey += (w[i] / W) * y[i];
     }
+    s->prev2_estx[f] = s->prev_estx[f];
+    s->prev2_esty[f] = s->prev_esty[f];
+    s->prev_estx[f] = s->estx[f];
+    s->prev_esty[f] = s->esty[f];
     s->estx[f] = ex;
     s->esty[f] = ey;
     double dxe = ex - s->tx[it], dye = ey - s->ty[it];
@@ -703,10 +712,13 @@ void oc_reward(const oc_config* c, const oc_state* s, const double* err, double*
 }
 
 /* ------------------------------------------------------------------------ */
-/* Learned range-only estimator inputs: append this step's measurement list  */
-/* of filter (a,k) to its 16-entry ring, then build the 96 features:         */
-/* 16 slots newest first x [(qx - ax)/S, (qy - ay)/S, r/S, (g - g_m)/16,    */
-/* valid], zero padded from 80 to 96.                                       */
+/* Learned range-only estimator inputs (reading C18): append this step's     */
+/* measurement list of filter (a,k) to its 16-entry ring.  After the step,   */
+/* the features of the filter's update are, in the local frame of the       */
+/* estimate e1 it updated (units of L): 16 slots newest first x             */
+/* [(q - e1)/L, (r - |q - e1|_3D)/L, (g - g_m)/16, valid], then the         */
+/* estimate's last motion (e1 - e2)/L, zero padded to 96; the label is the  */
+/* correction (x_true - e1)/L.                                              */
 /* ------------------------------------------------------------------------ */
 void oc_ring_append(const oc_config* c, oc_state* s, uint32_t g, const double* meas, const int32_t* meas_n) {
   const int AM = c->max_agents;
@@ -726,27 +738,32 @@ void oc_ring_append(const oc_config* c, oc_state* s, uint32_t g, const double* m
 }
 
 void oc_est_features(const oc_config* c, const oc_state* s, uint32_t g, double* feat, double* label) {
-  const double S = c->feature_scale;
+  const double L = c->est_scale;
   for (int e = 0; e < c->n_envs; ++e) {
     int A = env_agents(c, e), T = env_targets(c, e);
     for (int a = 0; a < A; ++a)
       for (int k = 0; k < T; ++k) {
         int f = filter_index(c, e, a, k);
-        int ia = c->agent_off[e] + a, it = c->target_off[e] + k;
+        int it = c->target_off[e] + k;
+        double e1x = s->prev_estx[f], e1y = s->prev_esty[f];
         double* x = feat + (int64_t)f * OC_FEAT;
         for (int j = 0; j < OC_FEAT; ++j) x[j] = 0.0;
         for (int sl = 0; sl < s->ring_count[f]; ++sl) {
           int pos = ((s->ring_head[f] - 1 - sl) % OC_RING + OC_RING) % OC_RING;
           const double* r = s->ring + ((int64_t)f * OC_RING + pos) * 4;
-          x[sl * 5 + 0] = (r[0] - s->ax[ia]) / S;
-          x[sl * 5 + 1] = (r[1] - s->ay[ia]) / S;
-          x[sl * 5 + 2] = r[2] / S;
+          double dx = r[0] - e1x, dy = r[1] - e1y, dz = s->tz[it];
+          double rho = sqrt(dx * dx + dy * dy + dz * dz);
+          x[sl * 5 + 0] = dx / L;
+          x[sl * 5 + 1] = dy / L;
+          x[sl * 5 + 2] = (r[2] - rho) / L;
           x[sl * 5 + 3] = ((double)g - r[3]) / 16.0;
           x[sl * 5 + 4] = 1.0;
         }
+        x[5 * OC_RING + 0] = (e1x - s->prev2_estx[f]) / L;
+        x[5 * OC_RING + 1] = (e1y - s->prev2_esty[f]) / L;
         if (label) {
-          label[(int64_t)f * 2 + 0] = (s->tx[it] - s->ax[ia]) / S;
-          label[(int64_t)f * 2 + 1] = (s->ty[it] - s->ay[ia]) / S;
+          label[(int64_t)f * 2 + 0] = (s->tx[it] - e1x) / L;
+          label[(int64_t)f * 2 + 1] = (s->ty[it] - e1y) / L;
         }
       }
   }

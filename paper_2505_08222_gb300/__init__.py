@@ -233,8 +233,8 @@ class Env:
         return loss.value, grad
 
     def est_train(self, X: torch.Tensor, Y: torch.Tensor, steps: int, batch: int, lr: float = 1e-3,
-                  cosine: bool = True, seed: int = 0, beta1=0.9, beta2=0.999, eps=1e-8) -> dict:
-        cfg = _abi.EstTrainConfig(steps, batch, lr, 1 if cosine else 0, beta1, beta2, eps, seed)
+                  cosine: bool = True, seed: int = 0, beta1=0.9, beta2=0.999, eps=1e-8, huber: float = 0.0) -> dict:
+        cfg = _abi.EstTrainConfig(steps, batch, lr, 1 if cosine else 0, beta1, beta2, eps, seed, huber)
         st = _abi.EstTrainStats()
         _check(lib.est_train(self.h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()), X.shape[0],
                              ctypes.byref(cfg), ctypes.byref(st)), self.h, "est_train")
@@ -301,6 +301,7 @@ class Env:
         shapes = {"ax": (NA,), "ay": (NA,), "apsi": (NA,), "tx": (NT,), "ty": (NT,), "tz": (NT,),
                   "tpsi": (NT,), "tspeed": (NT,), "px": (FP,), "py": (FP,), "pvx": (FP,), "pvy": (FP,),
                   "lpx": (NA * AM,), "lpy": (NA * AM,), "lpage": (NA * AM,), "estx": (F,), "esty": (F,),
+                  "prev_estx": (F,), "prev_esty": (F,), "prev2_estx": (F,), "prev2_esty": (F,),
                   "ring": (F, 16, 4), "ring_head": (F,), "ring_count": (F,)}
         out = {}
         for k, shp in shapes.items():

@@ -43,7 +43,7 @@ CONFIG_FIELDS = [
     ("reward_type", ctypes.c_int32), ("eps_min", ctypes.c_float), ("eps_max", ctypes.c_float),
     ("follow_dmin", ctypes.c_float), ("d_safe", ctypes.c_float),
     ("spawn_min", ctypes.c_float), ("spawn_radius", ctypes.c_float), ("spawn_tries", ctypes.c_int32),
-    ("feature_scale", ctypes.c_float),
+    ("feature_scale", ctypes.c_float), ("est_scale", ctypes.c_float),
     ("d_model", ctypes.c_int32), ("n_layers", ctypes.c_int32), ("n_heads", ctypes.c_int32),
 ]
 
@@ -58,7 +58,8 @@ class StepOut(ctypes.Structure):
 
 
 STATE_PTRS = ["ax", "ay", "apsi", "tx", "ty", "tz", "tpsi", "tspeed", "px", "py", "pvx", "pvy",
-              "lpx", "lpy", "lpage", "estx", "esty", "ring", "ring_head", "ring_count", "h"]
+              "lpx", "lpy", "lpage", "estx", "esty", "prev_estx", "prev_esty", "prev2_estx", "prev2_esty",
+              "ring", "ring_head", "ring_count", "h"]
 
 
 class StateView(ctypes.Structure):
@@ -78,7 +79,7 @@ class DebugView(ctypes.Structure):
 class EstTrainConfig(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
                 ("cosine", ctypes.c_int32), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
-                ("eps", ctypes.c_float), ("seed", ctypes.c_uint64)]
+                ("eps", ctypes.c_float), ("seed", ctypes.c_uint64), ("huber_delta", ctypes.c_float)]
 
 
 class EstTrainStats(ctypes.Structure):

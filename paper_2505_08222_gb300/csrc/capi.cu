@@ -88,6 +88,7 @@ ut_status validate(const ut_config* c, std::string& why) {
   if (c->spawn_tries < 1 || c->spawn_tries > 64) return bad("spawn_tries must be in 1..64");
   if (!(c->spawn_radius > 0.0f) || c->spawn_radius * 65536.0 > 8388607.0) return bad("spawn_radius out of range");
   if (!(c->feature_scale > 0.0f)) return bad("feature_scale must be > 0");
+  if (!(c->est_scale > 0.0f)) return bad("est_scale must be > 0");
   if (c->reward_type != 0 && c->reward_type != 1) return bad("reward_type must be 0 or 1");
   if (c->d_model < 0) return bad("d_model must be >= 0");
   if (c->d_model > 0) {
@@ -233,6 +234,7 @@ ut_status env_create(const ut_config* cfg, const ut_allocator* allocator, void* 
   d.spawn_dmin_int = (long long)std::floor((double)cfg->spawn_min * 65536.0);
   d.spawn_tries = cfg->spawn_tries;
   d.S = cfg->feature_scale;
+  d.est_scale = cfg->est_scale;
   d.ring_on = (cfg->flags & UT_FLAG_RING) ? 1 : 0;
   d.debug_on = (cfg->flags & UT_FLAG_DEBUG) ? 1 : 0;
 
@@ -260,6 +262,10 @@ ut_status env_create(const ut_config* cfg, const ut_allocator* allocator, void* 
   d.lpage = alloc_n<int32_t>(h, NA * AM, ok);
   d.estx = alloc_n<float>(h, F, ok);
   d.esty = alloc_n<float>(h, F, ok);
+  d.prev_estx = alloc_n<float>(h, F, ok);
+  d.prev_esty = alloc_n<float>(h, F, ok);
+  d.prev2_estx = alloc_n<float>(h, F, ok);
+  d.prev2_esty = alloc_n<float>(h, F, ok);
   d.err = alloc_n<float>(h, F, ok);
   d.ring = alloc_n<float>(h, d.ring_on ? F * kRing * 4 : 4, ok);
   d.ring_head = alloc_n<int32_t>(h, F, ok);
@@ -615,6 +621,8 @@ ut_status env_get_state(const ut_env* hc, ut_state_view* out) {
   out->px = d.px; out->py = d.py; out->pvx = d.pvx; out->pvy = d.pvy;
   out->lpx = d.lpx; out->lpy = d.lpy; out->lpage = d.lpage;
   out->estx = d.estx; out->esty = d.esty;
+  out->prev_estx = d.prev_estx; out->prev_esty = d.prev_esty;
+  out->prev2_estx = d.prev2_estx; out->prev2_esty = d.prev2_esty;
   out->ring = d.ring_on ? d.ring : nullptr;
   out->ring_head = d.ring_head; out->ring_count = d.ring_count;
   out->h = extension_h(h);
@@ -654,6 +662,10 @@ ut_status env_set_state(ut_env* h, const ut_state_view* in) {
   UT_CUDA(h, cp(d.lpage, in->lpage, NA * AM * 4));
   UT_CUDA(h, cp(d.estx, in->estx, F * 4));
   UT_CUDA(h, cp(d.esty, in->esty, F * 4));
+  UT_CUDA(h, cp(d.prev_estx, in->prev_estx, F * 4));
+  UT_CUDA(h, cp(d.prev_esty, in->prev_esty, F * 4));
+  UT_CUDA(h, cp(d.prev2_estx, in->prev2_estx, F * 4));
+  UT_CUDA(h, cp(d.prev2_esty, in->prev2_esty, F * 4));
   if (d.ring_on) UT_CUDA(h, cp(d.ring, in->ring, F * kRing * 16));
   UT_CUDA(h, cp(d.ring_head, in->ring_head, F * 4));
   UT_CUDA(h, cp(d.ring_count, in->ring_count, F * 4));

@@ -41,6 +41,10 @@ struct EnvDev {
   float *lpx, *lpy;
   int32_t* lpage;
   float *estx, *esty, *err;
+  // the two previous estimates of each filter (estimate history of the
+  // learned estimator's features; NULL where not kept)
+  float *prev_estx, *prev_esty, *prev2_estx, *prev2_esty;
+  float est_scale;  // L: metres per unit of the learned estimator's local frame
   float* ring;
   int32_t *ring_head, *ring_count;
   // per-step buffers

@@ -130,6 +130,8 @@ __global__ void __launch_bounds__(kInitThreads) reset_pf_kernel(EnvDev d, uint32
     for (int w = 0; w < kInitThreads / 32; ++w) { tx += s_x[w]; ty += s_y[w]; }
     d.estx[f] = tx / (float)d.P;
     d.esty[f] = ty / (float)d.P;
+    d.prev_estx[f] = d.prev2_estx[f] = d.estx[f];
+    d.prev_esty[f] = d.prev2_esty[f] = d.esty[f];
     d.ring_head[f] = 0;
     d.ring_count[f] = 0;
   }

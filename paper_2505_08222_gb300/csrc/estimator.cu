@@ -20,6 +20,7 @@ namespace {
 
 constexpr int kT = 128;
 constexpr uint32_t TAG_BATCH = 14;
+constexpr float kMaxCorr = 3.0f;  // largest correction per step, in units of L
 constexpr size_t kFwdSmem = 65536 + 65536;
 constexpr size_t kWgradSmem = 32768 + 65536;
 
@@ -43,11 +44,16 @@ __device__ __forceinline__ void copy_img(unsigned char* dst, const unsigned char
   for (size_t i = threadIdx.x; i < bytes / 16; i += kT) t[i] = __ldg(s + i);
 }
 
-// Estimator features of filter f at step g from its ping ring (reading C18):
-// 16 slots newest first, [(qx - ax)/S, (qy - ay)/S, r/S, (g - g_m)/16, 1].
-__device__ __forceinline__ void ring_features(const EnvDev& d, int f, uint32_t g, float (&x)[IN]) {
-  const int ia = d.filt_agent[f];
-  const float ax = d.ax[ia], ay = d.ay[ia];
+// Estimator features of filter f for its update at step g (reading C18):
+// in the local frame of the filter's current estimate e1 (units of L), each
+// of the 16 most recent pings, newest first, as [(q - e1) / L, range
+// innovation (r - |q - e1|_3D) / L, (g - g_m) / 16, 1], then the last motion
+// of the estimate (e1 - e2) / L; zero padded to 96.  The network's output is
+// the correction (x - e1) / L.
+__device__ __forceinline__ void ring_features(const EnvDev& d, int f, uint32_t g, float e1x, float e1y, float e2x,
+                                              float e2y, float (&x)[IN]) {
+  const float dz = d.tz[d.filt_target[f]];  // target depth; senders at the surface
+  const float L = d.est_scale;
   const int head = d.ring_head[f], cnt = d.ring_count[f];
   const float4* ring = reinterpret_cast<const float4*>(d.ring) + (long long)f * kRing;
 #pragma unroll
@@ -55,14 +61,18 @@ __device__ __forceinline__ void ring_features(const EnvDev& d, int f, uint32_t g
     float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
     const bool on = s < cnt;
     if (on) e = ring[(head - 1 - s) & (kRing - 1)];
-    x[5 * s + 0] = on ? (e.x - ax) / d.S : 0.0f;
-    x[5 * s + 1] = on ? (e.y - ay) / d.S : 0.0f;
-    x[5 * s + 2] = on ? e.z / d.S : 0.0f;
+    const float dx = e.x - e1x, dy = e.y - e1y;
+    const float rho = sqrtf(dx * dx + dy * dy + dz * dz);
+    x[5 * s + 0] = on ? dx / L : 0.0f;
+    x[5 * s + 1] = on ? dy / L : 0.0f;
+    x[5 * s + 2] = on ? (e.z - rho) / L : 0.0f;
     x[5 * s + 3] = on ? ((float)g - e.w) / 16.0f : 0.0f;
     x[5 * s + 4] = on ? 1.0f : 0.0f;
   }
+  x[5 * kRing] = (e1x - e2x) / L;
+  x[5 * kRing + 1] = (e1y - e2y) / L;
 #pragma unroll
-  for (int i = 5 * kRing; i < IN; ++i) x[i] = 0.0f;
+  for (int i = 5 * kRing + 2; i < IN; ++i) x[i] = 0.0f;
 }
 
 struct FwdArgs {
@@ -96,11 +106,16 @@ __global__ void __launch_bounds__(kT, 1) fwd_kernel(FwdArgs p) {
   if (tid == 0) tc::mbar_init(&mbar, 1);
 
   float x[IN];
+  float e1x = 0.0f, e1y = 0.0f;
   if (ENV) {
-    if (valid) ring_features(p.d, (int)b, p.d.counters[0] + 1u, x);
-    else
+    if (valid) {
+      e1x = p.d.estx[b];
+      e1y = p.d.esty[b];
+      ring_features(p.d, (int)b, p.d.counters[0] + 1u, e1x, e1y, p.d.prev_estx[b], p.d.prev_esty[b], x);
+    } else {
 #pragma unroll
       for (int i = 0; i < IN; ++i) x[i] = 0.0f;
+    }
   } else {
     const long long src = valid ? (p.rows ? (long long)p.rows[b] : b) : 0;
 #pragma unroll
@@ -185,8 +200,20 @@ __global__ void __launch_bounds__(kT, 1) fwd_kernel(FwdArgs p) {
   if (valid && ok) {
     if (ENV) {
       const int f = (int)b;
-      const int ia = p.d.filt_agent[f], it = p.d.filt_target[f];
-      const float ex = p.d.ax[ia] + p.d.S * o0, ey = p.d.ay[ia] + p.d.S * o1;
+      const int it = p.d.filt_target[f];
+      // Bounded update (dropped if not finite): with a ping received this step
+      // the estimate may move up to kMaxCorr L; without one it may move no
+      // farther than a target can in one step (v_cap dt), so that stale
+      // inputs cannot drive the closed loop away.
+      const bool fresh = x[3] == 0.0f && x[4] == 1.0f;
+      const float lim = fresh ? kMaxCorr : p.d.pf_vcap * p.d.dt / p.d.est_scale;
+      const float c0 = isfinite(o0) ? fminf(fmaxf(o0, -lim), lim) : 0.0f;
+      const float c1 = isfinite(o1) ? fminf(fmaxf(o1, -lim), lim) : 0.0f;
+      const float ex = e1x + p.d.est_scale * c0, ey = e1y + p.d.est_scale * c1;
+      p.d.prev2_estx[f] = p.d.prev_estx[f];
+      p.d.prev2_esty[f] = p.d.prev_esty[f];
+      p.d.prev_estx[f] = e1x;
+      p.d.prev_esty[f] = e1y;
       p.d.estx[f] = ex;
       p.d.esty[f] = ey;
       const float dx = ex - p.d.tx[it], dy = ey - p.d.ty[it];
@@ -244,13 +271,25 @@ __global__ void __launch_bounds__(kT, 1) bwd_kernel(Net net, TrainBufs t, int* s
   float* s_db4 = s_db1 + HID;
 
   // output layer: dL/dout = (out - y) / B
+  // loss per row: sum over the two outputs of e^2 / 2 (Huber with delta > 0:
+  // quadratic inside |e| <= delta, linear outside); gradient / B
   float d0 = 0.0f, d1 = 0.0f;
   double se = 0.0;
   if (valid) {
-    const float e0 = t.out[b * OUT] - t.Y[row * OUT], e1 = t.out[b * OUT + 1] - t.Y[row * OUT + 1];
-    d0 = e0 / (float)t.B;
-    d1 = e1 / (float)t.B;
-    se = (double)e0 * e0 + (double)e1 * e1;
+    const float e[2] = {t.out[b * OUT] - t.Y[row * OUT], t.out[b * OUT + 1] - t.Y[row * OUT + 1]};
+    float g[2];
+    for (int c = 0; c < 2; ++c) {
+      const float ae = fabsf(e[c]);
+      if (t.huber > 0.0f && ae > t.huber) {
+        g[c] = copysignf(t.huber, e[c]);
+        se += (double)t.huber * ((double)ae - 0.5 * t.huber);
+      } else {
+        g[c] = e[c];
+        se += 0.5 * (double)e[c] * e[c];
+      }
+    }
+    d0 = g[0] / (float)t.B;
+    d1 = g[1] / (float)t.B;
   }
   se = warp_sum_d(se);
   if (lanei == 0) atomicAdd(&s_loss, se);
@@ -329,7 +368,7 @@ __global__ void __launch_bounds__(kT, 1) bwd_kernel(Net net, TrainBufs t, int* s
     atomicAdd(&t.grad[B1_OFF + i], s_db1[i]);
   }
   if (tid < 2) atomicAdd(&t.grad[B4_OFF + tid], s_db4[tid]);
-  if (tid == 0) atomicAdd(t.loss, s_loss / (2.0 * t.B));
+  if (tid == 0) atomicAdd(t.loss, s_loss / t.B);
   if (!ok && tid == 0) raise_status(status, 2);
   if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
@@ -463,14 +502,16 @@ __global__ void batch_rows_kernel(int32_t* rows, int B, uint32_t n_rows, uint64_
 __global__ void record_kernel(EnvDev d, float* feat, float* label) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= d.F) return;
+  // after the step: the update's inputs are the estimate history
+  const float e1x = d.prev_estx[f], e1y = d.prev_esty[f];
   float x[IN];
-  ring_features(d, f, d.counters[0], x);
+  ring_features(d, f, d.counters[0], e1x, e1y, d.prev2_estx[f], d.prev2_esty[f], x);
 #pragma unroll
   for (int i = 0; i < IN; i += 4)
     *reinterpret_cast<float4*>(feat + (long long)f * IN + i) = make_float4(x[i], x[i + 1], x[i + 2], x[i + 3]);
-  const int ia = d.filt_agent[f], it = d.filt_target[f];
-  label[(long long)f * 2] = (d.tx[it] - d.ax[ia]) / d.S;
-  label[(long long)f * 2 + 1] = (d.ty[it] - d.ay[ia]) / d.S;
+  const int it = d.filt_target[f];
+  label[(long long)f * 2] = (d.tx[it] - e1x) / d.est_scale;
+  label[(long long)f * 2 + 1] = (d.ty[it] - e1y) / d.est_scale;
 }
 
 template <typename K>

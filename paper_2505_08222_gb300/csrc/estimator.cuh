@@ -56,7 +56,8 @@ struct TrainBufs {
   float* out;            // [B][2]
   uint16_t* dz;          // [3][B][256] BF16 gradients w.r.t. z
   float* grad;           // [NPARAM] FP32 gradient
-  double* loss;          // [1] sum of squared errors / (2B)
+  double* loss;          // [1] loss of the batch
+  float huber;           // 0: squared error; > 0: Huber threshold (label units)
   int B;
 };
 

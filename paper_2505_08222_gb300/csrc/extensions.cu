@@ -263,7 +263,7 @@ est::Net est_net(ut_env* h) {
 }
 
 // Forward + backward of one batch into es->grad (cleared first) and es->loss.
-cudaError_t est_grad_batch(ut_env* h, const float* X, const float* Y, const int32_t* rows, int B) {
+cudaError_t est_grad_batch(ut_env* h, const float* X, const float* Y, const int32_t* rows, int B, float huber) {
   EstimatorState* es = h->est;
   cudaStream_t s = h->stream;
   cudaError_t e = cudaMemsetAsync(es->grad, 0, est::NPARAM * 4, s);
@@ -280,6 +280,7 @@ cudaError_t est_grad_batch(ut_env* h, const float* X, const float* Y, const int3
   t.dz = es->dz;
   t.grad = es->grad;
   t.loss = es->loss;
+  t.huber = huber;
   t.B = B;
   return est::launch_backward(est_net(h), t, s);
 }
@@ -351,7 +352,7 @@ extern "C" ut_status est_loss_grad(ut_env* h, const float* X_dev, const float* Y
   if (!h->est || !h->est->weights_set) return est_fail(h, UT_ERR_STATE, "est_loss_grad: no weights");
   ut_status st = est_alloc_batch(h, B);
   if (st != UT_OK) return st;
-  cudaError_t e = est_grad_batch(h, X_dev, Y_dev, nullptr, B);
+  cudaError_t e = est_grad_batch(h, X_dev, Y_dev, nullptr, B, 0.0f);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(grad_dev, h->est->grad, est::NPARAM * 4, cudaMemcpyDeviceToDevice, h->stream);
   double loss = 0.0;
@@ -384,7 +385,7 @@ extern "C" ut_status est_train(ut_env* h, const float* X_dev, const float* Y_dev
       e = est::launch_batch_rows(es->rows, B, n_rows, cfg->seed, (uint32_t)s, h->stream);
       rows = es->rows;
     }
-    if (e == cudaSuccess) e = est_grad_batch(h, X_dev, Y_dev, rows, B);
+    if (e == cudaSuccess) e = est_grad_batch(h, X_dev, Y_dev, rows, B, cfg->huber_delta);
     // cosine decay of the learning rate over the run (reading C18)
     const double frac = cfg->steps > 1 ? (double)s / (double)(cfg->steps - 1) : 0.0;
     const float lr = cfg->cosine ? (float)(cfg->lr * 0.5 * (1.0 + std::cos(3.14159265358979 * frac))) : cfg->lr;

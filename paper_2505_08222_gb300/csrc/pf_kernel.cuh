@@ -361,6 +361,12 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
   // estimate
   if (tid == 0) {
     const float ex = swx / sw, ey = swy / sw;
+    if (d.prev_estx) {  // estimate history: the update's inputs
+      d.prev2_estx[f] = d.prev_estx[f];
+      d.prev2_esty[f] = d.prev_esty[f];
+      d.prev_estx[f] = d.estx[f];
+      d.prev_esty[f] = d.esty[f];
+    }
     d.estx[f] = ex;
     d.esty[f] = ey;
     const float dx = ex - sh.tgt[0], dy = ey - sh.tgt[1];

@@ -71,6 +71,7 @@ class EnvParams:
     spawn_radius: float = 100.0
     spawn_tries: int = 64
     feature_scale: float = FEATURE_SCALE
+    est_scale: float = 100.0
     # transformer agent; d_model == 0 means no policy (random actions)
     d_model: int = 0
     n_layers: int = 0
