@@ -292,8 +292,8 @@ ut_status policy_forward(ut_env* env, const uint16_t* tokens_dev, const int32_t*
 /* [(q - e1)/L, (r - |q - e1|_3D)/L, (g - g_m)/16, 1], then the estimate's  */
 /* last motion (e1 - e2)/L, zero padded to 96 (FP32).  Output: the          */
 /* correction (x - e1)/L; the new estimate is e1 + L * output, each output   */
-/* clamped to +-3 in the step (+-v_cap dt / L when no ping arrived this     */
-/* step).  Canonical                                                         */
+/* clamped to +-3 in the step (the estimate is held when no ping arrived    */
+/* this step).  Canonical                                                    */
 /* order W1[256][96], b1, W2[256][256], b2, W3[256][256], b3, W4[2][256], b4 */
 /* parameter order (156,930 floats).  Hidden layers on the tensor cores (BF16 */
 /* FP32 accumulation; the first layer multiplies the features' BF16 high and */

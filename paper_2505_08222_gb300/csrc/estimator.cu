@@ -202,11 +202,10 @@ __global__ void __launch_bounds__(kT, 1) fwd_kernel(FwdArgs p) {
       const int f = (int)b;
       const int it = p.d.filt_target[f];
       // Bounded update (dropped if not finite): with a ping received this step
-      // the estimate may move up to kMaxCorr L; without one it may move no
-      // farther than a target can in one step (v_cap dt), so that stale
-      // inputs cannot drive the closed loop away.
+      // the estimate may move up to kMaxCorr L; without one it is held, so
+      // that stale inputs cannot drive the closed loop away.
       const bool fresh = x[3] == 0.0f && x[4] == 1.0f;
-      const float lim = fresh ? kMaxCorr : p.d.pf_vcap * p.d.dt / p.d.est_scale;
+      const float lim = fresh ? kMaxCorr : 0.0f;
       const float c0 = isfinite(o0) ? fminf(fmaxf(o0, -lim), lim) : 0.0f;
       const float c1 = isfinite(o1) ? fminf(fmaxf(o1, -lim), lim) : 0.0f;
       const float ex = e1x + p.d.est_scale * c0, ey = e1y + p.d.est_scale * c1;
