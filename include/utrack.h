@@ -393,7 +393,7 @@ ut_status tc_gemm_bf16(const uint16_t* A_dev, const uint16_t* B_dev, float* C_de
  *   px/py/pvx/pvy_dev [E*A*T*P]: particles, updated in place;
  *   estx/esty/err_dev [E*A*T]: estimate and its 2-D error (written).
  * Intermediates (layout tables, per-filter measurement lists) live in a
- * static device array of about 4.6 MB that every GPU loading the library
+ * static device array of about 5.1 MB that every GPU loading the library
  * holds until exit; the call itself allocates nothing (no cudaMalloc, no
  * allocator callback).  Limit: at most 8192 environments and 32768 filters
  * (E*A*T) per call; larger sizes return UT_ERR_INVALID with a message on

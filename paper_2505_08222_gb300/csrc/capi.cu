@@ -272,6 +272,7 @@ ut_status env_create(const ut_config* cfg, const ut_allocator* allocator, void* 
   d.ring_count = alloc_n<int32_t>(h, F, ok);
   d.meas = alloc_n<float4>(h, F * AM, ok);
   d.meas_n = alloc_n<int32_t>(h, F, ok);
+  d.meas_hdr = alloc_n<float4>(h, F, ok);
   d.actions = alloc_n<int32_t>(h, NA, ok);
   d.obs = alloc_n<uint16_t>(h, NA * d.NS * 8, ok);
   d.reward = alloc_n<float>(h, E, ok);

@@ -50,6 +50,7 @@ struct EnvDev {
   // per-step buffers
   float4* meas;               // [F][AM]
   int32_t* meas_n;            // [F]
+  float4* meas_hdr;           // [F] (target x, target y, target depth^2, list length)
   float* range;               // [F] (debug)
   int32_t* valid;             // [F] (debug)
   int32_t* recv;              // [NA][AM] (debug)

@@ -287,6 +287,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) step_env_kernel(EnvDev d,
       }
     }
     d.meas_n[f] = n;
+    // per-filter header read by the filter step (no dependent loads there)
+    d.meas_hdr[f] = make_float4(s_tx[wid][k], s_ty[wid][k], s_tz[wid][k] * s_tz[wid][k], (float)n);
     if (d.ring_on) {
       d.ring_head[f] = head;
       d.ring_count[f] = cnt;

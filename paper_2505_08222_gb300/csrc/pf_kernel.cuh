@@ -86,8 +86,10 @@ __device__ __forceinline__ void block_sum3(float& a, float& b, float& c, float* 
 }
 
 // Exclusive block scan of int64 values; also returns the block total.
+// s_tot / s_pre [32] are used once per CTA (no trailing barrier).
 template <int NT>
-__device__ __forceinline__ long long block_excl_scan(long long v, long long* s_tmp, long long& total) {
+__device__ __forceinline__ long long block_excl_scan(long long v, long long* s_tot, long long* s_pre,
+                                                     long long& total) {
   constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   long long incl = v;
@@ -100,27 +102,26 @@ __device__ __forceinline__ long long block_excl_scan(long long v, long long* s_t
     total = __shfl_sync(0xffffffffu, incl, 31);
     return incl - v;
   }
-  if (lane == 31) s_tmp[wid] = incl;
+  if (lane == 31) s_tot[wid] = incl;
   __syncthreads();
   if (wid == 0) {
-    long long w = lane < NW ? s_tmp[lane] : 0;
+    long long w = lane < NW ? s_tot[lane] : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       long long t = __shfl_up_sync(0xffffffffu, w, o);
       if (lane >= o) w += t;
     }
-    if (lane < NW) s_tmp[lane] = w;
+    if (lane < NW) s_pre[lane] = w;
   }
   __syncthreads();
-  const long long before = wid > 0 ? s_tmp[wid - 1] : 0;
-  total = s_tmp[NW - 1];
-  __syncthreads();
-  return before + incl - v;
+  total = s_pre[NW - 1];
+  return (wid > 0 ? s_pre[wid - 1] : 0) + incl - v;
 }
 
 // Maximum over all earlier threads of each thread's value (identity -1).
+// s_tot / s_pre [32] are used once per CTA (no trailing barrier).
 template <int NT>
-__device__ __forceinline__ int block_excl_max(int v, int* s_tmp) {
+__device__ __forceinline__ int block_excl_max(int v, int* s_tot, int* s_pre) {
   constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int incl = v;
@@ -132,22 +133,26 @@ __device__ __forceinline__ int block_excl_max(int v, int* s_tmp) {
   int excl = __shfl_up_sync(0xffffffffu, incl, 1);
   if (lane == 0) excl = -1;
   if (NW == 1) return excl;
-  if (lane == 31) s_tmp[wid] = incl;
+  if (lane == 31) s_tot[wid] = incl;
   __syncthreads();
   if (wid == 0) {
-    int w = lane < NW ? s_tmp[lane] : -1;
+    int w = lane < NW ? s_tot[lane] : -1;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       int t = __shfl_up_sync(0xffffffffu, w, o);
       if (lane >= o) w = max(w, t);
     }
-    if (lane < NW) s_tmp[lane] = w;
+    if (lane < NW) s_pre[lane] = w;
   }
   __syncthreads();
-  const int before = wid > 0 ? s_tmp[wid - 1] : -1;
-  __syncthreads();
-  return max(before, excl);
+  return max(wid > 0 ? s_pre[wid - 1] : -1, excl);
 }
+
+// Cross-warp scratch of the resample map (each array used once per CTA).
+struct ScanScratch {
+  long long tot[32], pre[32];
+  int mtot[32], mpre[32];
+};
 
 // count(X) = #{ j in [0, P) : j W + U0 < X } = clamp(ceil((X - U0) / W), 0, P),
 // exact.  A float estimate v = (X - U0) * (1/W) has absolute error below 2e-3
@@ -179,7 +184,7 @@ __device__ __forceinline__ int slot_of(int i) {
 // base + q (0 for slots >= P).  Writes idx[q] for outputs base + q.
 template <int NT, int PPT>
 __device__ __forceinline__ void resample_map(const float (&w)[PPT], int base, int P, uint64_t u64, int* s_mark,
-                                             long long* s_ll, int* s_int, int (&idx)[PPT]) {
+                                             ScanScratch* sc, int (&idx)[PPT]) {
   long long incl[PPT];
   long long acc = 0;
 #pragma unroll
@@ -192,7 +197,7 @@ __device__ __forceinline__ void resample_map(const float (&w)[PPT], int base, in
   for (int q = 0; q < PPT; q += 4)
     *reinterpret_cast<int4*>(s_mark + base + q) = make_int4(-1, -1, -1, -1);
   long long W;
-  const long long excl = block_excl_scan<NT>(acc, s_ll, W);  // ends with a barrier
+  const long long excl = block_excl_scan<NT>(acc, sc->tot, sc->pre, W);  // contains barriers
   if (NT == 32) __syncwarp();  // single-warp blocks: order the marker initialisation
   const long long U0 = (long long)__umul64hi(u64, (unsigned long long)W);
   const float invW = 1.0f / __ll2float_rn(W);
@@ -218,7 +223,7 @@ __device__ __forceinline__ void resample_map(const float (&w)[PPT], int base, in
     if (base + q >= P) m[q] = -1;
     run = max(run, m[q]);
   }
-  int before = block_excl_max<NT>(run, s_int);
+  int before = block_excl_max<NT>(run, sc->mtot, sc->mpre);
 #pragma unroll
   for (int q = 0; q < PPT; ++q) {
     before = max(before, m[q]);
@@ -229,10 +234,10 @@ __device__ __forceinline__ void resample_map(const float (&w)[PPT], int base, in
 
 struct Shared {
   float red[3 * 32];
-  long long ll[32];
-  int in[32];
+  ScanScratch scan;
   float4 meas[kMaxAgents];  // (qx, qy, (z_target - qz)^2, r)
   float tgt[2];
+  float dz2;
   int nm;
   unsigned long long u64;
 };
@@ -252,19 +257,26 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
   const int base = tid * PPT;
   const long long off = (long long)f * P;
 
-  if (tid < d.AM) {
-    const int it = d.filt_target[f];
-    float4 m = d.meas[(long long)f * d.AM + tid];
-    const float dz = d.tz[it] - m.z;
-    m.z = dz * dz;
-    sh.meas[tid] = m;
-    if (tid == 0) {
-      sh.nm = d.meas_n[f];
-      sh.tgt[0] = d.tx[it];
-      sh.tgt[1] = d.ty[it];
-      Rand4 r = philox((uint32_t)f, 0u, g, TAG_RESAMPLE, d.seed);
-      sh.u64 = (unsigned long long)r.x[0] | ((unsigned long long)r.x[1] << 32);
-    }
+  // estimate history, fetched early so that its latency hides behind the
+  // particle loads (thread 0 writes it back before a block barrier)
+  float hist[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  if (tid == 0 && d.prev_estx) {
+    hist[0] = d.estx[f];
+    hist[1] = d.esty[f];
+    hist[2] = d.prev_estx[f];
+    hist[3] = d.prev_esty[f];
+  }
+  // measurement list and the filter's header (senders are at the surface:
+  // the vertical offset of every range is the target depth)
+  if (tid < d.AM) sh.meas[tid] = d.meas[(long long)f * d.AM + tid];
+  if (tid == 0) {
+    const float4 hd = d.meas_hdr[f];
+    sh.tgt[0] = hd.x;
+    sh.tgt[1] = hd.y;
+    sh.dz2 = hd.z;
+    sh.nm = (int)hd.w;
+    Rand4 r = philox((uint32_t)f, 0u, g, TAG_RESAMPLE, d.seed);
+    sh.u64 = (unsigned long long)r.x[0] | ((unsigned long long)r.x[1] << 32);
   }
 
   float x[PPT], y[PPT], vx[PPT], vy[PPT];
@@ -328,6 +340,7 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
 
   // weight (log domain); measurements outer, particles inner
   const int nm = sh.nm;
+  const float dz2 = sh.dz2;
   float acc[PPT];
 #pragma unroll
   for (int q = 0; q < PPT; ++q) acc[q] = 0.0f;
@@ -336,7 +349,7 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
       const float dx = x[q] - mm.x, dy = y[q] - mm.y;
-      const float res = mm.w - sqrt_approx(fmaf(dx, dx, fmaf(dy, dy, mm.z)));
+      const float res = mm.w - sqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz2)));
       acc[q] = fmaf(res, res, acc[q]);
     }
   }
@@ -362,10 +375,10 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
   if (tid == 0) {
     const float ex = swx / sw, ey = swy / sw;
     if (d.prev_estx) {  // estimate history: the update's inputs
-      d.prev2_estx[f] = d.prev_estx[f];
-      d.prev2_esty[f] = d.prev_esty[f];
-      d.prev_estx[f] = d.estx[f];
-      d.prev_esty[f] = d.esty[f];
+      d.prev2_estx[f] = hist[2];
+      d.prev2_esty[f] = hist[3];
+      d.prev_estx[f] = hist[0];
+      d.prev_esty[f] = hist[1];
     }
     d.estx[f] = ex;
     d.esty[f] = ey;
@@ -391,7 +404,7 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
   if (nm > 0) {
 #pragma unroll
     for (int q = 0; q < PPT; ++q) s_part[q * NT + tid] = make_float4(x[q], y[q], vx[q], vy[q]);
-    resample_map<NT, PPT>(w, base, P, sh.u64, s_mark, sh.ll, sh.in, idx);
+    resample_map<NT, PPT>(w, base, P, sh.u64, s_mark, &sh.scan, idx);
     // (resample_map contains barriers after the s_part stores)
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
@@ -444,15 +457,14 @@ __global__ void __launch_bounds__(NT) pf_resample_kernel(const float* __restrict
                                                           int32_t* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int* s_mark = reinterpret_cast<int*>(smem_raw);
-  __shared__ long long s_ll[32];
-  __shared__ int s_in[32];
+  __shared__ ScanScratch s_scan;
   const long long f = blockIdx.x;
   const int base = threadIdx.x * PPT;
   float w[PPT];
 #pragma unroll
   for (int q = 0; q < PPT; ++q) w[q] = base + q < P ? wmax[f * P + base + q] : 0.0f;
   int idx[PPT];
-  resample_map<NT, PPT>(w, base, P, u64[f], s_mark, s_ll, s_in, idx);
+  resample_map<NT, PPT>(w, base, P, u64[f], s_mark, &s_scan, idx);
 #pragma unroll
   for (int q = 0; q < PPT; ++q)
     if (base + q < P) out[f * P + base + q] = idx[q];

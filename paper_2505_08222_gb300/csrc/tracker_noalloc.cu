@@ -31,19 +31,21 @@ constexpr int kNoallocMaxFilters = 32768;
 // Scratch layout (bytes, each region 256-byte aligned):
 //   meas      [kNoallocMaxFilters][kMaxAgents] float4   measurement lists
 //   meas_n    [kNoallocMaxFilters] int32
+//   meas_hdr  [kNoallocMaxFilters] float4 (target x, y, depth^2, list length)
 //   filt_agent, filt_target [kNoallocMaxFilters] int32
 //   agent_off, target_off, filter_off [kNoallocMaxEnvs + 1] int32
 //   counters  [4] uint32
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kMeasOff = 0;
 constexpr size_t kMeasNOff = kMeasOff + align256((size_t)kNoallocMaxFilters * kMaxAgents * sizeof(float4));
-constexpr size_t kFiltAgentOff = kMeasNOff + align256((size_t)kNoallocMaxFilters * 4);
+constexpr size_t kMeasHdrOff = kMeasNOff + align256((size_t)kNoallocMaxFilters * 4);
+constexpr size_t kFiltAgentOff = kMeasHdrOff + align256((size_t)kNoallocMaxFilters * sizeof(float4));
 constexpr size_t kFiltTargetOff = kFiltAgentOff + align256((size_t)kNoallocMaxFilters * 4);
 constexpr size_t kAgentOffOff = kFiltTargetOff + align256((size_t)kNoallocMaxFilters * 4);
 constexpr size_t kTargetOffOff = kAgentOffOff + align256((size_t)(kNoallocMaxEnvs + 1) * 4);
 constexpr size_t kFilterOffOff = kTargetOffOff + align256((size_t)(kNoallocMaxEnvs + 1) * 4);
 constexpr size_t kCountersOff = kFilterOffOff + align256((size_t)(kNoallocMaxEnvs + 1) * 4);
-constexpr size_t kScratchBytes = kCountersOff + 256;  // about 4.6 MB
+constexpr size_t kScratchBytes = kCountersOff + 256;  // about 5.1 MB
 
 static __device__ __align__(256) unsigned char g_tracker_scratch[kScratchBytes];
 
@@ -130,6 +132,7 @@ __global__ void __launch_bounds__(kNoallocWarps * 32) noalloc_lists_kernel(EnvDe
       }
     }
     d.meas_n[f0 + p] = n;
+    d.meas_hdr[f0 + p] = make_float4(s_tx[wid][k], s_ty[wid][k], s_tz[wid][k] * s_tz[wid][k], (float)n);
   }
 }
 
@@ -217,6 +220,7 @@ extern "C" ut_status tracker_update_noalloc(const ut_config* cfg, uint64_t seed,
   d.err = err_dev;
   d.meas = reinterpret_cast<float4*>(s + kMeasOff);
   d.meas_n = reinterpret_cast<int32_t*>(s + kMeasNOff);
+  d.meas_hdr = reinterpret_cast<float4*>(s + kMeasHdrOff);
   d.filt_agent = reinterpret_cast<int32_t*>(s + kFiltAgentOff);
   d.filt_target = reinterpret_cast<int32_t*>(s + kFiltTargetOff);
   d.agent_off = reinterpret_cast<int32_t*>(s + kAgentOffOff);
