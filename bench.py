@@ -11,9 +11,10 @@ kinematics -> targets -> pings -> communication -> particle filter
 
 The timed region replays one CUDA graph of K steps (rollout(K), captured and
 uploaded before timing).  Particle state (3.4 GB) is far larger than L2
-(129 MB), so no L2 flush is needed between steps.  Under torchrun each rank
-runs its own 4096-env shard (weak scaling, no data-path collective); rank 0
-prints one JSON line.  --impl reference times the FP64 oracle on the host
+(129 MB), so no L2 flush is needed between steps.  Under torchrun the job is
+one batch of N x 4096 envs and rank r steps envs [4096 r, 4096 (r+1)) with
+global random-draw ids (weak scaling, no data-path collective; only the
+timings and counts are reduced); rank 0 prints one JSON line.  --impl reference times the FP64 oracle on the host
 cores on a bounded sample of the same workload.
 """
 from __future__ import annotations
@@ -277,14 +278,20 @@ def run_ours(args):
     import paper_2505_08222_gb300 as ut
     import synth
 
+    from paper_2505_08222_gb300 import shard
+
     p = _workload(args.workload)
+    if world > 1:
+        # weak scaling: the job is one batch of world x n_envs envs; rank r
+        # steps its contiguous shard, random draws keyed by global ids
+        p = shard.shard_params(p.replace(n_envs=p.n_envs * world), rank, world)
     env = ut.Env(p)
     if p.d_model > 0 and hasattr(env, "set_policy"):
         env.set_policy(synth.policy_params(synth.PolicyDims(p.d_model, p.n_layers, p.n_heads, p.n_actions)))
-    env.reset(1000 + rank)
+    env.reset(1000)
     if not args.no_autotune:
         env.autotune(5)  # picks the filter launch variant, then the episode restarts
-        env.reset(1000 + rank)
+        env.reset(1000)
     stream = torch.cuda.current_stream()
     K, W = args.steps, args.warmup
     policy_on = bool(getattr(env, "policy_ready", False))
@@ -317,7 +324,7 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
         dist.barrier()
-    agent_steps = stats["agent_steps"] * world
+    agent_steps = float(shard.reduce_sums([stats["agent_steps"]])[0])
     # dominant-kernel duration: CUDA events around each particle-filter launch
     # on its stream, over K eager steps of the same workload right after the
     # timed graph run (events recorded by graph nodes cannot be timed)
@@ -371,7 +378,7 @@ def run_ours(args):
         t = torch.tensor([e2e_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
-    e2e_value = K * NA * world / (e2e_ms / 1e3)
+    e2e_value = K * float(shard.reduce_sums([NA])[0]) / (e2e_ms / 1e3)
 
     if rank == 0:
         line = {

@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define UT_ABI_VERSION 1u
+#define UT_ABI_VERSION 2u
 #define UT_MAX_AGENTS 8      /* per environment */
 #define UT_MAX_TARGETS 8     /* per environment */
 #define UT_MAX_PARTICLES 4096
@@ -111,6 +111,11 @@ typedef struct ut_config {
   int32_t spawn_tries;         /* rejection-sampling tries per entity (64) */
   float feature_scale;         /* S: metres per unit in observation tokens */
   float est_scale;             /* L: metres per unit of the learned estimator's local frame (100) */
+  /* Global index of this batch's first env / agent / target / filter when a
+   * larger batch is split over several handles (one per GPU): random draws
+   * are keyed by global ids, so the shards together reproduce the draws of
+   * the whole batch.  0 for an unsplit batch. */
+  uint32_t id_env0, id_agent0, id_target0, id_filter0;
   int32_t d_model;             /* transformer agent width; 0 = no policy */
   int32_t n_layers;            /* transformer blocks */
   int32_t n_heads;             /* attention heads (d_model % n_heads == 0) */
@@ -273,9 +278,10 @@ ut_status env_metrics_reset(ut_env* env);
 ut_status env_set_policy(ut_env* env, const float* params_host, int64_t n_params);
 
 /* Transformer agent forward on caller buffers with the handle's weights:
- * tokens_dev [n_agents][n_slots][8] BF16 (16-byte aligned), n_ent_dev
- * [n_agents] entity tokens in use (<= n_slots), h_dev [n_agents][d_model]
- * BF16 recurrent embedding, read and replaced by the block output at the
+ * tokens_dev [n_agents][n_slots][8] BF16 (16-byte aligned), n_slots in
+ * 1 .. UT_MAX_AGENTS + UT_MAX_TARGETS, n_ent_dev [n_agents] entity tokens in
+ * use (clamped to 0 .. n_slots), h_dev [n_agents][d_model] BF16 recurrent
+ * embedding (16-byte aligned), read and replaced by the block output at the
  * recurrent token; logits_dev [n_agents][n_actions] FP32 written;
  * actions_dev [n_agents] (optional) receives Gumbel-max samples drawn at
  * global step `step`.  Errors: UT_ERR_STATE (no weights), UT_ERR_INVALID. */

@@ -112,8 +112,8 @@ def _declare(L):
                                     ctypes.c_uint32, _dp, _dp]
     L.oc_reset.argtypes = [ctypes.POINTER(OcConfig), ctypes.POINTER(OcState), ctypes.c_uint32]
     L.oc_random_actions.argtypes = [ctypes.POINTER(OcConfig), ctypes.c_uint32, ctypes.c_int32, _ip]
-    L.oc_gumbel_actions.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32, _dp,
-                                    _ip, _dp]
+    L.oc_gumbel_actions.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_int32, _dp, _ip, _dp]
     L.oc_step.argtypes = [ctypes.POINTER(OcConfig), ctypes.POINTER(OcState), _ip, ctypes.POINTER(OcStepOut)]
     L.oc_systematic_resample.argtypes = [ctypes.c_int32, _dp, ctypes.c_uint64, _ip]
     L.oc_tracking_reward.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
@@ -182,7 +182,7 @@ def uniform_normal(seed, id0, id1, step, tag):
 class OracleEnv:
     """Batched environment state in float64 plus the stage functions."""
 
-    def __init__(self, params, seed: int, id_base=(0, 0, 0, 0)):
+    def __init__(self, params, seed: int, id_base=None):
         self.p = params
         a, t = params.counts()
         self.n_agents_env, self.n_targets_env = a, t
@@ -207,6 +207,8 @@ class OracleEnv:
                      "est_scale"):
             setattr(c, name, getattr(params, name))
         c.seed = seed
+        if id_base is None:  # global ids of a shard of a larger batch, else 0
+            id_base = tuple(getattr(params, k, 0) for k in ("id_env0", "id_agent0", "id_target0", "id_filter0"))
         c.env0, c.agent0, c.target0, c.filter0 = (int(v) for v in id_base)
         self.seed = seed
         AM = params.max_agents
@@ -309,12 +311,12 @@ def tracking_reward(err: float, eps_min: float = 10.0, eps_max: float = 50.0) ->
     return lib().oc_tracking_reward(err, eps_min, eps_max)
 
 
-def gumbel_actions(seed: int, g: int, logits: np.ndarray):
+def gumbel_actions(seed: int, g: int, logits: np.ndarray, agent0: int = 0):
     lg = _f64(logits)
     n, k = lg.shape
     act = np.zeros(n, np.int32)
     gum = np.zeros((n, k))
-    lib().oc_gumbel_actions(ctypes.c_uint64(seed), g, n, k, _p(lg), _p(act, _ip), _p(gum))
+    lib().oc_gumbel_actions(ctypes.c_uint64(seed), g, agent0, n, k, _p(lg), _p(act, _ip), _p(gum))
     return act, gum
 
 

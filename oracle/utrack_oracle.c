@@ -337,14 +337,14 @@ void oc_random_actions(const oc_config* c, uint32_t g, int32_t n_agents, int32_t
 
 /* Sampling from the categorical policy output by the Gumbel-max rule:
  * argmax_j (logit_j - log(-log u_j)), first index on ties. */
-void oc_gumbel_actions(uint64_t seed, uint32_t g, int32_t n_agents, int32_t n_act, const double* logits,
-                       int32_t* act, double* gumbel_out) {
+void oc_gumbel_actions(uint64_t seed, uint32_t g, int32_t agent0, int32_t n_agents, int32_t n_act,
+                       const double* logits, int32_t* act, double* gumbel_out) {
   for (int i = 0; i < n_agents; ++i) {
     double best = -INFINITY;
     int32_t arg = 0;
     for (int j = 0; j < n_act; ++j) {
       uint32_t x[4];
-      draw(seed, (uint32_t)i, (uint32_t)(j / 4), g, OC_TAG_GUMBEL, x);
+      draw(seed, (uint32_t)(agent0 + i), (uint32_t)(j / 4), g, OC_TAG_GUMBEL, x);
       double gj = -log(-log(u01_mid(x[j % 4])));
       if (gumbel_out) gumbel_out[(int64_t)i * n_act + j] = gj;
       double v = logits[(int64_t)i * n_act + j] + gj;

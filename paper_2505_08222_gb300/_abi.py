@@ -7,7 +7,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libutrack.so")
 
-UT_ABI_VERSION = 1
+UT_ABI_VERSION = 2
 UT_FLAG_DEBUG = 1
 UT_FLAG_RING = 2
 
@@ -44,6 +44,8 @@ CONFIG_FIELDS = [
     ("follow_dmin", ctypes.c_float), ("d_safe", ctypes.c_float),
     ("spawn_min", ctypes.c_float), ("spawn_radius", ctypes.c_float), ("spawn_tries", ctypes.c_int32),
     ("feature_scale", ctypes.c_float), ("est_scale", ctypes.c_float),
+    ("id_env0", ctypes.c_uint32), ("id_agent0", ctypes.c_uint32), ("id_target0", ctypes.c_uint32),
+    ("id_filter0", ctypes.c_uint32),
     ("d_model", ctypes.c_int32), ("n_layers", ctypes.c_int32), ("n_heads", ctypes.c_int32),
 ]
 

@@ -234,6 +234,10 @@ ut_status env_create(const ut_config* cfg, const ut_allocator* allocator, void* 
   d.spawn_dmin_int = (long long)std::floor((double)cfg->spawn_min * 65536.0);
   d.spawn_tries = cfg->spawn_tries;
   d.S = cfg->feature_scale;
+  d.gid_env = cfg->id_env0;
+  d.gid_agent = cfg->id_agent0;
+  d.gid_target = cfg->id_target0;
+  d.gid_filter = cfg->id_filter0;
   d.est_scale = cfg->est_scale;
   d.ring_on = (cfg->flags & UT_FLAG_RING) ? 1 : 0;
   d.debug_on = (cfg->flags & UT_FLAG_DEBUG) ? 1 : 0;

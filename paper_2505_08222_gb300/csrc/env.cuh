@@ -22,6 +22,7 @@ struct EnvDev {
   const int32_t* filt_target; // [F] global target index of filter f
   // constants
   uint64_t seed;
+  uint32_t gid_env, gid_agent, gid_target, gid_filter;  // global id offsets
   float dt, agent_speed, heading_noise;
   float dpsi[8];              // heading change of each action
   int target_model;

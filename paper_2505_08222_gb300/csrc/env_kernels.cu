@@ -30,7 +30,7 @@ __global__ void reset_spawn_kernel(EnvDev d, uint32_t g) {
   for (int n = 0; n < A + T; ++n) {
     long long cx = 0, cy = 0;
     for (int t = 0; t < d.spawn_tries; ++t) {
-      Rand4 r = philox((uint32_t)e, (uint32_t)(n * 64 + t), g, TAG_SPAWN, d.seed);
+      Rand4 r = philox(d.gid_env + (uint32_t)e, (uint32_t)(n * 64 + t), g, TAG_SPAWN, d.seed);
       long long ux = (long long)(r.x[0] >> 8) - 8388608LL;
       long long uy = (long long)(r.x[1] >> 8) - 8388608LL;
       if (ux * ux + uy * uy > r2) continue;
@@ -48,14 +48,14 @@ __global__ void reset_spawn_kernel(EnvDev d, uint32_t g) {
   }
   for (int a = 0; a < A; ++a) {
     const int i = a0 + a;
-    Rand4 r = philox((uint32_t)i, 0u, g, TAG_AGENT_INIT, d.seed);
+    Rand4 r = philox(d.gid_agent + (uint32_t)i, 0u, g, TAG_AGENT_INIT, d.seed);
     d.ax[i] = (float)X[a] * 0x1p-16f;
     d.ay[i] = (float)Y[a] * 0x1p-16f;
     d.apsi[i] = (2.0f * unif(r.x[0]) - 1.0f) * kPi;
   }
   for (int k = 0; k < T; ++k) {
     const int j = t0 + k;
-    Rand4 r = philox((uint32_t)j, 0u, g, TAG_TARGET_INIT, d.seed);
+    Rand4 r = philox(d.gid_target + (uint32_t)j, 0u, g, TAG_TARGET_INIT, d.seed);
     d.tx[j] = (float)X[A + k] * 0x1p-16f;
     d.ty[j] = (float)Y[A + k] * 0x1p-16f;
     d.tpsi[j] = (2.0f * unif(r.x[0]) - 1.0f) * kPi;
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kInitThreads) reset_pf_kernel(EnvDev d, uint32
   const float dx = axv - d.tx[it], dy = ayv - d.ty[it], dz = 0.0f - d.tz[it];
   const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
   const bool heard = dist <= d.det_radius;
-  Rand4 rp = philox((uint32_t)f, 0u, g, TAG_RESET_PING, d.seed);
+  Rand4 rp = philox(d.gid_filter + (uint32_t)f, 0u, g, TAG_RESET_PING, d.seed);
   float n0, n1;
   box_muller(rp.x[0], rp.x[1], n0, n1);
   const float r0 = dist + d.range_sigma * n0;
@@ -95,8 +95,8 @@ __global__ void __launch_bounds__(kInitThreads) reset_pf_kernel(EnvDev d, uint32
   float sx = 0.0f, sy = 0.0f;
   const long long base = (long long)f * d.P;
   for (int i = threadIdx.x; i < d.P; i += kInitThreads) {
-    Rand4 r = philox((uint32_t)f, (uint32_t)i, g, TAG_PF_INIT, d.seed);
-    Rand4 q = philox((uint32_t)f, (uint32_t)i, g, TAG_PF_INIT2, d.seed);
+    Rand4 r = philox(d.gid_filter + (uint32_t)f, (uint32_t)i, g, TAG_PF_INIT, d.seed);
+    Rand4 q = philox(d.gid_filter + (uint32_t)f, (uint32_t)i, g, TAG_PF_INIT2, d.seed);
     float rho;
     if (heard) {
       float m0, m1;
@@ -179,11 +179,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) step_env_kernel(EnvDev d,
         act = act < 0 ? 0 : d.n_act - 1;
       }
     } else {
-      Rand4 r = philox((uint32_t)i, 0u, g, TAG_ACTION, d.seed);
+      Rand4 r = philox(d.gid_agent + (uint32_t)i, 0u, g, TAG_ACTION, d.seed);
       act = (int)__umulhi(r.x[0], (uint32_t)d.n_act);
     }
     d.actions[i] = act;
-    Rand4 r = philox((uint32_t)i, 0u, g, TAG_AGENT_NOISE, d.seed);
+    Rand4 r = philox(d.gid_agent + (uint32_t)i, 0u, g, TAG_AGENT_NOISE, d.seed);
     float n0, n1;
     box_muller(r.x[0], r.x[1], n0, n1);
     const float psi = wrap_angle(d.apsi[i] + d.dpsi[act] + d.heading_noise * n0);
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) step_env_kernel(EnvDev d,
     s_ay[wid][lane] = y;
   } else if (lane >= 8 && lane - 8 < T) {
     const int k = lane - 8, j = t0 + k;
-    Rand4 r = philox((uint32_t)j, 0u, g, TAG_TARGET_MOVE, d.seed);
+    Rand4 r = philox(d.gid_target + (uint32_t)j, 0u, g, TAG_TARGET_MOVE, d.seed);
     float psi;
     if (d.target_model == 0) {
       psi = wrap_angle(kTwoPi * unif(r.x[0]));
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) step_env_kernel(EnvDev d,
     const int a = p / T, k = p - a * T;
     const float dx = s_ax[wid][a] - s_tx[wid][k], dy = s_ay[wid][a] - s_ty[wid][k], dz = 0.0f - s_tz[wid][k];
     const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
-    Rand4 r = philox((uint32_t)(f0 + p), 0u, g, TAG_PING, d.seed);
+    Rand4 r = philox(d.gid_filter + (uint32_t)(f0 + p), 0u, g, TAG_PING, d.seed);
     float n0, n1;
     box_muller(r.x[0], r.x[1], n0, n1);
     const int v = dist <= d.det_radius;
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) step_env_kernel(EnvDev d,
         rcv = 1;
       } else {
         const float dx = s_ax[wid][a] - s_ax[wid][b], dy = s_ay[wid][a] - s_ay[wid][b];
-        Rand4 r = philox((uint32_t)ia, (uint32_t)b, g, TAG_COMM, d.seed);
+        Rand4 r = philox(d.gid_agent + (uint32_t)ia, (uint32_t)b, g, TAG_COMM, d.seed);
         rcv = (sqrtf(dx * dx + dy * dy) <= d.comm_radius) && !(unif(r.x[0]) < d.comm_drop);
         const long long o = (long long)ia * d.AM + b;
         if (rcv) {

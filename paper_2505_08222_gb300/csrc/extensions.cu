@@ -67,6 +67,7 @@ static PolicyDev policy_dev(ut_env* h) {
   p.head_w = ps->head + 2 * ps->d;
   p.head_b = ps->head + 2 * ps->d + (size_t)ps->n_act * ps->d;
   p.seed = h->d.seed;
+  p.gid_agent = h->d.gid_agent;
   p.counters = h->d.counters;
   p.sample = 1;
   p.status = h->d.status;
@@ -179,12 +180,13 @@ extern "C" ut_status policy_forward(ut_env* h, const uint16_t* tokens_dev, const
     h->err = "policy_forward: no policy weights set";
     return UT_ERR_STATE;
   }
-  if (n_agents < 0 || n_slots < 1 || n_slots > 127 || !tokens_dev || !n_ent_dev || !h_dev || !logits_dev) {
+  if (n_agents < 0 || n_slots < 1 || n_slots > UT_MAX_AGENTS + UT_MAX_TARGETS || !tokens_dev || !n_ent_dev ||
+      !h_dev || !logits_dev) {
     h->err = "policy_forward: invalid arguments";
     return UT_ERR_INVALID;
   }
-  if (reinterpret_cast<uintptr_t>(tokens_dev) & 15) {
-    h->err = "policy_forward: tokens must be 16-byte aligned";
+  if ((reinterpret_cast<uintptr_t>(tokens_dev) | reinterpret_cast<uintptr_t>(h_dev)) & 15) {
+    h->err = "policy_forward: tokens and h must be 16-byte aligned";
     return UT_ERR_INVALID;
   }
   PolicyDev p = policy_dev(h);

@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
     sh.tgt[1] = hd.y;
     sh.dz2 = hd.z;
     sh.nm = (int)hd.w;
-    Rand4 r = philox((uint32_t)f, 0u, g, TAG_RESAMPLE, d.seed);
+    Rand4 r = philox(d.gid_filter + (uint32_t)f, 0u, g, TAG_RESAMPLE, d.seed);
     sh.u64 = (unsigned long long)r.x[0] | ((unsigned long long)r.x[1] << 32);
   }
 
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
     const int i = base + q;
     float n[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     if (i < P) {
-      Rand4 r = philox((uint32_t)f, (uint32_t)(i >> 1), g, TAG_PF_PREDICT, d.seed);
+      Rand4 r = philox(d.gid_filter + (uint32_t)f, (uint32_t)(i >> 1), g, TAG_PF_PREDICT, d.seed);
       box_muller_fast(r.x[0], r.x[1], n[0], n[1]);
       box_muller_fast(r.x[2], r.x[3], n[2], n[3]);
     }

@@ -2,14 +2,18 @@
 //
 // Each agent's tokens are its recurrent embedding h followed by its entity
 // vectors (self, teammates, targets; observation tokens of Sec. III-A.2).
-// Agents are packed R = 1 + max entities rows apart into 128-row tiles; one
-// CTA of 128 threads owns a tile and thread r owns row r from start to end:
+// Agents are packed R = 1 + max entities rows apart into 128-row tiles.  One
+// CTA of 256 threads owns a tile: thread t works on row t % 128 and on the
+// column half t / 128 of that row, keeping its half of the residual stream X
+// in registers from start to end:
 //
 //   X = [h ; W_emb tok + b_emb]                         (CUDA cores, FP32)
 //   per block l:   Y = LN1(X) -> BF16 operand A
-//                  Q, K, V = Y Wq^T, Y Wk^T, Y Wv^T      (tcgen05.mma, TMEM)
+//                  Q, K, V = Y Wq^T, Y Wk^T, Y Wv^T      (three tcgen05.mma
+//                      groups issued together, FP32 in TMEM)
 //                  O = softmax(Q K^T / 4) V per head, within the agent's
-//                      valid tokens                      (CUDA cores)
+//                      valid tokens                      (CUDA cores, each
+//                      column half takes half the heads)
 //                  X += O Wo^T + bo                      (tcgen05.mma)
 //                  X += W2 GELU(W1 LN2(X) + b1) + b2      (tcgen05.mma, hidden
 //                      units in chunks of 128 accumulated in TMEM)
@@ -20,7 +24,9 @@
 // Readings (C16): pre-LN blocks, FFN width 4d with exact erf-GELU, LN eps
 // 1e-5, head dimension 16.  Matrix operands are BF16, every accumulation is
 // FP32.  Weights are packed once into the tensor cores' K-major operand
-// layout (tc.cuh) so that each operand tile is one contiguous copy.
+// layout (tc.cuh); each weight image is one contiguous bulk copy, streamed
+// through a three-slot shared-memory ring by the bulk-copy engine while the
+// CUDA cores work on the previous stage.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -33,126 +39,230 @@
 namespace ut {
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;
+constexpr int kSlots = 3;                                  // weight ring depth
+constexpr int kMaxTok = 1 + UT_MAX_AGENTS + UT_MAX_TARGETS;  // tokens per agent
 constexpr float kLnEps = 1e-5f;
+constexpr uint32_t kPolls = 1u << 22;                      // bounded mbarrier waits
 
 template <int D>
 struct Geo {
   static constexpr int H = D / 16;                 // heads of width 16
-  static constexpr int XS = D + 1;                 // fp32 row stride of X (bank-conflict free)
+  static constexpr int HALF = D / 2;               // columns per thread
+  static constexpr int HH = H / 2;                 // heads per thread
   static constexpr int KVS = D + 8;                // bf16 row stride of K / V
   static constexpr int NC = (4 * D) / 128;         // FFN hidden chunks of 128
-  static constexpr size_t X_BYTES = (size_t)128 * XS * 4;
-  static constexpr size_t A_BYTES = (size_t)128 * D * 2;
-  static constexpr size_t B_BYTES = (size_t)128 * D * 2;
-  static constexpr size_t KV_BYTES = (size_t)2 * 128 * KVS * 2;
-  static constexpr size_t X_OFF = 0;
-  static constexpr size_t A_OFF = (X_OFF + X_BYTES + 127) & ~(size_t)127;
-  static constexpr size_t B_OFF = A_OFF + A_BYTES;
-  static constexpr size_t KV_OFF = B_OFF + B_BYTES;
-  static constexpr size_t SMEM = KV_OFF + KV_BYTES;
-  static constexpr uint32_t TMEM_COLS = D == 64 ? 256 : 512;
-  static constexpr uint32_t COL_Q = 0;             // Q, later the FFN output accumulator
-  static constexpr uint32_t COL_S = TMEM_COLS / 2; // scratch accumulator (<= 128 columns)
+  static constexpr int NSTG = 4 + 2 * NC;          // weight images per layer
+  static constexpr int VEC = 13 * D;               // per-layer vector floats
   // packed weight images of one layer (bytes)
   static constexpr size_t IMG_DD = (size_t)D * D * 2;
   static constexpr size_t IMG_W1 = (size_t)128 * D * 2;
   static constexpr size_t IMG_W2 = (size_t)D * 128 * 2;
-  static constexpr size_t OFF_Q = 0, OFF_K = IMG_DD, OFF_V = 2 * IMG_DD, OFF_O = 3 * IMG_DD;
+  // Wq, Wk, Wv, Wo at i * IMG_DD (i = 0 .. 3), then the FFN chunks
   static constexpr size_t OFF_W1 = 4 * IMG_DD;
   static constexpr size_t OFF_W2 = OFF_W1 + NC * IMG_W1;
   static constexpr size_t LAYER_BYTES = OFF_W2 + NC * IMG_W2;
+  static constexpr size_t SLOT = IMG_W1 > IMG_DD ? IMG_W1 : IMG_DD;
+  // shared memory
+  static constexpr size_t A_OFF = 0;
+  static constexpr size_t A_BYTES = (size_t)128 * D * 2;
+  static constexpr size_t RING_OFF = A_OFF + A_BYTES;
+  static constexpr size_t KV_OFF = RING_OFF + kSlots * SLOT;
+  static constexpr size_t KV_BYTES = (size_t)2 * 128 * KVS * 2;
+  static constexpr size_t VEC_OFF = KV_OFF + KV_BYTES;
+  static constexpr size_t STAT_OFF = VEC_OFF + (size_t)2 * VEC * 4;
+  static constexpr size_t SMEM = STAT_OFF + (size_t)2 * 128 * 8;
+  // tensor memory columns
+  static constexpr uint32_t TMEM_COLS = D == 64 ? 256 : 512;
+  static constexpr uint32_t COL_Q = 0, COL_K = D, COL_V = 2 * D;
+  static constexpr uint32_t COL_S = D;             // O-projection / W1 chunk (after K, V are drained)
+  static constexpr uint32_t COL_ACC = 0;           // FFN output (after Q is consumed)
   static_assert(KV_BYTES >= (size_t)128 * 128 * 2, "hidden chunk must fit in the K/V region");
+  static_assert(COL_S + 128 <= TMEM_COLS && 3 * D <= (int)TMEM_COLS, "TMEM plan");
+  static_assert(SLOT % 16 == 0 && IMG_W2 <= SLOT, "bulk copies are 16-byte multiples");
 };
 
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 
-// Copy a contiguous operand image global -> shared (16 B per thread-step).
-__device__ __forceinline__ void copy_image(unsigned char* dst, const unsigned char* __restrict__ src, size_t bytes) {
-  const uint4* s = reinterpret_cast<const uint4*>(src);
-  uint4* t = reinterpret_cast<uint4*>(dst);
-  for (size_t i = threadIdx.x; i < bytes / 16; i += kThreads) t[i] = __ldg(s + i);
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+
+__device__ __forceinline__ uint32_t pack_bf2(float a, float b) {
+  return (uint32_t)f2bf_bits(a) | ((uint32_t)f2bf_bits(b) << 16);
 }
 
 // Store 8 consecutive K values of `row` into a K-major operand image.
 __device__ __forceinline__ void store8(unsigned char* img, int row, int k0, int rows, const float* v) {
-  uint4 p;
-  p.x = (uint32_t)f2bf_bits(v[0]) | ((uint32_t)f2bf_bits(v[1]) << 16);
-  p.y = (uint32_t)f2bf_bits(v[2]) | ((uint32_t)f2bf_bits(v[3]) << 16);
-  p.z = (uint32_t)f2bf_bits(v[4]) | ((uint32_t)f2bf_bits(v[5]) << 16);
-  p.w = (uint32_t)f2bf_bits(v[6]) | ((uint32_t)f2bf_bits(v[7]) << 16);
-  *reinterpret_cast<uint4*>(img + tc::kmajor_offset(row, k0, rows)) = p;
+  uint4 q;
+  q.x = pack_bf2(v[0], v[1]);
+  q.y = pack_bf2(v[2], v[3]);
+  q.z = pack_bf2(v[4], v[5]);
+  q.w = pack_bf2(v[6], v[7]);
+  *reinterpret_cast<uint4*>(img + tc::kmajor_offset(row, k0, rows)) = q;
 }
 
-// LayerNorm of this thread's X row into the A operand (BF16).
+// ---- bulk-copy engine (weights global -> shared) ---------------------------
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_addr(mbar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          tc::smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(tc::smem_addr(mbar))
+      : "memory");
+}
+
+// Weight image of global stage s (layer-major; within a layer: Wq, Wk, Wv,
+// Wo, then W1 chunk c and W2 chunk c for c = 0 .. NC-1).
 template <int D>
-__device__ __forceinline__ void ln_to_a(const float* xr, const float* __restrict__ g, const float* __restrict__ b,
-                                        unsigned char* sA, int row) {
-  float mu = 0.0f;
-#pragma unroll 16
-  for (int c = 0; c < D; ++c) mu += xr[c];
-  mu *= (1.0f / D);
-  float var = 0.0f;
-#pragma unroll 16
-  for (int c = 0; c < D; ++c) {
-    const float t = xr[c] - mu;
-    var = fmaf(t, t, var);
+__device__ __forceinline__ void stage_image(int s, size_t& off, uint32_t& bytes) {
+  using G = Geo<D>;
+  const int l = s / G::NSTG, i = s - l * G::NSTG;
+  if (i < 4) {
+    off = (size_t)i * G::IMG_DD;
+    bytes = (uint32_t)G::IMG_DD;
+  } else {
+    const int c = (i - 4) >> 1;
+    if (((i - 4) & 1) == 0) {
+      off = G::OFF_W1 + (size_t)c * G::IMG_W1;
+      bytes = (uint32_t)G::IMG_W1;
+    } else {
+      off = G::OFF_W2 + (size_t)c * G::IMG_W2;
+      bytes = (uint32_t)G::IMG_W2;
+    }
   }
-  const float inv = rsqrtf(var * (1.0f / D) + kLnEps);
-#pragma unroll
-  for (int c0 = 0; c0 < D; c0 += 8) {
-    float v[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = fmaf((xr[c0 + i] - mu) * inv, __ldg(g + c0 + i), __ldg(b + c0 + i));
-    store8(sA, row, c0, 128, v);
+  off += (size_t)l * G::LAYER_BYTES;
+}
+
+// Loader state, meaningful in thread 0 (the only thread that issues copies
+// and MMAs): stage `next` is the next image to fetch; slot s % kSlots may be
+// refilled once the MMA that read stage s - kSlots has completed.
+struct Loader {
+  int next, done, total;
+};
+
+template <int D>
+__device__ __forceinline__ void pump(Loader& ld, const unsigned char* __restrict__ wimg, unsigned char* ring,
+                                     uint64_t* full) {
+  while (ld.next < ld.total && ld.next < ld.done + kSlots) {
+    size_t off;
+    uint32_t bytes;
+    stage_image<D>(ld.next, off, bytes);
+    const int slot = ld.next % kSlots;
+    mbar_expect_tx(&full[slot], bytes);
+    bulk_g2s(ring + slot * Geo<D>::SLOT, wimg + off, bytes, &full[slot]);
+    ++ld.next;
   }
 }
 
-// One MMA stage: acc[tmem_col .. +N) (+)= A[128 x K] * B[N x K]^T.
-// Publishes the operands written by every thread, issues from thread 0,
-// waits for completion.  Returns false if the bounded wait gave up.
-__device__ __forceinline__ bool mma_stage(uint32_t tmem, uint32_t a_addr, uint32_t b_addr, int N, int K,
-                                          bool accumulate, uint64_t* mbar, uint32_t& phase) {
+// acc[128 x N] (+)= A[128 x K] * B[N x K]^T, issued by the calling thread.
+__device__ __forceinline__ void issue_mma(uint32_t d_tmem, uint32_t a_addr, uint32_t b_addr, int N, int K,
+                                          bool accumulate) {
+  const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)N);
+  for (int k = 0; k < K / 16; ++k) {
+    const uint64_t ad = tc::smem_desc(a_addr + k * 2 * 128 * 16, 128 * 16, 128);
+    const uint64_t bd = tc::smem_desc(b_addr + k * 2 * N * 16, N * 16, 128);
+    tc::mma_bf16(d_tmem, ad, bd, idesc, (accumulate || k > 0) ? 1u : 0u);
+  }
+}
+
+// Make every thread's shared-memory operand writes (and TMEM reads) visible
+// before thread 0 issues the next MMA group.
+__device__ __forceinline__ void publish() {
   tc::fence_async_smem();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (threadIdx.x == 0) {
-    const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)N);
-    for (int k = 0; k < K / 16; ++k) {
-      const uint64_t ad = tc::smem_desc(a_addr + k * 2 * 128 * 16, 128 * 16, 128);
-      const uint64_t bd = tc::smem_desc(b_addr + k * 2 * N * 16, N * 16, 128);
-      tc::mma_bf16(tmem, ad, bd, idesc, (accumulate || k > 0) ? 1u : 0u);
-    }
-    tc::mma_commit(mbar);
+}
+
+// LayerNorm of a row whose two column halves live in two threads (t and
+// t + 128): each half's mean and centred sum of squares are combined
+// (pairwise update of Chan et al.), then this thread writes its half of the
+// normalised row into the BF16 A operand.  Contains a block barrier.
+template <int D>
+__device__ __forceinline__ void ln_half_to_a(const float (&x)[D / 2], const float* g, const float* b,
+                                             unsigned char* sA, float2* sStat, int row, int half) {
+  constexpr int HALF = D / 2;
+  float s = 0.0f;
+#pragma unroll
+  for (int c = 0; c < HALF; ++c) s += x[c];
+  const float m = s * (1.0f / HALF);
+  float q = 0.0f;
+#pragma unroll
+  for (int c = 0; c < HALF; ++c) {
+    const float t = x[c] - m;
+    q = fmaf(t, t, q);
   }
-  const bool ok = tc::mbar_wait(mbar, phase, 1u << 22);
-  phase ^= 1u;
-  tc::fence_after_sync();
-  return ok;
+  sStat[half * 128 + row] = make_float2(m, q);
+  __syncthreads();
+  const float2 o = sStat[(half ^ 1) * 128 + row];
+  const float mean = 0.5f * (m + o.x);
+  const float dlt = o.x - m;
+  const float m2 = q + o.y + dlt * dlt * (0.25f * D);
+  const float inv = rsqrtf(m2 * (1.0f / D) + kLnEps);
+  const int c_lo = half * HALF;
+#pragma unroll
+  for (int c0 = 0; c0 < HALF; c0 += 8) {
+    float v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = fmaf((x[c0 + i] - mean) * inv, g[c_lo + c0 + i], b[c_lo + c0 + i]);
+    store8(sA, row, c_lo + c0, 128, v);
+  }
+}
+
+// 16 BF16 values (two 16-byte words) -> FP32.
+__device__ __forceinline__ void load16_bf(const uint16_t* src, float (&v)[16]) {
+  const uint4 a = *reinterpret_cast<const uint4*>(src);
+  const uint4 b = *reinterpret_cast<const uint4*>(src + 8);
+  const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    v[2 * i] = bf_lo(w[i]);
+    v[2 * i + 1] = bf_hi(w[i]);
+  }
+}
+
+// FP32 -> 16 BF16 values (two 16-byte words).
+__device__ __forceinline__ void store16_bf(uint16_t* dst, const float (&v)[16]) {
+  uint4 a, b;
+  a.x = pack_bf2(v[0], v[1]);
+  a.y = pack_bf2(v[2], v[3]);
+  a.z = pack_bf2(v[4], v[5]);
+  a.w = pack_bf2(v[6], v[7]);
+  b.x = pack_bf2(v[8], v[9]);
+  b.y = pack_bf2(v[10], v[11]);
+  b.z = pack_bf2(v[12], v[13]);
+  b.w = pack_bf2(v[14], v[15]);
+  *reinterpret_cast<uint4*>(dst) = a;
+  *reinterpret_cast<uint4*>(dst + 8) = b;
 }
 
 template <int D>
-__global__ void __launch_bounds__(kThreads, 1) policy_fwd_kernel(PolicyDev p) {
+__global__ void __launch_bounds__(kThreads, D == 64 ? 2 : 1) policy_fwd_kernel(PolicyDev p) {
   using G = Geo<D>;
+  constexpr int HALF = G::HALF;
   extern __shared__ __align__(1024) unsigned char smem[];
-  float* sX = reinterpret_cast<float*>(smem + G::X_OFF);
   unsigned char* sA = smem + G::A_OFF;
-  unsigned char* sB = smem + G::B_OFF;
-  unsigned char* sKV = smem + G::KV_OFF;
-  uint16_t* sK = reinterpret_cast<uint16_t*>(sKV);
+  unsigned char* ring = smem + G::RING_OFF;
+  uint16_t* sK = reinterpret_cast<uint16_t*>(smem + G::KV_OFF);
   uint16_t* sV = sK + 128 * G::KVS;
-  unsigned char* sH = sKV;  // FFN hidden chunk image [128 x 128] (K/V are dead by then)
-  __shared__ __align__(8) uint64_t mbar;
+  unsigned char* sH = smem + G::KV_OFF;  // FFN hidden chunk image [128 x 128] (K/V are dead by then)
+  float* sVec = reinterpret_cast<float*>(smem + G::VEC_OFF);
+  float2* sStat = reinterpret_cast<float2*>(smem + G::STAT_OFF);
+  __shared__ __align__(8) uint64_t full[kSlots];
+  __shared__ __align__(8) uint64_t mma_bar;
   __shared__ uint32_t tmem_base_s;
   __shared__ int bad;
 
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int row = tid;
+  const int row = tid & 127, half = tid >> 7;
+  const int c_lo = half * HALF;
   const int slot = row / p.R, tok = row - slot * p.R;
   const long long ag = (long long)blockIdx.x * p.apt + slot;
   const bool agent_ok = slot < p.apt && ag < p.NA;
-  const int n_tok = agent_ok ? 1 + p.n_ent[ag] : 0;
+  const int n_tok = agent_ok ? 1 + min(max(p.n_ent[ag], 0), p.NS) : 0;
   const bool row_ok = tok < n_tok;
   const int row0 = slot * p.R;  // first row of this agent
 
@@ -160,98 +270,151 @@ __global__ void __launch_bounds__(kThreads, 1) policy_fwd_kernel(PolicyDev p) {
     tc::tmem_alloc(&tmem_base_s, G::TMEM_COLS);
     tc::tmem_relinquish();
   }
-  if (tid == 0) {
-    tc::mbar_init(&mbar, 1);
+  if (tid == 32) {
+    for (int k = 0; k < kSlots; ++k) tc::mbar_init(&full[k], 1);
+    tc::mbar_init(&mma_bar, 1);
     bad = 0;
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base_s;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-  const uint32_t tQ = tmem + lane_base + G::COL_Q, tS = tmem + lane_base + G::COL_S;
-  const uint32_t aA = tc::smem_addr(sA), aB = tc::smem_addr(sB), aH = tc::smem_addr(sH);
-  uint32_t phase = 0;
-  bool ok = true;  // all bounded waits succeeded
+  const uint32_t tl = tmem + ((uint32_t)(warp & 3) << 21);  // this warp's lane quarter (lane 32 (w % 4))
+  const uint32_t aA = tc::smem_addr(sA), aH = tc::smem_addr(sH), aRing = tc::smem_addr(ring);
+  Loader ld{0, 0, p.L * G::NSTG};
+  if (tid == 0) pump<D>(ld, p.wimg, ring, full);
+  uint32_t mphase = 0;
+  bool ok = true;  // every bounded wait of this thread succeeded
+  int s = 0;       // global weight stage
+
+  // Thread 0: wait for the images of stages s .. s + n - 1 (bounded).
+  auto wait_images = [&](int n) {
+    for (int j = 0; j < n; ++j) ok &= tc::mbar_wait(&full[(s + j) % kSlots], (uint32_t)(((s + j) / kSlots) & 1), kPolls);
+  };
+  // Every thread: wait for the MMA group just committed, then refill the ring.
+  auto wait_mma = [&](int n) {
+    ok &= tc::mbar_wait(&mma_bar, mphase, kPolls);
+    mphase ^= 1u;
+    tc::fence_after_sync();
+    s += n;
+    if (tid == 0) {
+      ld.done = s;
+      pump<D>(ld, p.wimg, ring, full);
+    }
+  };
+  auto slot_addr = [&](int stage) { return aRing + (uint32_t)((stage % kSlots) * G::SLOT); };
 
   // ---- token rows ----------------------------------------------------------
-  float* xr = sX + row * G::XS;
+  float x[HALF];
   if (row_ok && tok == 0) {
-    const uint16_t* hp = p.h + ag * D;
-#pragma unroll 8
-    for (int c = 0; c < D; ++c) xr[c] = bf_bits2f(hp[c]);
+    const uint16_t* hp = p.h + ag * D + c_lo;
+#pragma unroll
+    for (int c0 = 0; c0 < HALF; c0 += 16) {
+      float v[16];
+      load16_bf(hp + c0, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) x[c0 + i] = v[i];
+    }
   } else if (row_ok) {
     const uint4 t4 = *reinterpret_cast<const uint4*>(p.tokens + (ag * p.NS + (tok - 1)) * 8);
-    float t[8] = {bf_bits2f(t4.x & 0xFFFF), bf_bits2f(t4.x >> 16), bf_bits2f(t4.y & 0xFFFF), bf_bits2f(t4.y >> 16),
-                  bf_bits2f(t4.z & 0xFFFF), bf_bits2f(t4.z >> 16), bf_bits2f(t4.w & 0xFFFF), bf_bits2f(t4.w >> 16)};
-#pragma unroll 4
-    for (int c = 0; c < D; ++c) {
-      float acc = __ldg(p.emb_b + c);
+    const float t[8] = {bf_lo(t4.x), bf_hi(t4.x), bf_lo(t4.y), bf_hi(t4.y),
+                        bf_lo(t4.z), bf_hi(t4.z), bf_lo(t4.w), bf_hi(t4.w)};
+    const float4* w4 = reinterpret_cast<const float4*>(p.emb_w) + c_lo * 2;
 #pragma unroll
-      for (int f = 0; f < 8; ++f) acc = fmaf(__ldg(p.emb_w + c * 8 + f), t[f], acc);
-      xr[c] = acc;
+    for (int c = 0; c < HALF; ++c) {
+      const float4 wa = __ldg(w4 + 2 * c), wb = __ldg(w4 + 2 * c + 1);
+      float acc = __ldg(p.emb_b + c_lo + c);
+      acc = fmaf(wa.x, t[0], acc);
+      acc = fmaf(wa.y, t[1], acc);
+      acc = fmaf(wa.z, t[2], acc);
+      acc = fmaf(wa.w, t[3], acc);
+      acc = fmaf(wb.x, t[4], acc);
+      acc = fmaf(wb.y, t[5], acc);
+      acc = fmaf(wb.z, t[6], acc);
+      acc = fmaf(wb.w, t[7], acc);
+      x[c] = acc;
     }
   } else {
-#pragma unroll 8
-    for (int c = 0; c < D; ++c) xr[c] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < HALF; ++c) x[c] = 0.0f;
   }
 
   // Every thread runs every stage (the barriers stay uniform); a wait that
   // gave up only marks the result invalid.
   for (int l = 0; l < p.L; ++l) {
-    const unsigned char* img = p.wimg + (size_t)l * G::LAYER_BYTES;
-    const float* vec = p.vec + (size_t)l * 13 * D;
+    float* vec = sVec + (l & 1) * G::VEC;  // double-buffered: the previous layer may still read its copy
+    {
+      const float4* src = reinterpret_cast<const float4*>(p.vec + (size_t)l * G::VEC);
+      for (int i = tid; i < G::VEC / 4; i += kThreads) reinterpret_cast<float4*>(vec)[i] = __ldg(src + i);
+    }
     const float *ln1g = vec, *ln1b = vec + D, *bq = vec + 2 * D, *bk = vec + 3 * D, *bv = vec + 4 * D;
     const float *bo = vec + 5 * D, *ln2g = vec + 6 * D, *ln2b = vec + 7 * D, *b1 = vec + 8 * D, *b2 = vec + 12 * D;
 
-    // ---- attention sub-block ----
-    ln_to_a<D>(xr, ln1g, ln1b, sA, row);
-    copy_image(sB, img + G::OFF_Q, G::IMG_DD);
-    ok &= mma_stage(tmem + G::COL_Q, aA, aB, D, D, false, &mbar, phase);
-    // K and V through the scratch accumulator into shared memory
-    for (int kv = 0; kv < 2; ++kv) {
-      copy_image(sB, img + (kv == 0 ? G::OFF_K : G::OFF_V), G::IMG_DD);
-      ok &= mma_stage(tmem + G::COL_S, aA, aB, D, D, false, &mbar, phase);
-      const float* bias = kv == 0 ? bk : bv;
-      uint16_t* dst = (kv == 0 ? sK : sV) + row * G::KVS;
-#pragma unroll 1
-      for (int c0 = 0; c0 < D; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(tS + c0, v);
+    // ---- attention sub-block: Q, K, V in one MMA group ----
+    ln_half_to_a<D>(x, ln1g, ln1b, sA, sStat, row, half);  // its barrier also publishes `vec`
+    publish();
+    if (tid == 0) {
+      wait_images(3);
+      issue_mma(tmem + G::COL_Q, aA, slot_addr(s), D, D, false);
+      issue_mma(tmem + G::COL_K, aA, slot_addr(s + 1), D, D, false);
+      issue_mma(tmem + G::COL_V, aA, slot_addr(s + 2), D, D, false);
+      tc::mma_commit(&mma_bar);
+    }
+    wait_mma(3);
+    // K and V (+ bias) -> shared memory as BF16, this thread's half of the columns
 #pragma unroll
-        for (int i = 0; i < 16; i += 2) {
-          const uint32_t pk = (uint32_t)f2bf_bits(v[i] + __ldg(bias + c0 + i)) |
-                              ((uint32_t)f2bf_bits(v[i + 1] + __ldg(bias + c0 + i + 1)) << 16);
-          *reinterpret_cast<uint32_t*>(dst + c0 + i) = pk;
-        }
+    for (int kv = 0; kv < 2; ++kv) {
+      const float* bias = kv == 0 ? bk : bv;
+      uint16_t* dst = (kv == 0 ? sK : sV) + row * G::KVS + c_lo;
+#pragma unroll
+      for (int c0 = 0; c0 < HALF; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(tl + (kv == 0 ? G::COL_K : G::COL_V) + c_lo + c0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] += bias[c_lo + c0 + i];
+        store16_bf(dst + c0, v);
       }
     }
     __syncthreads();  // K, V of every row visible
-    // per-head softmax attention over the agent's valid tokens
+    // per-head softmax attention over the agent's valid tokens (this
+    // thread's heads: half * HH .. +HH); scores stay in registers
 #pragma unroll 1
-    for (int h = 0; h < G::H; ++h) {
+    for (int hh = 0; hh < G::HH; ++hh) {
+      const int h = half * G::HH + hh;
       float q[16];
-      tc::tmem_ld16(tQ + h * 16, q);
+      tc::tmem_ld16(tl + G::COL_Q + h * 16, q);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) q[i] = (q[i] + bq[h * 16 + i]) * 0.25f;  // 1 / sqrt(16)
       float o[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        q[i] = (q[i] + __ldg(bq + h * 16 + i)) * 0.25f;  // 1 / sqrt(16)
-        o[i] = 0.0f;
-      }
+      for (int i = 0; i < 16; ++i) o[i] = 0.0f;
       if (row_ok) {
-        float m = -INFINITY, den = 0.0f;
-        for (int j = 0; j < n_tok; ++j) {
-          const uint16_t* kr = sK + (row0 + j) * G::KVS + h * 16;
-          const uint16_t* vr = sV + (row0 + j) * G::KVS + h * 16;
-          float s = 0.0f;
+        float sc[kMaxTok];
+        float m = -INFINITY;
 #pragma unroll
-          for (int i = 0; i < 16; ++i) s = fmaf(q[i], bf_bits2f(kr[i]), s);
-          const float mn = fmaxf(m, s);
-          const float corr = __expf(m - mn), e = __expf(s - mn);
-          den = den * corr + e;
+        for (int j = 0; j < kMaxTok; ++j) {
+          sc[j] = -INFINITY;
+          if (j < n_tok) {
+            float kr[16];
+            load16_bf(sK + (row0 + j) * G::KVS + h * 16, kr);
+            float a = 0.0f;
 #pragma unroll
-          for (int i = 0; i < 16; ++i) o[i] = fmaf(e, bf_bits2f(vr[i]), o[i] * corr);
-          m = mn;
+            for (int i = 0; i < 16; ++i) a = fmaf(q[i], kr[i], a);
+            sc[j] = a;
+            m = fmaxf(m, a);
+          }
+        }
+        float den = 0.0f;
+#pragma unroll
+        for (int j = 0; j < kMaxTok; ++j) {
+          if (j < n_tok) {
+            const float e = __expf(sc[j] - m);
+            den += e;
+            float vr[16];
+            load16_bf(sV + (row0 + j) * G::KVS + h * 16, vr);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) o[i] = fmaf(e, vr[i], o[i]);
+          }
         }
         const float inv = 1.0f / den;
 #pragma unroll
@@ -260,79 +423,132 @@ __global__ void __launch_bounds__(kThreads, 1) policy_fwd_kernel(PolicyDev p) {
       store8(sA, row, h * 16, 128, o);
       store8(sA, row, h * 16 + 8, 128, o + 8);
     }
-    copy_image(sB, img + G::OFF_O, G::IMG_DD);
-    ok &= mma_stage(tmem + G::COL_S, aA, aB, D, D, false, &mbar, phase);
-#pragma unroll 1
-    for (int c0 = 0; c0 < D; c0 += 16) {
-      float v[16];
-      tc::tmem_ld16(tS + c0, v);
+    publish();
+    if (tid == 0) {
+      wait_images(1);
+      issue_mma(tmem + G::COL_S, aA, slot_addr(s), D, D, false);
+      tc::mma_commit(&mma_bar);
+    }
+    wait_mma(1);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) xr[c0 + i] += v[i] + __ldg(bo + c0 + i);
+    for (int c0 = 0; c0 < HALF; c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(tl + G::COL_S + c_lo + c0, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) x[c0 + i] += v[i] + bo[c_lo + c0 + i];
     }
 
     // ---- feed-forward sub-block ----
-    ln_to_a<D>(xr, ln2g, ln2b, sA, row);
+    ln_half_to_a<D>(x, ln2g, ln2b, sA, sStat, row, half);
 #pragma unroll 1
     for (int c = 0; c < G::NC; ++c) {
-      copy_image(sB, img + G::OFF_W1 + c * G::IMG_W1, G::IMG_W1);
-      ok &= mma_stage(tmem + G::COL_S, aA, aB, 128, D, false, &mbar, phase);
-#pragma unroll 1
-      for (int c0 = 0; c0 < 128; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(tS + c0, v);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = gelu(v[i] + __ldg(b1 + c * 128 + c0 + i));
-        store8(sH, row, c0, 128, v);
-        store8(sH, row, c0 + 8, 128, v + 8);
+      publish();
+      if (tid == 0) {
+        wait_images(1);
+        issue_mma(tmem + G::COL_S, aA, slot_addr(s), 128, D, false);
+        tc::mma_commit(&mma_bar);
       }
-      copy_image(sB, img + G::OFF_W2 + c * G::IMG_W2, G::IMG_W2);
-      ok &= mma_stage(tmem + G::COL_Q, aH, aB, D, 128, c > 0, &mbar, phase);
-    }
-#pragma unroll 1
-    for (int c0 = 0; c0 < D; c0 += 16) {
-      float v[16];
-      tc::tmem_ld16(tQ + c0, v);
+      wait_mma(1);
+      // GELU of this thread's 64 hidden units of the chunk -> BF16 operand
 #pragma unroll
-      for (int i = 0; i < 16; ++i) xr[c0 + i] += v[i] + __ldg(b2 + c0 + i);
+      for (int c0 = 0; c0 < 64; c0 += 16) {
+        float v[16];
+        const int hc = half * 64 + c0;
+        tc::tmem_ld16(tl + G::COL_S + hc, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = gelu(v[i] + b1[c * 128 + hc + i]);
+        store8(sH, row, hc, 128, v);
+        store8(sH, row, hc + 8, 128, v + 8);
+      }
+      publish();
+      if (tid == 0) {
+        wait_images(1);
+        issue_mma(tmem + G::COL_ACC, aH, slot_addr(s), D, 128, c > 0);
+        tc::mma_commit(&mma_bar);
+      }
+      wait_mma(1);
+    }
+#pragma unroll
+    for (int c0 = 0; c0 < HALF; c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(tl + G::COL_ACC + c_lo + c0, v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) x[c0 + i] += v[i] + b2[c_lo + c0 + i];
     }
   }
 
   // ---- head on the recurrent token ----------------------------------------
-  if (!ok && tid == 0) atomicExch(&bad, 1);
-  if (agent_ok && tok == 0 && ok) {
-    uint16_t* hp = p.h + ag * D;
-    float mu = 0.0f, var = 0.0f;
-    for (int c = 0; c < D; ++c) {
-      hp[c] = f2bf_bits(xr[c]);
-      mu += xr[c];
+  // The recurrent rows' X goes to shared memory (the K/V region is free once
+  // the last MMA has completed); one thread per (agent, action) computes a
+  // logit, then one thread per agent draws the action.
+  float* sXr = reinterpret_cast<float*>(smem + G::KV_OFF);
+  float* sLog = sXr + p.apt * D;
+  if (!ok) atomicExch(&bad, 1);
+  if (agent_ok && tok == 0) {
+    uint16_t* hp = p.h + ag * D + c_lo;
+#pragma unroll
+    for (int c0 = 0; c0 < HALF; c0 += 16) {
+      float v[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        v[i] = x[c0 + i];
+        sXr[slot * D + c_lo + c0 + i] = v[i];
+      }
+      store16_bf(hp + c0, v);
     }
-    mu *= (1.0f / D);
-    for (int c = 0; c < D; ++c) var = fmaf(xr[c] - mu, xr[c] - mu, var);
-    const float inv = rsqrtf(var * (1.0f / D) + kLnEps);
-    float best = -INFINITY;
-    int arg = 0;
-    const uint32_t g = p.counters ? p.counters[0] + 1u : p.step;
-    for (int j = 0; j < p.n_act; ++j) {
-      float acc = __ldg(p.head_b + j);
+  }
+  __syncthreads();
+  const bool good = bad == 0;
+  const int n_act = p.n_act;
+  for (int t = tid; t < p.apt * n_act; t += kThreads) {
+    const int sl = t / n_act, j = t - sl * n_act;
+    const long long a2 = (long long)blockIdx.x * p.apt + sl;
+    float acc = 0.0f;
+    if (a2 < p.NA && good) {
+      const float* xr = sXr + sl * D;
+      float mu = 0.0f;
+      for (int c = 0; c < D; ++c) mu += xr[c];
+      mu *= (1.0f / D);
+      float var = 0.0f;
+      for (int c = 0; c < D; ++c) var = fmaf(xr[c] - mu, xr[c] - mu, var);
+      const float inv = rsqrtf(var * (1.0f / D) + kLnEps);
+      acc = __ldg(p.head_b + j);
+      const float* w = p.head_w + j * D;
       for (int c = 0; c < D; ++c)
-        acc = fmaf(__ldg(p.head_w + j * D + c), fmaf((xr[c] - mu) * inv, __ldg(p.lnf_g + c), __ldg(p.lnf_b + c)),
-                   acc);
-      p.logits[ag * p.n_act + j] = acc;
-      if (p.sample) {
-        Rand4 r = philox((uint32_t)ag, (uint32_t)(j >> 2), g, TAG_GUMBEL, p.seed);
+        acc = fmaf(__ldg(w + c), fmaf((xr[c] - mu) * inv, __ldg(p.lnf_g + c), __ldg(p.lnf_b + c)), acc);
+      p.logits[a2 * n_act + j] = acc;
+    }
+    sLog[t] = acc;
+  }
+  __syncthreads();
+  if (p.sample && good && tid < p.apt) {
+    const long long a2 = (long long)blockIdx.x * p.apt + tid;
+    if (a2 < p.NA) {
+      const uint32_t g = p.counters ? p.counters[0] + 1u : p.step;
+      float best = -INFINITY;
+      int arg = 0;
+      for (int j = 0; j < n_act; ++j) {
+        Rand4 r = philox(p.gid_agent + (uint32_t)a2, (uint32_t)(j >> 2), g, TAG_GUMBEL, p.seed);
         const float gum = -logf(-logf(unif_mid(r.x[j & 3])));
-        if (acc + gum > best) {
-          best = acc + gum;
+        const float z = sLog[tid * n_act + j] + gum;
+        if (z > best) {
+          best = z;
           arg = j;
         }
       }
+      p.actions[a2] = arg;
     }
-    if (p.sample) p.actions[ag] = arg;
   }
 
+  // no copy may still be landing in shared memory when the CTA exits
+  if (tid == 0 && !good)
+    for (int k = 0; k < kSlots && k < ld.next; ++k) {
+      const int last = ld.next - 1 - ((ld.next - 1 - k) % kSlots);  // last stage fetched into slot k
+      tc::mbar_wait(&full[k], (uint32_t)((last / kSlots) & 1), kPolls);
+    }
   tc::fence_before_sync();
   __syncthreads();
-  if (bad && tid == 0) raise_status(p.status, 2);
+  if (good == false && tid == 0) raise_status(p.status, 2);
   if (warp == 0) tc::tmem_dealloc(tmem, G::TMEM_COLS);
 }
 

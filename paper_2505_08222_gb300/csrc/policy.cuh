@@ -28,6 +28,7 @@ struct PolicyDev {
   const float* head_w;        // [n_act][d]
   const float* head_b;        // [n_act]
   uint64_t seed;
+  uint32_t gid_agent;         // global id of agent 0 (sharded batches)
   const uint32_t* counters;   // step counter (g = counters[0] + 1), or NULL: use `step`
   uint32_t step;
   int sample;                 // draw Gumbel-max actions

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kNoallocWarps * 32) noalloc_lists_kernel(EnvDe
     const int a = p / T, k = p - a * T;
     const float dx = s_ax[wid][a] - s_tx[wid][k], dy = s_ay[wid][a] - s_ty[wid][k], dz = 0.0f - s_tz[wid][k];
     const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
-    Rand4 r = philox((uint32_t)(f0 + p), 0u, g, TAG_PING, d.seed);
+    Rand4 r = philox(d.gid_filter + (uint32_t)(f0 + p), 0u, g, TAG_PING, d.seed);
     float n0, n1;
     box_muller(r.x[0], r.x[1], n0, n1);
     const int v = dist <= d.det_radius;
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kNoallocWarps * 32) noalloc_lists_kernel(EnvDe
     int rcv = 1;
     if (a != b) {
       const float dx = s_ax[wid][a] - s_ax[wid][b], dy = s_ay[wid][a] - s_ay[wid][b];
-      Rand4 r = philox((uint32_t)(a0 + a), (uint32_t)b, g, TAG_COMM, d.seed);
+      Rand4 r = philox(d.gid_agent + (uint32_t)(a0 + a), (uint32_t)b, g, TAG_COMM, d.seed);
       rcv = (sqrtf(dx * dx + dy * dy) <= d.comm_radius) && !(unif(r.x[0]) < d.comm_drop);
     }
     s_recv[wid][a * kMaxAgents + b] = rcv;

@@ -72,6 +72,11 @@ class EnvParams:
     spawn_tries: int = 64
     feature_scale: float = FEATURE_SCALE
     est_scale: float = 100.0
+    # global ids of the first env / agent / target / filter (sharded batches)
+    id_env0: int = 0
+    id_agent0: int = 0
+    id_target0: int = 0
+    id_filter0: int = 0
     # transformer agent; d_model == 0 means no policy (random actions)
     d_model: int = 0
     n_layers: int = 0

