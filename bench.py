@@ -264,6 +264,38 @@ def run_reference(args):
     return 0
 
 
+PF_SOURCES = ("pf_kernel.cuh", "pf_kernel.cu", "pf_inst_a.cu", "pf_inst_b.cu", "pf_variants.h", "common.cuh",
+              "env.cuh")
+TRAFFIC_NOTE = os.path.join(ROOT, "profiles", "pf_step_kernel_fleet5.md")
+
+
+def pf_source_hash() -> str:
+    """SHA-256 (first 16 hex digits) over the filter kernel's sources."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in PF_SOURCES:
+        with open(os.path.join(ROOT, "paper_2505_08222_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _pf_traffic(variant: str, particles: int):
+    """DRAM bytes per launch from the committed ncu summary: its line
+    `traffic: variant=V sources=H bytes_per_particle=B` applies only while
+    the kernel sources still hash to H and the launch variant is V; the
+    capture's bytes per particle are scaled to this launch's particles."""
+    try:
+        for line in open(TRAFFIC_NOTE):
+            if line.startswith("traffic:"):
+                kv = dict(t.split("=", 1) for t in line.split()[1:])
+                if kv.get("variant") == variant and kv.get("sources") == pf_source_hash():
+                    return float(kv["bytes_per_particle"]) * particles
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -289,7 +321,12 @@ def run_ours(args):
     if p.d_model > 0 and hasattr(env, "set_policy"):
         env.set_policy(synth.policy_params(synth.PolicyDims(p.d_model, p.n_layers, p.n_heads, p.n_actions)))
     env.reset(1000)
-    if not args.no_autotune:
+    if args.pf_variant:
+        names = {ut.lib.pf_variant_label(v).decode(): v for v in env.pf_variants()}
+        if args.pf_variant not in names:
+            raise SystemExit(f"--pf-variant: {args.pf_variant!r} not usable here; choose from {sorted(names)}")
+        env.set_pf_variant(names[args.pf_variant])
+    elif not args.no_autotune:
         env.autotune(5)  # picks the filter launch variant, then the episode restarts
         env.reset(1000)
     stream = torch.cuda.current_stream()
@@ -326,8 +363,12 @@ def run_ours(args):
         dist.barrier()
     agent_steps = float(shard.reduce_sums([stats["agent_steps"]])[0])
     # dominant-kernel duration: CUDA events around each particle-filter launch
-    # on its stream, over K eager steps of the same workload right after the
-    # timed graph run (events recorded by graph nodes cannot be timed)
+    # on its stream (events recorded by graph nodes cannot be timed), over an
+    # eager replay of the timed steps: same seed, W untimed steps, then the
+    # same K steps the graph ran
+    env.reset(1000)
+    for _ in range(W):
+        env.step()
     env.profile(True)
     for _ in range(K):
         env.step()
@@ -340,15 +381,7 @@ def run_ours(args):
     bytes_per_launch = env.F * env.P * BYTES_PER_PARTICLE
     pf_avg_ms = pf_ms / max(pf_launches, 1)
     achieved = bytes_per_launch / (pf_avg_ms / 1e3) / 1e9
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "pf_step_traffic.json")
-    if os.path.exists(tr_path):
-        try:
-            tr = json.load(open(tr_path))
-            if tr.get("workload") == args.workload and tr.get("variant") == env.pf_variant_name():
-                traffic = tr.get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = _pf_traffic(env.pf_variant_name(), env.F * env.P)
 
     # end to end through the C ABI with host buffers: per step, host actions
     # (pinned) -> device, env_step, reward + done -> pinned host
@@ -395,7 +428,7 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                          "kernel": "pf_step_kernel", "avg_launch_ms": pf_avg_ms, "launches": pf_launches,
-                         "timing": "CUDA events around each launch, K eager steps after the timed graph run",
+                         "timing": "CUDA events around each launch on its stream, eager replay of the K timed steps (same seed and warm-up)",
                          "peak_kind": f"{peak_kind} copy bandwidth (burst)",
                          "algorithmic_bytes_per_launch": bytes_per_launch},
             "e2e": {"value": e2e_value, "unit": "agent-steps/s", "h2d_bytes_per_step": NA * 4,
@@ -427,6 +460,7 @@ def main():
     ap.add_argument("--workload", default="fleet5")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--pf-variant", default=None, help="fixed filter launch variant (e.g. nt512x4m3), no autotune")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-estimator form")
     ap.add_argument("--train-rows", type=int, default=10_000_000)
     ap.add_argument("--train-steps", type=int, default=3000)
