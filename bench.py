@@ -172,12 +172,18 @@ def learned_form(args, p, K, W, rank):
     steps_rec = max(1, args.train_rows // F)
     X = torch.empty((steps_rec * F, 96), dtype=torch.float32, device="cuda")
     Y = torch.empty((steps_rec * F, 2), dtype=torch.float32, device="cuda")
+    T_eval = args.eval_steps
+    LEARNED = 2  # est_set_mode: the network also moves the estimate on steps without a fresh ping
 
-    def record(t0_step, n_steps, seed, learned):
+    def record(t0_step, n_rec, seed, learned):
+        # one episode from reset, long enough to span the evaluation horizon;
+        # every `every`-th step is recorded
+        every = max(1, -(-T_eval // n_rec))
         env.est_set_mode(learned)
         env.reset(seed)
-        for t in range(t0_step, t0_step + n_steps):
-            env.step()
+        for t in range(t0_step, t0_step + n_rec):
+            for _ in range(every):
+                env.step()
             env.est_record(X[t * F:(t + 1) * F], Y[t * F:(t + 1) * F])
         env.est_set_mode(False)
 
@@ -195,7 +201,7 @@ def learned_form(args, p, K, W, rank):
     losses = [tr["loss_last"]]
     train_ms = tr["ms"]
     for r, (a, n) in enumerate([(half, quarter), (half + quarter, steps_rec - half - quarter)]):
-        record(a, n, 7100 + 10 * r + rank, True)
+        record(a, n, 7100 + 10 * r + rank, LEARNED)
         upto = (a + n) * F
         tr = env.est_train(X[:upto], Y[:upto], steps=args.train_steps // 2, batch=16384, lr=5e-4, seed=rank + r + 1,
                            huber=1.0)
@@ -206,17 +212,16 @@ def learned_form(args, p, K, W, rank):
     del X, Y
     torch.cuda.empty_cache()
 
-    def eval_rmse(learned: bool, seed: int, T: int) -> float:
+    def eval_rmse(learned: int, seed: int, T: int) -> float:
         env.est_set_mode(learned)
         env.reset(seed)
         return env.rollout(T)["rmse"]
 
-    T_eval = args.eval_steps
     seeds = [9000 + rank, 9100 + rank]
     pf_rmse = [eval_rmse(False, s, T_eval) for s in seeds]
-    le_rmse = [eval_rmse(True, s, T_eval) for s in seeds]
+    le_rmse = [eval_rmse(LEARNED, s, T_eval) for s in seeds]
     # timed learned-form rollout
-    env.est_set_mode(True)
+    env.est_set_mode(LEARNED)
     env.reset(1000 + rank)
     for _ in range(W):
         env.step()
@@ -242,8 +247,10 @@ def learned_form(args, p, K, W, rank):
             "estimator_kernel_ms": est_ms / max(est_n, 1),
             "rmse_m": le_mean, "pf_rmse_m": pf_mean, "rmse_ratio": le_mean / pf_mean,
             "eval": f"{len(seeds)} held-out seeds x {T_eval} steps each form, pooled RMSE per run, mean over seeds",
+            "stale_rule": "network applied on steps without a fresh ping too (est_set_mode 2)",
             "train": {"rows": steps_rec * F, "wall_s": rec_s, "steps": 2 * args.train_steps, "batch": 16384,
-                      "schedule": "50% filter-driven rows, then 2 x 25% network-driven rows (retrain each)",
+                      "schedule": "50% filter-driven rows, then 2 x 25% network-driven rows (retrain each); each "
+                                  "round one episode over the evaluation horizon, rows every k-th step",
                       "loss_last_per_round": losses, "train_ms": train_ms, "loss": "Huber, delta = 1 L"}}
 
 

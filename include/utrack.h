@@ -330,8 +330,12 @@ typedef struct ut_est_train_stats {
 ut_status est_set_weights(ut_env* env, const float* params_host, int64_t n_params);
 /* Copies the FP32 master weights out (synchronising). */
 ut_status est_get_weights(ut_env* env, float* params_host, int64_t n_params);
-/* 0: particle filter (default); 1: the learned estimator replaces the filter
- * stage of every step (needs weights and a handle created with UT_FLAG_RING). */
+/* 0: particle filter (default); 1-3: the learned estimator replaces the
+ * filter stage of every step (needs weights and a handle created with
+ * UT_FLAG_RING).  On a step without a fresh ping the estimate is held (1),
+ * moved by the network all the same (2), or coasts by its last motion e1 - e2
+ * (3, constant velocity); with a fresh ping the network's correction applies.
+ * Errors: UT_ERR_INVALID (mode outside 0..3), UT_ERR_STATE. */
 ut_status est_set_mode(ut_env* env, int32_t mode);
 /* Raw network outputs out_dev [n_rows][2] of features X_dev [n_rows][96]. */
 ut_status est_forward(ut_env* env, const float* X_dev, float* out_dev, int64_t n_rows);

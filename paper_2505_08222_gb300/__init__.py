@@ -208,8 +208,11 @@ class Env:
         _check(lib.est_get_weights(self.h, out.ctypes.data_as(ctypes.c_void_p), out.size), self.h, "est_get_weights")
         return out
 
-    def est_set_mode(self, learned: bool):
-        _check(lib.est_set_mode(self.h, 1 if learned else 0), self.h, "est_set_mode")
+    def est_set_mode(self, mode):
+        """0 / False: particle filter; 1 / True: learned estimator, estimate held
+        on steps without a fresh ping; 2: network on every step; 3: coast at the
+        estimate's last motion on steps without a fresh ping."""
+        _check(lib.est_set_mode(self.h, int(mode)), self.h, "est_set_mode")
 
     def est_forward(self, X: torch.Tensor) -> torch.Tensor:
         assert X.is_cuda and X.dtype == torch.float32 and X.shape[-1] == 96

@@ -472,7 +472,7 @@ static ut_status graph_ensure(ut_env* h, int32_t T) {
     UT_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     UT_CUDA(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   }
-  const int key = T * 4 + (h->policy_ready ? 1 : 0) + (h->est_mode ? 2 : 0);
+  const int key = T * 8 + (h->policy_ready ? 1 : 0) + 2 * h->est_mode;
   if (!h->graph_exec || h->graph_key != key || h->graph_variant != h->pf_variant) {
     if (h->graph_exec) {
       cudaGraphExecDestroy(h->graph_exec);

@@ -84,6 +84,7 @@ struct FwdArgs {
   float* z;     // training: [3][B][256], else NULL
   uint16_t* a;  // training: [3][B][256], else NULL
   EnvDev d;     // env mode
+  int stale;    // env mode, steps without a fresh ping: 0 hold, 1 network, 2 coast at e1 - e2
   int* status;
 };
 
@@ -202,12 +203,18 @@ __global__ void __launch_bounds__(kT, 1) fwd_kernel(FwdArgs p) {
       const int f = (int)b;
       const int it = p.d.filt_target[f];
       // Bounded update (dropped if not finite): with a ping received this step
-      // the estimate may move up to kMaxCorr L; without one it is held, so
-      // that stale inputs cannot drive the closed loop away.
+      // the estimate may move up to kMaxCorr L.  Without one, the rule chosen
+      // by the mode applies: hold the estimate (stale inputs cannot drive the
+      // closed loop away), apply the network all the same, or coast by the
+      // estimate's last motion e1 - e2 (constant velocity).
       const bool fresh = x[3] == 0.0f && x[4] == 1.0f;
-      const float lim = fresh ? kMaxCorr : 0.0f;
-      const float c0 = isfinite(o0) ? fminf(fmaxf(o0, -lim), lim) : 0.0f;
-      const float c1 = isfinite(o1) ? fminf(fmaxf(o1, -lim), lim) : 0.0f;
+      const float lim = (fresh || p.stale == 1) ? kMaxCorr : 0.0f;
+      float c0 = isfinite(o0) ? fminf(fmaxf(o0, -lim), lim) : 0.0f;
+      float c1 = isfinite(o1) ? fminf(fmaxf(o1, -lim), lim) : 0.0f;
+      if (!fresh && p.stale == 2) {
+        c0 = fminf(fmaxf(x[5 * kRing], -kMaxCorr), kMaxCorr);
+        c1 = fminf(fmaxf(x[5 * kRing + 1], -kMaxCorr), kMaxCorr);
+      }
       const float ex = e1x + p.d.est_scale * c0, ey = e1y + p.d.est_scale * c1;
       p.d.prev2_estx[f] = p.d.prev_estx[f];
       p.d.prev2_esty[f] = p.d.prev_esty[f];
@@ -542,7 +549,7 @@ cudaError_t launch_forward(const Net& net, const float* X, const int32_t* rows, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_forward_env(const Net& net, const EnvDev& d, cudaStream_t s) {
+cudaError_t launch_forward_env(const Net& net, const EnvDev& d, int stale, cudaStream_t s) {
   static int ready = 0;
   cudaError_t e = smem_optin(fwd_kernel<true>, kFwdSmem, ready);
   if (e != cudaSuccess) return e;
@@ -551,6 +558,7 @@ cudaError_t launch_forward_env(const Net& net, const EnvDev& d, cudaStream_t s) 
   memset(&p, 0, sizeof(p));
   p.net = net;
   p.d = d;
+  p.stale = stale;
   p.status = d.status;
   fwd_kernel<true><<<(d.F + kT - 1) / kT, kT, kFwdSmem, s>>>(p);
   return cudaGetLastError();

@@ -63,7 +63,7 @@ struct TrainBufs {
 
 cudaError_t launch_forward(const Net& net, const float* X, const int32_t* rows, int B, float* out, float* z,
                            uint16_t* a, cudaStream_t s);
-cudaError_t launch_forward_env(const Net& net, const EnvDev& d, cudaStream_t s);
+cudaError_t launch_forward_env(const Net& net, const EnvDev& d, int stale, cudaStream_t s);
 cudaError_t launch_record(const EnvDev& d, float* feat, float* label, cudaStream_t s);
 cudaError_t launch_backward(const Net& net, const TrainBufs& t, cudaStream_t s);
 cudaError_t launch_adam(float* master, float* m, float* v, const float* grad, int step, float lr, float beta1,

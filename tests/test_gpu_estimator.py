@@ -185,3 +185,39 @@ def test_learned_mode_step_uses_network():
     e1 = np.stack([st["prev_estx"].cpu().numpy(), st["prev_esty"].cpu().numpy()], 1)
     np.testing.assert_allclose(est, e1 + 100.0 * pred.cpu().numpy(), atol=2e-3)
     env.est_set_mode(False)
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+def test_learned_mode_stale_rules(mode):
+    """With a short detection radius many filters get no ping; their update
+    follows the mode's rule (hold / network / coast by e1 - e2), while filters
+    with a fresh ping take the network's clamped correction in every mode."""
+    env, p = _env(n_envs=32, det_radius=120.0)
+    params = synth.mlp_params(seed=17, bias_scale=0.1)
+    env.est_set_weights(params)
+    env.reset(5)
+    for _ in range(3):
+        env.step()
+    env.est_set_mode(mode)
+    F = env.F
+    feat = torch.empty((F, 96), device="cuda")
+    lab = torch.empty((F, 2), device="cuda")
+    out = env.step()
+    env.est_record(feat, lab)
+    st = env.state()
+    X = feat.cpu().numpy()
+    corr = np.clip(env.est_forward(feat).cpu().numpy(), -3.0, 3.0)
+    est = np.stack([out["estx"].cpu().numpy(), out["esty"].cpu().numpy()], 1)
+    e1 = np.stack([st["prev_estx"].cpu().numpy(), st["prev_esty"].cpu().numpy()], 1)
+    fresh = (X[:, 3] == 0) & (X[:, 4] == 1)
+    assert 0 < fresh.sum() < F, fresh.sum()
+    np.testing.assert_allclose(est[fresh], e1[fresh] + 100.0 * corr[fresh], atol=2e-3)
+    stale = ~fresh
+    if mode == 1:
+        want = e1[stale]
+    elif mode == 2:
+        want = e1[stale] + 100.0 * corr[stale]
+    else:
+        want = e1[stale] + 100.0 * np.clip(X[stale, 80:82], -3.0, 3.0)
+    np.testing.assert_allclose(est[stale], want, atol=2e-3)
+    env.est_set_mode(0)
