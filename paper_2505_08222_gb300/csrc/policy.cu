@@ -3,9 +3,10 @@
 // Each agent's tokens are its recurrent embedding h followed by its entity
 // vectors (self, teammates, targets; observation tokens of Sec. III-A.2).
 // Agents are packed R = 1 + max entities rows apart into 128-row tiles.  One
-// CTA of 256 threads owns a tile: thread t works on row t % 128 and on the
-// column half t / 128 of that row, keeping its half of the residual stream X
-// in registers from start to end:
+// CTA of 128 NS threads owns a tile (NS = 2 column parts for d = 64, 4 for
+// d = 128): thread t works on row t % 128 and on column part t / 128 of that
+// row, keeping its part of the residual stream X in registers from start to
+// end:
 //
 //   X = [h ; W_emb tok + b_emb]                         (CUDA cores, FP32)
 //   per block l:   Y = LN1(X) -> BF16 operand A
@@ -13,7 +14,7 @@
 //                      groups issued together, FP32 in TMEM)
 //                  O = softmax(Q K^T / 4) V per head, within the agent's
 //                      valid tokens                      (CUDA cores, each
-//                      column half takes half the heads)
+//                      column part takes H / NS heads)
 //                  X += O Wo^T + bo                      (tcgen05.mma)
 //                  X += W2 GELU(W1 LN2(X) + b1) + b2      (tcgen05.mma, hidden
 //                      units in chunks of 128 accumulated in TMEM)
@@ -39,7 +40,6 @@
 namespace ut {
 namespace {
 
-constexpr int kThreads = 256;
 constexpr int kSlots = 3;                                  // weight ring depth
 constexpr int kMaxTok = 1 + UT_MAX_AGENTS + UT_MAX_TARGETS;  // tokens per agent
 constexpr float kLnEps = 1e-5f;
@@ -48,8 +48,11 @@ constexpr uint32_t kPolls = 1u << 22;                      // bounded mbarrier w
 template <int D>
 struct Geo {
   static constexpr int H = D / 16;                 // heads of width 16
-  static constexpr int HALF = D / 2;               // columns per thread
-  static constexpr int HH = H / 2;                 // heads per thread
+  static constexpr int NS = D == 64 ? 2 : 4;       // column parts per row
+  static constexpr int THREADS = 128 * NS;
+  static constexpr int COLS = D / NS;              // columns per thread
+  static constexpr int HH = H / NS;                // heads per thread
+  static constexpr int HCOLS = 128 / NS;           // hidden units per thread in an FFN chunk
   static constexpr int KVS = D + 8;                // bf16 row stride of K / V
   static constexpr int NC = (4 * D) / 128;         // FFN hidden chunks of 128
   static constexpr int NSTG = 4 + 2 * NC;          // weight images per layer
@@ -71,7 +74,7 @@ struct Geo {
   static constexpr size_t KV_BYTES = (size_t)2 * 128 * KVS * 2;
   static constexpr size_t VEC_OFF = KV_OFF + KV_BYTES;
   static constexpr size_t STAT_OFF = VEC_OFF + (size_t)2 * VEC * 4;
-  static constexpr size_t SMEM = STAT_OFF + (size_t)2 * 128 * 8;
+  static constexpr size_t SMEM = STAT_OFF + (size_t)NS * 128 * 8;
   // tensor memory columns
   static constexpr uint32_t TMEM_COLS = D == 64 ? 256 : 512;
   static constexpr uint32_t COL_Q = 0, COL_K = D, COL_V = 2 * D;
@@ -192,34 +195,46 @@ __device__ __forceinline__ void publish() {
   tc::fence_after_sync();
 }
 
-// LayerNorm of a row whose two column halves live in two threads (t and
-// t + 128): each half's mean and centred sum of squares are combined
-// (pairwise update of Chan et al.), then this thread writes its half of the
-// normalised row into the BF16 A operand.  Contains a block barrier.
+// LayerNorm of a row whose NS column parts live in NS threads (t, t + 128,
+// ...): each part's mean and centred sum of squares are combined (pairwise
+// update of Chan et al. for equal counts), then this thread writes its part
+// of the normalised row into the BF16 A operand.  Contains a block barrier.
 template <int D>
-__device__ __forceinline__ void ln_half_to_a(const float (&x)[D / 2], const float* g, const float* b,
-                                             unsigned char* sA, float2* sStat, int row, int half) {
-  constexpr int HALF = D / 2;
+__device__ __forceinline__ void ln_part_to_a(const float (&x)[Geo<D>::COLS], const float* g, const float* b,
+                                             unsigned char* sA, float2* sStat, int row, int part) {
+  constexpr int NS = Geo<D>::NS, COLS = Geo<D>::COLS;
   float s = 0.0f;
 #pragma unroll
-  for (int c = 0; c < HALF; ++c) s += x[c];
-  const float m = s * (1.0f / HALF);
+  for (int c = 0; c < COLS; ++c) s += x[c];
+  const float m = s * (1.0f / COLS);
   float q = 0.0f;
 #pragma unroll
-  for (int c = 0; c < HALF; ++c) {
+  for (int c = 0; c < COLS; ++c) {
     const float t = x[c] - m;
     q = fmaf(t, t, q);
   }
-  sStat[half * 128 + row] = make_float2(m, q);
+  sStat[part * 128 + row] = make_float2(m, q);
   __syncthreads();
-  const float2 o = sStat[(half ^ 1) * 128 + row];
-  const float mean = 0.5f * (m + o.x);
-  const float dlt = o.x - m;
-  const float m2 = q + o.y + dlt * dlt * (0.25f * D);
-  const float inv = rsqrtf(m2 * (1.0f / D) + kLnEps);
-  const int c_lo = half * HALF;
+  float2 st[NS];
+  float mean = 0.0f;
 #pragma unroll
-  for (int c0 = 0; c0 < HALF; c0 += 8) {
+  for (int k = 0; k < NS; ++k) {
+    st[k] = sStat[k * 128 + row];
+    mean += st[k].x;
+  }
+  mean *= (1.0f / NS);
+  float m2 = 0.0f, dev = 0.0f;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const float dl = st[k].x - mean;
+    m2 += st[k].y;
+    dev = fmaf(dl, dl, dev);
+  }
+  m2 = fmaf(dev, (float)COLS, m2);
+  const float inv = rsqrtf(m2 * (1.0f / D) + kLnEps);
+  const int c_lo = part * COLS;
+#pragma unroll
+  for (int c0 = 0; c0 < COLS; c0 += 8) {
     float v[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = fmaf((x[c0 + i] - mean) * inv, g[c_lo + c0 + i], b[c_lo + c0 + i]);
@@ -255,9 +270,9 @@ __device__ __forceinline__ void store16_bf(uint16_t* dst, const float (&v)[16]) 
 }
 
 template <int D>
-__global__ void __launch_bounds__(kThreads, D == 64 ? 2 : 1) policy_fwd_kernel(PolicyDev p) {
+__global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_kernel(PolicyDev p) {
   using G = Geo<D>;
-  constexpr int HALF = G::HALF;
+  constexpr int COLS = G::COLS, kThreads = G::THREADS;
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem + G::A_OFF;
   unsigned char* ring = smem + G::RING_OFF;
@@ -272,8 +287,8 @@ __global__ void __launch_bounds__(kThreads, D == 64 ? 2 : 1) policy_fwd_kernel(P
   __shared__ int bad;
 
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int row = tid & 127, half = tid >> 7;
-  const int c_lo = half * HALF;
+  const int row = tid & 127, part = tid >> 7;
+  const int c_lo = part * COLS;
   const int slot = row / p.R, tok = row - slot * p.R;
   const long long ag = (long long)blockIdx.x * p.apt + slot;
   const bool agent_ok = slot < p.apt && ag < p.NA;
@@ -320,11 +335,11 @@ __global__ void __launch_bounds__(kThreads, D == 64 ? 2 : 1) policy_fwd_kernel(P
   auto slot_addr = [&](int stage) { return aRing + (uint32_t)((stage % kSlots) * G::SLOT); };
 
   // ---- token rows ----------------------------------------------------------
-  float x[HALF];
+  float x[COLS];
   if (row_ok && tok == 0) {
     const uint16_t* hp = p.h + ag * D + c_lo;
 #pragma unroll
-    for (int c0 = 0; c0 < HALF; c0 += 16) {
+    for (int c0 = 0; c0 < COLS; c0 += 16) {
       float v[16];
       load16_bf(hp + c0, v);
 #pragma unroll
@@ -336,7 +351,7 @@ __global__ void __launch_bounds__(kThreads, D == 64 ? 2 : 1) policy_fwd_kernel(P
                         bf_lo(t4.z), bf_hi(t4.z), bf_lo(t4.w), bf_hi(t4.w)};
     const float4* w4 = reinterpret_cast<const float4*>(p.emb_w) + c_lo * 2;
 #pragma unroll
-    for (int c = 0; c < HALF; ++c) {
+    for (int c = 0; c < COLS; ++c) {
       const float4 wa = __ldg(w4 + 2 * c), wb = __ldg(w4 + 2 * c + 1);
       float acc = __ldg(p.emb_b + c_lo + c);
       acc = fmaf(wa.x, t[0], acc);
@@ -351,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, D == 64 ? 2 : 1) policy_fwd_kernel(P
     }
   } else {
 #pragma unroll
-    for (int c = 0; c < HALF; ++c) x[c] = 0.0f;
+    for (int c = 0; c < COLS; ++c) x[c] = 0.0f;
   }
 
   // Every thread runs every stage (the barriers stay uniform); a wait that
@@ -366,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, D == 64 ? 2 : 1) policy_fwd_kernel(P
     const float *bo = vec + 5 * D, *ln2g = vec + 6 * D, *ln2b = vec + 7 * D, *b1 = vec + 8 * D, *b2 = vec + 12 * D;
 
     // ---- attention sub-block: Q, K, V in one MMA group ----
-    ln_half_to_a<D>(x, ln1g, ln1b, sA, sStat, row, half);  // its barrier also publishes `vec`
+    ln_part_to_a<D>(x, ln1g, ln1b, sA, sStat, row, part);  // its barrier also publishes `vec`
     publish();
     if (tid == 0) {
       wait_images(3);
@@ -376,13 +391,13 @@ __global__ void __launch_bounds__(kThreads, D == 64 ? 2 : 1) policy_fwd_kernel(P
       tc::mma_commit(&mma_bar);
     }
     wait_mma(3);
-    // K and V (+ bias) -> shared memory as BF16, this thread's half of the columns
+    // K and V (+ bias) -> shared memory as BF16, this thread's part of the columns
 #pragma unroll 1
     for (int kv = 0; kv < 2; ++kv) {
       const float* bias = kv == 0 ? bk : bv;
       uint16_t* dst = (kv == 0 ? sK : sV) + row * G::KVS + c_lo;
 #pragma unroll 1
-      for (int c0 = 0; c0 < HALF; c0 += 16) {
+      for (int c0 = 0; c0 < COLS; c0 += 16) {
         float v[16];
         tc::tmem_ld16(tl + (kv == 0 ? G::COL_K : G::COL_V) + c_lo + c0, v);
 #pragma unroll
@@ -392,10 +407,10 @@ __global__ void __launch_bounds__(kThreads, D == 64 ? 2 : 1) policy_fwd_kernel(P
     }
     __syncthreads();  // K, V of every row visible
     // per-head softmax attention over the agent's valid tokens (this
-    // thread's heads: half * HH .. +HH); scores stay in registers
+    // thread's heads: part * HH .. +HH); scores stay in registers
 #pragma unroll 1
     for (int hh = 0; hh < G::HH; ++hh) {
-      const int h = half * G::HH + hh;
+      const int h = part * G::HH + hh;
       float q[16];
       tc::tmem_ld16(tl + G::COL_Q + h * 16, q);
 #pragma unroll
@@ -446,7 +461,7 @@ __global__ void __launch_bounds__(kThreads, D == 64 ? 2 : 1) policy_fwd_kernel(P
     }
     wait_mma(1);
 #pragma unroll
-    for (int c0 = 0; c0 < HALF; c0 += 16) {
+    for (int c0 = 0; c0 < COLS; c0 += 16) {
       float v[16];
       tc::tmem_ld16(tl + G::COL_S + c_lo + c0, v);
 #pragma unroll
@@ -454,7 +469,7 @@ __global__ void __launch_bounds__(kThreads, D == 64 ? 2 : 1) policy_fwd_kernel(P
     }
 
     // ---- feed-forward sub-block ----
-    ln_half_to_a<D>(x, ln2g, ln2b, sA, sStat, row, half);
+    ln_part_to_a<D>(x, ln2g, ln2b, sA, sStat, row, part);
 #pragma unroll 1
     for (int c = 0; c < G::NC; ++c) {
       publish();
@@ -464,11 +479,11 @@ __global__ void __launch_bounds__(kThreads, D == 64 ? 2 : 1) policy_fwd_kernel(P
         tc::mma_commit(&mma_bar);
       }
       wait_mma(1);
-      // GELU of this thread's 64 hidden units of the chunk -> BF16 operand
+      // GELU of this thread's hidden units of the chunk -> BF16 operand
 #pragma unroll 1
-      for (int c0 = 0; c0 < 64; c0 += 16) {
+      for (int c0 = 0; c0 < G::HCOLS; c0 += 16) {
         float v[16];
-        const int hc = half * 64 + c0;
+        const int hc = part * G::HCOLS + c0;
         tc::tmem_ld16(tl + G::COL_S + hc, v);
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = gelu(v[i] + b1[c * 128 + hc + i]);
@@ -484,7 +499,7 @@ __global__ void __launch_bounds__(kThreads, D == 64 ? 2 : 1) policy_fwd_kernel(P
       wait_mma(1);
     }
 #pragma unroll
-    for (int c0 = 0; c0 < HALF; c0 += 16) {
+    for (int c0 = 0; c0 < COLS; c0 += 16) {
       float v[16];
       tc::tmem_ld16(tl + G::COL_ACC + c_lo + c0, v);
 #pragma unroll
@@ -502,7 +517,7 @@ __global__ void __launch_bounds__(kThreads, D == 64 ? 2 : 1) policy_fwd_kernel(P
   if (agent_ok && tok == 0) {
     uint16_t* hp = p.h + ag * D + c_lo;
 #pragma unroll
-    for (int c0 = 0; c0 < HALF; c0 += 16) {
+    for (int c0 = 0; c0 < COLS; c0 += 16) {
       float v[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
@@ -577,7 +592,7 @@ cudaError_t launch_policy_t(const PolicyDev& p, cudaStream_t s) {
     ready = 1;
   }
   const long long tiles = (p.NA + p.apt - 1) / p.apt;
-  if (tiles > 0) policy_fwd_kernel<D><<<(unsigned)tiles, kThreads, Geo<D>::SMEM, s>>>(p);
+  if (tiles > 0) policy_fwd_kernel<D><<<(unsigned)tiles, Geo<D>::THREADS, Geo<D>::SMEM, s>>>(p);
   return cudaGetLastError();
 }
 
