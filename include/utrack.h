@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define UT_ABI_VERSION 2u
+#define UT_ABI_VERSION 3u
 #define UT_MAX_AGENTS 8      /* per environment */
 #define UT_MAX_TARGETS 8     /* per environment */
 #define UT_MAX_PARTICLES 4096
@@ -145,6 +145,8 @@ typedef struct ut_state_view {
   float *estx, *esty;                 /* tracker estimates [F] */
   float *prev_estx, *prev_esty;       /* estimate before the last update [F] */
   float *prev2_estx, *prev2_esty;     /* estimate before that [F] */
+  float *velx, *vely;                 /* smoothed motion of the estimate per step [F]:
+                                         v <- 0.85 v + 0.15 (e1 - e2) at every update */
   float* ring;                        /* estimator ring [F][16][4] (qx, qy, r, step) */
   int32_t *ring_head, *ring_count;    /* [F] */
   uint16_t* h;                        /* recurrent token bf16 [NA][d_model] (NULL without policy) */
@@ -296,7 +298,8 @@ ut_status policy_forward(ut_env* env, const uint16_t* tokens_dev, const int32_t*
 /* filter's estimate e1.  Features of a filter, in e1's local frame (units   */
 /* of L = est_scale): its 16 most recent received pings, newest first, each */
 /* [(q - e1)/L, (r - |q - e1|_3D)/L, (g - g_m)/16, 1], then the estimate's  */
-/* last motion (e1 - e2)/L, zero padded to 96 (FP32).  Output: the          */
+/* last motion (e1 - e2)/L and smoothed motion v/L (v <- 0.85 v + 0.15      */
+/* (e1 - e2) at each update), zero padded to 96 (FP32).  Output: the        */
 /* correction (x - e1)/L; the new estimate is e1 + L * output, each output   */
 /* clamped to +-3 in the step (the estimate is held when no ping arrived    */
 /* this step).  Canonical                                                    */
@@ -333,8 +336,9 @@ ut_status est_get_weights(ut_env* env, float* params_host, int64_t n_params);
 /* 0: particle filter (default); 1-3: the learned estimator replaces the
  * filter stage of every step (needs weights and a handle created with
  * UT_FLAG_RING).  On a step without a fresh ping the estimate is held (1),
- * moved by the network all the same (2), or coasts by its last motion e1 - e2
- * (3, constant velocity); with a fresh ping the network's correction applies.
+ * moved by the network all the same (2), or coasts by its smoothed motion v
+ * (3, constant velocity; see ut_state_view.velx); with a fresh ping the
+ * network's correction applies.
  * Errors: UT_ERR_INVALID (mode outside 0..3), UT_ERR_STATE. */
 ut_status est_set_mode(ut_env* env, int32_t mode);
 /* Raw network outputs out_dev [n_rows][2] of features X_dev [n_rows][96]. */

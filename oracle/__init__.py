@@ -86,7 +86,7 @@ class OcState(ctypes.Structure):
     _fields_ = [(n, _dp) for n in ("ax", "ay", "apsi", "tx", "ty", "tz", "tpsi", "tspeed",
                                    "px", "py", "pvx", "pvy", "lpx", "lpy")] + [
         ("lpage", _ip), ("estx", _dp), ("esty", _dp), ("prev_estx", _dp), ("prev_esty", _dp),
-        ("prev2_estx", _dp), ("prev2_esty", _dp), ("ring", _dp), ("ring_head", _ip),
+        ("prev2_estx", _dp), ("prev2_esty", _dp), ("velx", _dp), ("vely", _dp), ("ring", _dp), ("ring_head", _ip),
         ("ring_count", _ip), ("step", ctypes.c_uint32), ("t_ep", ctypes.c_int32)]
 
 
@@ -223,6 +223,7 @@ class OracleEnv:
             "estx": np.zeros(self.F), "esty": np.zeros(self.F),
             "prev_estx": np.zeros(self.F), "prev_esty": np.zeros(self.F),
             "prev2_estx": np.zeros(self.F), "prev2_esty": np.zeros(self.F),
+            "velx": np.zeros(self.F), "vely": np.zeros(self.F),
             "ring": np.zeros(self.F * RING * 4), "ring_head": np.zeros(self.F, np.int32),
             "ring_count": np.zeros(self.F, np.int32),
         }

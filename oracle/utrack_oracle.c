@@ -47,6 +47,7 @@
 #define OC_MAX_MEAS OC_MAX_AGENTS
 #define OC_RING 16
 #define OC_FEAT 96
+#define OC_VEL_KEEP 0.85 /* smoothing of the estimate motion (reading C18) */
 #define OC_TOKEN 8
 
 /* Philox stream tags (counter word 3). */
@@ -100,6 +101,7 @@ typedef struct {
   double *estx, *esty;                      /* tracker estimate [F] */
   double *prev_estx, *prev_esty;            /* estimate before the last update [F] */
   double *prev2_estx, *prev2_esty;          /* estimate before that [F] */
+  double *velx, *vely;                      /* smoothed motion of the estimate [F] */
   double *ring;                             /* [F*16*4]: qx, qy, r, step */
   int32_t *ring_head, *ring_count;          /* [F] */
   uint32_t step;                            /* global step counter g */
@@ -314,6 +316,7 @@ void oc_reset(const oc_config* c, oc_state* s, uint32_t g) {
         s->esty[f] = sy / P;
         s->prev_estx[f] = s->prev2_estx[f] = s->estx[f];
         s->prev_esty[f] = s->prev2_esty[f] = s->esty[f];
+        s->velx[f] = s->vely[f] = 0.0;
         s->ring_head[f] = 0;
         s->ring_count[f] = 0;
         for (int j = 0; j < OC_RING * 4; ++j) s->ring[(int64_t)f * OC_RING * 4 + j] = 0.0;
@@ -574,6 +577,10 @@ void oc_pf_update(const oc_config* c, oc_state* s, uint32_t g, const double* mea
       ex += (w[i] / W) * x[i];
       ey += (w[i] / W) * y[i];
     }
+    /* smoothed motion of the estimate (reading C18): v <- 0.85 v + 0.15 (e1 - e2)
+     * with e1 the estimate before this update and e2 the one before that */
+    s->velx[f] = OC_VEL_KEEP * s->velx[f] + (1.0 - OC_VEL_KEEP) * (s->estx[f] - s->prev_estx[f]);
+    s->vely[f] = OC_VEL_KEEP * s->vely[f] + (1.0 - OC_VEL_KEEP) * (s->esty[f] - s->prev_esty[f]);
     s->prev2_estx[f] = s->prev_estx[f];
     s->prev2_esty[f] = s->prev_esty[f];
     s->prev_estx[f] = s->estx[f];
@@ -761,6 +768,8 @@ void oc_est_features(const oc_config* c, const oc_state* s, uint32_t g, double* 
         }
         x[5 * OC_RING + 0] = (e1x - s->prev2_estx[f]) / L;
         x[5 * OC_RING + 1] = (e1y - s->prev2_esty[f]) / L;
+        x[5 * OC_RING + 2] = s->velx[f] / L;
+        x[5 * OC_RING + 3] = s->vely[f] / L;
         if (label) {
           label[(int64_t)f * 2 + 0] = (s->tx[it] - e1x) / L;
           label[(int64_t)f * 2 + 1] = (s->ty[it] - e1y) / L;

@@ -211,7 +211,7 @@ class Env:
     def est_set_mode(self, mode):
         """0 / False: particle filter; 1 / True: learned estimator, estimate held
         on steps without a fresh ping; 2: network on every step; 3: coast at the
-        estimate's last motion on steps without a fresh ping."""
+        estimate's smoothed motion on steps without a fresh ping."""
         _check(lib.est_set_mode(self.h, int(mode)), self.h, "est_set_mode")
 
     def est_forward(self, X: torch.Tensor) -> torch.Tensor:
@@ -305,6 +305,7 @@ class Env:
                   "tpsi": (NT,), "tspeed": (NT,), "px": (FP,), "py": (FP,), "pvx": (FP,), "pvy": (FP,),
                   "lpx": (NA * AM,), "lpy": (NA * AM,), "lpage": (NA * AM,), "estx": (F,), "esty": (F,),
                   "prev_estx": (F,), "prev_esty": (F,), "prev2_estx": (F,), "prev2_esty": (F,),
+                  "velx": (F,), "vely": (F,),
                   "ring": (F, 16, 4), "ring_head": (F,), "ring_count": (F,)}
         out = {}
         for k, shp in shapes.items():

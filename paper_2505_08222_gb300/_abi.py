@@ -7,7 +7,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libutrack.so")
 
-UT_ABI_VERSION = 2
+UT_ABI_VERSION = 3
 UT_FLAG_DEBUG = 1
 UT_FLAG_RING = 2
 
@@ -61,7 +61,7 @@ class StepOut(ctypes.Structure):
 
 STATE_PTRS = ["ax", "ay", "apsi", "tx", "ty", "tz", "tpsi", "tspeed", "px", "py", "pvx", "pvy",
               "lpx", "lpy", "lpage", "estx", "esty", "prev_estx", "prev_esty", "prev2_estx", "prev2_esty",
-              "ring", "ring_head", "ring_count", "h"]
+              "velx", "vely", "ring", "ring_head", "ring_count", "h"]
 
 
 class StateView(ctypes.Structure):

@@ -270,6 +270,8 @@ ut_status env_create(const ut_config* cfg, const ut_allocator* allocator, void* 
   d.prev_esty = alloc_n<float>(h, F, ok);
   d.prev2_estx = alloc_n<float>(h, F, ok);
   d.prev2_esty = alloc_n<float>(h, F, ok);
+  d.velx = alloc_n<float>(h, F, ok);
+  d.vely = alloc_n<float>(h, F, ok);
   d.err = alloc_n<float>(h, F, ok);
   d.ring = alloc_n<float>(h, d.ring_on ? F * kRing * 4 : 4, ok);
   d.ring_head = alloc_n<int32_t>(h, F, ok);
@@ -628,6 +630,7 @@ ut_status env_get_state(const ut_env* hc, ut_state_view* out) {
   out->estx = d.estx; out->esty = d.esty;
   out->prev_estx = d.prev_estx; out->prev_esty = d.prev_esty;
   out->prev2_estx = d.prev2_estx; out->prev2_esty = d.prev2_esty;
+  out->velx = d.velx; out->vely = d.vely;
   out->ring = d.ring_on ? d.ring : nullptr;
   out->ring_head = d.ring_head; out->ring_count = d.ring_count;
   out->h = extension_h(h);
@@ -671,6 +674,8 @@ ut_status env_set_state(ut_env* h, const ut_state_view* in) {
   UT_CUDA(h, cp(d.prev_esty, in->prev_esty, F * 4));
   UT_CUDA(h, cp(d.prev2_estx, in->prev2_estx, F * 4));
   UT_CUDA(h, cp(d.prev2_esty, in->prev2_esty, F * 4));
+  UT_CUDA(h, cp(d.velx, in->velx, F * 4));
+  UT_CUDA(h, cp(d.vely, in->vely, F * 4));
   if (d.ring_on) UT_CUDA(h, cp(d.ring, in->ring, F * kRing * 16));
   UT_CUDA(h, cp(d.ring_head, in->ring_head, F * 4));
   UT_CUDA(h, cp(d.ring_count, in->ring_count, F * 4));

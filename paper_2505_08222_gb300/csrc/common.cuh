@@ -37,6 +37,9 @@ constexpr int kMaxTargets = 8;
 constexpr int kRing = 16;
 constexpr int kFeat = 96;
 constexpr float kPi = 3.14159265358979323846f;
+// Smoothing of the estimate's motion: v <- kVelKeep v + (1 - kVelKeep) (e1 - e2)
+// at every tracker update (learned estimator features, readings C18).
+constexpr float kVelKeep = 0.85f;
 constexpr float kTwoPi = 6.28318530717958647692f;
 
 struct Rand4 {

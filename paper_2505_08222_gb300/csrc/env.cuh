@@ -45,6 +45,8 @@ struct EnvDev {
   // the two previous estimates of each filter (estimate history of the
   // learned estimator's features; NULL where not kept)
   float *prev_estx, *prev_esty, *prev2_estx, *prev2_esty;
+  // smoothed motion of the estimate per step (EMA over the updates' e1 - e2)
+  float *velx, *vely;
   float est_scale;  // L: metres per unit of the learned estimator's local frame
   float* ring;
   int32_t *ring_head, *ring_count;

@@ -132,6 +132,8 @@ __global__ void __launch_bounds__(kInitThreads) reset_pf_kernel(EnvDev d, uint32
     d.esty[f] = ty / (float)d.P;
     d.prev_estx[f] = d.prev2_estx[f] = d.estx[f];
     d.prev_esty[f] = d.prev2_esty[f] = d.esty[f];
+    d.velx[f] = 0.0f;
+    d.vely[f] = 0.0f;
     d.ring_head[f] = 0;
     d.ring_count[f] = 0;
   }

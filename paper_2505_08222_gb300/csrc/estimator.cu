@@ -48,10 +48,11 @@ __device__ __forceinline__ void copy_img(unsigned char* dst, const unsigned char
 // in the local frame of the filter's current estimate e1 (units of L), each
 // of the 16 most recent pings, newest first, as [(q - e1) / L, range
 // innovation (r - |q - e1|_3D) / L, (g - g_m) / 16, 1], then the last motion
-// of the estimate (e1 - e2) / L; zero padded to 96.  The network's output is
-// the correction (x - e1) / L.
+// of the estimate (e1 - e2) / L and its smoothed motion v / L (the velocity
+// EMA including this update's e1 - e2); zero padded to 96.  The network's
+// output is the correction (x - e1) / L.
 __device__ __forceinline__ void ring_features(const EnvDev& d, int f, uint32_t g, float e1x, float e1y, float e2x,
-                                              float e2y, float (&x)[IN]) {
+                                              float e2y, float vx, float vy, float (&x)[IN]) {
   const float dz = d.tz[d.filt_target[f]];  // target depth; senders at the surface
   const float L = d.est_scale;
   const int head = d.ring_head[f], cnt = d.ring_count[f];
@@ -71,8 +72,10 @@ __device__ __forceinline__ void ring_features(const EnvDev& d, int f, uint32_t g
   }
   x[5 * kRing] = (e1x - e2x) / L;
   x[5 * kRing + 1] = (e1y - e2y) / L;
+  x[5 * kRing + 2] = vx / L;
+  x[5 * kRing + 3] = vy / L;
 #pragma unroll
-  for (int i = 5 * kRing + 2; i < IN; ++i) x[i] = 0.0f;
+  for (int i = 5 * kRing + 4; i < IN; ++i) x[i] = 0.0f;
 }
 
 struct FwdArgs {
@@ -84,7 +87,7 @@ struct FwdArgs {
   float* z;     // training: [3][B][256], else NULL
   uint16_t* a;  // training: [3][B][256], else NULL
   EnvDev d;     // env mode
-  int stale;    // env mode, steps without a fresh ping: 0 hold, 1 network, 2 coast at e1 - e2
+  int stale;    // env mode, steps without a fresh ping: 0 hold, 1 network, 2 coast at the smoothed motion
   int* status;
 };
 
@@ -107,12 +110,15 @@ __global__ void __launch_bounds__(kT, 1) fwd_kernel(FwdArgs p) {
   if (tid == 0) tc::mbar_init(&mbar, 1);
 
   float x[IN];
-  float e1x = 0.0f, e1y = 0.0f;
+  float e1x = 0.0f, e1y = 0.0f, vnx = 0.0f, vny = 0.0f;
   if (ENV) {
     if (valid) {
       e1x = p.d.estx[b];
       e1y = p.d.esty[b];
-      ring_features(p.d, (int)b, p.d.counters[0] + 1u, e1x, e1y, p.d.prev_estx[b], p.d.prev_esty[b], x);
+      const float e2x = p.d.prev_estx[b], e2y = p.d.prev_esty[b];
+      vnx = fmaf(kVelKeep, p.d.velx[b], (1.0f - kVelKeep) * (e1x - e2x));
+      vny = fmaf(kVelKeep, p.d.vely[b], (1.0f - kVelKeep) * (e1y - e2y));
+      ring_features(p.d, (int)b, p.d.counters[0] + 1u, e1x, e1y, e2x, e2y, vnx, vny, x);
     } else {
 #pragma unroll
       for (int i = 0; i < IN; ++i) x[i] = 0.0f;
@@ -206,20 +212,22 @@ __global__ void __launch_bounds__(kT, 1) fwd_kernel(FwdArgs p) {
       // the estimate may move up to kMaxCorr L.  Without one, the rule chosen
       // by the mode applies: hold the estimate (stale inputs cannot drive the
       // closed loop away), apply the network all the same, or coast by the
-      // estimate's last motion e1 - e2 (constant velocity).
+      // estimate's smoothed motion v (constant velocity).
       const bool fresh = x[3] == 0.0f && x[4] == 1.0f;
       const float lim = (fresh || p.stale == 1) ? kMaxCorr : 0.0f;
       float c0 = isfinite(o0) ? fminf(fmaxf(o0, -lim), lim) : 0.0f;
       float c1 = isfinite(o1) ? fminf(fmaxf(o1, -lim), lim) : 0.0f;
       if (!fresh && p.stale == 2) {
-        c0 = fminf(fmaxf(x[5 * kRing], -kMaxCorr), kMaxCorr);
-        c1 = fminf(fmaxf(x[5 * kRing + 1], -kMaxCorr), kMaxCorr);
+        c0 = fminf(fmaxf(x[5 * kRing + 2], -kMaxCorr), kMaxCorr);
+        c1 = fminf(fmaxf(x[5 * kRing + 3], -kMaxCorr), kMaxCorr);
       }
       const float ex = e1x + p.d.est_scale * c0, ey = e1y + p.d.est_scale * c1;
       p.d.prev2_estx[f] = p.d.prev_estx[f];
       p.d.prev2_esty[f] = p.d.prev_esty[f];
       p.d.prev_estx[f] = e1x;
       p.d.prev_esty[f] = e1y;
+      p.d.velx[f] = vnx;
+      p.d.vely[f] = vny;
       p.d.estx[f] = ex;
       p.d.esty[f] = ey;
       const float dx = ex - p.d.tx[it], dy = ey - p.d.ty[it];
@@ -511,7 +519,7 @@ __global__ void record_kernel(EnvDev d, float* feat, float* label) {
   // after the step: the update's inputs are the estimate history
   const float e1x = d.prev_estx[f], e1y = d.prev_esty[f];
   float x[IN];
-  ring_features(d, f, d.counters[0], e1x, e1y, d.prev2_estx[f], d.prev2_esty[f], x);
+  ring_features(d, f, d.counters[0], e1x, e1y, d.prev2_estx[f], d.prev2_esty[f], d.velx[f], d.vely[f], x);
 #pragma unroll
   for (int i = 0; i < IN; i += 4)
     *reinterpret_cast<float4*>(feat + (long long)f * IN + i) = make_float4(x[i], x[i + 1], x[i + 2], x[i + 3]);

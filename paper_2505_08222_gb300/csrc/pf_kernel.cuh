@@ -259,12 +259,16 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
 
   // estimate history, fetched early so that its latency hides behind the
   // particle loads (thread 0 writes it back before a block barrier)
-  float hist[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  float hist[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
   if (tid == 0 && d.prev_estx) {
     hist[0] = d.estx[f];
     hist[1] = d.esty[f];
     hist[2] = d.prev_estx[f];
     hist[3] = d.prev_esty[f];
+    if (d.velx) {
+      hist[4] = d.velx[f];
+      hist[5] = d.vely[f];
+    }
   }
   // measurement list and the filter's header (senders are at the surface:
   // the vertical offset of every range is the target depth)
@@ -379,6 +383,10 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
       d.prev2_esty[f] = hist[3];
       d.prev_estx[f] = hist[0];
       d.prev_esty[f] = hist[1];
+      if (d.velx) {  // motion of the previous update folded into the smoothed velocity
+        d.velx[f] = fmaf(kVelKeep, hist[4], (1.0f - kVelKeep) * (hist[0] - hist[2]));
+        d.vely[f] = fmaf(kVelKeep, hist[5], (1.0f - kVelKeep) * (hist[1] - hist[3]));
+      }
     }
     d.estx[f] = ex;
     d.esty[f] = ey;

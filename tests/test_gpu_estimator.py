@@ -86,7 +86,7 @@ def test_record_features_match_oracle():
     for t in range(1, 6):
         o.step(np.random.default_rng(t).integers(0, 7, o.NA).astype(np.int32))
     keys = ["ax", "ay", "apsi", "tx", "ty", "tz", "tpsi", "tspeed", "px", "py", "pvx", "pvy", "lpx", "lpy", "estx",
-            "esty", "prev_estx", "prev_esty", "prev2_estx", "prev2_esty", "ring"]
+            "esty", "prev_estx", "prev_esty", "prev2_estx", "prev2_esty", "velx", "vely", "ring"]
     st = {k: o.arr[k].astype(np.float32) for k in keys}
     st.update(lpage=o.arr["lpage"], ring_head=o.arr["ring_head"], ring_count=o.arr["ring_count"])
     tens = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in st.items()}
@@ -190,7 +190,7 @@ def test_learned_mode_step_uses_network():
 @pytest.mark.parametrize("mode", [1, 2, 3])
 def test_learned_mode_stale_rules(mode):
     """With a short detection radius many filters get no ping; their update
-    follows the mode's rule (hold / network / coast by e1 - e2), while filters
+    follows the mode's rule (hold / network / coast by the smoothed motion), while filters
     with a fresh ping take the network's clamped correction in every mode."""
     env, p = _env(n_envs=32, det_radius=120.0)
     params = synth.mlp_params(seed=17, bias_scale=0.1)
@@ -218,6 +218,6 @@ def test_learned_mode_stale_rules(mode):
     elif mode == 2:
         want = e1[stale] + 100.0 * corr[stale]
     else:
-        want = e1[stale] + 100.0 * np.clip(X[stale, 80:82], -3.0, 3.0)
+        want = e1[stale] + 100.0 * np.clip(X[stale, 82:84], -3.0, 3.0)
     np.testing.assert_allclose(est[stale], want, atol=2e-3)
     env.est_set_mode(0)

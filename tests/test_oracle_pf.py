@@ -149,3 +149,59 @@ def test_static_target_trilateration_convergence():
         ls = _ls_trilateration(m[:, :2], m[:, 3])
         assert np.linalg.norm(ls - truth) < 1.0
         assert np.linalg.norm(est - ls) < 1.5
+
+
+def test_estimate_motion_features_closed_form():
+    """Identical particles, no noise, nothing heard: the estimate moves by
+    u = dt v every step, so after n updates the last-motion feature is u / L
+    and the smoothed motion is the geometric sum u (1 - 0.85^(n-1)) / L
+    (reading C18: v <- 0.85 v + 0.15 (e1 - e2), v = 0 at reset)."""
+    P = 16
+    e = _env(n_envs=1, n_particles=P, pf_accel_sigma=0.0, det_radius=0.0, target_depth_max=0.0)
+    F = e.F
+    vx0, vy0 = 0.7, -0.4
+    X, Y = np.linspace(-50, 50, F), np.linspace(20, 80, F)
+    e.set_arrays(px=np.repeat(X, P), py=np.repeat(Y, P), pvx=np.full(F * P, vx0), pvy=np.full(F * P, vy0),
+                 estx=X, esty=Y, prev_estx=X, prev_esty=Y, prev2_estx=X, prev2_esty=Y)
+    L = e.p.est_scale
+    for n in range(1, 9):
+        e.step(np.full(e.NA, 3, np.int32))
+        feat, _ = e.est_features(e.step_count)
+        if n >= 2:
+            np.testing.assert_allclose(feat[:, 80], 30 * vx0 / L, rtol=1e-9)
+            np.testing.assert_allclose(feat[:, 81], 30 * vy0 / L, rtol=1e-9)
+        np.testing.assert_allclose(feat[:, 82], 30 * vx0 * (1 - 0.85 ** (n - 1)) / L, rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(feat[:, 83], 30 * vy0 * (1 - 0.85 ** (n - 1)) / L, rtol=1e-9, atol=1e-12)
+
+
+def test_estimator_features_translation_invariant():
+    """Features live in the estimate's local frame: shifting every position
+    (estimates, ping senders, targets) by one vector leaves them unchanged;
+    a ping whose range equals the 3-D distance from the estimate has zero
+    innovation."""
+    e = _env(n_envs=3, n_particles=32, comm_drop=0.0)
+    for t in range(1, 5):
+        e.step(np.random.default_rng(t).integers(0, 7, e.NA).astype(np.int32))
+    f0, _ = e.est_features(e.step_count)
+    shift = np.array([123.25, -77.5])
+    ring = e.arr["ring"].reshape(e.F, 16, 4).copy()
+    ring[:, :, 0] += shift[0]
+    ring[:, :, 1] += shift[1]
+    e.set_arrays(ring=ring.reshape(-1), **{k: e.arr[k] + shift[i % 2] for i, k in
+                                           enumerate(["estx", "esty", "prev_estx", "prev_esty",
+                                                      "prev2_estx", "prev2_esty", "tx", "ty"])})
+    f1, _ = e.est_features(e.step_count)
+    np.testing.assert_allclose(f1, f0, atol=1e-9)
+    # zero innovation for a range equal to the distance from e1
+    ring = e.arr["ring"].reshape(e.F, 16, 4).copy()
+    head = e.arr["ring_head"]
+    newest = (head - 1) % 16
+    rows = np.arange(e.F)
+    e1x, e1y = e.arr["prev_estx"], e.arr["prev_esty"]
+    depth = np.array([e.arr["tz"][e.target_off[f // 25] + (f % 25) % 5] for f in range(e.F)])
+    ring[rows, newest, 2] = np.sqrt((ring[rows, newest, 0] - e1x) ** 2 + (ring[rows, newest, 1] - e1y) ** 2
+                                    + depth ** 2)
+    e.set_arrays(ring=ring.reshape(-1))
+    f2, _ = e.est_features(e.step_count)
+    has = e.arr["ring_count"] > 0
+    np.testing.assert_allclose(f2[has, 2], 0.0, atol=1e-12)
