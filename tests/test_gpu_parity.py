@@ -294,3 +294,40 @@ def test_full_size_fleet5_sampled():
         for fl in range(25):
             want = oracle.systematic_resample(wmax[fl].astype(np.float64), resample_u64(11, 25 * e + fl, 1))
             np.testing.assert_array_equal(idx[25 * e + fl].cpu().numpy(), want)
+
+
+def test_full_size_large_sampled():
+    """The largest workload: 65536 envs x 8 agents x 8 targets with 512
+    particles per filter, exactly 2^31 particles, so the last filters' particle
+    offsets need 64-bit indexing.  The first, a middle and the last
+    environment are replayed by the oracle (global-id offsets) and compared
+    on the predicted particles, the weights and the exact resample map."""
+    p = preset("large").replace(d_model=0)
+    P, A, T = p.n_particles, p.max_agents, p.max_targets
+    FA = A * T
+    env = ut.Env(p, debug=True)
+    assert env.F * P == 2 ** 31
+    env.reset(13)
+    env.step()
+    torch.cuda.synchronize()
+    dbg = env.debug()
+    st = env.state()
+    for e in (0, 33333, p.n_envs - 1):
+        o = oracle.OracleEnv(p.replace(n_envs=1), 13, id_base=(e, A * e, T * e, FA * e))
+        o.reset(0)
+        ref = o.step(o.random_actions(1), want=("pred_px", "pred_py", "weight"))
+        sa = slice(A * e, A * (e + 1))
+        sf = slice(FA * e * P, FA * (e + 1) * P)
+        assert np.all(rel_close(st["ax"][sa].cpu().numpy(), o.arr["ax"], 1e-5, 100.0))
+        assert np.all(rel_close(dbg["pred_px"][sf].cpu().numpy(), ref["pred_px"], 1e-5, 100.0))
+        assert np.all(rel_close(dbg["pred_py"][sf].cpu().numpy(), ref["pred_py"], 1e-5, 100.0))
+        wg = dbg["weight"][sf].cpu().numpy().reshape(FA, P)
+        wo = ref["weight"].reshape(FA, P)
+        assert np.all(np.abs(wg - wo) <= 3e-3 * wo.max(1, keepdims=True) + 1e-7)
+        wmax = dbg["wmax"][sf].cpu().numpy().reshape(FA, P)
+        idx = dbg["idx"][sf].cpu().numpy().reshape(FA, P)
+        for fl in range(FA):
+            want = oracle.systematic_resample(wmax[fl].astype(np.float64), resample_u64(13, FA * e + fl, 1))
+            np.testing.assert_array_equal(idx[fl], want)
+    del env, dbg, st
+    torch.cuda.empty_cache()
