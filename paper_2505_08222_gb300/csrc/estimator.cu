@@ -2,8 +2,9 @@
 // input-gradient pass, weight-gradient pass, Adam, feature recording.
 //
 // All three hidden layers run on the tensor cores (tcgen05.mma, BF16 x BF16 ->
-// FP32 in TMEM) with 128 rows per CTA and one thread per row in the
-// epilogues.  The first layer's inputs are FP32 features split into a BF16
+// FP32 in TMEM) with 128 rows per CTA: one thread per row in the epilogues of
+// the training / stand-alone forward, four per row in the environment step's
+// forward (fwd_env_kernel).  The first layer's inputs are FP32 features split into a BF16
 // high part and a BF16 remainder that are multiplied by the same weights and
 // accumulated together: ranges of hundreds of metres keep ~1e-5 relative
 // precision instead of BF16's 4e-3, which matters for metre-level tracking.
@@ -86,12 +87,9 @@ struct FwdArgs {
   float* out;
   float* z;     // training: [3][B][256], else NULL
   uint16_t* a;  // training: [3][B][256], else NULL
-  EnvDev d;     // env mode
-  int stale;    // env mode, steps without a fresh ping: 0 hold, 1 network, 2 coast at the smoothed motion
   int* status;
 };
 
-template <bool ENV>
 __global__ void __launch_bounds__(kT, 1) fwd_kernel(FwdArgs p) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;          // features hi | lo, then hidden activations [128 x 256]
@@ -100,7 +98,7 @@ __global__ void __launch_bounds__(kT, 1) fwd_kernel(FwdArgs p) {
   __shared__ uint32_t tbase;
   const int tid = threadIdx.x, warp = tid >> 5;
   const long long b = (long long)blockIdx.x * kT + tid;
-  const long long n = ENV ? (long long)p.d.F : (long long)p.B;
+  const long long n = (long long)p.B;
   const bool valid = b < n;
 
   if (warp == 0) {
@@ -110,20 +108,7 @@ __global__ void __launch_bounds__(kT, 1) fwd_kernel(FwdArgs p) {
   if (tid == 0) tc::mbar_init(&mbar, 1);
 
   float x[IN];
-  float e1x = 0.0f, e1y = 0.0f, vnx = 0.0f, vny = 0.0f;
-  if (ENV) {
-    if (valid) {
-      e1x = p.d.estx[b];
-      e1y = p.d.esty[b];
-      const float e2x = p.d.prev_estx[b], e2y = p.d.prev_esty[b];
-      vnx = fmaf(kVelKeep, p.d.velx[b], (1.0f - kVelKeep) * (e1x - e2x));
-      vny = fmaf(kVelKeep, p.d.vely[b], (1.0f - kVelKeep) * (e1y - e2y));
-      ring_features(p.d, (int)b, p.d.counters[0] + 1u, e1x, e1y, e2x, e2y, vnx, vny, x);
-    } else {
-#pragma unroll
-      for (int i = 0; i < IN; ++i) x[i] = 0.0f;
-    }
-  } else {
+  {
     const long long src = valid ? (p.rows ? (long long)p.rows[b] : b) : 0;
 #pragma unroll
     for (int i = 0; i < IN; i += 4) {
@@ -205,39 +190,214 @@ __global__ void __launch_bounds__(kT, 1) fwd_kernel(FwdArgs p) {
   o0 += __ldg(mst + B4_OFF);
   o1 += __ldg(mst + B4_OFF + 1);
   if (valid && ok) {
-    if (ENV) {
-      const int f = (int)b;
-      const int it = p.d.filt_target[f];
-      // Bounded update (dropped if not finite): with a ping received this step
-      // the estimate may move up to kMaxCorr L.  Without one, the rule chosen
-      // by the mode applies: hold the estimate (stale inputs cannot drive the
-      // closed loop away), apply the network all the same, or coast by the
-      // estimate's smoothed motion v (constant velocity).
-      const bool fresh = x[3] == 0.0f && x[4] == 1.0f;
-      const float lim = (fresh || p.stale == 1) ? kMaxCorr : 0.0f;
-      float c0 = isfinite(o0) ? fminf(fmaxf(o0, -lim), lim) : 0.0f;
-      float c1 = isfinite(o1) ? fminf(fmaxf(o1, -lim), lim) : 0.0f;
-      if (!fresh && p.stale == 2) {
-        c0 = fminf(fmaxf(x[5 * kRing + 2], -kMaxCorr), kMaxCorr);
-        c1 = fminf(fmaxf(x[5 * kRing + 3], -kMaxCorr), kMaxCorr);
-      }
-      const float ex = e1x + p.d.est_scale * c0, ey = e1y + p.d.est_scale * c1;
-      p.d.prev2_estx[f] = p.d.prev_estx[f];
-      p.d.prev2_esty[f] = p.d.prev_esty[f];
-      p.d.prev_estx[f] = e1x;
-      p.d.prev_esty[f] = e1y;
-      p.d.velx[f] = vnx;
-      p.d.vely[f] = vny;
-      p.d.estx[f] = ex;
-      p.d.esty[f] = ey;
-      const float dx = ex - p.d.tx[it], dy = ey - p.d.ty[it];
-      p.d.err[f] = sqrtf(dx * dx + dy * dy);
-    } else {
-      p.out[b * OUT] = o0;
-      p.out[b * OUT + 1] = o1;
-    }
+    p.out[b * OUT] = o0;
+    p.out[b * OUT + 1] = o1;
   }
   if (!ok && tid == 0) raise_status(p.status, 2);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+// ---------------------------------------------------------------------------
+// Estimator step in the environment (learned form): one CTA of 512 threads
+// per 128 filters, thread = filter row x one of 4 column parts.  Part 0
+// builds the row's features; the hidden-layer epilogues (bias, erf-GELU,
+// BF16 operand) split the 256 hidden units 4 ways; the weight images (N-halves
+// of W1, W2, W3) stream through two shared-memory slots by the bulk-copy
+// engine, so the next layer's weights arrive during the current epilogue.
+// ---------------------------------------------------------------------------
+constexpr int kTE = 512;
+constexpr int kParts = kTE / 128;
+constexpr int kEnvStages = 6;                               // W1, W2, W3, two N-halves each
+constexpr size_t kEnvSlot = (size_t)128 * HID * 2;          // largest half image (64 KB)
+constexpr size_t kEnvSmem = 65536 + 2 * kEnvSlot;           // A operand + two weight slots
+constexpr uint32_t kEnvPolls = 1u << 22;
+
+__device__ __forceinline__ void env_stage(int s, size_t& off, uint32_t& bytes) {
+  if (s < 2) {
+    off = IMG_W1_OFF + (size_t)s * 128 * IN * 2;
+    bytes = (uint32_t)(128 * IN * 2);
+  } else {
+    const int l = (s - 2) >> 1, h = (s - 2) & 1;
+    off = (l == 0 ? IMG_W2_OFF : IMG_W3_OFF) + (size_t)h * 128 * HID * 2;
+    bytes = (uint32_t)(128 * HID * 2);
+  }
+}
+
+__global__ void __launch_bounds__(kTE, 1) fwd_env_kernel(Net net, EnvDev d, int stale) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sA = smem;           // features hi | lo [2 x 128 x 96], then hidden activations [128 x 256]
+  unsigned char* sW = smem + 65536;   // two weight slots
+  __shared__ __align__(8) uint64_t full[2];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tbase;
+  __shared__ float sOut[kParts][2][128];
+  __shared__ int bad;
+  const int tid = threadIdx.x, warp = tid >> 5, row = tid & 127, part = tid >> 7;
+  const long long f = (long long)blockIdx.x * 128 + row;
+  const bool valid = f < d.F;
+
+  if (warp == 0) {
+    tc::tmem_alloc(&tbase, 256);
+    tc::tmem_relinquish();
+  }
+  if (tid == 32) {
+    tc::mbar_init(&full[0], 1);
+    tc::mbar_init(&full[1], 1);
+    tc::mbar_init(&mbar, 1);
+    bad = 0;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tbase;
+  const uint32_t tl = tmem + ((uint32_t)(warp & 3) << 21);  // this warp's lane quarter
+  const uint32_t aA = tc::smem_addr(sA), aW = tc::smem_addr(sW);
+  auto fetch = [&](int st) {  // thread 0: stage st into slot st % 2
+    size_t off;
+    uint32_t bytes;
+    env_stage(st, off, bytes);
+    tc::mbar_expect_tx(&full[st & 1], bytes);
+    tc::bulk_g2s(sW + (st & 1) * kEnvSlot, net.img + off, bytes, &full[st & 1]);
+  };
+  if (tid == 0) {
+    fetch(0);
+    fetch(1);
+  }
+
+  // features of this row (part 0) -> A operand as BF16 high and low parts
+  float x[IN];
+  float e1x = 0.0f, e1y = 0.0f, vnx = 0.0f, vny = 0.0f;
+  if (part == 0) {
+    if (valid) {
+      e1x = d.estx[f];
+      e1y = d.esty[f];
+      const float e2x = d.prev_estx[f], e2y = d.prev_esty[f];
+      vnx = fmaf(kVelKeep, d.velx[f], (1.0f - kVelKeep) * (e1x - e2x));
+      vny = fmaf(kVelKeep, d.vely[f], (1.0f - kVelKeep) * (e1y - e2y));
+      ring_features(d, (int)f, d.counters[0] + 1u, e1x, e1y, e2x, e2y, vnx, vny, x);
+    } else {
+#pragma unroll
+      for (int i = 0; i < IN; ++i) x[i] = 0.0f;
+    }
+#pragma unroll
+    for (int c0 = 0; c0 < IN; c0 += 8) {
+      float hi[8], lo[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        hi[i] = bf_bits2f(f2bf_bits(x[c0 + i]));
+        lo[i] = x[c0 + i] - hi[i];
+      }
+      store8(sA, row, c0, 128, hi);
+      store8(sA + 128 * IN * 2, row, c0, 128, lo);
+    }
+  }
+
+  bool ok = true;
+  uint32_t mphase = 0;
+  int stage = 0;
+  const float* mst = net.master;
+  float o0 = 0.0f, o1 = 0.0f;
+  for (int l = 0; l < 3; ++l) {
+    // MMA group of layer l: both N-halves (and, for layer 1, both feature parts)
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0) {
+      const int K = l == 0 ? IN : HID;
+      const uint32_t idesc = tc::idesc_bf16(128, 128);
+      for (int h = 0; h < 2; ++h) {
+        ok &= tc::mbar_wait(&full[(stage + h) & 1], (uint32_t)(((stage + h) >> 1) & 1), kEnvPolls);
+        const uint32_t bB = aW + (uint32_t)(((stage + h) & 1) * kEnvSlot);
+        const int nA = l == 0 ? 2 : 1;
+        bool acc = false;
+        for (int j = 0; j < nA; ++j) {
+          const uint32_t a0 = aA + (uint32_t)(j * 128 * IN * 2);
+          for (int k = 0; k < K / 16; ++k) {
+            const uint64_t ad = tc::smem_desc(a0 + k * 2 * 128 * 16, 128 * 16, 128);
+            const uint64_t bd = tc::smem_desc(bB + k * 2 * 128 * 16, 128 * 16, 128);
+            tc::mma_bf16(tmem + 128 * h, ad, bd, idesc, acc ? 1u : 0u);
+            acc = true;
+          }
+        }
+      }
+      tc::mma_commit(&mbar);
+    }
+    ok &= tc::mbar_wait(&mbar, mphase, kEnvPolls);
+    mphase ^= 1u;
+    tc::fence_after_sync();
+    stage += 2;
+    if (tid == 0 && stage < kEnvStages) {  // both slots are free again: next layer's weights
+      fetch(stage);
+      fetch(stage + 1);
+    }
+    // epilogue of hidden layer l on this thread's 64 hidden units
+    const float* bias = mst + (l == 0 ? B1_OFF : (l == 1 ? B2_OFF : B3_OFF));
+#pragma unroll 1
+    for (int c0 = part * (HID / kParts); c0 < (part + 1) * (HID / kParts); c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(tl + c0, v);
+      float av[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) av[i] = gelu(v[i] + __ldg(bias + c0 + i));
+      if (l < 2) {
+        store8(sA, row, c0, 128, av);
+        store8(sA, row, c0 + 8, 128, av + 8);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          o0 = fmaf(__ldg(mst + W4_OFF + c0 + i), av[i], o0);
+          o1 = fmaf(__ldg(mst + W4_OFF + HID + c0 + i), av[i], o1);
+        }
+      }
+    }
+  }
+  sOut[part][0][row] = o0;
+  sOut[part][1][row] = o1;
+  if (!ok) atomicExch(&bad, 1);
+  __syncthreads();
+  if (part == 0 && valid && bad == 0) {
+    o0 = __ldg(mst + B4_OFF);
+    o1 = __ldg(mst + B4_OFF + 1);
+#pragma unroll
+    for (int k = 0; k < kParts; ++k) {
+      o0 += sOut[k][0][row];
+      o1 += sOut[k][1][row];
+    }
+    const int it = d.filt_target[f];
+    // Bounded update (dropped if not finite): with a ping received this step
+    // the estimate may move up to kMaxCorr L.  Without one, the rule chosen
+    // by the mode applies: hold the estimate (stale inputs cannot drive the
+    // closed loop away), apply the network all the same, or coast by the
+    // estimate's smoothed motion v (constant velocity).
+    const bool fresh = x[3] == 0.0f && x[4] == 1.0f;
+    const float lim = (fresh || stale == 1) ? kMaxCorr : 0.0f;
+    float c0 = isfinite(o0) ? fminf(fmaxf(o0, -lim), lim) : 0.0f;
+    float c1 = isfinite(o1) ? fminf(fmaxf(o1, -lim), lim) : 0.0f;
+    if (!fresh && stale == 2) {
+      c0 = fminf(fmaxf(x[5 * kRing + 2], -kMaxCorr), kMaxCorr);
+      c1 = fminf(fmaxf(x[5 * kRing + 3], -kMaxCorr), kMaxCorr);
+    }
+    const float ex = e1x + d.est_scale * c0, ey = e1y + d.est_scale * c1;
+    d.prev2_estx[f] = d.prev_estx[f];
+    d.prev2_esty[f] = d.prev_esty[f];
+    d.prev_estx[f] = e1x;
+    d.prev_esty[f] = e1y;
+    d.velx[f] = vnx;
+    d.vely[f] = vny;
+    d.estx[f] = ex;
+    d.esty[f] = ey;
+    const float dx = ex - d.tx[it], dy = ey - d.ty[it];
+    d.err[f] = sqrtf(dx * dx + dy * dy);
+  }
+  if (bad && tid == 0) {
+    // no copy may still be landing in shared memory when the CTA exits
+    for (int st = kEnvStages - 2; st < kEnvStages; ++st)
+      tc::mbar_wait(&full[st & 1], (uint32_t)((st >> 1) & 1), kEnvPolls);
+    raise_status(d.status, 2);
+  }
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, 256);
@@ -541,7 +701,7 @@ cudaError_t smem_optin(K k, size_t bytes, int& done) {
 cudaError_t launch_forward(const Net& net, const float* X, const int32_t* rows, int B, float* out, float* z,
                            uint16_t* a, cudaStream_t s) {
   static int ready = 0;
-  cudaError_t e = smem_optin(fwd_kernel<false>, kFwdSmem, ready);
+  cudaError_t e = smem_optin(fwd_kernel, kFwdSmem, ready);
   if (e != cudaSuccess) return e;
   if (B <= 0) return cudaSuccess;
   FwdArgs p;
@@ -553,22 +713,16 @@ cudaError_t launch_forward(const Net& net, const float* X, const int32_t* rows, 
   p.out = out;
   p.z = z;
   p.a = a;
-  fwd_kernel<false><<<(B + kT - 1) / kT, kT, kFwdSmem, s>>>(p);
+  fwd_kernel<<<(B + kT - 1) / kT, kT, kFwdSmem, s>>>(p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_forward_env(const Net& net, const EnvDev& d, int stale, cudaStream_t s) {
   static int ready = 0;
-  cudaError_t e = smem_optin(fwd_kernel<true>, kFwdSmem, ready);
+  cudaError_t e = smem_optin(fwd_env_kernel, kEnvSmem, ready);
   if (e != cudaSuccess) return e;
   if (d.F <= 0) return cudaSuccess;
-  FwdArgs p;
-  memset(&p, 0, sizeof(p));
-  p.net = net;
-  p.d = d;
-  p.stale = stale;
-  p.status = d.status;
-  fwd_kernel<true><<<(d.F + kT - 1) / kT, kT, kFwdSmem, s>>>(p);
+  fwd_env_kernel<<<(d.F + 127) / 128, kTE, kEnvSmem, s>>>(net, d, stale);
   return cudaGetLastError();
 }
 

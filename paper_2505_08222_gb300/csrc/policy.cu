@@ -119,19 +119,6 @@ __device__ __forceinline__ void store8(unsigned char* img, int row, int k0, int 
   *reinterpret_cast<uint4*>(img + tc::kmajor_offset(row, k0, rows)) = q;
 }
 
-// ---- bulk-copy engine (weights global -> shared) ---------------------------
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_addr(mbar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          tc::smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(tc::smem_addr(mbar))
-      : "memory");
-}
-
 // Weight image of global stage s (layer-major; within a layer: Wq, Wk, Wv,
 // Wo, then W1 chunk c and W2 chunk c for c = 0 .. NC-1).
 template <int D>
@@ -169,8 +156,8 @@ __device__ __forceinline__ void pump(Loader& ld, const unsigned char* __restrict
     uint32_t bytes;
     stage_image<D>(ld.next, off, bytes);
     const int slot = ld.next % kSlots;
-    mbar_expect_tx(&full[slot], bytes);
-    bulk_g2s(ring + slot * Geo<D>::SLOT, wimg + off, bytes, &full[slot]);
+    tc::mbar_expect_tx(&full[slot], bytes);
+    tc::bulk_g2s(ring + slot * Geo<D>::SLOT, wimg + off, bytes, &full[slot]);
     ++ld.next;
   }
 }

@@ -114,6 +114,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint3
   return false;
 }
 
+// ---- bulk-copy engine (global -> shared, completion on an mbarrier) --------
+// The issuing thread announces the bytes, then starts one contiguous copy
+// (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+      : "memory");
+}
+
 // ---- TMEM -> registers -----------------------------------------------------
 // 16 consecutive FP32 columns of this thread's TMEM lane (warp w reads lanes
 // 32 (w % 4) .. +31; `taddr` carries that lane base in bits 31..16).
