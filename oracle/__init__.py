@@ -115,6 +115,8 @@ def _declare(L):
     L.oc_gumbel_actions.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32,
                                     ctypes.c_int32, _dp, _ip, _dp]
     L.oc_step.argtypes = [ctypes.POINTER(OcConfig), ctypes.POINTER(OcState), _ip, ctypes.POINTER(OcStepOut)]
+    L.oc_step_learned.argtypes = [ctypes.POINTER(OcConfig), ctypes.POINTER(OcState), _ip, _dp, ctypes.c_int32,
+                                  ctypes.POINTER(OcStepOut)]
     L.oc_systematic_resample.argtypes = [ctypes.c_int32, _dp, ctypes.c_uint64, _ip]
     L.oc_tracking_reward.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.oc_tracking_reward.restype = ctypes.c_double
@@ -255,8 +257,11 @@ class OracleEnv:
         lib().oc_random_actions(ctypes.byref(self.cfg), g, self.NA, _p(act, _ip))
         return act
 
-    def step(self, actions: np.ndarray, want=()) -> dict:
-        """One step.  ``want`` names the intermediates to return."""
+    def step(self, actions: np.ndarray, want=(), mlp=None, mode: int = 2) -> dict:
+        """One step.  ``want`` names the intermediates to return.  With ``mlp``
+        (estimator parameters, canonical order) the learned tracker replaces
+        the particle filter (``mode`` 1 hold / 2 network / 3 coast on steps
+        without a fresh ping)."""
         P, AM = self.p.n_particles, self.p.max_agents
         NS = self.p.max_agents + self.p.max_targets
         shapes = {"range": (self.F, np.float64), "valid": (self.F, np.int32),
@@ -275,7 +280,12 @@ class OracleEnv:
         for k, v in out.items():
             setattr(so, k, _p(v, _ip if v.dtype == np.int32 else _dp))
         act = _i32(actions)
-        lib().oc_step(ctypes.byref(self.cfg), ctypes.byref(self.st), _p(act, _ip), ctypes.byref(so))
+        if mlp is None:
+            lib().oc_step(ctypes.byref(self.cfg), ctypes.byref(self.st), _p(act, _ip), ctypes.byref(so))
+        else:
+            prm = _f64(mlp)
+            lib().oc_step_learned(ctypes.byref(self.cfg), ctypes.byref(self.st), _p(act, _ip), _p(prm), int(mode),
+                                  ctypes.byref(so))
         if "tokens" in out:
             out["tokens"] = out["tokens"].reshape(self.NA, NS, 8)
         if "meas" in out:

@@ -782,7 +782,59 @@ void oc_est_features(const oc_config* c, const oc_state* s, uint32_t g, double* 
 /* One environment step in the order of reading C7: move agents, move        */
 /* targets, ping, communicate, update trackers, observe, reward.             */
 /* ------------------------------------------------------------------------ */
-void oc_step(const oc_config* c, oc_state* s, const int32_t* act, oc_step_out* o) {
+/* ------------------------------------------------------------------------ */
+/* Learned form of the tracker update (readings C18): the estimator network  */
+/* (oc_mlp_forward, utrack_oracle_nn.c) moves each filter's estimate e1 by    */
+/* L * clamp(out, +-3) on a step with a fresh ping.  Without one, mode 1      */
+/* holds e1, mode 2 applies the network all the same, mode 3 coasts by the    */
+/* smoothed motion v.  The history (e2 <- e1 <- estimate, v) is advanced      */
+/* first, so the features are those of oc_est_features for this step.        */
+/* ------------------------------------------------------------------------ */
+void oc_mlp_forward(int32_t B, const double* params, const double* X, double* out, double* pre);
+
+static void oc_learned_update(const oc_config* c, oc_state* s, uint32_t g, const double* mlp, int32_t mode,
+                              double* err) {
+  const int F = c->filter_off[c->n_envs];
+  const double L = c->est_scale;
+  for (int f = 0; f < F; ++f) {
+    s->velx[f] = OC_VEL_KEEP * s->velx[f] + (1.0 - OC_VEL_KEEP) * (s->estx[f] - s->prev_estx[f]);
+    s->vely[f] = OC_VEL_KEEP * s->vely[f] + (1.0 - OC_VEL_KEEP) * (s->esty[f] - s->prev_esty[f]);
+    s->prev2_estx[f] = s->prev_estx[f];
+    s->prev2_esty[f] = s->prev_esty[f];
+    s->prev_estx[f] = s->estx[f];
+    s->prev_esty[f] = s->esty[f];
+  }
+  double* feat = (double*)malloc(sizeof(double) * (size_t)F * OC_FEAT);
+  double* out = (double*)malloc(sizeof(double) * (size_t)F * 2);
+  oc_est_features(c, s, g, feat, NULL);
+  oc_mlp_forward(F, mlp, feat, out, NULL);
+  for (int e = 0; e < c->n_envs; ++e) {
+    int A = env_agents(c, e), T = env_targets(c, e);
+    for (int a = 0; a < A; ++a)
+      for (int k = 0; k < T; ++k) {
+        int f = filter_index(c, e, a, k);
+        int it = c->target_off[e] + k;
+        const double* x = feat + (int64_t)f * OC_FEAT;
+        int fresh = x[3] == 0.0 && x[4] == 1.0;
+        double lim = (fresh || mode == 2) ? 3.0 : 0.0;
+        double c0 = fmin(fmax(out[2 * (int64_t)f], -lim), lim);
+        double c1 = fmin(fmax(out[2 * (int64_t)f + 1], -lim), lim);
+        if (!fresh && mode == 3) {
+          c0 = fmin(fmax(x[5 * OC_RING + 2], -3.0), 3.0);
+          c1 = fmin(fmax(x[5 * OC_RING + 3], -3.0), 3.0);
+        }
+        s->estx[f] = s->prev_estx[f] + L * c0;
+        s->esty[f] = s->prev_esty[f] + L * c1;
+        double dx = s->estx[f] - s->tx[it], dy = s->esty[f] - s->ty[it];
+        err[f] = sqrt(dx * dx + dy * dy);
+      }
+  }
+  free(feat);
+  free(out);
+}
+
+static void step_impl(const oc_config* c, oc_state* s, const int32_t* act, oc_step_out* o, const double* mlp,
+                      int32_t mode) {
   int F = c->filter_off[c->n_envs];
   int NA = c->agent_off[c->n_envs];
   int AM = c->max_agents;
@@ -801,7 +853,10 @@ void oc_step(const oc_config* c, oc_state* s, const int32_t* act, oc_step_out* o
   oc_step_out local = {0};
   if (o) local = *o;
   local.err = err;
-  oc_pf_update(c, s, g, meas, meas_n, &local);
+  if (mlp)
+    oc_learned_update(c, s, g, mlp, mode, err);
+  else
+    oc_pf_update(c, s, g, meas, meas_n, &local);
   if (o && o->tokens) oc_obs(c, s, o->tokens);
   if (o && o->reward) oc_reward(c, s, err, o->reward, o->crash);
   if (o && o->range) memcpy(o->range, range, sizeof(double) * F);
@@ -813,4 +868,12 @@ void oc_step(const oc_config* c, oc_state* s, const int32_t* act, oc_step_out* o
   s->step = g;
   s->t_ep += 1;
   free(range); free(valid); free(recv); free(meas); free(meas_n); free(err);
+}
+
+void oc_step(const oc_config* c, oc_state* s, const int32_t* act, oc_step_out* o) { step_impl(c, s, act, o, NULL, 0); }
+
+/* The same step with the learned tracker (mode 1, 2 or 3 as above). */
+void oc_step_learned(const oc_config* c, oc_state* s, const int32_t* act, const double* mlp, int32_t mode,
+                     oc_step_out* o) {
+  step_impl(c, s, act, o, mlp, mode);
 }

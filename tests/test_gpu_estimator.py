@@ -221,3 +221,47 @@ def test_learned_mode_stale_rules(mode):
         want = e1[stale] + 100.0 * np.clip(X[stale, 82:84], -3.0, 3.0)
     np.testing.assert_allclose(est[stale], want, atol=2e-3)
     env.est_set_mode(0)
+
+
+def _inject_oracle_state(env, o):
+    """The oracle's state in float32 (history, smoothed motion and ping rings
+    included) into both the GPU handle and the oracle itself."""
+    keys = ["ax", "ay", "apsi", "tx", "ty", "tz", "tpsi", "tspeed", "px", "py", "pvx", "pvy", "lpx", "lpy", "estx",
+            "esty", "prev_estx", "prev_esty", "prev2_estx", "prev2_esty", "velx", "vely", "ring"]
+    st = {k: o.arr[k].astype(np.float32) for k in keys}
+    st.update(lpage=o.arr["lpage"], ring_head=o.arr["ring_head"], ring_count=o.arr["ring_count"])
+    tens = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in st.items()}
+    env.set_state(o.step_count, 4, **tens)
+    o.set_arrays(**{k: v.astype(np.float64) if v.dtype == np.float32 else v for k, v in st.items()})
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+def test_learned_step_matches_oracle(mode):
+    """One learned-form step from an injected oracle state, GPU against the
+    oracle's learned tracker: with a constant-output network (weights zero,
+    output bias exactly representable) the update rule must agree to float32
+    rounding; with a random network to the forward pass's BF16 tolerance
+    (2e-2 + 2e-2 |out| in units of L = 100 m, outputs clamped to 3)."""
+    const = np.zeros(NP, np.float32)
+    const[-2:] = (0.5, -4.0)
+    for params, atol in ((const, 1e-2), (synth.mlp_params(seed=21, bias_scale=0.1), 8.0)):
+        env, p = _env(n_envs=6, det_radius=130.0, comm_drop=0.2)
+        env.reset(8)
+        o = oracle.OracleEnv(p, 8)
+        o.reset(0)
+        for t in range(1, 5):
+            o.step(np.random.default_rng(t).integers(0, 7, o.NA).astype(np.int32))
+        _inject_oracle_state(env, o)
+        env.est_set_weights(params)
+        env.est_set_mode(mode)
+        act = np.random.default_rng(99).integers(0, 7, o.NA).astype(np.int32)
+        out = env.step(torch.from_numpy(act).cuda())
+        ref = o.step(act, mlp=params.astype(np.float64), mode=mode)
+        got = np.stack([out["estx"].cpu().numpy(), out["esty"].cpu().numpy()], 1)
+        want = np.stack([o.arr["estx"], o.arr["esty"]], 1)
+        err = np.abs(got - want)
+        print(f"mode {mode} atol {atol}: max |d est| {err.max():.3e} m, median {np.median(err):.3e} m")
+        assert np.all(err <= atol), float(err.max())
+        np.testing.assert_allclose(out["err"].cpu().numpy(), ref["err"], atol=atol * 1.5)
+        env.est_set_mode(0)
+        env.close()

@@ -186,3 +186,61 @@ def test_adam_matches_torch():
         p.grad = torch.tensor(g)
         opt.step()
     np.testing.assert_allclose(theta, p.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+def _learned_env(**kw):
+    from synth import preset
+    p = preset("fleet5", n_envs=3).replace(n_particles=64, d_model=0, **kw)
+    o = oracle.OracleEnv(p, 5)
+    o.reset(0)
+    for t in range(1, 4):
+        o.step(o.random_actions(t))
+    return o
+
+
+def _const_net(c0, c1):
+    prm = np.zeros(oracle.mlp_param_count())
+    prm[-2:] = (c0, c1)  # b4: the network outputs (c0, c1) for every input
+    return prm
+
+
+def test_learned_step_update_rule_closed_forms():
+    """The learned tracker's update with a constant-output network
+    (all weights zero, output bias (c0, c1)): with a fresh ping the estimate
+    moves by L clamp(c, +-3); without one it is held (mode 1), moved all the
+    same (mode 2) or coasts by the smoothed motion (mode 3)."""
+    L = 100.0
+    for mode in (1, 2, 3):
+        o = _learned_env(det_radius=130.0)
+        e0x, e0y = o.arr["estx"].copy(), o.arr["esty"].copy()
+        p0x, p0y = o.arr["prev_estx"].copy(), o.arr["prev_esty"].copy()
+        v0x = o.arr["velx"].copy()
+        o.step(o.random_actions(4), mlp=_const_net(0.5, -4.0), mode=mode)
+        feat, _ = o.est_features(o.step_count)
+        fresh = (feat[:, 3] == 0) & (feat[:, 4] == 1)
+        assert 0 < fresh.sum() < o.F
+        np.testing.assert_allclose(o.arr["prev_estx"], e0x)
+        np.testing.assert_allclose(o.arr["velx"], 0.85 * v0x + 0.15 * (e0x - p0x), rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(o.arr["estx"][fresh], e0x[fresh] + 0.5 * L, rtol=1e-12)
+        np.testing.assert_allclose(o.arr["esty"][fresh], e0y[fresh] - 3.0 * L, rtol=1e-12)
+        st = ~fresh
+        if mode == 1:
+            np.testing.assert_array_equal(o.arr["estx"][st], e0x[st])
+        elif mode == 2:
+            np.testing.assert_allclose(o.arr["estx"][st], e0x[st] + 0.5 * L, rtol=1e-12)
+        else:
+            vx = o.arr["velx"][st]
+            np.testing.assert_allclose(o.arr["estx"][st], e0x[st] + np.clip(vx, -3 * L, 3 * L), rtol=1e-12)
+
+
+def test_learned_step_zero_network_holds_estimates():
+    """A network that outputs zero leaves every estimate where it was; the
+    reported error is then the distance from it to the (moved) target."""
+    o = _learned_env()
+    e0x, e0y = o.arr["estx"].copy(), o.arr["esty"].copy()
+    out = o.step(o.random_actions(4), mlp=np.zeros(oracle.mlp_param_count()), mode=2)
+    np.testing.assert_array_equal(o.arr["estx"], e0x)
+    np.testing.assert_array_equal(o.arr["esty"], e0y)
+    f = np.arange(o.F)
+    tgt = (f // 25) * 5 + f % 5  # 5 x 5 fleets: filter (env, agent, target) -> target index
+    np.testing.assert_allclose(out["err"], np.hypot(e0x - o.arr["tx"][tgt], e0y - o.arr["ty"][tgt]), rtol=1e-12)
