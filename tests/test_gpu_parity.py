@@ -197,7 +197,8 @@ def test_step_parity_from_injected_state(name, n_envs, P, kw):
 
 
 # ---------------------------------------------------------------- whole rollouts
-@pytest.mark.parametrize("name,n_envs,T,P", [("small", 1024, 200, 1000), ("fleet5", 64, 100, 2048)])
+@pytest.mark.parametrize("name,n_envs,T,P", [("small", 1024, 200, 1000), ("fleet5", 64, 100, 2048),
+                                           ("ragged", 96, 60, 1024)])
 def test_rollout_rmse_matches_oracle(name, n_envs, T, P):
     """Mean tracking RMSE of whole rollouts agrees within 2% (north-star
     bound).  'Mean tracking RMSE' = mean over filters of each filter's RMSE
