@@ -13,8 +13,8 @@
 //                  Q, K, V = Y Wq^T, Y Wk^T, Y Wv^T      (three tcgen05.mma
 //                      groups issued together, FP32 in TMEM)
 //                  O = softmax(Q K^T / 4) V per head, within the agent's
-//                      valid tokens                      (CUDA cores, each
-//                      column part takes H / NS heads)
+//                      valid tokens                      (warp-level MMAs, one
+//                      warp per agent and head)
 //                  X += O Wo^T + bo                      (tcgen05.mma)
 //                  X += W2 GELU(W1 LN2(X) + b1) + b2      (tcgen05.mma, hidden
 //                      units in chunks of 128 accumulated in TMEM)
@@ -41,7 +41,7 @@ namespace ut {
 namespace {
 
 constexpr int kSlots = 3;                                  // weight ring depth
-constexpr int kMaxTok = 1 + UT_MAX_AGENTS + UT_MAX_TARGETS;  // tokens per agent
+static_assert(1 + UT_MAX_AGENTS + UT_MAX_TARGETS <= 32, "attention tiles cover at most 32 rows per agent");
 constexpr float kLnEps = 1e-5f;
 constexpr uint32_t kPolls = 1u << 22;                      // bounded mbarrier waits
 
@@ -51,9 +51,7 @@ struct Geo {
   static constexpr int NS = D == 64 ? 2 : 4;       // column parts per row
   static constexpr int THREADS = 128 * NS;
   static constexpr int COLS = D / NS;              // columns per thread
-  static constexpr int HH = H / NS;                // heads per thread
   static constexpr int HCOLS = 128 / NS;           // hidden units per thread in an FFN chunk
-  static constexpr int KVS = D + 8;                // bf16 row stride of K / V
   static constexpr int NC = (4 * D) / 128;         // FFN hidden chunks of 128
   static constexpr int NSTG = 4 + 2 * NC;          // weight images per layer
   static constexpr int VEC = 13 * D;               // per-layer vector floats
@@ -71,7 +69,7 @@ struct Geo {
   static constexpr size_t A_BYTES = (size_t)128 * D * 2;
   static constexpr size_t RING_OFF = A_OFF + A_BYTES;
   static constexpr size_t KV_OFF = RING_OFF + kSlots * SLOT;
-  static constexpr size_t KV_BYTES = (size_t)2 * 128 * KVS * 2;
+  static constexpr size_t KV_BYTES = (size_t)2 * 128 * D * 2;   // K, V as K-major images
   static constexpr size_t VEC_OFF = KV_OFF + KV_BYTES;
   static constexpr size_t STAT_OFF = VEC_OFF + (size_t)2 * VEC * 4;
   static constexpr size_t SMEM = STAT_OFF + (size_t)NS * 128 * 8;
@@ -256,6 +254,148 @@ __device__ __forceinline__ void store16_bf(uint16_t* dst, const float (&v)[16]) 
   *reinterpret_cast<uint4*>(dst + 8) = b;
 }
 
+// ---- per-agent attention on warp-level MMAs ------------------------------
+// Q (bias added, scaled by log2(e) / 4), K and V sit in shared memory as
+// K-major BF16 operand images [128 rows x d] (tc.cuh layout: every 8 columns
+// of a row form one 16-byte chunk), which ldmatrix reads directly.  One warp
+// takes one (agent, head): S = Q_h K_h^T and O = softmax(S) V_h with
+// mma.sync.m16n8k16 (BF16 inputs, FP32 accumulation) over the agent's rows
+// padded to 16 (R <= 16) or 32; the softmax runs on the accumulator
+// fragments (a row lives in the 4 lanes of a quad) and P is re-packed into A
+// fragments in registers.
+__device__ __forceinline__ uint32_t kmajor_row(uint32_t base, int row, int k0) {
+  return base + (uint32_t)((k0 >> 3) * (128 * 16) + row * 16);
+}
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t (&r)[4]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t (&r)[4]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
+// D (16 x 8, FP32) += A (16 x 16, BF16, row) * B (16 x 8, BF16, col)
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// One (agent, head) on the calling warp: the agent's rows r0 .. r0 + R - 1,
+// keys r0 .. r0 + nt - 1 valid; writes O_h into the agent's rows of aO (the
+// same K-major image as Q).  MT = 16-row tiles covering R.
+template <int MT>
+__device__ __forceinline__ void attend_warp(uint32_t aQ, uint32_t aK, uint32_t aV, int r0, int R, int nt, int h) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3;
+  const int mi = lane >> 3, rr = lane & 7;
+  uint32_t qa[MT][4];
+#pragma unroll
+  for (int m = 0; m < MT; ++m) {  // A: rows r0 + 16 m .., head columns 16 h ..
+    const int row = min(r0 + 16 * m + rr + (mi & 1) * 8, 127);
+    ldsm_x4(kmajor_row(aQ, row, 16 * h + (mi >> 1) * 8), qa[m]);
+  }
+  float sc[MT][2 * MT][4];
+#pragma unroll
+  for (int m = 0; m < MT; ++m)
+#pragma unroll
+    for (int n = 0; n < 2 * MT; ++n)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) sc[m][n][i] = 0.0f;
+#pragma unroll
+  for (int kt = 0; kt < MT; ++kt) {  // keys 16 kt .. 16 kt + 15: B fragments of two 8-key tiles
+    uint32_t kb[4];
+    const int key = min(r0 + 16 * kt + rr + (mi >> 1) * 8, 127);
+    ldsm_x4(kmajor_row(aK, key, 16 * h + (mi & 1) * 8), kb);
+#pragma unroll
+    for (int m = 0; m < MT; ++m) {
+      mma16816(sc[m][2 * kt], qa[m], kb[0], kb[1]);
+      mma16816(sc[m][2 * kt + 1], qa[m], kb[2], kb[3]);
+    }
+  }
+  // softmax along each query row (base-2: Q carries the log2(e) factor)
+  float inv[MT][2];
+#pragma unroll
+  for (int m = 0; m < MT; ++m)
+#pragma unroll
+    for (int hr = 0; hr < 2; ++hr) {
+      float mx = -INFINITY;
+#pragma unroll
+      for (int n = 0; n < 2 * MT; ++n)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int col = 8 * n + 2 * tig + j;
+          const float v = col < nt ? sc[m][n][2 * hr + j] : -INFINITY;
+          sc[m][n][2 * hr + j] = v;
+          mx = fmaxf(mx, v);
+        }
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+      float sum = 0.0f;
+#pragma unroll
+      for (int n = 0; n < 2 * MT; ++n)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const float e = ex2_approx(sc[m][n][2 * hr + j] - mx);
+          sc[m][n][2 * hr + j] = e;
+          sum += e;
+        }
+      sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+      sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+      inv[m][hr] = 1.0f / sum;
+    }
+  // O = P V: P from the score fragments, V through transposing loads
+  float o[MT][2][4];
+#pragma unroll
+  for (int m = 0; m < MT; ++m)
+#pragma unroll
+    for (int dn = 0; dn < 2; ++dn)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) o[m][dn][i] = 0.0f;
+#pragma unroll
+  for (int kk = 0; kk < MT; ++kk) {
+    uint32_t vb[4];
+    const int key = min(r0 + 16 * kk + rr + (mi & 1) * 8, 127);
+    ldsm_x4_t(kmajor_row(aV, key, 16 * h + (mi >> 1) * 8), vb);
+#pragma unroll
+    for (int m = 0; m < MT; ++m) {
+      uint32_t pa[4];
+      pa[0] = pack_bf2(sc[m][2 * kk][0], sc[m][2 * kk][1]);
+      pa[1] = pack_bf2(sc[m][2 * kk][2], sc[m][2 * kk][3]);
+      pa[2] = pack_bf2(sc[m][2 * kk + 1][0], sc[m][2 * kk + 1][1]);
+      pa[3] = pack_bf2(sc[m][2 * kk + 1][2], sc[m][2 * kk + 1][3]);
+      mma16816(o[m][0], pa, vb[0], vb[1]);
+      mma16816(o[m][1], pa, vb[2], vb[3]);
+    }
+  }
+  __syncwarp();
+  // normalised O into the agent's own rows (other rows of the 16-row tiles
+  // belong to the next agent or to padding)
+#pragma unroll
+  for (int m = 0; m < MT; ++m)
+#pragma unroll
+    for (int hr = 0; hr < 2; ++hr) {
+      const int row = r0 + 16 * m + g + 8 * hr;
+      if (row < r0 + R && row < 128) {
+#pragma unroll
+        for (int dn = 0; dn < 2; ++dn) {
+          const int k = 16 * h + 8 * dn + 2 * tig;
+          const uint32_t w = pack_bf2(o[m][dn][2 * hr] * inv[m][hr], o[m][dn][2 * hr + 1] * inv[m][hr]);
+          asm volatile("st.shared.b32 [%0], %1;" ::"r"(kmajor_row(aQ, row, k) + (uint32_t)((k & 7) * 2)), "r"(w)
+                       : "memory");
+        }
+      }
+    }
+}
+
 template <int D>
 __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_kernel(PolicyDev p) {
   using G = Geo<D>;
@@ -263,8 +403,8 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem + G::A_OFF;
   unsigned char* ring = smem + G::RING_OFF;
-  uint16_t* sK = reinterpret_cast<uint16_t*>(smem + G::KV_OFF);
-  uint16_t* sV = sK + 128 * G::KVS;
+  unsigned char* sK = smem + G::KV_OFF;             // K-major image [128 x D]
+  unsigned char* sV = sK + (size_t)128 * D * 2;      // K-major image [128 x D]
   unsigned char* sH = smem + G::KV_OFF;  // FFN hidden chunk image [128 x 128] (K/V are dead by then)
   float* sVec = reinterpret_cast<float*>(smem + G::VEC_OFF);
   float2* sStat = reinterpret_cast<float2*>(smem + G::STAT_OFF);
@@ -281,7 +421,6 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
   const bool agent_ok = slot < p.apt && ag < p.NA;
   const int n_tok = agent_ok ? 1 + min(max(p.n_ent[ag], 0), p.NS) : 0;
   const bool row_ok = tok < n_tok;
-  const int row0 = slot * p.R;  // first row of this agent
 
   if (warp == 0) {
     tc::tmem_alloc(&tmem_base_s, G::TMEM_COLS);
@@ -378,67 +517,41 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
       tc::mma_commit(&mma_bar);
     }
     wait_mma(3);
-    // K and V (+ bias) -> shared memory as BF16, this thread's part of the columns
+    // Q (+ bias, times log2(e) / 4 for a base-2 softmax), K and V (+ bias) ->
+    // K-major BF16 images, this thread's part of the columns; Q replaces the
+    // LayerNorm output in the A image (the QKV group has completed)
 #pragma unroll 1
-    for (int kv = 0; kv < 2; ++kv) {
-      const float* bias = kv == 0 ? bk : bv;
-      uint16_t* dst = (kv == 0 ? sK : sV) + row * G::KVS + c_lo;
+    for (int qkv = 0; qkv < 3; ++qkv) {
+      const float* bias = qkv == 0 ? bq : (qkv == 1 ? bk : bv);
+      const float scale = qkv == 0 ? 0.25f * 1.44269504088896341f : 1.0f;  // 1 / sqrt(16), log2(e)
+      unsigned char* dst = qkv == 0 ? sA : (qkv == 1 ? sK : sV);
+      const uint32_t col = qkv == 0 ? G::COL_Q : (qkv == 1 ? G::COL_K : G::COL_V);
 #pragma unroll 1
       for (int c0 = 0; c0 < COLS; c0 += 16) {
         float v[16];
-        tc::tmem_ld16(tl + (kv == 0 ? G::COL_K : G::COL_V) + c_lo + c0, v);
+        tc::tmem_ld16(tl + col + c_lo + c0, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] += bias[c_lo + c0 + i];
-        store16_bf(dst + c0, v);
+        for (int i = 0; i < 16; ++i) v[i] = (v[i] + bias[c_lo + c0 + i]) * scale;
+        store8(dst, row, c_lo + c0, 128, v);
+        store8(dst, row, c_lo + c0 + 8, 128, v + 8);
       }
     }
-    __syncthreads();  // K, V of every row visible
-    // per-head softmax attention over the agent's valid tokens (this
-    // thread's heads: part * HH .. +HH); scores stay in registers
+    __syncthreads();  // Q, K, V of every row visible
+    // softmax attention per (agent, head) on warp-level MMAs; O overwrites Q
+    // in the agent's rows and the head's columns
+    {
+      const uint32_t aK = tc::smem_addr(sK), aV = tc::smem_addr(sV);
 #pragma unroll 1
-    for (int hh = 0; hh < G::HH; ++hh) {
-      const int h = part * G::HH + hh;
-      float q[16];
-      tc::tmem_ld16(tl + G::COL_Q + h * 16, q);
-#pragma unroll
-      for (int i = 0; i < 16; ++i) q[i] = (q[i] + bq[h * 16 + i]) * 0.25f;  // 1 / sqrt(16)
-      float o[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) o[i] = 0.0f;
-      if (row_ok) {
-        float sc[kMaxTok];
-        float m = -INFINITY;
-#pragma unroll
-        for (int j = 0; j < kMaxTok; ++j) {
-          sc[j] = -INFINITY;
-          if (j < n_tok) {
-            float kr[16];
-            load16_bf(sK + (row0 + j) * G::KVS + h * 16, kr);
-            float a = 0.0f;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) a = fmaf(q[i], kr[i], a);
-            sc[j] = a;
-            m = fmaxf(m, a);
-          }
-        }
-        float den = 0.0f;
-#pragma unroll
-        for (int j = 0; j < kMaxTok; ++j) {
-          if (j < n_tok) {
-            const float e = __expf(sc[j] - m);
-            den += e;
-            float vr[16];
-            load16_bf(sV + (row0 + j) * G::KVS + h * 16, vr);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) o[i] = fmaf(e, vr[i], o[i]);
-          }
-        }
-        const float inv = 1.0f / den;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) o[i] *= inv;
+      for (int task = warp; task < p.apt * G::H; task += kThreads / 32) {
+        const int a = task / G::H, h = task - a * G::H;
+        const long long ag2 = (long long)blockIdx.x * p.apt + a;
+        if (ag2 >= p.NA) continue;  // warp-uniform
+        const int nt = 1 + min(max(p.n_ent[ag2], 0), p.NS);
+        if (p.R <= 16)
+          attend_warp<1>(aA, aK, aV, a * p.R, p.R, nt, h);
+        else
+          attend_warp<2>(aA, aK, aV, a * p.R, p.R, nt, h);
       }
-      store8(sA, row, h * 16, 128, o);
-      store8(sA, row, h * 16 + 8, 128, o + 8);
     }
     publish();
     if (tid == 0) {
