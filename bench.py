@@ -249,14 +249,34 @@ def learned_form(args, p, K, W, rank):
         env.step()
     est_ms, est_n = env.stage_time()
     env.profile(False)
+
+    # least-squares trilateration tracker (est_set_mode 4) on the same seeds,
+    # and a timed rollout of that form
+    ls_rmse = [eval_rmse(4, s, T_eval) for s in seeds]
+    env.est_set_mode(4)
+    env.reset(1000 + rank)
+    for _ in range(W):
+        env.step()
+    env.rollout_prepare(K)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    st_ls = env.rollout(K)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_ls = ev0.elapsed_time(ev1)
+    env.est_set_mode(0)
     env.close()
     pf_mean = sum(pf_rmse) / len(pf_rmse)
     le_mean = sum(le_rmse) / len(le_rmse)
+    ls_mean = sum(ls_rmse) / len(ls_rmse)
     return {"value": st["agent_steps"] / (ms / 1e3), "unit": "agent-steps/s", "ms_per_step": ms / K,
             "estimator_kernel_ms": est_ms / max(est_n, 1),
             "rmse_m": le_mean, "pf_rmse_m": pf_mean, "rmse_ratio": le_mean / pf_mean,
             "eval": f"{len(seeds)} held-out seeds x {T_eval} steps each form, pooled RMSE per run, mean over seeds",
             "stale_rule": "network applied on steps without a fresh ping too (est_set_mode 2)",
+            "ls_form": {"value": st_ls["agent_steps"] / (ms_ls / 1e3), "unit": "agent-steps/s", "ms_per_step": ms_ls / K,
+                        "rmse_m": ls_mean, "rmse_ratio": ls_mean / pf_mean,
+                        "tracker": "least-squares trilateration over each filter's 16 newest pings (est_set_mode 4)"},
             "train": {"rows": steps_rec * F, "wall_s": rec_s, "steps": 2 * args.train_steps, "batch": 16384,
                       "candidates": len(cands), "validation_rmse_m": [round(v, 1) for v, _, _, _ in cands],
                       "chosen": c_best, "validation": "seed 8000, same horizon; evaluation seeds 9000 and 9100",

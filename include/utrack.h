@@ -338,8 +338,12 @@ ut_status est_get_weights(ut_env* env, float* params_host, int64_t n_params);
  * UT_FLAG_RING).  On a step without a fresh ping the estimate is held (1),
  * moved by the network all the same (2), or coasts by its smoothed motion v
  * (3, constant velocity; see ut_state_view.velx); with a fresh ping the
- * network's correction applies.
- * Errors: UT_ERR_INVALID (mode outside 0..3), UT_ERR_STATE. */
+ * network's correction applies.  4: least-squares trilateration tracker
+ * (Sec. II-A; Sec. III-A.2 names LS next to the PF) over the pings in each
+ * filter's ring, the target taken as static over the window, depth known
+ * (needs UT_FLAG_RING, no weights); the estimate is held with fewer than 3
+ * pings or collinear senders (det A <= 1e-3 (tr A)^2 for the 2 x 2 normal
+ * matrix A).  Errors: UT_ERR_INVALID (mode outside 0..4), UT_ERR_STATE. */
 ut_status est_set_mode(ut_env* env, int32_t mode);
 /* Raw network outputs out_dev [n_rows][2] of features X_dev [n_rows][96]. */
 ut_status est_forward(ut_env* env, const float* X_dev, float* out_dev, int64_t n_rows);

@@ -115,6 +115,7 @@ def _declare(L):
     L.oc_gumbel_actions.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_int32,
                                     ctypes.c_int32, _dp, _ip, _dp]
     L.oc_step.argtypes = [ctypes.POINTER(OcConfig), ctypes.POINTER(OcState), _ip, ctypes.POINTER(OcStepOut)]
+    L.oc_ls_update.argtypes = [ctypes.POINTER(OcConfig), ctypes.POINTER(OcState), _dp]
     L.oc_step_learned.argtypes = [ctypes.POINTER(OcConfig), ctypes.POINTER(OcState), _ip, _dp, ctypes.c_int32,
                                   ctypes.POINTER(OcStepOut)]
     L.oc_systematic_resample.argtypes = [ctypes.c_int32, _dp, ctypes.c_uint64, _ip]
@@ -261,7 +262,7 @@ class OracleEnv:
         """One step.  ``want`` names the intermediates to return.  With ``mlp``
         (estimator parameters, canonical order) the learned tracker replaces
         the particle filter (``mode`` 1 hold / 2 network / 3 coast on steps
-        without a fresh ping)."""
+        without a fresh ping); ``mode=4`` selects the least-squares tracker."""
         P, AM = self.p.n_particles, self.p.max_agents
         NS = self.p.max_agents + self.p.max_targets
         shapes = {"range": (self.F, np.float64), "valid": (self.F, np.int32),
@@ -280,7 +281,10 @@ class OracleEnv:
         for k, v in out.items():
             setattr(so, k, _p(v, _ip if v.dtype == np.int32 else _dp))
         act = _i32(actions)
-        if mlp is None:
+        if mode == 4:  # least-squares tracker
+            lib().oc_step_learned(ctypes.byref(self.cfg), ctypes.byref(self.st), _p(act, _ip), None, 4,
+                                  ctypes.byref(so))
+        elif mlp is None:
             lib().oc_step(ctypes.byref(self.cfg), ctypes.byref(self.st), _p(act, _ip), ctypes.byref(so))
         else:
             prm = _f64(mlp)
@@ -291,6 +295,13 @@ class OracleEnv:
         if "meas" in out:
             out["meas"] = out["meas"].reshape(self.F, AM, 4)
         return out
+
+    def ls_update(self) -> np.ndarray:
+        """The least-squares tracker's update on the current rings alone
+        (history advanced, estimates replaced); returns the errors [F]."""
+        err = np.zeros(self.F)
+        lib().oc_ls_update(ctypes.byref(self.cfg), ctypes.byref(self.st), _p(err))
+        return err
 
     def obs(self) -> np.ndarray:
         """Observation tokens of the current state [NA, A_max + T_max, 8]."""

@@ -833,6 +833,74 @@ static void oc_learned_update(const oc_config* c, oc_state* s, uint32_t g, const
   free(out);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Least-squares trilateration tracker (Sec. II-A; Sec. III-A.2 names LS and  */
+/* PF as the two tracking models), reading C21.  The pings in the filter's    */
+/* ring, horizontal ranges rho = sqrt(max(r^2 - dz^2, 0)) with the target     */
+/* depth known, the target static over the window: |x - q|^2 = rho^2 gives    */
+/* 2 q.x = |x|^2 + a, a = |q|^2 - rho^2; subtracting the mean over the pings  */
+/* leaves the linear system 2 (q_m - qbar).x = a_m - abar, solved in the      */
+/* least-squares sense by the 2 x 2 normal equations.  Positions relative to  */
+/* the previous estimate e1.  Fewer than 3 pings, or det A <= 1e-3 (tr A)^2,  */
+/* hold e1.                                                                   */
+/* ------------------------------------------------------------------------ */
+#define OC_LS_MIN_DET_RATIO 1e-3
+
+void oc_ls_update(const oc_config* c, oc_state* s, double* err) {
+  for (int e = 0; e < c->n_envs; ++e) {
+    int A = env_agents(c, e), T = env_targets(c, e);
+    for (int a = 0; a < A; ++a)
+      for (int k = 0; k < T; ++k) {
+        int f = filter_index(c, e, a, k);
+        int it = c->target_off[e] + k;
+        double e1x = s->estx[f], e1y = s->esty[f], dz = s->tz[it];
+        int n = s->ring_count[f];
+        double qx[OC_RING], qy[OC_RING], av[OC_RING], mx = 0.0, my = 0.0, ma = 0.0;
+        for (int sl = 0; sl < n; ++sl) {
+          int pos = ((s->ring_head[f] - 1 - sl) % OC_RING + OC_RING) % OC_RING;
+          const double* r = s->ring + ((int64_t)f * OC_RING + pos) * 4;
+          double rho2 = fmax(r[2] * r[2] - dz * dz, 0.0);
+          qx[sl] = r[0] - e1x;
+          qy[sl] = r[1] - e1y;
+          av[sl] = qx[sl] * qx[sl] + qy[sl] * qy[sl] - rho2;
+          mx += qx[sl];
+          my += qy[sl];
+          ma += av[sl];
+        }
+        double ex = e1x, ey = e1y;
+        if (n >= 3) {
+          mx /= n;
+          my /= n;
+          ma /= n;
+          double a00 = 0.0, a01 = 0.0, a11 = 0.0, b0 = 0.0, b1 = 0.0;
+          for (int sl = 0; sl < n; ++sl) {
+            double dx = qx[sl] - mx, dy = qy[sl] - my, da = av[sl] - ma;
+            a00 += dx * dx;
+            a01 += dx * dy;
+            a11 += dy * dy;
+            b0 += 0.5 * dx * da;
+            b1 += 0.5 * dy * da;
+          }
+          double det = a00 * a11 - a01 * a01, tr = a00 + a11;
+          if (det > OC_LS_MIN_DET_RATIO * tr * tr) {
+            ex = e1x + (a11 * b0 - a01 * b1) / det;
+            ey = e1y + (a00 * b1 - a01 * b0) / det;
+          }
+        }
+        s->velx[f] = OC_VEL_KEEP * s->velx[f] + (1.0 - OC_VEL_KEEP) * (e1x - s->prev_estx[f]);
+        s->vely[f] = OC_VEL_KEEP * s->vely[f] + (1.0 - OC_VEL_KEEP) * (e1y - s->prev_esty[f]);
+        s->prev2_estx[f] = s->prev_estx[f];
+        s->prev2_esty[f] = s->prev_esty[f];
+        s->prev_estx[f] = e1x;
+        s->prev_esty[f] = e1y;
+        s->estx[f] = ex;
+        s->esty[f] = ey;
+        double dxe = ex - s->tx[it], dye = ey - s->ty[it];
+        err[f] = sqrt(dxe * dxe + dye * dye);
+      }
+  }
+}
+
 static void step_impl(const oc_config* c, oc_state* s, const int32_t* act, oc_step_out* o, const double* mlp,
                       int32_t mode) {
   int F = c->filter_off[c->n_envs];
@@ -853,7 +921,9 @@ static void step_impl(const oc_config* c, oc_state* s, const int32_t* act, oc_st
   oc_step_out local = {0};
   if (o) local = *o;
   local.err = err;
-  if (mlp)
+  if (mode == 4)
+    oc_ls_update(c, s, err);
+  else if (mlp)
     oc_learned_update(c, s, g, mlp, mode, err);
   else
     oc_pf_update(c, s, g, meas, meas_n, &local);
@@ -872,7 +942,8 @@ static void step_impl(const oc_config* c, oc_state* s, const int32_t* act, oc_st
 
 void oc_step(const oc_config* c, oc_state* s, const int32_t* act, oc_step_out* o) { step_impl(c, s, act, o, NULL, 0); }
 
-/* The same step with the learned tracker (mode 1, 2 or 3 as above). */
+/* The same step with the learned tracker (mode 1, 2 or 3 as above) or, with
+ * mode 4, the least-squares tracker (mlp unused). */
 void oc_step_learned(const oc_config* c, oc_state* s, const int32_t* act, const double* mlp, int32_t mode,
                      oc_step_out* o) {
   step_impl(c, s, act, o, mlp, mode);

@@ -211,7 +211,8 @@ class Env:
     def est_set_mode(self, mode):
         """0 / False: particle filter; 1 / True: learned estimator, estimate held
         on steps without a fresh ping; 2: network on every step; 3: coast at the
-        estimate's smoothed motion on steps without a fresh ping."""
+        estimate's smoothed motion on steps without a fresh ping; 4: least-squares
+        trilateration over the ring's pings (no network)."""
         _check(lib.est_set_mode(self.h, int(mode)), self.h, "est_set_mode")
 
     def est_forward(self, X: torch.Tensor) -> torch.Tensor:

@@ -474,7 +474,7 @@ static ut_status graph_ensure(ut_env* h, int32_t T) {
     UT_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     UT_CUDA(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   }
-  const int key = T * 8 + (h->policy_ready ? 1 : 0) + 2 * h->est_mode;
+  const int key = T * 16 + (h->policy_ready ? 1 : 0) + 2 * h->est_mode;  // est_mode 0..4
   if (!h->graph_exec || h->graph_key != key || h->graph_variant != h->pf_variant) {
     if (h->graph_exec) {
       cudaGraphExecDestroy(h->graph_exec);

@@ -77,6 +77,7 @@ cudaError_t launch_step_env(const EnvDev& d, const int32_t* act_in, cudaStream_t
 cudaError_t launch_obs_reward(const EnvDev& d, int after_reset, cudaStream_t s);
 cudaError_t launch_advance(const EnvDev& d, cudaStream_t s);
 cudaError_t launch_pf_step(const EnvDev& d, int variant, cudaStream_t s);
+cudaError_t launch_ls_update(const EnvDev& d, cudaStream_t s);
 int pf_default_variant(int P);
 int pf_variant_count();
 const char* pf_variant_name(int v);

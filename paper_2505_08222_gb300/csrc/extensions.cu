@@ -291,6 +291,7 @@ cudaError_t est_grad_batch(ut_env* h, const float* X, const float* Y, const int3
 
 namespace ut {
 cudaError_t extension_estimate_impl(ut_env* h, cudaStream_t s) {
+  if (h->est_mode == 4) return launch_ls_update(h->d, s);
   if (h->est_mode < 1 || !h->est || !h->est->weights_set) return cudaErrorNotReady;
   return est::launch_forward_env(est_net(h), h->d, h->est_mode - 1, s);
 }
@@ -323,8 +324,9 @@ extern "C" ut_status est_get_weights(ut_env* h, float* params_host, int64_t n_pa
 }
 
 extern "C" ut_status est_set_mode(ut_env* h, int32_t mode) {
-  if (!h || mode < 0 || mode > 3) return UT_ERR_INVALID;
-  if (mode >= 1) {
+  if (!h || mode < 0 || mode > 4) return UT_ERR_INVALID;
+  if (mode == 4 && !h->d.ring_on) return est_fail(h, UT_ERR_STATE, "est_set_mode: handle created without UT_FLAG_RING");
+  if (mode >= 1 && mode <= 3) {
     if (!h->est || !h->est->weights_set) return est_fail(h, UT_ERR_STATE, "est_set_mode: no estimator weights");
     if (!h->d.ring_on) return est_fail(h, UT_ERR_STATE, "est_set_mode: handle created without UT_FLAG_RING");
   }

@@ -265,3 +265,44 @@ def test_learned_step_matches_oracle(mode):
         np.testing.assert_allclose(out["err"].cpu().numpy(), ref["err"], atol=atol * 1.5)
         env.est_set_mode(0)
         env.close()
+
+
+def test_ls_step_matches_oracle():
+    """Least-squares tracker (est_set_mode 4): one step from an injected oracle
+    state, GPU (FP32, positions relative to the previous estimate) against the
+    oracle (FP64).  Filters whose normal matrix sits within a factor 2 of the
+    degeneracy threshold may take the other branch in FP32 and are left out;
+    elsewhere the bound is 1 m (FP32 rounding of a = |q|^2 - rho^2 on
+    kilometre baselines, amplified by at most the 1e3 condition limit)."""
+    env, p = _env(n_envs=8, comm_drop=0.2, target_depth_max=40.0)
+    env.reset(8)
+    o = oracle.OracleEnv(p, 8)
+    o.reset(0)
+    for t in range(1, 6):
+        o.step(np.random.default_rng(t).integers(0, 7, o.NA).astype(np.int32))
+    _inject_oracle_state(env, o)
+    env.est_set_mode(4)
+    act = np.random.default_rng(77).integers(0, 7, o.NA).astype(np.int32)
+    out = env.step(torch.from_numpy(act).cuda())
+    ref = o.step(act, mode=4)
+    got = np.stack([out["estx"].cpu().numpy(), out["esty"].cpu().numpy()], 1)
+    want = np.stack([o.arr["estx"], o.arr["esty"]], 1)
+    # the oracle's normal matrices on its rings after the step
+    ring = o.arr["ring"].reshape(o.F, 16, 4)
+    n = o.arr["ring_count"]
+    e1 = np.stack([o.arr["prev_estx"], o.arr["prev_esty"]], 1)
+    ratio = np.zeros(o.F)
+    for f in range(o.F):
+        if n[f] >= 3:
+            idx = (o.arr["ring_head"][f] - 1 - np.arange(n[f])) % 16
+            q = ring[f, idx, :2] - e1[f]
+            dq = q - q.mean(0)
+            A = dq.T @ dq
+            ratio[f] = np.linalg.det(A) / np.trace(A) ** 2
+    border = (ratio > 0.5e-3) & (ratio < 2e-3)
+    err = np.abs(got - want).max(1)
+    print(f"LS: {int((~border).sum())} filters compared, max |d est| {err[~border].max():.3e} m, "
+          f"median {np.median(err[~border]):.3e} m; {int(border.sum())} near the threshold")
+    assert np.all(err[~border] <= 1.0), float(err[~border].max())
+    assert border.mean() < 0.05
+    env.est_set_mode(0)
