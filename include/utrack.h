@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define UT_ABI_VERSION 3u
+#define UT_ABI_VERSION 4u
 #define UT_MAX_AGENTS 8      /* per environment */
 #define UT_MAX_TARGETS 8     /* per environment */
 #define UT_MAX_PARTICLES 4096
@@ -87,7 +87,12 @@ typedef struct ut_config {
   float dt;                    /* step length, s (30 s, Sec. III-A.2) */
   float agent_speed;           /* m/s (1.0, Actions Space paragraph) */
   float heading_noise;         /* std of Gaussian heading noise, rad (0.02, Sec. III-A.3) */
-  int32_t action_mode;         /* 0: {-turn, 0, +turn}; 1: equidistant rudder angles */
+  int32_t action_mode;         /* 0: {-turn, 0, +turn}; 1: equidistant rudder angles;
+                                  2: rudder with adjacent moves (Sec. III-A.2 Actions Space):
+                                  n_rudder equidistant angles, the agent's action moves its
+                                  rudder one position down (0), keeps it (1) or moves it up (2),
+                                  clamped at the ends; needs n_actions == 3 */
+  int32_t n_rudder;            /* action_mode 2: rudder positions (5 in the paper), 2..8 */
   int32_t n_actions;           /* 3 for mode 0; 2..8 for mode 1 (7 default) */
   float turn_angle;            /* mode 0 heading change, rad */
   float rudder_max;            /* mode 1: rudder in [-rudder_max, rudder_max] (0.24 rad) */
@@ -145,6 +150,7 @@ typedef struct ut_state_view {
   float *estx, *esty;                 /* tracker estimates [F] */
   float *prev_estx, *prev_esty;       /* estimate before the last update [F] */
   float *prev2_estx, *prev2_esty;     /* estimate before that [F] */
+  int32_t* rudder;                    /* rudder position per agent [NA] (action_mode 2) */
   float *velx, *vely;                 /* smoothed motion of the estimate per step [F]:
                                          v <- 0.85 v + 0.15 (e1 - e2) at every update */
   float* ring;                        /* estimator ring [F][16][4] (qx, qy, r, step) */

@@ -63,7 +63,7 @@ class OcConfig(ctypes.Structure):
         ("n_particles", ctypes.c_int32),
         ("agent_off", _ip), ("target_off", _ip), ("filter_off", _ip),
         ("dt", ctypes.c_double), ("agent_speed", ctypes.c_double), ("heading_noise", ctypes.c_double),
-        ("action_mode", ctypes.c_int32), ("n_actions", ctypes.c_int32),
+        ("action_mode", ctypes.c_int32), ("n_rudder", ctypes.c_int32), ("n_actions", ctypes.c_int32),
         ("turn_angle", ctypes.c_double), ("rudder_max", ctypes.c_double), ("rudder_gain", ctypes.c_double),
         ("target_model", ctypes.c_int32),
         ("target_speed_min", ctypes.c_double), ("target_speed_max", ctypes.c_double),
@@ -86,7 +86,8 @@ class OcState(ctypes.Structure):
     _fields_ = [(n, _dp) for n in ("ax", "ay", "apsi", "tx", "ty", "tz", "tpsi", "tspeed",
                                    "px", "py", "pvx", "pvy", "lpx", "lpy")] + [
         ("lpage", _ip), ("estx", _dp), ("esty", _dp), ("prev_estx", _dp), ("prev_esty", _dp),
-        ("prev2_estx", _dp), ("prev2_esty", _dp), ("velx", _dp), ("vely", _dp), ("ring", _dp), ("ring_head", _ip),
+        ("prev2_estx", _dp), ("prev2_esty", _dp), ("velx", _dp), ("vely", _dp), ("rudder", _ip), ("ring", _dp),
+        ("ring_head", _ip),
         ("ring_count", _ip), ("step", ctypes.c_uint32), ("t_ep", ctypes.c_int32)]
 
 
@@ -202,7 +203,7 @@ class OracleEnv:
                                                                 params.max_targets, P)
         c.agent_off, c.target_off, c.filter_off = (_p(self.agent_off, _ip), _p(self.target_off, _ip),
                                                    _p(self.filter_off, _ip))
-        for name in ("dt", "agent_speed", "heading_noise", "action_mode", "n_actions", "turn_angle",
+        for name in ("dt", "agent_speed", "heading_noise", "action_mode", "n_rudder", "n_actions", "turn_angle",
                      "rudder_max", "rudder_gain", "target_model", "target_speed_min", "target_speed_max",
                      "target_drift_sigma", "target_depth_max", "range_sigma", "det_radius", "comm_radius",
                      "comm_drop", "pf_accel_sigma", "pf_vcap", "reward_type", "eps_min", "eps_max",
@@ -226,7 +227,7 @@ class OracleEnv:
             "estx": np.zeros(self.F), "esty": np.zeros(self.F),
             "prev_estx": np.zeros(self.F), "prev_esty": np.zeros(self.F),
             "prev2_estx": np.zeros(self.F), "prev2_esty": np.zeros(self.F),
-            "velx": np.zeros(self.F), "vely": np.zeros(self.F),
+            "velx": np.zeros(self.F), "vely": np.zeros(self.F), "rudder": np.zeros(self.NA, np.int32),
             "ring": np.zeros(self.F * RING * 4), "ring_head": np.zeros(self.F, np.int32),
             "ring_count": np.zeros(self.F, np.int32),
         }

@@ -72,7 +72,8 @@ typedef struct {
   int32_t n_envs, max_agents, max_targets, n_particles;
   const int32_t *agent_off, *target_off, *filter_off; /* [n_envs+1] */
   double dt, agent_speed, heading_noise;
-  int32_t action_mode; /* 0: {-turn,0,+turn}; 1: rudder angles */
+  int32_t action_mode; /* 0: {-turn,0,+turn}; 1: rudder angles; 2: rudder, adjacent moves */
+  int32_t n_rudder;    /* action_mode 2: rudder positions */
   int32_t n_actions;
   double turn_angle, rudder_max, rudder_gain;
   int32_t target_model; /* 0: heading redrawn each step; 1: heading drift */
@@ -102,6 +103,7 @@ typedef struct {
   double *prev_estx, *prev_esty;            /* estimate before the last update [F] */
   double *prev2_estx, *prev2_esty;          /* estimate before that [F] */
   double *velx, *vely;                      /* smoothed motion of the estimate [F] */
+  int32_t *rudder;                          /* rudder position per agent [NA] (action_mode 2) */
   double *ring;                             /* [F*16*4]: qx, qy, r, step */
   int32_t *ring_head, *ring_count;          /* [F] */
   uint32_t step;                            /* global step counter g */
@@ -185,10 +187,13 @@ static double wrap_angle(double a) { return a - 2.0 * M_PI * floor((a + M_PI) / 
 /* Heading change of action j.  Mode 0: {-turn, 0, +turn}.  Mode 1: rudder
  * angle gamma_j equidistant in [-rudder_max, rudder_max] and the linear map
  * dpsi = theta(gamma) = rudder_gain * gamma (Sec. III-A.3; the Actions Space
- * paragraph fixes +-0.24 rad rudder <-> +-1.45 rad heading at 1 m/s, 30 s). */
+ * paragraph fixes +-0.24 rad rudder <-> +-1.45 rad heading at 1 m/s, 30 s).
+ * Mode 2 (the Actions Space paragraph's rudder that moves only to an
+ * adjacent angle): j is the rudder position reached, out of n_rudder. */
 static double action_dpsi(const oc_config* c, int32_t j) {
   if (c->action_mode == 0) return (double)(j - 1) * c->turn_angle;
-  double gamma = -c->rudder_max + 2.0 * c->rudder_max * (double)j / (double)(c->n_actions - 1);
+  int n = c->action_mode == 2 ? c->n_rudder : c->n_actions;
+  double gamma = -c->rudder_max + 2.0 * c->rudder_max * (double)j / (double)(n - 1);
   return c->rudder_gain * gamma;
 }
 
@@ -257,6 +262,7 @@ void oc_reset(const oc_config* c, oc_state* s, uint32_t g) {
       s->ax[a0 + a] = ex[a];
       s->ay[a0 + a] = ey[a];
       s->apsi[a0 + a] = M_PI * (2.0 * u01(x[0]) - 1.0);
+      s->rudder[a0 + a] = (c->n_rudder - 1) / 2; /* straight (action_mode 2) */
     }
     for (int k = 0; k < T; ++k) {
       uint32_t x[4];
@@ -368,7 +374,14 @@ void oc_move_agents(const oc_config* c, oc_state* s, const int32_t* act, uint32_
     draw(c->seed, (uint32_t)(c->agent0 + i), 0, g, OC_TAG_AGENT_NOISE, x);
     double n0, n1;
     normal_pair(x[0], x[1], &n0, &n1);
-    double psi = wrap_angle(s->apsi[i] + action_dpsi(c, act[i]) + c->heading_noise * n0);
+    int32_t ang = act[i];
+    if (c->action_mode == 2) { /* down / keep / up, clamped at the ends */
+      ang = s->rudder[i] + act[i] - 1;
+      if (ang < 0) ang = 0;
+      if (ang > c->n_rudder - 1) ang = c->n_rudder - 1;
+      s->rudder[i] = ang;
+    }
+    double psi = wrap_angle(s->apsi[i] + action_dpsi(c, ang) + c->heading_noise * n0);
     s->apsi[i] = psi;
     s->ax[i] += c->agent_speed * c->dt * cos(psi);
     s->ay[i] += c->agent_speed * c->dt * sin(psi);

@@ -306,11 +306,11 @@ class Env:
                   "tpsi": (NT,), "tspeed": (NT,), "px": (FP,), "py": (FP,), "pvx": (FP,), "pvy": (FP,),
                   "lpx": (NA * AM,), "lpy": (NA * AM,), "lpage": (NA * AM,), "estx": (F,), "esty": (F,),
                   "prev_estx": (F,), "prev_esty": (F,), "prev2_estx": (F,), "prev2_esty": (F,),
-                  "velx": (F,), "vely": (F,),
+                  "rudder": (NA,), "velx": (F,), "vely": (F,),
                   "ring": (F, 16, 4), "ring_head": (F,), "ring_count": (F,)}
         out = {}
         for k, shp in shapes.items():
-            dt = torch.int32 if k in ("lpage", "ring_head", "ring_count") else torch.float32
+            dt = torch.int32 if k in ("lpage", "ring_head", "ring_count", "rudder") else torch.float32
             out[k] = device_view(getattr(v, k), shp, dt)
         d = getattr(self.params, "d_model", 0)
         out["h"] = device_view(v.h, (NA, d), torch.int16) if d else None

@@ -7,7 +7,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libutrack.so")
 
-UT_ABI_VERSION = 3
+UT_ABI_VERSION = 4
 UT_FLAG_DEBUG = 1
 UT_FLAG_RING = 2
 
@@ -33,7 +33,7 @@ CONFIG_FIELDS = [
     ("n_particles", ctypes.c_int32), ("horizon", ctypes.c_int32),
     ("agents_per_env_host", _i32p), ("targets_per_env_host", _i32p),
     ("dt", ctypes.c_float), ("agent_speed", ctypes.c_float), ("heading_noise", ctypes.c_float),
-    ("action_mode", ctypes.c_int32), ("n_actions", ctypes.c_int32),
+    ("action_mode", ctypes.c_int32), ("n_rudder", ctypes.c_int32), ("n_actions", ctypes.c_int32),
     ("turn_angle", ctypes.c_float), ("rudder_max", ctypes.c_float), ("rudder_gain", ctypes.c_float),
     ("target_model", ctypes.c_int32),
     ("target_speed_min", ctypes.c_float), ("target_speed_max", ctypes.c_float),
@@ -61,7 +61,7 @@ class StepOut(ctypes.Structure):
 
 STATE_PTRS = ["ax", "ay", "apsi", "tx", "ty", "tz", "tpsi", "tspeed", "px", "py", "pvx", "pvy",
               "lpx", "lpy", "lpage", "estx", "esty", "prev_estx", "prev_esty", "prev2_estx", "prev2_esty",
-              "velx", "vely", "ring", "ring_head", "ring_count", "h"]
+              "rudder", "velx", "vely", "ring", "ring_head", "ring_count", "h"]
 
 
 class StateView(ctypes.Structure):

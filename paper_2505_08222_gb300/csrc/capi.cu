@@ -82,7 +82,9 @@ ut_status validate(const ut_config* c, std::string& why) {
   if (c->horizon < 1) return bad("horizon must be >= 1");
   if (c->action_mode == 0 && c->n_actions != 3) return bad("action_mode 0 needs n_actions == 3");
   if (c->action_mode == 1 && (c->n_actions < 2 || c->n_actions > 8)) return bad("n_actions must be in 2..8");
-  if (c->action_mode != 0 && c->action_mode != 1) return bad("action_mode must be 0 or 1");
+  if (c->action_mode == 2 && c->n_actions != 3) return bad("action_mode 2 needs n_actions == 3 (down, keep, up)");
+  if (c->action_mode == 2 && (c->n_rudder < 2 || c->n_rudder > 8)) return bad("n_rudder must be in 2..8");
+  if (c->action_mode < 0 || c->action_mode > 2) return bad("action_mode must be 0, 1 or 2");
   if (!(c->range_sigma > 0.0f)) return bad("range_sigma must be > 0");
   if (!(c->dt > 0.0f)) return bad("dt must be > 0");
   if (c->spawn_tries < 1 || c->spawn_tries > 64) return bad("spawn_tries must be in 1..64");
@@ -201,13 +203,16 @@ ut_status env_create(const ut_config* cfg, const ut_allocator* allocator, void* 
   d.dt = cfg->dt;
   d.agent_speed = cfg->agent_speed;
   d.heading_noise = cfg->heading_noise;
+  d.rudder_mode = cfg->action_mode == 2 ? 1 : 0;
+  d.n_rudder = cfg->action_mode == 2 ? cfg->n_rudder : 0;
+  const int n_ang = cfg->action_mode == 2 ? cfg->n_rudder : cfg->n_actions;  // rudder angles in the table
   for (int j = 0; j < 8; ++j) {
     double v = 0.0;
-    if (j < cfg->n_actions) {
+    if (j < n_ang) {
       if (cfg->action_mode == 0) {
         v = (double)(j - 1) * (double)cfg->turn_angle;
       } else {
-        const double gam = -(double)cfg->rudder_max + 2.0 * cfg->rudder_max * j / (double)(cfg->n_actions - 1);
+        const double gam = -(double)cfg->rudder_max + 2.0 * cfg->rudder_max * j / (double)(n_ang - 1);
         v = (double)cfg->rudder_gain * gam;
       }
     }
@@ -270,6 +275,7 @@ ut_status env_create(const ut_config* cfg, const ut_allocator* allocator, void* 
   d.prev_esty = alloc_n<float>(h, F, ok);
   d.prev2_estx = alloc_n<float>(h, F, ok);
   d.prev2_esty = alloc_n<float>(h, F, ok);
+  d.rudder = alloc_n<int32_t>(h, NA, ok);
   d.velx = alloc_n<float>(h, F, ok);
   d.vely = alloc_n<float>(h, F, ok);
   d.err = alloc_n<float>(h, F, ok);
@@ -630,6 +636,7 @@ ut_status env_get_state(const ut_env* hc, ut_state_view* out) {
   out->estx = d.estx; out->esty = d.esty;
   out->prev_estx = d.prev_estx; out->prev_esty = d.prev_esty;
   out->prev2_estx = d.prev2_estx; out->prev2_esty = d.prev2_esty;
+  out->rudder = d.rudder;
   out->velx = d.velx; out->vely = d.vely;
   out->ring = d.ring_on ? d.ring : nullptr;
   out->ring_head = d.ring_head; out->ring_count = d.ring_count;
@@ -674,6 +681,7 @@ ut_status env_set_state(ut_env* h, const ut_state_view* in) {
   UT_CUDA(h, cp(d.prev_esty, in->prev_esty, F * 4));
   UT_CUDA(h, cp(d.prev2_estx, in->prev2_estx, F * 4));
   UT_CUDA(h, cp(d.prev2_esty, in->prev2_esty, F * 4));
+  UT_CUDA(h, cp(d.rudder, in->rudder, NA * 4));
   UT_CUDA(h, cp(d.velx, in->velx, F * 4));
   UT_CUDA(h, cp(d.vely, in->vely, F * 4));
   if (d.ring_on) UT_CUDA(h, cp(d.ring, in->ring, F * kRing * 16));

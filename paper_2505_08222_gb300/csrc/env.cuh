@@ -24,7 +24,9 @@ struct EnvDev {
   uint64_t seed;
   uint32_t gid_env, gid_agent, gid_target, gid_filter;  // global id offsets
   float dt, agent_speed, heading_noise;
-  float dpsi[8];              // heading change of each action
+  float dpsi[8];              // heading change of each action (action_mode 2: of each rudder position)
+  int rudder_mode;            // action_mode 2: actions move the rudder position
+  int n_rudder;
   int target_model;
   float ts_min, ts_max, drift, depth_max;
   float range_sigma, inv_two_s2, det_radius, comm_radius, comm_drop;
@@ -45,6 +47,7 @@ struct EnvDev {
   // the two previous estimates of each filter (estimate history of the
   // learned estimator's features; NULL where not kept)
   float *prev_estx, *prev_esty, *prev2_estx, *prev2_esty;
+  int32_t* rudder;            // [NA] rudder position (action_mode 2)
   // smoothed motion of the estimate per step (EMA over the updates' e1 - e2)
   float *velx, *vely;
   float est_scale;  // L: metres per unit of the learned estimator's local frame

@@ -52,6 +52,7 @@ __global__ void reset_spawn_kernel(EnvDev d, uint32_t g) {
     d.ax[i] = (float)X[a] * 0x1p-16f;
     d.ay[i] = (float)Y[a] * 0x1p-16f;
     d.apsi[i] = (2.0f * unif(r.x[0]) - 1.0f) * kPi;
+    d.rudder[i] = (d.n_rudder - 1) / 2;  // straight (action_mode 2)
   }
   for (int k = 0; k < T; ++k) {
     const int j = t0 + k;
@@ -185,10 +186,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) step_env_kernel(EnvDev d,
       act = (int)__umulhi(r.x[0], (uint32_t)d.n_act);
     }
     d.actions[i] = act;
+    int ang = act;  // index into the heading-change table
+    if (d.rudder_mode) {  // the action moves the rudder down / keeps it / moves it up
+      ang = min(max(d.rudder[i] + act - 1, 0), d.n_rudder - 1);
+      d.rudder[i] = ang;
+    }
     Rand4 r = philox(d.gid_agent + (uint32_t)i, 0u, g, TAG_AGENT_NOISE, d.seed);
     float n0, n1;
     box_muller(r.x[0], r.x[1], n0, n1);
-    const float psi = wrap_angle(d.apsi[i] + d.dpsi[act] + d.heading_noise * n0);
+    const float psi = wrap_angle(d.apsi[i] + d.dpsi[ang] + d.heading_noise * n0);
     float s, c;
     sincosf(psi, &s, &c);
     const float step_len = d.agent_speed * d.dt;

@@ -46,7 +46,8 @@ class EnvParams:
     dt: float = 30.0
     agent_speed: float = 1.0
     heading_noise: float = 0.0
-    action_mode: int = 0            # 0: {-turn, 0, +turn}; 1: rudder angles
+    action_mode: int = 0            # 0: {-turn, 0, +turn}; 1: rudder angles; 2: rudder, adjacent moves
+    n_rudder: int = 5               # action_mode 2: rudder positions
     n_actions: int = 3
     turn_angle: float = math.pi / 6
     rudder_max: float = 0.24

@@ -9,7 +9,7 @@ import oracle
 
 STATE_KEYS_F = ["ax", "ay", "apsi", "tx", "ty", "tz", "tpsi", "tspeed", "px", "py", "pvx", "pvy", "lpx", "lpy",
                 "estx", "esty"]
-STATE_KEYS_I = ["lpage"]
+STATE_KEYS_I = ["lpage", "rudder"]
 
 
 def gpu_state(env) -> dict:
@@ -28,6 +28,7 @@ def oracle_state_f32(o: oracle.OracleEnv) -> dict:
     """The oracle's state rounded to float32 (what a GPU handle can hold)."""
     out = {k: o.arr[k].astype(np.float32) for k in STATE_KEYS_F}
     out["lpage"] = o.arr["lpage"].copy()
+    out["rudder"] = o.arr["rudder"].copy()
     return out
 
 

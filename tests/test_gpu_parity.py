@@ -112,7 +112,8 @@ def _compare_step(env, o, actions, check_tokens=True):
     g = gpu_state(env)
     ref = o.step(actions, want=("range", "valid", "recv", "meas", "meas_n", "pred_px", "weight", "wmax", "idx",
                                 "tokens"))
-    # kinematics
+    # kinematics (and, for action_mode 2, the rudder positions, exactly)
+    np.testing.assert_array_equal(g["rudder"], o.arr["rudder"])
     assert np.all(rel_close(g["ax"], o.arr["ax"], 1e-5, 100.0)) and np.all(rel_close(g["ay"], o.arr["ay"], 1e-5, 100.0))
     assert np.all(angle_diff(g["apsi"], o.arr["apsi"]) < 1e-5)
     assert np.all(rel_close(g["tx"], o.arr["tx"], 1e-5, 100.0)) and np.all(rel_close(g["ty"], o.arr["ty"], 1e-5, 100.0))
@@ -180,6 +181,7 @@ def _compare_step(env, o, actions, check_tokens=True):
     ("fleet5", 8, 2048, {}),
     ("fleet5", 4, 13, {"comm_drop": 0.3, "comm_radius": 300.0, "target_depth_max": 50.0}),
     ("fleet5", 4, 512, {"det_radius": 60.0}),
+    ("fleet5", 6, 256, {"action_mode": 2, "n_rudder": 5, "n_actions": 3}),
     ("ragged", 24, 100, {}),
     ("large", 2, 512, {}),
 ])

@@ -69,6 +69,34 @@ def test_rudder_anchor_heading_change():
     np.testing.assert_allclose(d, -gold["heading_change_max"], atol=1e-12)
 
 
+def test_rudder_adjacent_moves():
+    """Actions Space paragraph, five rudder angles in [-0.24, 0.24] rad that
+    change only to an adjacent angle (action_mode 2: down / keep / up): the
+    rudder starts straight, moves one position per up / down action, stops at
+    the ends, and the heading turns by 1.45 / 0.24 times the rudder angle
+    reached (1.45 rad at the end stop)."""
+    gold = _golden("paper_constants.txt")
+    e = _env("fleet5", n_envs=2, heading_noise=0.0, action_mode=2, n_rudder=5, n_actions=3)
+    assert np.all(e.arr["rudder"] == 2)
+    seq = [2, 2, 2, 0, 1, 0, 0, 0, 0]
+    want_k = [3, 4, 4, 3, 3, 2, 1, 0, 0]
+    for a, k in zip(seq, want_k):
+        psi0 = e.arr["apsi"].copy()
+        e.step(np.full(e.NA, a, np.int32))
+        assert np.all(e.arr["rudder"] == k)
+        d = np.angle(np.exp(1j * (e.arr["apsi"] - psi0)))
+        gamma = -0.24 + 0.12 * k
+        np.testing.assert_allclose(d, gold["heading_change_max"] * gamma / 0.24, atol=1e-12)
+    # random actions: never more than one position per step, always in range
+    rng = np.random.default_rng(3)
+    prev = e.arr["rudder"].copy()
+    for _ in range(50):
+        e.step(rng.integers(0, 3, e.NA).astype(np.int32))
+        k = e.arr["rudder"]
+        assert np.all(np.abs(k - prev) <= 1) and np.all((k >= 0) & (k <= 4))
+        prev = k.copy()
+
+
 def test_heading_noise_std():
     """Sec. III-A.3: Gaussian heading noise of std 0.02 rad."""
     e = _env("fleet5", n_envs=400, n_particles=4, heading_noise=0.02)
