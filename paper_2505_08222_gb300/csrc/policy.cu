@@ -89,15 +89,47 @@ struct Geo {
 // t = 1 / (1 + p z), z >= 0, absolute error <= 1.5e-7 (the coefficients below
 // are that formula's, halved).  In FP32 the GELU error stays below 5e-7
 // absolute, far inside the BF16 rounding its output receives.
-__device__ __forceinline__ float gelu(float x) {
-  const float z = fabsf(x) * 0.70710678118654752f;
-  const float t = __fdividef(1.0f, fmaf(0.3275911f, z, 1.0f));
-  float c = fmaf(t, 0.5307027145f, -0.7265760135f);  // a5/2, a4/2
-  c = fmaf(t, c, 0.7107068705f);                     // a3/2
-  c = fmaf(t, c, -0.1422483680f);                    // a2/2
-  c = fmaf(t, c, 0.1274147960f);                     // a1/2
-  c *= t * __expf(-z * z);                           // Phi(-|x|)
-  return x * (x >= 0.0f ? 1.0f - c : c);
+// Evaluated for two values at once on the packed FP32 pipe (fma / mul
+// .rn.f32x2, each lane rounded like the scalar operation; the SFU reciprocal
+// and exponential stay per lane).
+__device__ __forceinline__ unsigned long long f2pk(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2upk(unsigned long long r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2mul(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ void gelu2(float& x0, float& x1) {
+  const unsigned long long x = f2pk(x0, x1);
+  const unsigned long long z = f2mul(f2pk(fabsf(x0), fabsf(x1)), f2pk(0.70710678118654752f, 0.70710678118654752f));
+  float d0, d1;
+  f2upk(f2fma(f2pk(0.3275911f, 0.3275911f), z, f2pk(1.0f, 1.0f)), d0, d1);
+  const unsigned long long t = f2pk(__fdividef(1.0f, d0), __fdividef(1.0f, d1));
+  unsigned long long c = f2fma(t, f2pk(0.5307027145f, 0.5307027145f), f2pk(-0.7265760135f, -0.7265760135f));
+  c = f2fma(t, c, f2pk(0.7107068705f, 0.7107068705f));
+  c = f2fma(t, c, f2pk(-0.1422483680f, -0.1422483680f));
+  c = f2fma(t, c, f2pk(0.1274147960f, 0.1274147960f));
+  float z0, z1;
+  f2upk(z, z0, z1);
+  c = f2mul(c, f2mul(t, f2pk(__expf(-z0 * z0), __expf(-z1 * z1))));
+  float c0, c1;
+  f2upk(c, c0, c1);
+  float y0, y1;
+  f2upk(f2mul(x, f2pk(x0 >= 0.0f ? 1.0f - c0 : c0, x1 >= 0.0f ? 1.0f - c1 : c1)), y0, y1);
+  x0 = y0;
+  x1 = y1;
 }
 
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
@@ -586,7 +618,9 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
         const int hc = part * G::HCOLS + c0;
         tc::tmem_ld16(tl + G::COL_S + hc, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = gelu(v[i] + b1[c * 128 + hc + i]);
+        for (int i = 0; i < 16; ++i) v[i] += b1[c * 128 + hc + i];
+#pragma unroll
+        for (int i = 0; i < 16; i += 2) gelu2(v[i], v[i + 1]);
         store8(sH, row, hc, 128, v);
         store8(sH, row, hc + 8, 128, v + 8);
       }

@@ -63,6 +63,8 @@ def _cfg(**kw):
 @pytest.mark.parametrize("kw", [
     {"n_envs": 0}, {"max_agents": 9}, {"max_targets": 0}, {"n_particles": 0}, {"n_particles": 4097},
     {"range_sigma": 0.0}, {"n_heads": 3}, {"n_actions": 9}, {"reward_type": 2}, {"spawn_tries": 65},
+    {"action_mode": 3}, {"action_mode": 2, "n_actions": 7}, {"action_mode": 2, "n_actions": 3, "n_rudder": 1},
+    {"action_mode": 2, "n_actions": 3, "n_rudder": 9},
 ])
 def test_create_rejects_invalid_config(lib, kw):
     from paper_2505_08222_gb300 import _abi
@@ -89,3 +91,9 @@ def test_standalone_ops_validate_arguments(lib):
     assert ut.lib.pf_resample(None, None, -1, 16, None, None) == 1
     assert ut.lib.pf_resample(None, None, 4, 0, None, None) == 1
     assert ut.lib.ut_philox(None, 0, None, -3, None) == 1
+
+
+def test_estimator_entry_points_reject_null_handles(lib):
+    import paper_2505_08222_gb300 as ut
+    assert ut.lib.est_set_mode(None, 1) == 1
+    assert ut.lib.est_set_mode(None, 4) == 1

@@ -306,3 +306,21 @@ def test_ls_step_matches_oracle():
     assert np.all(err[~border] <= 1.0), float(err[~border].max())
     assert border.mean() < 0.05
     env.est_set_mode(0)
+
+
+def test_estimator_mode_errors():
+    """est_set_mode: modes outside 0..4 are invalid; the learned modes need
+    weights, the learned and LS modes a handle with the ping ring."""
+    p = preset("fleet5", n_envs=2).replace(d_model=0)
+    plain = ut.Env(p)
+    with pytest.raises(ut.UtError, match="UT_ERR_INVALID"):
+        plain.est_set_mode(5)
+    with pytest.raises(ut.UtError, match="UT_ERR_STATE"):
+        plain.est_set_mode(4)
+    ringed = ut.Env(p, ring=True)
+    with pytest.raises(ut.UtError, match="UT_ERR_STATE"):
+        ringed.est_set_mode(1)
+    ringed.est_set_mode(4)
+    ringed.est_set_mode(0)
+    plain.close()
+    ringed.close()
