@@ -10,6 +10,7 @@
 // precision instead of BF16's 4e-3, which matters for metre-level tracking.
 // The 2-wide output layer runs on CUDA cores.
 #include "estimator.cuh"
+#include "gelu.cuh"
 #include "tc.cuh"
 
 #include <cmath>
@@ -25,7 +26,9 @@ constexpr float kMaxCorr = 3.0f;  // largest correction per step, in units of L
 constexpr size_t kFwdSmem = 65536 + 65536;
 constexpr size_t kWgradSmem = 32768 + 65536;
 
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// Derivative of erf-GELU for the backward pass: Phi(x) + x phi(x).  (The
+// forward passes evaluate GELU with the A&S 7.1.26 erfc of gelu.cuh, within
+// 5e-7 of the erf form.)
 __device__ __forceinline__ float gelu_grad(float x) {
   return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
 }
@@ -157,8 +160,10 @@ __global__ void __launch_bounds__(kT, 1) fwd_kernel(FwdArgs p) {
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         v[i] += __ldg(bias + c0 + i);
-        av[i] = gelu(v[i]);
+        av[i] = v[i];
       }
+#pragma unroll
+      for (int i = 0; i < 16; i += 2) gelu2(av[i], av[i + 1]);  // same GELU as the environment step
       if (p.z && valid) {
         float* zr = p.z + ((long long)l * p.B + b) * HID + c0;
         uint16_t* ar = p.a + ((long long)l * p.B + b) * HID + c0;
@@ -202,8 +207,9 @@ __global__ void __launch_bounds__(kT, 1) fwd_kernel(FwdArgs p) {
 // ---------------------------------------------------------------------------
 // Estimator step in the environment (learned form): one CTA of 512 threads
 // per 128 filters, thread = filter row x one of 4 column parts.  Part 0
-// builds the row's features; the hidden-layer epilogues (bias, erf-GELU,
-// BF16 operand) split the 256 hidden units 4 ways; the weight images (N-halves
+// builds the row's features; the hidden-layer epilogues (bias, erf-GELU with
+// erf from Abramowitz & Stegun 7.1.26 in packed pairs, BF16 operand) split
+// the 256 hidden units 4 ways; the weight images (N-halves
 // of W1, W2, W3) stream through two shared-memory slots by the bulk-copy
 // engine, so the next layer's weights arrive during the current epilogue.
 // ---------------------------------------------------------------------------
@@ -341,7 +347,9 @@ __global__ void __launch_bounds__(kTE, 1) fwd_env_kernel(Net net, EnvDev d, int 
       tc::tmem_ld16(tl + c0, v);
       float av[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) av[i] = gelu(v[i] + __ldg(bias + c0 + i));
+      for (int i = 0; i < 16; ++i) av[i] = v[i] + __ldg(bias + c0 + i);
+#pragma unroll
+      for (int i = 0; i < 16; i += 2) gelu2(av[i], av[i + 1]);  // A&S 7.1.26 erf-GELU, packed pairs
       if (l < 2) {
         store8(sA, row, c0, 128, av);
         store8(sA, row, c0 + 8, 128, av + 8);
@@ -482,7 +490,7 @@ __global__ void __launch_bounds__(kT, 1) bwd_kernel(Net net, TrainBufs t, int* s
     for (int i = 0; i < 16; ++i) {
       const int k = c0 + i;
       const float z = valid ? t.z[((long long)2 * t.B + b) * HID + k] : 0.0f;
-      const float a = valid ? gelu(z) : 0.0f;
+      const float a = valid ? gelu1(z) : 0.0f;  // the forward's GELU
       const float w0 = warp_sum(d0 * a), w1 = warp_sum(d1 * a);
       if (lanei == 0) {
         atomicAdd(&s_dW4[k], w0);

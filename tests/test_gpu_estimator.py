@@ -123,6 +123,17 @@ def test_adam_step_matches_oracle():
     assert np.all(np.abs(step_g) <= lr * 1.001 + 1e-7)
 
 
+def _close_to_forward(got, want):
+    """The environment step's network (4 threads per row, its own summation
+    order) against the stand-alone forward on the same features: equal up to
+    FP32 reassociation, except where an intermediate rounds to the other
+    neighbouring BF16 value; one such flip of a hidden activation (<= 3) moves
+    an output by at most 2^-8 * 3 * |W4| <= 3e-3 L = 0.3 m."""
+    d = np.abs(np.asarray(got, np.float64) - np.asarray(want, np.float64))
+    assert np.all(d <= 0.3), float(d.max())
+    assert np.mean(d <= 2e-3) >= 0.98, float(np.mean(d <= 2e-3))
+
+
 def _naive_last_ping(X):
     """Correction that moves the estimate onto the newest ping's range circle
     along the line to its sender (features are in the estimate's frame:
@@ -183,7 +194,7 @@ def test_learned_mode_step_uses_network():
     # new estimate = previous estimate + L * network(features)
     est = np.stack([out["estx"].cpu().numpy(), out["esty"].cpu().numpy()], 1)
     e1 = np.stack([st["prev_estx"].cpu().numpy(), st["prev_esty"].cpu().numpy()], 1)
-    np.testing.assert_allclose(est, e1 + 100.0 * pred.cpu().numpy(), atol=2e-3)
+    _close_to_forward(est, e1 + 100.0 * pred.cpu().numpy())
     env.est_set_mode(False)
 
 
@@ -211,7 +222,7 @@ def test_learned_mode_stale_rules(mode):
     e1 = np.stack([st["prev_estx"].cpu().numpy(), st["prev_esty"].cpu().numpy()], 1)
     fresh = (X[:, 3] == 0) & (X[:, 4] == 1)
     assert 0 < fresh.sum() < F, fresh.sum()
-    np.testing.assert_allclose(est[fresh], e1[fresh] + 100.0 * corr[fresh], atol=2e-3)
+    _close_to_forward(est[fresh], e1[fresh] + 100.0 * corr[fresh])
     stale = ~fresh
     if mode == 1:
         want = e1[stale]
@@ -219,7 +230,7 @@ def test_learned_mode_stale_rules(mode):
         want = e1[stale] + 100.0 * corr[stale]
     else:
         want = e1[stale] + 100.0 * np.clip(X[stale, 82:84], -3.0, 3.0)
-    np.testing.assert_allclose(est[stale], want, atol=2e-3)
+    _close_to_forward(est[stale], want)
     env.est_set_mode(0)
 
 
