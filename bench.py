@@ -176,31 +176,40 @@ def learned_form(args, p, K, W, rank):
     LEARNED = 2  # est_set_mode: the network also moves the estimate on steps without a fresh ping
 
     def record(t0_step, n_rec, seed, learned):
-        # one episode from reset, long enough to span the evaluation horizon;
-        # every `every`-th step is recorded
-        every = max(1, -(-T_eval // n_rec))
-        env.est_set_mode(learned)
-        env.reset(seed)
-        for t in range(t0_step, t0_step + n_rec):
-            for _ in range(every):
-                env.step()
-            env.est_record(X[t * F:(t + 1) * F], Y[t * F:(t + 1) * F])
+        # n_rec rows spread over EPISODES episodes from reset, each spanning the
+        # evaluation horizon with a row every k-th step
+        per = [n_rec // EPISODES + (1 if k < n_rec % EPISODES else 0) for k in range(EPISODES)]
+        t = t0_step
+        for k, nr in enumerate(per):
+            if nr == 0:
+                continue
+            every = max(1, -(-T_eval // nr))
+            env.est_set_mode(learned)
+            env.reset(seed + 17 * k)
+            for _ in range(nr):
+                for _ in range(every):
+                    env.step()
+                env.est_record(X[t * F:(t + 1) * F], Y[t * F:(t + 1) * F])
+                t += 1
         env.est_set_mode(False)
 
     # DAgger-style schedule: half the rows from filter-driven rollouts (the
-    # filter's estimates as the update's inputs), then two rounds of rows from
-    # rollouts driven by the network itself, retraining after each round.
-    # Closed-loop quality varies with the training seed, so several
-    # candidates are trained and the one with the lowest RMSE on a validation
-    # seed (distinct from the held-out evaluation seeds) is kept.
+    # filter's estimates as the update's inputs), then ROUNDS rounds of rows
+    # from rollouts driven by the network itself, retraining on everything
+    # recorded so far after each round.  Closed-loop quality varies with the
+    # training seed, so several candidates are trained and the one with the
+    # lowest RMSE on a validation seed (distinct from the held-out evaluation
+    # seeds) is kept.
     def eval_rmse(learned: int, seed: int, T: int) -> float:
         env.est_set_mode(learned)
         env.reset(seed)
         return env.rollout(T)["rmse"]
 
+    ROUNDS, EPISODES = 8, 4
     t0 = time.perf_counter()
     half = steps_rec // 2
-    quarter = (steps_rec - half) // 2
+    rest = steps_rec - half
+    chunks = [rest // ROUNDS + (1 if k < rest % ROUNDS else 0) for k in range(ROUNDS)]
     record(0, half, 7000 + rank, False)
     train_ms = 0.0
     cands = []
@@ -210,11 +219,12 @@ def learned_form(args, p, K, W, rank):
                            seed=rank + 100 * c, huber=1.0)
         losses = [tr["loss_last"]]
         train_ms += tr["ms"]
-        for r, (a, n) in enumerate([(half, quarter), (half + quarter, steps_rec - half - quarter)]):
-            record(a, n, 7100 + 10 * r + rank + 1000 * c, LEARNED)
-            upto = (a + n) * F
-            tr = env.est_train(X[:upto], Y[:upto], steps=args.train_steps // 2, batch=16384, lr=5e-4,
-                               seed=rank + 100 * c + r + 1, huber=1.0)
+        upto = half
+        for r, n in enumerate(chunks):
+            record(upto, n, 7100 + 10 * r + rank + 1000 * c, LEARNED)
+            upto += n
+            tr = env.est_train(X[:upto * F], Y[:upto * F], steps=max(500, args.train_steps // ROUNDS), batch=16384,
+                               lr=5e-4, seed=rank + 100 * c + r + 1, huber=1.0)
             losses.append(tr["loss_last"])
             train_ms += tr["ms"]
         val = eval_rmse(LEARNED, 8000 + rank, T_eval)
@@ -277,11 +287,13 @@ def learned_form(args, p, K, W, rank):
             "ls_form": {"value": st_ls["agent_steps"] / (ms_ls / 1e3), "unit": "agent-steps/s", "ms_per_step": ms_ls / K,
                         "rmse_m": ls_mean, "rmse_ratio": ls_mean / pf_mean,
                         "tracker": "least-squares trilateration over each filter's 16 newest pings (est_set_mode 4)"},
-            "train": {"rows": steps_rec * F, "wall_s": rec_s, "steps": 2 * args.train_steps, "batch": 16384,
+            "train": {"rows": steps_rec * F, "wall_s": rec_s,
+                      "steps": args.train_steps + ROUNDS * max(500, args.train_steps // ROUNDS), "batch": 16384,
                       "candidates": len(cands), "validation_rmse_m": [round(v, 1) for v, _, _, _ in cands],
                       "chosen": c_best, "validation": "seed 8000, same horizon; evaluation seeds 9000 and 9100",
-                      "schedule": "50% filter-driven rows, then 2 x 25% network-driven rows (retrain each); each "
-                                  "round one episode over the evaluation horizon, rows every k-th step",
+                      "schedule": f"50% filter-driven rows, then {ROUNDS} rounds of network-driven rows (retrain "
+                                  f"after each); every round's rows from {EPISODES} episodes over the evaluation "
+                                  "horizon, a row every k-th step",
                       "loss_last_per_round": losses, "train_ms": train_ms, "loss": "Huber, delta = 1 L"}}
 
 
