@@ -155,7 +155,7 @@ def cpu_baseline(workload: str, budget_s: float = 12.0, n_envs: int = 64):
 
 
 def learned_form(args, p, K, W, rank):
-    """The learned-estimator form of the same workload: record ~10M
+    """The learned-estimator form of the same workload: record ~20M
     (feature, label) transitions from filter-form rollouts, train the MLP with
     the library's kernels, then time a learned-form rollout and compare mean
     tracking RMSE against the filter form on held-out seeds."""
@@ -223,7 +223,7 @@ def learned_form(args, p, K, W, rank):
         for r, n in enumerate(chunks):
             record(upto, n, 7100 + 10 * r + rank + 1000 * c, LEARNED)
             upto += n
-            tr = env.est_train(X[:upto * F], Y[:upto * F], steps=max(500, args.train_steps // ROUNDS), batch=16384,
+            tr = env.est_train(X[:upto * F], Y[:upto * F], steps=args.round_steps, batch=16384,
                                lr=5e-4, seed=rank + 100 * c + r + 1, huber=1.0)
             losses.append(tr["loss_last"])
             train_ms += tr["ms"]
@@ -288,7 +288,7 @@ def learned_form(args, p, K, W, rank):
                         "rmse_m": ls_mean, "rmse_ratio": ls_mean / pf_mean,
                         "tracker": "least-squares trilateration over each filter's 16 newest pings (est_set_mode 4)"},
             "train": {"rows": steps_rec * F, "wall_s": rec_s,
-                      "steps": args.train_steps + ROUNDS * max(500, args.train_steps // ROUNDS), "batch": 16384,
+                      "steps": args.train_steps + ROUNDS * args.round_steps, "batch": 16384,
                       "candidates": len(cands), "validation_rmse_m": [round(v, 1) for v, _, _, _ in cands],
                       "chosen": c_best, "validation": "seed 8000, same horizon; evaluation seeds 9000 and 9100",
                       "schedule": f"50% filter-driven rows, then {ROUNDS} rounds of network-driven rows (retrain "
@@ -512,8 +512,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--pf-variant", default=None, help="fixed filter launch variant (e.g. nt512x4m3), no autotune")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-estimator form")
-    ap.add_argument("--train-rows", type=int, default=10_000_000)
-    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--train-rows", type=int, default=20_000_000)
+    ap.add_argument("--train-steps", type=int, default=3000, help="Adam steps on the filter-driven rows")
+    ap.add_argument("--round-steps", type=int, default=800, help="Adam steps after each DAgger round")
     ap.add_argument("--eval-steps", type=int, default=100)
     ap.add_argument("--est-candidates", type=int, default=3, help="estimator trainings to choose from")
     ap.add_argument("--envs", type=int, default=None, help="override the env count (profiling cases)")
