@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define UT_ABI_VERSION 4u
+#define UT_ABI_VERSION 5u
 #define UT_MAX_AGENTS 8      /* per environment */
 #define UT_MAX_TARGETS 8     /* per environment */
 #define UT_MAX_PARTICLES 4096
@@ -357,11 +357,25 @@ ut_status est_forward(ut_env* env, const float* X_dev, float* out_dev, int64_t n
  * last update (call after a step; e1, e2 = the estimates before it); needs
  * UT_FLAG_RING. */
 ut_status est_record(ut_env* env, float* feat_dev, float* label_dev);
-/* Loss = (1/(2B)) sum over rows and both outputs of (out - y)^2 on rows
- * 0..B-1 and its gradient grad_dev [156930] (device, canonical order).
- * Synchronising; *loss_host (optional) receives L. */
-ut_status est_loss_grad(ut_env* env, const float* X_dev, const float* Y_dev, int32_t B, float* grad_dev,
-                        double* loss_host);
+/* Loss of one batch of B rows of X_dev [n_rows][96], Y_dev [n_rows][2]
+ * (device) and its gradient grad_dev [156930] (device, canonical order).
+ * B == n_rows: the rows in order; otherwise B rows drawn uniformly with
+ * replacement by the same counter-based stream as est_train's step `step`
+ * under `seed` (so a loop of est_loss_grad + est_adam_step with est_train's
+ * learning-rate schedule repeats est_train).  huber_delta == 0:
+ * L = (1/(2B)) sum over rows and both outputs of (out - y)^2; > 0: the Huber
+ * loss with that threshold (label units), (1/B) sum of the per-output loss.
+ * Synchronising; *loss_host (optional) receives L.
+ * Errors: UT_ERR_INVALID (sizes, B > 2^22, negative threshold),
+ * UT_ERR_STATE (no weights), UT_ERR_NOMEM, UT_ERR_CUDA. */
+ut_status est_loss_grad(ut_env* env, const float* X_dev, const float* Y_dev, int64_t n_rows, int32_t B,
+                        uint64_t seed, uint32_t step, float huber_delta, float* grad_dev, double* loss_host);
+/* One bias-corrected Adam update of the FP32 master weights with the given
+ * gradient grad_dev [156930] (device; e.g. the average of the ranks'
+ * est_loss_grad results in data-parallel training); the handle counts the
+ * steps for the bias correction (reset by est_set_weights / est_load).
+ * Asynchronous on the handle's stream.  Errors: UT_ERR_INVALID, UT_ERR_STATE. */
+ut_status est_adam_step(ut_env* env, const float* grad_dev, float lr, float beta1, float beta2, float eps);
 /* Adam (bias-corrected) over cfg->steps batches of X_dev / Y_dev
  * ([n_rows][96], [n_rows][2], device).  Synchronising; stats optional. */
 ut_status est_train(ut_env* env, const float* X_dev, const float* Y_dev, int64_t n_rows,

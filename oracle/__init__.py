@@ -130,7 +130,7 @@ def _declare(L):
                                     _ip, _dp, _dp, _dp]
     L.oc_mlp_param_count.restype = ctypes.c_int64
     L.oc_mlp_forward.argtypes = [ctypes.c_int32, _dp, _dp, _dp, _dp]
-    L.oc_mlp_loss_grad.argtypes = [ctypes.c_int32, _dp, _dp, _dp, _dp]
+    L.oc_mlp_loss_grad.argtypes = [ctypes.c_int32, _dp, _dp, _dp, _dp, ctypes.c_double]
     L.oc_mlp_loss_grad.restype = ctypes.c_double
     L.oc_adam.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, ctypes.c_int32, ctypes.c_double,
                           ctypes.c_double, ctypes.c_double, ctypes.c_double]
@@ -380,12 +380,14 @@ def mlp_forward(params, X, want_pre=False):
     return (out, pre) if want_pre else out
 
 
-def mlp_loss_grad(params, X, Y):
+def mlp_loss_grad(params, X, Y, huber=0.0):
+    """Mean over rows of the summed per-output loss (squared error / 2, or
+    the Huber loss with threshold ``huber`` > 0) and its gradient."""
     prm = _f64(params)
     x = _f64(X)
     y = _f64(Y)
     g = np.zeros_like(prm)
-    loss = lib().oc_mlp_loss_grad(x.shape[0], _p(prm), _p(x), _p(y), _p(g))
+    loss = lib().oc_mlp_loss_grad(x.shape[0], _p(prm), _p(x), _p(y), _p(g), float(huber))
     return loss, g
 
 

@@ -201,9 +201,24 @@ void oc_mlp_forward(int32_t B, const double* params, const double* X, double* ou
   }
 }
 
-/* Loss L = (1/(2B)) sum_r sum_c (out_rc - y_rc)^2 and its gradient with
- * respect to every parameter (same layout as params).  Returns L. */
-double oc_mlp_loss_grad(int32_t B, const double* params, const double* X, const double* Y, double* grad) {
+/* Per-output loss rho(e) of the residual e = out - y and its derivative:
+ * delta == 0, rho = e^2 / 2 (squared error); delta > 0, the Huber loss
+ * (Huber 1964): e^2 / 2 for |e| <= delta, delta (|e| - delta / 2) beyond. */
+static double loss_rho(double e, double delta, double* drho) {
+  double ae = fabs(e);
+  if (delta > 0.0 && ae > delta) {
+    *drho = e > 0.0 ? delta : -delta;
+    return delta * (ae - 0.5 * delta);
+  }
+  *drho = e;
+  return 0.5 * e * e;
+}
+
+/* Loss L = (1/B) sum_r sum_c rho(out_rc - y_rc) (rho of loss_rho; with
+ * delta == 0 that is (1/(2B)) sum (out - y)^2) and its gradient with respect
+ * to every parameter (same layout as params).  Returns L. */
+double oc_mlp_loss_grad(int32_t B, const double* params, const double* X, const double* Y, double* grad,
+                        double delta) {
   mlp_view v = mlp_split(params);
   int64_t np = oc_mlp_param_count();
   double* pre = (double*)malloc(sizeof(double) * 3 * (size_t)B * MLP_H);
@@ -224,9 +239,9 @@ double oc_mlp_loss_grad(int32_t B, const double* params, const double* X, const 
   for (int r = 0; r < B; ++r) {
     double dout[MLP_OUT], dz[MLP_H], da[MLP_H];
     for (int c = 0; c < MLP_OUT; ++c) {
-      double e = out[(int64_t)r * MLP_OUT + c] - Y[(int64_t)r * MLP_OUT + c];
-      loss += e * e;
-      dout[c] = e / B;
+      double e = out[(int64_t)r * MLP_OUT + c] - Y[(int64_t)r * MLP_OUT + c], drho;
+      loss += loss_rho(e, delta, &drho);
+      dout[c] = drho / B;
     }
     /* layer 4 (linear head) */
     const double* z3 = pre + ((int64_t)2 * B + r) * MLP_H;
@@ -263,7 +278,7 @@ double oc_mlp_loss_grad(int32_t B, const double* params, const double* X, const 
   }
   free(pre);
   free(out);
-  return loss / (2.0 * B);
+  return loss / B;
 }
 
 /* One Adam step (Kingma & Ba 2015, Algorithm 1) at iteration t >= 1. */

@@ -229,12 +229,28 @@ class Env:
         _check(lib.est_record(self.h, ctypes.c_void_p(feat.data_ptr()), ctypes.c_void_p(label.data_ptr())), self.h,
                "est_record")
 
-    def est_loss_grad(self, X: torch.Tensor, Y: torch.Tensor):
+    def est_loss_grad(self, X: torch.Tensor, Y: torch.Tensor, huber: float = 0.0, batch: Optional[int] = None,
+                      seed: int = 0, step: int = 0):
+        """Loss and gradient [156930] (device) of one batch: all rows of X, Y
+        in order (``batch`` None or len(X)), else ``batch`` rows drawn as
+        :meth:`est_train`'s step ``step`` under ``seed``."""
+        for t, c in ((X, 96), (Y, 2)):
+            assert t.is_cuda and t.dtype == torch.float32 and t.dim() == 2 and t.shape[1] == c and t.is_contiguous()
+        assert X.shape[0] == Y.shape[0]
+        n = X.shape[0]
         grad = torch.empty(156930, dtype=torch.float32, device="cuda")
         loss = ctypes.c_double()
-        _check(lib.est_loss_grad(self.h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()), X.shape[0],
+        _check(lib.est_loss_grad(self.h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()), n,
+                                 n if batch is None else int(batch), seed, step, huber,
                                  ctypes.c_void_p(grad.data_ptr()), ctypes.byref(loss)), self.h, "est_loss_grad")
         return loss.value, grad
+
+    def est_adam_step(self, grad: torch.Tensor, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+                      eps: float = 1e-8):
+        """One Adam update of the master weights with ``grad`` [156930] (device)."""
+        assert grad.is_cuda and grad.dtype == torch.float32 and grad.numel() == 156930 and grad.is_contiguous()
+        _check(lib.est_adam_step(self.h, ctypes.c_void_p(grad.data_ptr()), lr, beta1, beta2, eps), self.h,
+               "est_adam_step")
 
     def est_train(self, X: torch.Tensor, Y: torch.Tensor, steps: int, batch: int, lr: float = 1e-3,
                   cosine: bool = True, seed: int = 0, beta1=0.9, beta2=0.999, eps=1e-8, huber: float = 0.0) -> dict:

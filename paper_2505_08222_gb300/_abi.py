@@ -7,7 +7,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libutrack.so")
 
-UT_ABI_VERSION = 4
+UT_ABI_VERSION = 5
 UT_FLAG_DEBUG = 1
 UT_FLAG_RING = 2
 
@@ -126,7 +126,9 @@ SIGNATURES = {
     "est_set_mode": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "est_forward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64]),
     "est_record": (ctypes.c_int, [_vp, _vp, _vp]),
-    "est_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, _vp, ctypes.POINTER(ctypes.c_double)]),
+    "est_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                                     ctypes.c_uint32, ctypes.c_float, _vp, ctypes.POINTER(ctypes.c_double)]),
+    "est_adam_step": (ctypes.c_int, [_vp, _vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
     "est_train": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, ctypes.POINTER(EstTrainConfig),
                                  ctypes.POINTER(EstTrainStats)]),
     "est_save": (ctypes.c_int, [_vp, ctypes.c_char_p]),

@@ -350,13 +350,22 @@ extern "C" ut_status est_record(ut_env* h, float* feat_dev, float* label_dev) {
   return e == cudaSuccess ? UT_OK : est_fail(h, UT_ERR_CUDA, cudaGetErrorString(e));
 }
 
-extern "C" ut_status est_loss_grad(ut_env* h, const float* X_dev, const float* Y_dev, int32_t B, float* grad_dev,
+extern "C" ut_status est_loss_grad(ut_env* h, const float* X_dev, const float* Y_dev, int64_t n_rows, int32_t B,
+                                   uint64_t seed, uint32_t step, float huber_delta, float* grad_dev,
                                    double* loss_host) {
-  if (!h || !X_dev || !Y_dev || B < 1 || !grad_dev) return UT_ERR_INVALID;
+  if (!h || !X_dev || !Y_dev || n_rows < 1 || n_rows >= (1ll << 32) || B < 1 || B > (1 << 22) || !grad_dev ||
+      !(huber_delta >= 0.0f))
+    return UT_ERR_INVALID;
   if (!h->est || !h->est->weights_set) return est_fail(h, UT_ERR_STATE, "est_loss_grad: no weights");
   ut_status st = est_alloc_batch(h, B);
   if (st != UT_OK) return st;
-  cudaError_t e = est_grad_batch(h, X_dev, Y_dev, nullptr, B, 0.0f);
+  const int32_t* rows = nullptr;
+  if (B != n_rows) {
+    const cudaError_t er = est::launch_batch_rows(h->est->rows, B, n_rows, seed, step, h->stream);
+    if (er != cudaSuccess) return est_fail(h, UT_ERR_CUDA, cudaGetErrorString(er));
+    rows = h->est->rows;
+  }
+  cudaError_t e = est_grad_batch(h, X_dev, Y_dev, rows, B, huber_delta);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(grad_dev, h->est->grad, est::NPARAM * 4, cudaMemcpyDeviceToDevice, h->stream);
   double loss = 0.0;
@@ -365,6 +374,18 @@ extern "C" ut_status est_loss_grad(ut_env* h, const float* X_dev, const float* Y
   if (e != cudaSuccess) return est_fail(h, UT_ERR_CUDA, cudaGetErrorString(e));
   if (loss_host) *loss_host = loss;
   return UT_OK;
+}
+
+extern "C" ut_status est_adam_step(ut_env* h, const float* grad_dev, float lr, float beta1, float beta2, float eps) {
+  if (!h || !grad_dev || !(lr > 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) ||
+      !(eps > 0.0f))
+    return UT_ERR_INVALID;
+  if (!h->est || !h->est->weights_set) return est_fail(h, UT_ERR_STATE, "est_adam_step: no weights");
+  EstimatorState* es = h->est;
+  es->adam_t += 1;
+  cudaError_t e = est::launch_adam(es->master, es->m, es->v, grad_dev, es->adam_t, lr, beta1, beta2, eps, es->img,
+                                   h->stream);
+  return e == cudaSuccess ? UT_OK : est_fail(h, UT_ERR_CUDA, cudaGetErrorString(e));
 }
 
 extern "C" ut_status est_train(ut_env* h, const float* X_dev, const float* Y_dev, int64_t n_rows,
@@ -392,7 +413,7 @@ extern "C" ut_status est_train(ut_env* h, const float* X_dev, const float* Y_dev
     if (e == cudaSuccess) e = est_grad_batch(h, X_dev, Y_dev, rows, B, cfg->huber_delta);
     // cosine decay of the learning rate over the run (reading C18)
     const double frac = cfg->steps > 1 ? (double)s / (double)(cfg->steps - 1) : 0.0;
-    const float lr = cfg->cosine ? (float)(cfg->lr * 0.5 * (1.0 + std::cos(3.14159265358979 * frac))) : cfg->lr;
+    const float lr = cfg->cosine ? (float)(cfg->lr * 0.5 * (1.0 + std::cos(3.141592653589793 * frac))) : cfg->lr;
     es->adam_t += 1;
     if (e == cudaSuccess)
       e = est::launch_adam(es->master, es->m, es->v, es->grad, es->adam_t, lr, cfg->beta1, cfg->beta2, cfg->eps,

@@ -75,6 +75,107 @@ def test_est_gradients_match_oracle():
         off += n
 
 
+def test_est_huber_gradients_match_oracle():
+    """The Huber loss (threshold between the residuals' quartiles, so both
+    branches occur) against the oracle's."""
+    env, _ = _env()
+    params = synth.mlp_params(seed=6, bias_scale=0.1)
+    env.est_set_weights(params)
+    X = _features(600, 3)
+    Y = (np.random.default_rng(4).standard_normal((600, 2)) * 0.4).astype(np.float32)
+    delta = 0.25
+    loss, grad = env.est_loss_grad(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), huber=delta)
+    ref_loss, ref_grad = oracle.mlp_loss_grad(params, X, Y, huber=delta)
+    r = np.abs(oracle.mlp_forward(params, X) - Y)
+    assert np.mean(r > delta) > 0.2 and np.mean(r < delta) > 0.2
+    assert abs(loss - ref_loss) <= 2e-2 * ref_loss
+    g = grad.cpu().numpy().astype(np.float64)
+    off = 0
+    for name, shape, _ in synth.mlp_shapes():
+        n = int(np.prod(shape))
+        rel = np.linalg.norm(g[off:off + n] - ref_grad[off:off + n]) / np.linalg.norm(ref_grad[off:off + n])
+        assert rel < 5e-2, (name, rel)
+        off += n
+
+
+def test_half_batch_gradients_average_to_full_batch():
+    """The loss is a mean over rows, so the mean of the gradients of two
+    equal halves is the gradient of the whole batch (data-parallel
+    averaging); equal up to FP32 summation order."""
+    env, _ = _env()
+    env.est_set_weights(synth.mlp_params(seed=8, bias_scale=0.1))
+    X = torch.from_numpy(_features(1024, 5)).cuda()
+    Y = torch.from_numpy((np.random.default_rng(6).standard_normal((1024, 2)) * 0.3).astype(np.float32)).cuda()
+    lf, gf = env.est_loss_grad(X, Y, huber=1.0)
+    l0, g0 = env.est_loss_grad(X[:512].contiguous(), Y[:512].contiguous(), huber=1.0)
+    l1, g1 = env.est_loss_grad(X[512:].contiguous(), Y[512:].contiguous(), huber=1.0)
+    assert (l0 + l1) / 2 == pytest.approx(lf, rel=1e-5)
+    gm = ((g0 + g1) / 2).double()
+    rel = float((gm - gf.double()).norm() / gf.double().norm())
+    assert rel < 1e-5, rel
+
+
+def test_sampled_loss_grad_draws_est_train_rows():
+    """A sampled batch (B < n_rows) draws its rows from the counter-based
+    stream keyed by (seed, step): the same key gives the same gradient, a
+    different step another, and the whole-table batch is the in-order one."""
+    env, _ = _env()
+    env.est_set_weights(synth.mlp_params(seed=9, bias_scale=0.1))
+    X = torch.from_numpy(_features(2000, 7)).cuda()
+    Y = torch.from_numpy((np.random.default_rng(8).standard_normal((2000, 2)) * 0.3).astype(np.float32)).cuda()
+    la, ga = env.est_loss_grad(X, Y, batch=256, seed=3, step=1)
+    lb, gb = env.est_loss_grad(X, Y, batch=256, seed=3, step=1)
+    lc, _ = env.est_loss_grad(X, Y, batch=256, seed=3, step=2)
+    assert la == pytest.approx(lb, rel=1e-6) and float((ga - gb).abs().max()) <= 1e-6 * float(ga.abs().max())
+    assert la != lc
+    with pytest.raises(ut.UtError):
+        env.est_loss_grad(X, Y, huber=-1.0)
+
+
+def test_adam_step_entry_matches_oracle_adam():
+    """est_adam_step applied to a given gradient against the oracle's Adam
+    on the same gradient (two steps, so the moments and the bias correction
+    of step 2 are exercised)."""
+    env, _ = _env()
+    params = synth.mlp_params(seed=10, bias_scale=0.1)
+    env.est_set_weights(params)
+    rng = np.random.default_rng(11)
+    g1 = (rng.standard_normal(NP) * 1e-2).astype(np.float32)
+    g2 = (rng.standard_normal(NP) * 1e-2).astype(np.float32)
+    lr = 1e-3
+    for g in (g1, g2):
+        env.est_adam_step(torch.from_numpy(g).cuda(), lr)
+    got = env.est_get_weights().astype(np.float64)
+    th, m, v = oracle.adam(params, np.zeros(NP), np.zeros(NP), g1, 1, lr=lr)
+    th, m, v = oracle.adam(th, m, v, g2, 2, lr=lr)
+    np.testing.assert_allclose(got, th, rtol=0, atol=1e-6 * lr + 2e-7 * np.abs(th).max())
+
+
+def test_dp_train_one_rank_repeats_est_train():
+    """Data-parallel training on one rank is est_train step for step: the
+    same batches, schedule and updates.  The gradient sums use atomics, so
+    the two runs agree to rounding, not bit for bit; Adam's normalised
+    steps bound any remaining difference by 2 lr per step."""
+    from paper_2505_08222_gb300 import shard
+
+    X = torch.from_numpy(_features(4096, 12)).cuda()
+    Y = torch.from_numpy((np.random.default_rng(13).standard_normal((4096, 2)) * 0.3).astype(np.float32)).cuda()
+    init = synth.mlp_params(seed=14, bias_scale=0.1)
+    a, _ = _env()
+    b, _ = _env()
+    a.est_set_weights(init)
+    b.est_set_weights(init)
+    steps, lr = 6, 1e-3
+    st = shard.dp_train(a, X, Y, steps=steps, batch=512, lr=lr, seed=15, huber=1.0)
+    ref = b.est_train(X, Y, steps=steps, batch=512, lr=lr, seed=15, huber=1.0)
+    wa, wb = a.est_get_weights().astype(np.float64), b.est_get_weights().astype(np.float64)
+    d = np.abs(wa - wb)
+    assert d.max() <= 2 * lr * steps
+    assert np.mean(d <= 1e-2 * lr) >= 0.99, float(np.mean(d <= 1e-2 * lr))
+    assert np.abs(wa - init).max() > 0.5 * lr
+    assert st["loss_first"] == pytest.approx(ref["loss_first"], rel=1e-4)
+
+
 def test_record_features_match_oracle():
     """The oracle's state after a few steps (estimate history and ping rings
     included) is injected in float32; one more step on both sides, then the

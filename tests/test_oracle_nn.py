@@ -164,6 +164,51 @@ def test_mlp_grad_central_differences():
         assert grad[i] == pytest.approx(fd, rel=1e-5, abs=1e-9)
 
 
+def test_mlp_huber_matches_torch_huber_loss():
+    """The Huber loss of the training step against torch's huber_loss
+    (summed over outputs, averaged over rows) and autograd; the threshold is
+    chosen so that residuals fall on both sides of it."""
+    params = synth.mlp_params(seed=11, bias_scale=0.1)
+    X = synth.random_features(41, seed=12)
+    Y = np.random.default_rng(13).standard_normal((41, 2)) * 0.5
+    delta = 0.3
+    loss, grad = oracle.mlp_loss_grad(params, X, Y, huber=delta)
+    to, W = _torch_mlp(params, X)
+    e = np.abs(to.detach().numpy() - Y)
+    assert np.mean(e > delta) > 0.2 and np.mean(e < delta) > 0.2
+    tl = torch.nn.functional.huber_loss(to, torch.tensor(Y), reduction="sum", delta=delta) / 41
+    tl.backward()
+    assert loss == pytest.approx(tl.item(), rel=1e-12)
+    tg = np.concatenate([W[name].grad.numpy().ravel() for name, _, _ in synth.mlp_shapes()])
+    np.testing.assert_allclose(grad, tg, rtol=1e-9, atol=1e-13)
+
+
+def test_mlp_huber_constant_network_closed_form():
+    """All weights zero and output bias c: every row outputs c, so
+    L = mean_r sum_c rho(c - y) and dL/db4 = mean_r clip(c - y, -delta, delta)
+    with every other gradient zero (GELU(0) = 0); delta = 0 is the squared error."""
+    n = oracle.mlp_param_count()
+    params = np.zeros(n)
+    c = np.array([0.4, -1.1])
+    params[-2:] = c
+    X = synth.random_features(9, seed=1)
+    Y = np.random.default_rng(2).standard_normal((9, 2))
+    for delta in (0.0, 0.5, 100.0):
+        loss, grad = oracle.mlp_loss_grad(params, X, Y, huber=delta)
+        e = c - Y
+        if delta == 0.0:
+            rho, d = 0.5 * e * e, e
+        else:
+            rho = np.where(np.abs(e) <= delta, 0.5 * e * e, delta * (np.abs(e) - 0.5 * delta))
+            d = np.clip(e, -delta, delta)
+        assert loss == pytest.approx(rho.sum() / 9, rel=1e-13)
+        np.testing.assert_allclose(grad[-2:], d.mean(axis=0), rtol=1e-13, atol=1e-15)
+        assert np.all(grad[:-2] == 0.0)
+    # a threshold above every residual leaves the squared error unchanged
+    assert oracle.mlp_loss_grad(params, X, Y, huber=100.0)[0] == pytest.approx(
+        oracle.mlp_loss_grad(params, X, Y)[0], rel=1e-15)
+
+
 def test_adam_closed_form_constant_gradient():
     """With a constant gradient g, bias-corrected moments are exactly g and
     g^2, so every step moves theta by -lr g / (|g| + eps)."""
