@@ -374,7 +374,9 @@ ut_status est_loss_grad(ut_env* env, const float* X_dev, const float* Y_dev, int
  * gradient grad_dev [156930] (device; e.g. the average of the ranks'
  * est_loss_grad results in data-parallel training); the handle counts the
  * steps for the bias correction (reset by est_set_weights / est_load).
- * Asynchronous on the handle's stream.  Errors: UT_ERR_INVALID, UT_ERR_STATE. */
+ * lr >= 0 (a cosine schedule ends at 0: the moments still advance), beta1
+ * and beta2 in [0, 1), eps > 0.  Asynchronous on the handle's stream.
+ * Errors: UT_ERR_INVALID, UT_ERR_STATE. */
 ut_status est_adam_step(ut_env* env, const float* grad_dev, float lr, float beta1, float beta2, float eps);
 /* Adam (bias-corrected) over cfg->steps batches of X_dev / Y_dev
  * ([n_rows][96], [n_rows][2], device).  Synchronising; stats optional. */

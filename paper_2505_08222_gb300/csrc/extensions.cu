@@ -377,7 +377,7 @@ extern "C" ut_status est_loss_grad(ut_env* h, const float* X_dev, const float* Y
 }
 
 extern "C" ut_status est_adam_step(ut_env* h, const float* grad_dev, float lr, float beta1, float beta2, float eps) {
-  if (!h || !grad_dev || !(lr > 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) ||
+  if (!h || !grad_dev || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) ||
       !(eps > 0.0f))
     return UT_ERR_INVALID;
   if (!h->est || !h->est->weights_set) return est_fail(h, UT_ERR_STATE, "est_adam_step: no weights");
