@@ -9,16 +9,19 @@
 //             |v| capped, p += dt v                                 (reading C2)
 //   weight    l_i = -sum_m (r_m - |p_i - q_m|)^2 / (2 sigma_r^2); max by warp
 //             shuffles, w_i = exp(l_i - max l), sums by warp shuffles (C3)
-//   estimate  weighted mean before resampling                       (C6)
-//   resample  q_i = floor(w_i 2^38) (exact), int64 block scan -> Q, W;
-//             U0 = mulhi(u64, W); particle i owns the outputs
-//             [count(P Q_{i-1}), count(P Q_i)) with
-//             count(X) = #{j : j W + U0 < X}; its index is written at the
-//             first owned output and a block prefix-max fills the rest;
+//   estimate  weighted mean before resampling, the weight total taken as
+//             the exact integer total W below times 2^-38          (C6)
+//   resample  q_i = floor(w_i 2^38) (exact), int64 block scan -> Q, W (the
+//             scan also carries the estimate's sums); U0 = mulhi(u64, W);
+//             particle i owns the outputs [count(P Q_{i-1}), count(P Q_i))
+//             with count(X) = #{j : j W + U0 < X}; its index is written at
+//             the first owned output and a block prefix-max fills the rest;
 //             gather from shared memory.                            (C4, C5)
-// Integer arithmetic makes the resample map independent of summation order:
-// given the weights and the offset it is bit-identical to the definition
-// idx_j = min{i : P Q_i > j W + U0}.
+// The resample map is independent of summation order: given the weights and
+// the offset it is bit-identical to the definition
+// idx_j = min{i : P Q_i > j W + U0}.  count is evaluated in FP32 from a
+// running FP32 weight sum whose error is bounded (resample_map); where the
+// FP32 value lies within that bound of an integer, int64 arithmetic decides.
 //
 // Transcendentals in the per-particle loop use the SFU approximations
 // (lg2 / ex2 / sin / cos / sqrt .approx): their relative errors (~1e-7) are
@@ -48,129 +51,104 @@ __device__ __forceinline__ void box_muller_fast(uint32_t va, uint32_t vb, float&
   n1 = -rad * s;
 }
 
-template <int NT>
-__device__ __forceinline__ float block_max(float v, float* s_tmp) {
-  constexpr int NW = NT / 32;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  v = warp_max(v);
-  if (NW == 1) return v;
-  if (lane == 0) s_tmp[wid] = v;
-  __syncthreads();
-  float r = lane < NW ? s_tmp[lane] : -INFINITY;
-  r = warp_max(r);
-  __syncthreads();
+// Cross-warp scratch of the block-wide reductions (each array used once per
+// CTA, so no reduction needs a trailing barrier).
+struct ScanScratch {
+  float max[32];
+  long long tot[32], pre[32];  // pre[NW - 1] = the block total W after the scan
+  float fx[32], fy[32], fsum[2];
+  int mtot[32];
+  unsigned long long u64;  // the filter's resampling draw
+};
+
+// Warp maximum on the warp reduction unit (NaN inputs ignored, as by fmaxf).
+__device__ __forceinline__ float warp_max_redux(float v) {
+  float r;
+  asm("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
   return r;
 }
 
+// Block maximum.
 template <int NT>
-__device__ __forceinline__ void block_sum3(float& a, float& b, float& c, float* s_tmp) {
+__device__ __forceinline__ float block_max(float v, ScanScratch* sc) {
   constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  a = warp_sum(a);
-  b = warp_sum(b);
-  c = warp_sum(c);
-  if (NW == 1) return;
-  if (lane == 0) {
-    s_tmp[wid] = a;
-    s_tmp[NW + wid] = b;
-    s_tmp[2 * NW + wid] = c;
-  }
+  v = warp_max_redux(v);
+  if (NW == 1) return v;
+  if (lane == 0) sc->max[wid] = v;
   __syncthreads();
-  float ra = lane < NW ? s_tmp[lane] : 0.0f;
-  float rb = lane < NW ? s_tmp[NW + lane] : 0.0f;
-  float rc = lane < NW ? s_tmp[2 * NW + lane] : 0.0f;
-  a = warp_sum(ra);
-  b = warp_sum(rb);
-  c = warp_sum(rc);
-  __syncthreads();
+  return warp_max_redux(lane < NW ? sc->max[lane] : -INFINITY);
 }
 
-// Exclusive block scan of int64 values; also returns the block total.
-// s_tot / s_pre [32] are used once per CTA (no trailing barrier).
+// Exclusive block scan of the int64 v (returned; the block total in W),
+// fused with the block sums of fx and fy (returned in place): one exchange
+// through shared memory, scanned and summed by warp 0.
 template <int NT>
-__device__ __forceinline__ long long block_excl_scan(long long v, long long* s_tot, long long* s_pre,
-                                                     long long& total) {
+__device__ __forceinline__ long long block_scan_sums(long long v, float& fx, float& fy, ScanScratch* sc,
+                                                     long long& W) {
   constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   long long incl = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    long long t = __shfl_up_sync(0xffffffffu, incl, o);
+    const long long t = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += t;
   }
+  fx = warp_sum(fx);
+  fy = warp_sum(fy);
   if (NW == 1) {
-    total = __shfl_sync(0xffffffffu, incl, 31);
+    W = __shfl_sync(0xffffffffu, incl, 31);
+    if (lane == 0) sc->pre[0] = W;  // ordered by the caller's __syncwarp
     return incl - v;
   }
-  if (lane == 31) s_tot[wid] = incl;
-  __syncthreads();
-  if (wid == 0) {
-    long long w = lane < NW ? s_tot[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      long long t = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += t;
-    }
-    if (lane < NW) s_pre[lane] = w;
+  if (lane == 31) {
+    sc->tot[wid] = incl;
+    sc->fx[wid] = fx;
+    sc->fy[wid] = fy;
   }
   __syncthreads();
-  total = s_pre[NW - 1];
-  return (wid > 0 ? s_pre[wid - 1] : 0) + incl - v;
+  if (wid == 0) {
+    long long t = lane < NW ? sc->tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long u = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += u;
+    }
+    if (lane < NW) sc->pre[lane] = t;
+    const float a = warp_sum(lane < NW ? sc->fx[lane] : 0.0f);
+    const float b = warp_sum(lane < NW ? sc->fy[lane] : 0.0f);
+    if (lane == 0) {
+      sc->fsum[0] = a;
+      sc->fsum[1] = b;
+    }
+  }
+  __syncthreads();
+  W = sc->pre[NW - 1];
+  fx = sc->fsum[0];
+  fy = sc->fsum[1];
+  return (wid > 0 ? sc->pre[wid - 1] : 0) + incl - v;
 }
 
-// Maximum over all earlier threads of each thread's value (identity -1).
-// s_tot / s_pre [32] are used once per CTA (no trailing barrier).
+// The nearest marker before each thread's outputs (-1 if none), given the
+// last marker among the thread's own outputs (run, -1 if none).  Markers are
+// particle indices placed at increasing output positions in increasing
+// particle order, so the nearest earlier marker is also the largest: within
+// the warp it comes from the nearest lower lane that holds one (a ballot and
+// one shuffle), across warps from the maximum of the earlier warps' last
+// markers (warp reductions).  sc->mtot is used once per CTA.
 template <int NT>
-__device__ __forceinline__ int block_excl_max(int v, int* s_tot, int* s_pre) {
+__device__ __forceinline__ int block_prev_marker(int run, ScanScratch* sc) {
   constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int incl = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl = max(incl, t);
-  }
-  int excl = __shfl_up_sync(0xffffffffu, incl, 1);
-  if (lane == 0) excl = -1;
+  const unsigned below = __ballot_sync(0xffffffffu, run >= 0) & ((1u << lane) - 1u);
+  const int from = __shfl_sync(0xffffffffu, run, (31 - __clz(below)) & 31);
+  const int excl = below ? from : -1;
   if (NW == 1) return excl;
-  if (lane == 31) s_tot[wid] = incl;
+  const int last = __reduce_max_sync(0xffffffffu, run);
+  if (lane == 0) sc->mtot[wid] = last;
   __syncthreads();
-  if (wid == 0) {
-    int w = lane < NW ? s_tot[lane] : -1;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int t = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w = max(w, t);
-    }
-    if (lane < NW) s_pre[lane] = w;
-  }
-  __syncthreads();
-  return max(wid > 0 ? s_pre[wid - 1] : -1, excl);
-}
-
-// Cross-warp scratch of the resample map (each array used once per CTA).
-struct ScanScratch {
-  long long tot[32], pre[32];
-  int mtot[32], mpre[32];
-};
-
-// count(X) = #{ j in [0, P) : j W + U0 < X } = clamp(ceil((X - U0) / W), 0, P),
-// exact.  A float estimate v = (X - U0) * (1/W) has absolute error below 2e-3
-// for v <= 4096; ceil(v) is taken directly unless v lies within 4e-3 of an
-// integer, where one int64 comparison decides.
-__device__ __forceinline__ int resample_count(long long X, long long W, long long U0, float invW, int P) {
-  if (X <= U0) return 0;
-  const long long D = X - U0;
-  const float v = __ll2float_rn(D) * invW;
-  const float r = rintf(v);
-  int n;
-  if (fabsf(v - r) < 4e-3f) {
-    const int m = (int)r;
-    n = ((long long)m * W >= D) ? m : m + 1;
-  } else {
-    n = (int)ceilf(v);
-  }
-  return n < 0 ? 0 : (n > P ? P : n);
+  const int prev = __reduce_max_sync(0xffffffffu, lane < wid ? sc->mtot[lane] : -1);
+  return max(prev, excl);
 }
 
 // Shared-memory slot of particle i: thread t's PPT particles are spread NT
@@ -180,32 +158,84 @@ __device__ __forceinline__ int slot_of(int i) {
   return (i % PPT) * NT + i / PPT;
 }
 
-// Resample map of one filter.  w[q] = max-normalised weight of particle
-// base + q (0 for slots >= P).  Writes idx[q] for outputs base + q.
-template <int NT, int PPT>
-__device__ __forceinline__ void resample_map(const float (&w)[PPT], int base, int P, uint64_t u64, int* s_mark,
-                                             ScanScratch* sc, int (&idx)[PPT]) {
-  long long incl[PPT];
-  long long acc = 0;
+// Markers of the thread's PPT outputs set to -1 (vector stores; slots >= P
+// are never read).  Must precede the block barrier of the scan.
+template <int PPT>
+__device__ __forceinline__ void init_markers(int* s_mark, int base) {
 #pragma unroll
-  for (int q = 0; q < PPT; ++q) {
-    acc += __float2ll_rd(w[q] * 274877906944.0f);  // floor(w 2^38), exact
-    incl[q] = acc;
+  for (int q = 0; q < PPT; q += 4) *reinterpret_cast<int4*>(s_mark + base + q) = make_int4(-1, -1, -1, -1);
+}
+
+// Exact integer weight floor(w 2^38) (w in [0, 1]).
+__device__ __forceinline__ long long qweight(float w) { return __float2ll_rd(w * 274877906944.0f); }
+
+// count at the boundary after the thread's first nq particles, from its FP32
+// estimate v of D / W with D = P C - U0, U0 = mulhi(u64, W), C = excl + the
+// integer weights of those particles: count = clamp(ceil(D / W), 0, P).
+// If v lies within eps of an integer m, |D / W - m| < 2 eps < 1/2 and
+// D <= m W decides between m and m + 1 exactly; otherwise
+// ceil(v) = ceil(D / W).  The exact branch is rare: it reads the thread's
+// excl and weights (s_w [PPT]), W and u64 from shared memory and rebuilds C,
+// so that none of them holds a register through the common path.
+template <int PPT>
+__device__ __forceinline__ int count_at(float v, float eps, const float* s_w, int nq, const long long* s_excl,
+                                        const ScanScratch* sc, int NW, int P) {
+  const float r = rintf(v);
+  int n;
+  if (fabsf(v - r) < eps) {
+    const long long W = sc->pre[NW - 1];
+    const long long U0 = (long long)__umul64hi(sc->u64, (unsigned long long)W);
+    long long C = *s_excl;
+#pragma unroll
+    for (int t = 0; t < PPT; ++t)
+      if (t < nq) C += qweight(s_w[t]);
+    const long long D = (long long)P * C - U0;
+    const int m = (int)r;
+    n = (D <= (long long)m * W) ? m : m + 1;
+  } else {
+    n = __float2int_ru(v);
   }
-  // markers start at -1 (vector stores; slots >= P are never read)
+  return min(max(n, 0), P);
+}
+
+// Resample map of one filter.  w[q] = max-normalised weight of particle
+// base + q (0 for slots >= P); excl = the sum of the integer weights
+// floor(w 2^38) over all earlier threads, W = their total (block_scan_sums,
+// which also left W in sc->pre[NW - 1]); sc->u64 holds the filter's draw;
+// s_excl [NT] and s_w [NT*PPT] are scratch; the markers are -1
+// (init_markers) and the scan's barrier has passed.  Writes idx[q] for
+// outputs base + q.
+//
+// FP32 bound of v = fma(a, cw, b) against D / W, with u = 2^-24, W >= 2^38
+// (the heaviest particle has w = 1) so that a = P 2^38 / W <= P:
+// a carries 3u relative error, the running sum cw of PPT weights in [0, 1]
+// (PPT - 1)u, the product 1u, so a cw is within (PPT + 3) u P; b = (P excl -
+// U0) / W (|b| <= P + 1) within 4u (P + 1); the fma rounds by u (P + 1);
+// cw replaces the floored q's by w 2^-38 2^38, which moves v by at most
+// P PPT 2^-38.  Total below (PPT + 9) u (P + 1); eps is twice that.
+template <int NT, int PPT, bool FULL>
+__device__ __forceinline__ void resample_map(const float (&w)[PPT], long long excl, long long W, int base, int P,
+                                             long long* s_excl, float* s_w, int* s_mark, ScanScratch* sc,
+                                             int (&idx)[PPT]) {
+  constexpr int NW = NT / 32;
+  const long long U0 = (long long)__umul64hi(sc->u64, (unsigned long long)W);
+  const float invW = 1.0f / __ll2float_rn(W);
+  const float a = (float)P * 274877906944.0f * invW;
+  const float b = __ll2float_rn((long long)P * excl - U0) * invW;
+  const float eps = (float)(2 * (PPT + 9)) * 0x1p-24f * (float)(P + 1);
+  long long* my_excl = s_excl + threadIdx.x;
+  float* my_w = s_w + base;
+  *my_excl = excl;  // both read back by this thread only
 #pragma unroll
   for (int q = 0; q < PPT; q += 4)
-    *reinterpret_cast<int4*>(s_mark + base + q) = make_int4(-1, -1, -1, -1);
-  long long W;
-  const long long excl = block_excl_scan<NT>(acc, sc->tot, sc->pre, W);  // contains barriers
-  if (NT == 32) __syncwarp();  // single-warp blocks: order the marker initialisation
-  const long long U0 = (long long)__umul64hi(u64, (unsigned long long)W);
-  const float invW = 1.0f / __ll2float_rn(W);
-  int lo = resample_count((long long)P * excl, W, U0, invW, P);
+    *reinterpret_cast<float4*>(my_w + q) = make_float4(w[q], w[q + 1], w[q + 2], w[q + 3]);
+  int lo = count_at<PPT>(b, eps, my_w, 0, my_excl, sc, NW, P);
+  float cw = 0.0f;
 #pragma unroll
   for (int q = 0; q < PPT; ++q) {
-    if (base + q < P) {
-      const int hi = resample_count((long long)P * (excl + incl[q]), W, U0, invW, P);
+    if (FULL || base + q < P) {
+      cw += w[q];
+      const int hi = count_at<PPT>(fmaf(a, cw, b), eps, my_w, q + 1, my_excl, sc, NW, P);
       if (hi > lo) s_mark[lo] = base + q;
       lo = hi;
     }
@@ -220,10 +250,10 @@ __device__ __forceinline__ void resample_map(const float (&w)[PPT], int base, in
   }
 #pragma unroll
   for (int q = 0; q < PPT; ++q) {
-    if (base + q >= P) m[q] = -1;
+    if (!FULL && base + q >= P) m[q] = -1;
     run = max(run, m[q]);
   }
-  int before = block_excl_max<NT>(run, sc->mtot, sc->mpre);
+  int before = block_prev_marker<NT>(run, sc);
 #pragma unroll
   for (int q = 0; q < PPT; ++q) {
     before = max(before, m[q]);
@@ -233,21 +263,24 @@ __device__ __forceinline__ void resample_map(const float (&w)[PPT], int base, in
 }
 
 struct Shared {
-  float red[3 * 32];
   ScanScratch scan;
   float4 meas[kMaxAgents];  // (qx, qy, (z_target - qz)^2, r)
   float tgt[2];
   float dz2;
   int nm;
-  unsigned long long u64;
 };
 
-template <int NT, int PPT, int MINB, bool VEC>
+// MODE 0: any P (scalar loads); 1: P % 4 == 0 (float4 streams); 2: P equal
+// to NT * PPT (float4 streams, no slot is out of range).
+template <int NT, int PPT, int MINB, int MODE>
 __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
   static_assert(PPT % 4 == 0, "PPT must be a multiple of 4");
+  constexpr bool VEC = MODE >= 1, FULL = MODE == 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4* s_part = reinterpret_cast<float4*>(smem_raw);      // [NT*PPT], slot_of layout
-  int* s_mark = reinterpret_cast<int*>(s_part + NT * PPT);   // [NT*PPT]
+  float4* s_part = reinterpret_cast<float4*>(smem_raw);                 // [NT*PPT], slot_of layout
+  int* s_mark = reinterpret_cast<int*>(s_part + NT * PPT);              // [NT*PPT]
+  long long* s_excl = reinterpret_cast<long long*>(s_mark + NT * PPT);  // [NT]
+  float* s_w = reinterpret_cast<float*>(s_excl + NT);                  // [NT*PPT]
   __shared__ Shared sh;
 
   const int tid = threadIdx.x;
@@ -280,14 +313,14 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
     sh.dz2 = hd.z;
     sh.nm = (int)hd.w;
     Rand4 r = philox(d.gid_filter + (uint32_t)f, 0u, g, TAG_RESAMPLE, d.seed);
-    sh.u64 = (unsigned long long)r.x[0] | ((unsigned long long)r.x[1] << 32);
+    sh.scan.u64 = (unsigned long long)r.x[0] | ((unsigned long long)r.x[1] << 32);
   }
 
   float x[PPT], y[PPT], vx[PPT], vy[PPT];
   if (VEC) {
 #pragma unroll
     for (int q = 0; q < PPT; q += 4) {
-      if (base + q < P) {
+      if (FULL || base + q < P) {
         const float4 a = __ldcs(reinterpret_cast<const float4*>(d.px + off + base + q));
         const float4 b = __ldcs(reinterpret_cast<const float4*>(d.py + off + base + q));
         const float4 c = __ldcs(reinterpret_cast<const float4*>(d.pvx + off + base + q));
@@ -318,7 +351,7 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
   for (int q = 0; q < PPT; q += 2) {
     const int i = base + q;
     float n[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    if (i < P) {
+    if (FULL || i < P) {
       Rand4 r = philox(d.gid_filter + (uint32_t)f, (uint32_t)(i >> 1), g, TAG_PF_PREDICT, d.seed);
       box_muller_fast(r.x[0], r.x[1], n[0], n[1]);
       box_muller_fast(r.x[2], r.x[3], n[2], n[3]);
@@ -338,6 +371,17 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
       vy[qq] = uy;
       x[qq] = fmaf(d.dt, ux, x[qq]);
       y[qq] = fmaf(d.dt, uy, y[qq]);
+    }
+  }
+  // estimate history (the update's inputs), written as soon as it has arrived
+  if (tid == 0 && d.prev_estx) {
+    d.prev2_estx[f] = hist[2];
+    d.prev2_esty[f] = hist[3];
+    d.prev_estx[f] = hist[0];
+    d.prev_esty[f] = hist[1];
+    if (d.velx) {  // motion of the previous update folded into the smoothed velocity
+      d.velx[f] = fmaf(kVelKeep, hist[4], (1.0f - kVelKeep) * (hist[0] - hist[2]));
+      d.vely[f] = fmaf(kVelKeep, hist[5], (1.0f - kVelKeep) * (hist[1] - hist[3]));
     }
   }
   __syncthreads();  // sh.* visible
@@ -361,59 +405,56 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
 #pragma unroll
   for (int q = 0; q < PPT; ++q) {
     acc[q] = -acc[q] * d.inv_two_s2;  // log-likelihood
-    if (base + q < P) lmax = fmaxf(lmax, acc[q]);
+    if (FULL || base + q < P) lmax = fmaxf(lmax, acc[q]);
   }
-  lmax = block_max<NT>(lmax, sh.red);
+  lmax = block_max<NT>(lmax, &sh.scan);
+  // max-normalised weights, their exact integer images floor(w 2^38) summed
+  // per thread, and the estimate's weighted sums
   float w[PPT];
-  float sw = 0.0f, swx = 0.0f, swy = 0.0f;
+  long long qsum = 0;
+  float swx = 0.0f, swy = 0.0f;
 #pragma unroll
   for (int q = 0; q < PPT; ++q) {
-    w[q] = base + q < P ? __expf(acc[q] - lmax) : 0.0f;
-    sw += w[q];
+    w[q] = (FULL || base + q < P) ? __expf(acc[q] - lmax) : 0.0f;
     swx = fmaf(w[q], x[q], swx);
     swy = fmaf(w[q], y[q], swy);
+    qsum += qweight(w[q]);
   }
-  block_sum3<NT>(sw, swx, swy, sh.red);
-
-  // estimate
-  if (tid == 0) {
-    const float ex = swx / sw, ey = swy / sw;
-    if (d.prev_estx) {  // estimate history: the update's inputs
-      d.prev2_estx[f] = hist[2];
-      d.prev2_esty[f] = hist[3];
-      d.prev_estx[f] = hist[0];
-      d.prev_esty[f] = hist[1];
-      if (d.velx) {  // motion of the previous update folded into the smoothed velocity
-        d.velx[f] = fmaf(kVelKeep, hist[4], (1.0f - kVelKeep) * (hist[0] - hist[2]));
-        d.vely[f] = fmaf(kVelKeep, hist[5], (1.0f - kVelKeep) * (hist[1] - hist[3]));
-      }
-    }
-    d.estx[f] = ex;
-    d.esty[f] = ey;
-    const float dx = ex - sh.tgt[0], dy = ey - sh.tgt[1];
-    d.err[f] = sqrtf(dx * dx + dy * dy);
-  }
-  if (d.debug_on) {
-    const float inv = 1.0f / sw;
+  if (d.debug_on) {  // pre-resample state and weights (normalised below)
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
-      if (base + q < P) {
+      if (FULL || base + q < P) {
         d.dbg_px[off + base + q] = x[q];
         d.dbg_py[off + base + q] = y[q];
         d.dbg_pvx[off + base + q] = vx[q];
         d.dbg_pvy[off + base + q] = vy[q];
-        d.dbg_w[off + base + q] = w[q] * inv;
         d.dbg_wmax[off + base + q] = w[q];
       }
     }
   }
-
+  // estimate: thread 0, from the block sums and the integer weight total
+  auto write_estimate = [&](float sx, float sy, long long Wt) {
+    if (tid == 0) {
+      const float sw = __ll2float_rn(Wt) * 0x1p-38f;
+      const float ex = sx / sw, ey = sy / sw;
+      d.estx[f] = ex;
+      d.esty[f] = ey;
+      const float dx = ex - sh.tgt[0], dy = ey - sh.tgt[1];
+      d.err[f] = sqrtf(dx * dx + dy * dy);
+    }
+  };
+  // nm is the same for the whole CTA, so both branches keep their barriers
+  // uniform; the particles are dead across the scan in the resampling branch
+  long long W;
   int idx[PPT];
   if (nm > 0) {
 #pragma unroll
     for (int q = 0; q < PPT; ++q) s_part[q * NT + tid] = make_float4(x[q], y[q], vx[q], vy[q]);
-    resample_map<NT, PPT>(w, base, P, sh.u64, s_mark, &sh.scan, idx);
-    // (resample_map contains barriers after the s_part stores)
+    init_markers<PPT>(s_mark, base);
+    const long long excl = block_scan_sums<NT>(qsum, swx, swy, &sh.scan, W);  // contains barriers
+    if (NT == 32) __syncwarp();  // single-warp blocks: order the shared-memory stores
+    write_estimate(swx, swy, W);
+    resample_map<NT, PPT, FULL>(w, excl, W, base, P, s_excl, s_w, s_mark, &sh.scan, idx);
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
       const float4 pnew = s_part[slot_of<NT, PPT>(idx[q])];
@@ -423,20 +464,27 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
       vy[q] = pnew.w;
     }
   } else {
+    block_scan_sums<NT>(qsum, swx, swy, &sh.scan, W);
+    write_estimate(swx, swy, W);
 #pragma unroll
     for (int q = 0; q < PPT; ++q) idx[q] = base + q;
   }
   if (d.debug_on) {
+    const float inv = 1.0f / (__ll2float_rn(W) * 0x1p-38f);
 #pragma unroll
-    for (int q = 0; q < PPT; ++q)
-      if (base + q < P) d.dbg_idx[off + base + q] = idx[q];
+    for (int q = 0; q < PPT; ++q) {
+      if (FULL || base + q < P) {
+        d.dbg_w[off + base + q] = w[q] * inv;
+        d.dbg_idx[off + base + q] = idx[q];
+      }
+    }
   }
 
   // write back (streaming stores: the state is not reread this step)
   if (VEC) {
 #pragma unroll
     for (int q = 0; q < PPT; q += 4) {
-      if (base + q < P) {
+      if (FULL || base + q < P) {
         __stcs(reinterpret_cast<float4*>(d.px + off + base + q), make_float4(x[q], x[q + 1], x[q + 2], x[q + 3]));
         __stcs(reinterpret_cast<float4*>(d.py + off + base + q), make_float4(y[q], y[q + 1], y[q + 2], y[q + 3]));
         __stcs(reinterpret_cast<float4*>(d.pvx + off + base + q),
@@ -464,18 +512,39 @@ __global__ void __launch_bounds__(NT) pf_resample_kernel(const float* __restrict
                                                           const uint64_t* __restrict__ u64, int P,
                                                           int32_t* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  int* s_mark = reinterpret_cast<int*>(smem_raw);
+  int* s_mark = reinterpret_cast<int*>(smem_raw);                       // [NT*PPT]
+  long long* s_excl = reinterpret_cast<long long*>(s_mark + NT * PPT);  // [NT]
+  float* s_w = reinterpret_cast<float*>(s_excl + NT);                  // [NT*PPT]
   __shared__ ScanScratch s_scan;
   const long long f = blockIdx.x;
+  if (threadIdx.x == 0) s_scan.u64 = u64[f];  // ordered by the scan's barriers
   const int base = threadIdx.x * PPT;
   float w[PPT];
+  long long qsum = 0;
 #pragma unroll
-  for (int q = 0; q < PPT; ++q) w[q] = base + q < P ? wmax[f * P + base + q] : 0.0f;
+  for (int q = 0; q < PPT; ++q) {
+    w[q] = base + q < P ? wmax[f * P + base + q] : 0.0f;
+    qsum += qweight(w[q]);
+  }
+  init_markers<PPT>(s_mark, base);
+  float fx = 0.0f, fy = 0.0f;
+  long long W;
+  const long long excl = block_scan_sums<NT>(qsum, fx, fy, &s_scan, W);
+  if (NT == 32) __syncwarp();
   int idx[PPT];
-  resample_map<NT, PPT>(w, base, P, u64[f], s_mark, &s_scan, idx);
+  resample_map<NT, PPT, false>(w, excl, W, base, P, s_excl, s_w, s_mark, &s_scan, idx);
 #pragma unroll
   for (int q = 0; q < PPT; ++q)
     if (base + q < P) out[f * P + base + q] = idx[q];
+}
+
+// Dynamic shared memory of the step (particles, markers, per-thread excl,
+// weights) and of the stand-alone resample map (markers, excl, weights).
+constexpr size_t step_smem_bytes(int NT, int PPT) {
+  return (size_t)NT * PPT * (sizeof(float4) + 2 * sizeof(int)) + (size_t)NT * sizeof(long long);
+}
+constexpr size_t resample_smem_bytes(int NT, int PPT) {
+  return (size_t)NT * PPT * 2 * sizeof(int) + (size_t)NT * sizeof(long long);
 }
 
 // Opt in to the dynamic shared memory a kernel needs (once per process).
@@ -487,22 +556,24 @@ cudaError_t ensure_smem(K k, size_t smem, int& done) {
   return e;
 }
 
+template <int NT, int PPT, int MINB, int MODE>
+cudaError_t launch_mode(const EnvDev& d, cudaStream_t s) {
+  static int ready = 0;
+  const size_t smem = step_smem_bytes(NT, PPT);
+  auto k = pf_step_kernel<NT, PPT, MINB, MODE>;
+  cudaError_t e = ensure_smem(k, smem, ready);
+  if (e != cudaSuccess) return e;
+  if (d.F > 0) k<<<d.F, NT, smem, s>>>(d);
+  return cudaGetLastError();
+}
+
+// Requires NT * PPT >= P (the variant check).
 template <int NT, int PPT, int MINB>
 cudaError_t launch_step(const EnvDev& d, cudaStream_t s) {
-  static int ready_vec = 0, ready_scalar = 0;
-  const size_t smem = (size_t)NT * PPT * (sizeof(float4) + sizeof(int));
-  if (d.P % 4 == 0) {
-    auto k = pf_step_kernel<NT, PPT, MINB, true>;
-    cudaError_t e = ensure_smem(k, smem, ready_vec);
-    if (e != cudaSuccess) return e;
-    if (d.F > 0) k<<<d.F, NT, smem, s>>>(d);
-  } else {
-    auto k = pf_step_kernel<NT, PPT, MINB, false>;
-    cudaError_t e = ensure_smem(k, smem, ready_scalar);
-    if (e != cudaSuccess) return e;
-    if (d.F > 0) k<<<d.F, NT, smem, s>>>(d);
-  }
-  return cudaGetLastError();
+  if (d.P > NT * PPT) return cudaErrorInvalidValue;
+  if (d.P == NT * PPT) return launch_mode<NT, PPT, MINB, 2>(d, s);
+  if (d.P % 4 == 0) return launch_mode<NT, PPT, MINB, 1>(d, s);
+  return launch_mode<NT, PPT, MINB, 0>(d, s);
 }
 
 }  // namespace pf
