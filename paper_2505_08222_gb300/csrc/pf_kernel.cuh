@@ -30,9 +30,25 @@
 #pragma once
 
 #include "env.cuh"
+#include "gelu.cuh"
 
 namespace ut {
 namespace pf {
+
+// 4-byte asynchronous global -> shared copy, and the wait for all of the
+// calling thread's copies.
+__device__ __forceinline__ void cp_async4(float* dst_smem, const float* src) {
+  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(dst_smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(a), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Packed FP32 pair add (gelu.cuh has the pack, unpack, fma and mul forms).
+__device__ __forceinline__ unsigned long long f2add(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
 
 __device__ __forceinline__ float sqrt_approx(float x) {
   float y;
@@ -81,8 +97,9 @@ __device__ __forceinline__ float block_max(float v, ScanScratch* sc) {
 }
 
 // Exclusive block scan of the int64 v (returned; the block total in W),
-// fused with the block sums of fx and fy (returned in place): one exchange
-// through shared memory, scanned and summed by warp 0.
+// fused with the block sums of fx and fy (returned in place, and kept in
+// sc->fsum): one exchange through shared memory; the cross-warp scan and the
+// two sums run on three different warps.
 template <int NT>
 __device__ __forceinline__ long long block_scan_sums(long long v, float& fx, float& fy, ScanScratch* sc,
                                                      long long& W) {
@@ -98,7 +115,11 @@ __device__ __forceinline__ long long block_scan_sums(long long v, float& fx, flo
   fy = warp_sum(fy);
   if (NW == 1) {
     W = __shfl_sync(0xffffffffu, incl, 31);
-    if (lane == 0) sc->pre[0] = W;  // ordered by the caller's __syncwarp
+    if (lane == 0) {  // ordered by the caller's __syncwarp
+      sc->pre[0] = W;
+      sc->fsum[0] = fx;
+      sc->fsum[1] = fy;
+    }
     return incl - v;
   }
   if (lane == 31) {
@@ -107,20 +128,23 @@ __device__ __forceinline__ long long block_scan_sums(long long v, float& fx, flo
     sc->fy[wid] = fy;
   }
   __syncthreads();
+  constexpr int WX = NW >= 2 ? 1 : 0, WY = NW >= 3 ? 2 : WX;
   if (wid == 0) {
     long long t = lane < NW ? sc->tot[lane] : 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
+    for (int o = 1; o < NW; o <<= 1) {
       const long long u = __shfl_up_sync(0xffffffffu, t, o);
       if (lane >= o) t += u;
     }
     if (lane < NW) sc->pre[lane] = t;
+  }
+  if (wid == WX) {
     const float a = warp_sum(lane < NW ? sc->fx[lane] : 0.0f);
+    if (lane == 0) sc->fsum[0] = a;
+  }
+  if (wid == WY) {
     const float b = warp_sum(lane < NW ? sc->fy[lane] : 0.0f);
-    if (lane == 0) {
-      sc->fsum[0] = a;
-      sc->fsum[1] = b;
-    }
+    if (lane == 0) sc->fsum[1] = b;
   }
   __syncthreads();
   W = sc->pre[NW - 1];
@@ -264,6 +288,7 @@ __device__ __forceinline__ void resample_map(const float (&w)[PPT], long long ex
 
 struct Shared {
   ScanScratch scan;
+  float hist[6];  // estx, esty, prev_estx, prev_esty, velx, vely of the filter
   float4 meas[kMaxAgents];  // (qx, qy, (z_target - qz)^2, r)
   float tgt[2];
   float dz2;
@@ -290,17 +315,17 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
   const int base = tid * PPT;
   const long long off = (long long)f * P;
 
-  // estimate history, fetched early so that its latency hides behind the
-  // particle loads (thread 0 writes it back before a block barrier)
-  float hist[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-  if (tid == 0 && d.prev_estx) {
-    hist[0] = d.estx[f];
-    hist[1] = d.esty[f];
-    hist[2] = d.prev_estx[f];
-    hist[3] = d.prev_esty[f];
-    if (d.velx) {
-      hist[4] = d.velx[f];
-      hist[5] = d.vely[f];
+  // estimate history: thread 0 copies it to shared memory asynchronously
+  // and shifts it after the particles are written
+  const bool has_hist = d.prev_estx != nullptr, has_vel = d.velx != nullptr;
+  if (tid == 0 && has_hist) {
+    cp_async4(&sh.hist[0], d.estx + f);
+    cp_async4(&sh.hist[1], d.esty + f);
+    cp_async4(&sh.hist[2], d.prev_estx + f);
+    cp_async4(&sh.hist[3], d.prev_esty + f);
+    if (has_vel) {
+      cp_async4(&sh.hist[4], d.velx + f);
+      cp_async4(&sh.hist[5], d.vely + f);
     }
   }
   // measurement list and the filter's header (senders are at the surface:
@@ -312,6 +337,8 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
     sh.tgt[1] = hd.y;
     sh.dz2 = hd.z;
     sh.nm = (int)hd.w;
+  }
+  if (tid == NT - 1) {  // the resampling draw, on the warp with no other extra duty
     Rand4 r = philox(d.gid_filter + (uint32_t)f, 0u, g, TAG_RESAMPLE, d.seed);
     sh.scan.u64 = (unsigned long long)r.x[0] | ((unsigned long long)r.x[1] << 32);
   }
@@ -373,32 +400,42 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
       y[qq] = fmaf(d.dt, uy, y[qq]);
     }
   }
-  // estimate history (the update's inputs), written as soon as it has arrived
-  if (tid == 0 && d.prev_estx) {
-    d.prev2_estx[f] = hist[2];
-    d.prev2_esty[f] = hist[3];
-    d.prev_estx[f] = hist[0];
-    d.prev_esty[f] = hist[1];
-    if (d.velx) {  // motion of the previous update folded into the smoothed velocity
-      d.velx[f] = fmaf(kVelKeep, hist[4], (1.0f - kVelKeep) * (hist[0] - hist[2]));
-      d.vely[f] = fmaf(kVelKeep, hist[5], (1.0f - kVelKeep) * (hist[1] - hist[3]));
-    }
-  }
   __syncthreads();  // sh.* visible
 
   // weight (log domain); measurements outer, particles inner
   const int nm = sh.nm;
   const float dz2 = sh.dz2;
   float acc[PPT];
+  {
+    // particle pairs on the packed FP32 pipe: each lane rounds like the scalar
+    // operation, in the same order; (sqrt - r)^2 equals (r - sqrt)^2 bit for
+    // bit because rounding is symmetric.  Positions live only in packed form
+    // through the loop.
+    unsigned long long X[PPT / 2], Y[PPT / 2], A[PPT / 2];
 #pragma unroll
-  for (int q = 0; q < PPT; ++q) acc[q] = 0.0f;
-  for (int m = 0; m < nm; ++m) {
-    const float4 mm = sh.meas[m];
+    for (int h = 0; h < PPT / 2; ++h) {
+      X[h] = f2pk(x[2 * h], x[2 * h + 1]);
+      Y[h] = f2pk(y[2 * h], y[2 * h + 1]);
+      A[h] = 0ull;
+    }
+    const unsigned long long DZ2 = f2pk(dz2, dz2);
+    for (int m = 0; m < nm; ++m) {
+      const float4 mm = sh.meas[m];
+      const unsigned long long MX = f2pk(-mm.x, -mm.x), MY = f2pk(-mm.y, -mm.y), NR = f2pk(-mm.w, -mm.w);
 #pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-      const float dx = x[q] - mm.x, dy = y[q] - mm.y;
-      const float res = mm.w - sqrt_approx(fmaf(dx, dx, fmaf(dy, dy, dz2)));
-      acc[q] = fmaf(res, res, acc[q]);
+      for (int h = 0; h < PPT / 2; ++h) {
+        const unsigned long long dx = f2add(X[h], MX), dy = f2add(Y[h], MY);
+        float s0, s1;
+        f2upk(f2fma(dx, dx, f2fma(dy, dy, DZ2)), s0, s1);
+        const unsigned long long res = f2add(f2pk(sqrt_approx(s0), sqrt_approx(s1)), NR);
+        A[h] = f2fma(res, res, A[h]);
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < PPT / 2; ++h) {
+      f2upk(A[h], acc[2 * h], acc[2 * h + 1]);
+      f2upk(X[h], x[2 * h], x[2 * h + 1]);
+      f2upk(Y[h], y[2 * h], y[2 * h + 1]);
     }
   }
   float lmax = -INFINITY;
@@ -432,17 +469,6 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
       }
     }
   }
-  // estimate: thread 0, from the block sums and the integer weight total
-  auto write_estimate = [&](float sx, float sy, long long Wt) {
-    if (tid == 0) {
-      const float sw = __ll2float_rn(Wt) * 0x1p-38f;
-      const float ex = sx / sw, ey = sy / sw;
-      d.estx[f] = ex;
-      d.esty[f] = ey;
-      const float dx = ex - sh.tgt[0], dy = ey - sh.tgt[1];
-      d.err[f] = sqrtf(dx * dx + dy * dy);
-    }
-  };
   // nm is the same for the whole CTA, so both branches keep their barriers
   // uniform; the particles are dead across the scan in the resampling branch
   long long W;
@@ -453,7 +479,6 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
     init_markers<PPT>(s_mark, base);
     const long long excl = block_scan_sums<NT>(qsum, swx, swy, &sh.scan, W);  // contains barriers
     if (NT == 32) __syncwarp();  // single-warp blocks: order the shared-memory stores
-    write_estimate(swx, swy, W);
     resample_map<NT, PPT, FULL>(w, excl, W, base, P, s_excl, s_w, s_mark, &sh.scan, idx);
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
@@ -465,7 +490,7 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
     }
   } else {
     block_scan_sums<NT>(qsum, swx, swy, &sh.scan, W);
-    write_estimate(swx, swy, W);
+    if (NT == 32) __syncwarp();
 #pragma unroll
     for (int q = 0; q < PPT; ++q) idx[q] = base + q;
   }
@@ -503,6 +528,29 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
         d.pvy[off + base + q] = vy[q];
       }
     }
+  }
+  // estimate (from the block sums and the integer weight total, both left in
+  // shared memory by the scan) and the history shift by one update, after
+  // the particles: no barrier waits for thread 0 here
+  if (tid == 0) {
+    if (has_hist) {
+      cp_async_wait_all();  // thread 0's own copies
+      const float* h = sh.hist;
+      d.prev2_estx[f] = h[2];
+      d.prev2_esty[f] = h[3];
+      d.prev_estx[f] = h[0];
+      d.prev_esty[f] = h[1];
+      if (has_vel) {  // motion of the previous update folded into the smoothed velocity
+        d.velx[f] = fmaf(kVelKeep, h[4], (1.0f - kVelKeep) * (h[0] - h[2]));
+        d.vely[f] = fmaf(kVelKeep, h[5], (1.0f - kVelKeep) * (h[1] - h[3]));
+      }
+    }
+    const float sw = __ll2float_rn(sh.scan.pre[NT / 32 - 1]) * 0x1p-38f;
+    const float ex = sh.scan.fsum[0] / sw, ey = sh.scan.fsum[1] / sw;
+    d.estx[f] = ex;
+    d.esty[f] = ey;
+    const float dx = ex - sh.tgt[0], dy = ey - sh.tgt[1];
+    d.err[f] = sqrtf(dx * dx + dy * dy);
   }
 }
 
