@@ -433,35 +433,47 @@ def run_ours(args):
     achieved = bytes_per_launch / (pf_avg_ms / 1e3) / 1e9
     traffic = _pf_traffic(env.pf_variant_name(), env.F * env.P)
 
-    # end to end through the C ABI with host buffers: per step, host actions
-    # (pinned) -> device, env_step, reward + done -> pinned host
+    # end to end through the C ABI, eager steps, every step's reward + done
+    # read back into pinned host memory: (1) the step as timed above (the
+    # on-device policy, or the device's random actions, picks the actions: the
+    # step has no host input); (2) a host controller's actions (pinned) copied
+    # in every step in place of the policy
     NA, E = env.NA, env.E
-    act_host = torch.from_numpy(np.random.default_rng(rank).integers(0, p.n_actions, (K, NA)).astype(np.int32))
-    act_host = act_host.pin_memory()
-    act_dev = torch.empty(NA, dtype=torch.int32, device="cuda")
     rew_host = torch.empty((K, E), dtype=torch.float32).pin_memory()
     done_host = torch.empty((K, E), dtype=torch.int32).pin_memory()
-    for _ in range(2):
-        env.step(act_dev.zero_())
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for k in range(K):
+
+    def _e2e_loop(step_fn):
+        for _ in range(2):
+            step_fn(0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(K):
+            out = step_fn(k)
+            rew_host[k].copy_(out["reward"], non_blocking=True)
+            done_host[k].copy_(out["done"], non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_ms = max(e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([t_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_ms = float(t.item())
+        return K * float(shard.reduce_sums([NA])[0]) / (t_ms / 1e3)
+
+    e2e_policy = _e2e_loop(lambda k: env.step(None))
+    act_host = torch.from_numpy(np.random.default_rng(rank).integers(0, p.n_actions, (K, NA)).astype(np.int32))
+    act_host = act_host.pin_memory()
+    act_dev = torch.zeros(NA, dtype=torch.int32, device="cuda")
+
+    def _host_actions(k):
         act_dev.copy_(act_host[k], non_blocking=True)
-        out = env.step(act_dev)
-        rew_host[k].copy_(out["reward"], non_blocking=True)
-        done_host[k].copy_(out["done"], non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = max(e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = K * float(shard.reduce_sums([NA])[0]) / (e2e_ms / 1e3)
+        return env.step(act_dev)
+
+    e2e_host = _e2e_loop(_host_actions)
 
     if rank == 0:
         line = {
@@ -481,9 +493,12 @@ def run_ours(args):
                          "timing": "CUDA events around each launch on its stream, eager replay of the K timed steps (same seed and warm-up)",
                          "peak_kind": f"{peak_kind} copy bandwidth (burst)",
                          "algorithmic_bytes_per_launch": bytes_per_launch},
-            "e2e": {"value": e2e_value, "unit": "agent-steps/s", "h2d_bytes_per_step": NA * 4,
+            "e2e": {"value": e2e_policy, "unit": "agent-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": E * 8,
-                    "note": "host-supplied actions replace the on-device policy; reward and done read back"},
+                    "note": ("eager env_step calls, the same step as the timed one (actions from the device, "
+                             "no host input), reward and done read back to pinned host memory every step"),
+                    "host_actions": {"value": e2e_host, "h2d_bytes_per_step": NA * 4, "d2h_bytes_per_step": E * 8,
+                                     "note": "a host controller's actions copied in every step in place of the policy"}},
             "gpu_launches": stats["kernel_launches"],
             "clocks": clock_info,
             "rmse_m": stats["rmse"],

@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define UT_ABI_VERSION 5u
+#define UT_ABI_VERSION 6u
 #define UT_MAX_AGENTS 8      /* per environment */
 #define UT_MAX_TARGETS 8     /* per environment */
 #define UT_MAX_PARTICLES 4096
@@ -124,6 +124,15 @@ typedef struct ut_config {
   int32_t d_model;             /* transformer agent width; 0 = no policy */
   int32_t n_layers;            /* transformer blocks */
   int32_t n_heads;             /* attention heads (d_model % n_heads == 0) */
+  /* 0: one filter per (env, agent, target) (Sec. III-A.2: every agent
+   * tracks every target itself); 1: one filter per (env, target), fed every
+   * ping of that target in the env (no communication limit), initialised
+   * around the env's first agent, its estimate used by every agent. */
+  int32_t shared_filter;
+  /* Global index of this batch's first (agent, target) pair (pings are keyed
+   * by pair); used with shared_filter = 1, where pairs and filters differ.
+   * With per-agent filters a pair is its filter and id_filter0 applies. */
+  uint32_t id_pair0;
 } ut_config;
 
 typedef struct ut_env ut_env;
@@ -163,8 +172,11 @@ typedef struct ut_state_view {
 
 /* Borrowed device views of per-step intermediates (UT_FLAG_DEBUG only). */
 typedef struct ut_debug_view {
-  float* range;        /* [F] noisy range heard by agent a of target k (0 if not heard) */
-  int32_t* valid;      /* [F] detection bit */
+  /* (agent, target) pairs: sum over envs of A_e T_e, pair a T_e + k of env e
+   * after the pairs of the earlier envs (the filter index with per-agent
+   * filters) */
+  float* range;        /* [pairs] noisy range heard by agent a of target k (0 if not heard) */
+  int32_t* valid;      /* [pairs] detection bit */
   int32_t* recv;       /* [NA * A_max] agent a received agent b */
   float* meas;         /* [F][A_max][4] (qx, qy, qz, r) measurement list of each filter */
   int32_t* meas_n;     /* [F] */

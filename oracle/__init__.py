@@ -79,6 +79,7 @@ class OcConfig(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("env0", ctypes.c_int32), ("agent0", ctypes.c_int32), ("target0", ctypes.c_int32),
         ("filter0", ctypes.c_int32), ("est_scale", ctypes.c_double),
+        ("shared_filter", ctypes.c_int32), ("pair0", ctypes.c_int32), ("pair_off", _ip),
     ]
 
 
@@ -192,10 +193,13 @@ class OracleEnv:
         self.n_agents_env, self.n_targets_env = a, t
         self.agent_off = _i32(np.concatenate([[0], np.cumsum(a)]))
         self.target_off = _i32(np.concatenate([[0], np.cumsum(t)]))
-        self.filter_off = _i32(np.concatenate([[0], np.cumsum(a * t)]))
+        shared = int(getattr(params, "shared_filter", 0))
+        self.filter_off = _i32(np.concatenate([[0], np.cumsum(t if shared else a * t)]))
+        self.pair_off = _i32(np.concatenate([[0], np.cumsum(a * t)]))
         self.NA = int(self.agent_off[-1])
         self.NT = int(self.target_off[-1])
         self.F = int(self.filter_off[-1])
+        self.NPAIR = int(self.pair_off[-1])
         P = params.n_particles
         self.cfg = OcConfig()
         c = self.cfg
@@ -203,6 +207,8 @@ class OracleEnv:
                                                                 params.max_targets, P)
         c.agent_off, c.target_off, c.filter_off = (_p(self.agent_off, _ip), _p(self.target_off, _ip),
                                                    _p(self.filter_off, _ip))
+        c.pair_off = _p(self.pair_off, _ip)
+        c.shared_filter = shared
         for name in ("dt", "agent_speed", "heading_noise", "action_mode", "n_rudder", "n_actions", "turn_angle",
                      "rudder_max", "rudder_gain", "target_model", "target_speed_min", "target_speed_max",
                      "target_drift_sigma", "target_depth_max", "range_sigma", "det_radius", "comm_radius",
@@ -212,8 +218,10 @@ class OracleEnv:
             setattr(c, name, getattr(params, name))
         c.seed = seed
         if id_base is None:  # global ids of a shard of a larger batch, else 0
-            id_base = tuple(getattr(params, k, 0) for k in ("id_env0", "id_agent0", "id_target0", "id_filter0"))
-        c.env0, c.agent0, c.target0, c.filter0 = (int(v) for v in id_base)
+            id_base = tuple(getattr(params, k, 0)
+                            for k in ("id_env0", "id_agent0", "id_target0", "id_filter0", "id_pair0"))
+        id_base = tuple(id_base) + (0,) * (5 - len(id_base))
+        c.env0, c.agent0, c.target0, c.filter0, c.pair0 = (int(v) for v in id_base)
         self.seed = seed
         AM = params.max_agents
         self.arr = {
@@ -266,7 +274,7 @@ class OracleEnv:
         without a fresh ping); ``mode=4`` selects the least-squares tracker."""
         P, AM = self.p.n_particles, self.p.max_agents
         NS = self.p.max_agents + self.p.max_targets
-        shapes = {"range": (self.F, np.float64), "valid": (self.F, np.int32),
+        shapes = {"range": (self.NPAIR, np.float64), "valid": (self.NPAIR, np.int32),
                   "recv": (self.NA * AM, np.int32), "meas": (self.F * AM * 4, np.float64),
                   "meas_n": (self.F, np.int32), "pred_px": (self.F * P, np.float64),
                   "pred_py": (self.F * P, np.float64), "pred_pvx": (self.F * P, np.float64),

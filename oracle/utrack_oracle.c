@@ -91,6 +91,15 @@ typedef struct {
    * independent environments replays exactly the draws of the full batch. */
   int32_t env0, agent0, target0, filter0;
   double est_scale; /* L: local frame of the learned estimator's features */
+  /* 0: one filter per (env, agent, target), filter a T + k of the env;
+   * 1: one filter per (env, target), filter k, fed every ping of the target
+   * and anchored at the env's first agent (reading C22). */
+  int32_t shared_filter;
+  /* Global index of the first (agent, target) pair: pings are keyed by pair
+   * (pair a T + k of env e after pair_off[e]); with per-agent filters the
+   * pairs are the filters and filter0 applies. */
+  int32_t pair0;
+  const int32_t* pair_off; /* [n_envs+1] */
 } oc_config;
 
 typedef struct {
@@ -112,8 +121,8 @@ typedef struct {
 
 /* Per-step outputs and intermediates, all optional (NULL = not wanted). */
 typedef struct {
-  double *range;          /* [F] noisy range of target k at agent a */
-  int32_t *valid;         /* [F] detection bit */
+  double *range;          /* [pairs] noisy range of target k at agent a */
+  int32_t *valid;         /* [pairs] detection bit */
   int32_t *recv;          /* [NA*A_max] a received b this step */
   double *meas;           /* [F*A_max*4] qx, qy, qz, r */
   int32_t *meas_n;        /* [F] */
@@ -199,8 +208,20 @@ static double action_dpsi(const oc_config* c, int32_t j) {
 
 static int32_t env_agents(const oc_config* c, int e) { return c->agent_off[e + 1] - c->agent_off[e]; }
 static int32_t env_targets(const oc_config* c, int e) { return c->target_off[e + 1] - c->target_off[e]; }
+/* The filter agent a of env e uses for target k. */
 static int32_t filter_index(const oc_config* c, int e, int a, int k) {
-  return c->filter_off[e] + a * env_targets(c, e) + k;
+  return c->filter_off[e] + (c->shared_filter ? k : a * env_targets(c, e) + k);
+}
+/* Filters of env e, and the anchor agent and target of its j-th filter. */
+static int32_t env_filters(const oc_config* c, int e) { return c->filter_off[e + 1] - c->filter_off[e]; }
+static int32_t filter_agent(const oc_config* c, int e, int j) { return c->shared_filter ? 0 : j / env_targets(c, e); }
+static int32_t filter_target(const oc_config* c, int e, int j) { return c->shared_filter ? j : j % env_targets(c, e); }
+/* (agent, target) pair of env e, and the global key of its pings. */
+static int32_t pair_index(const oc_config* c, int e, int a, int k) {
+  return c->pair_off[e] + a * env_targets(c, e) + k;
+}
+static uint32_t pair_key(const oc_config* c, int32_t p) {
+  return (uint32_t)((c->shared_filter ? c->pair0 : c->filter0) + p);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -282,9 +303,9 @@ void oc_reset(const oc_config* c, oc_state* s, uint32_t g) {
         s->lpage[o] = 0;
       }
     /* First ping of each filter and particle initialisation around it. */
-    for (int a = 0; a < A; ++a)
-      for (int k = 0; k < T; ++k) {
-        int f = filter_index(c, e, a, k);
+    for (int j = 0; j < env_filters(c, e); ++j) {
+        int a = filter_agent(c, e, j), k = filter_target(c, e, j);
+        int f = c->filter_off[e] + j;
         int ia = a0 + a, it = t0 + k;
         double d = true_range(s, ia, it);
         int valid = d <= c->det_radius;
@@ -414,18 +435,19 @@ void oc_move_targets(const oc_config* c, oc_state* s, uint32_t g) {
  * UTracking difficult" paragraph): a target is heard iff its 3-D distance is
  * within det_radius; the heard range carries Gaussian noise (reading C3). */
 void oc_pings(const oc_config* c, const oc_state* s, uint32_t g, double* range, int32_t* valid) {
+  /* range, valid: [pairs] */
   for (int e = 0; e < c->n_envs; ++e) {
     int A = env_agents(c, e), T = env_targets(c, e);
     for (int a = 0; a < A; ++a)
       for (int k = 0; k < T; ++k) {
-        int f = filter_index(c, e, a, k);
+        int q = pair_index(c, e, a, k);
         double d = true_range(s, c->agent_off[e] + a, c->target_off[e] + k);
         uint32_t x[4];
-        draw(c->seed, (uint32_t)(c->filter0 + f), 0, g, OC_TAG_PING, x);
+        draw(c->seed, pair_key(c, q), 0, g, OC_TAG_PING, x);
         double n0, n1;
         normal_pair(x[0], x[1], &n0, &n1);
-        valid[f] = d <= c->det_radius;
-        range[f] = valid[f] ? d + c->range_sigma * n0 : 0.0;
+        valid[q] = d <= c->det_radius;
+        range[q] = valid[q] ? d + c->range_sigma * n0 : 0.0;
       }
   }
 }
@@ -467,23 +489,42 @@ void oc_comms(const oc_config* c, oc_state* s, uint32_t g, const double* range, 
         }
         recv[(int64_t)ia * AM + b] = r;
       }
+      if (c->shared_filter) continue;
       for (int k = 0; k < T; ++k) {
         int f = filter_index(c, e, a, k);
         int n = 0;
         for (int b = 0; b < A; ++b) {
-          int fb = filter_index(c, e, b, k);
-          if (recv[(int64_t)ia * AM + b] && valid[fb]) {
+          int qb = pair_index(c, e, b, k);
+          if (recv[(int64_t)ia * AM + b] && valid[qb]) {
             double* m = meas + ((int64_t)f * AM + n) * 4;
             m[0] = s->ax[a0 + b];
             m[1] = s->ay[a0 + b];
             m[2] = 0.0;
-            m[3] = range[fb];
+            m[3] = range[qb];
             n++;
           }
         }
         meas_n[f] = n;
       }
     }
+    /* a shared filter (C22) hears every agent of the env that heard its target */
+    if (c->shared_filter)
+      for (int k = 0; k < T; ++k) {
+        int f = c->filter_off[e] + k;
+        int n = 0;
+        for (int b = 0; b < A; ++b) {
+          int qb = pair_index(c, e, b, k);
+          if (valid[qb]) {
+            double* m = meas + ((int64_t)f * AM + n) * 4;
+            m[0] = s->ax[a0 + b];
+            m[1] = s->ay[a0 + b];
+            m[2] = 0.0;
+            m[3] = range[qb];
+            n++;
+          }
+        }
+        meas_n[f] = n;
+      }
   }
 }
 
@@ -705,8 +746,12 @@ void oc_reward(const oc_config* c, const oc_state* s, const double* err, double*
     for (int k = 0; k < T; ++k) {
       if (c->reward_type == 0) {
         double ek = 0.0;
-        for (int a = 0; a < A; ++a) ek += err[filter_index(c, e, a, k)];
-        ek /= A;
+        if (c->shared_filter) { /* every agent's error is the shared filter's */
+          ek = err[filter_index(c, e, 0, k)];
+        } else {
+          for (int a = 0; a < A; ++a) ek += err[filter_index(c, e, a, k)];
+          ek /= A;
+        }
         r += oc_tracking_reward(ek, c->eps_min, c->eps_max);
       } else {
         double dk = INFINITY;
@@ -760,10 +805,9 @@ void oc_ring_append(const oc_config* c, oc_state* s, uint32_t g, const double* m
 void oc_est_features(const oc_config* c, const oc_state* s, uint32_t g, double* feat, double* label) {
   const double L = c->est_scale;
   for (int e = 0; e < c->n_envs; ++e) {
-    int A = env_agents(c, e), T = env_targets(c, e);
-    for (int a = 0; a < A; ++a)
-      for (int k = 0; k < T; ++k) {
-        int f = filter_index(c, e, a, k);
+    for (int j = 0; j < env_filters(c, e); ++j) {
+        int k = filter_target(c, e, j);
+        int f = c->filter_off[e] + j;
         int it = c->target_off[e] + k;
         double e1x = s->prev_estx[f], e1y = s->prev_esty[f];
         double* x = feat + (int64_t)f * OC_FEAT;
@@ -822,10 +866,9 @@ static void oc_learned_update(const oc_config* c, oc_state* s, uint32_t g, const
   oc_est_features(c, s, g, feat, NULL);
   oc_mlp_forward(F, mlp, feat, out, NULL);
   for (int e = 0; e < c->n_envs; ++e) {
-    int A = env_agents(c, e), T = env_targets(c, e);
-    for (int a = 0; a < A; ++a)
-      for (int k = 0; k < T; ++k) {
-        int f = filter_index(c, e, a, k);
+    for (int j = 0; j < env_filters(c, e); ++j) {
+        int k = filter_target(c, e, j);
+        int f = c->filter_off[e] + j;
         int it = c->target_off[e] + k;
         const double* x = feat + (int64_t)f * OC_FEAT;
         int fresh = x[3] == 0.0 && x[4] == 1.0;
@@ -861,10 +904,9 @@ static void oc_learned_update(const oc_config* c, oc_state* s, uint32_t g, const
 
 void oc_ls_update(const oc_config* c, oc_state* s, double* err) {
   for (int e = 0; e < c->n_envs; ++e) {
-    int A = env_agents(c, e), T = env_targets(c, e);
-    for (int a = 0; a < A; ++a)
-      for (int k = 0; k < T; ++k) {
-        int f = filter_index(c, e, a, k);
+    for (int j = 0; j < env_filters(c, e); ++j) {
+        int k = filter_target(c, e, j);
+        int f = c->filter_off[e] + j;
         int it = c->target_off[e] + k;
         double e1x = s->estx[f], e1y = s->esty[f], dz = s->tz[it];
         int n = s->ring_count[f];
@@ -917,11 +959,12 @@ void oc_ls_update(const oc_config* c, oc_state* s, double* err) {
 static void step_impl(const oc_config* c, oc_state* s, const int32_t* act, oc_step_out* o, const double* mlp,
                       int32_t mode) {
   int F = c->filter_off[c->n_envs];
+  int NPAIR = c->pair_off[c->n_envs];
   int NA = c->agent_off[c->n_envs];
   int AM = c->max_agents;
   uint32_t g = s->step + 1;
-  double* range = (double*)malloc(sizeof(double) * F);
-  int32_t* valid = (int32_t*)malloc(sizeof(int32_t) * F);
+  double* range = (double*)malloc(sizeof(double) * NPAIR);
+  int32_t* valid = (int32_t*)malloc(sizeof(int32_t) * NPAIR);
   int32_t* recv = (int32_t*)malloc(sizeof(int32_t) * (size_t)NA * AM);
   double* meas = (double*)malloc(sizeof(double) * (size_t)F * AM * 4);
   int32_t* meas_n = (int32_t*)malloc(sizeof(int32_t) * F);
@@ -942,8 +985,8 @@ static void step_impl(const oc_config* c, oc_state* s, const int32_t* act, oc_st
     oc_pf_update(c, s, g, meas, meas_n, &local);
   if (o && o->tokens) oc_obs(c, s, o->tokens);
   if (o && o->reward) oc_reward(c, s, err, o->reward, o->crash);
-  if (o && o->range) memcpy(o->range, range, sizeof(double) * F);
-  if (o && o->valid) memcpy(o->valid, valid, sizeof(int32_t) * F);
+  if (o && o->range) memcpy(o->range, range, sizeof(double) * NPAIR);
+  if (o && o->valid) memcpy(o->valid, valid, sizeof(int32_t) * NPAIR);
   if (o && o->recv) memcpy(o->recv, recv, sizeof(int32_t) * (size_t)NA * AM);
   if (o && o->meas) memcpy(o->meas, meas, sizeof(double) * (size_t)F * AM * 4);
   if (o && o->meas_n) memcpy(o->meas_n, meas_n, sizeof(int32_t) * F);

@@ -125,6 +125,8 @@ class Env:
         self.h = h
         st = self._state_view()
         self.NA, self.NT, self.F = st.n_agents, st.n_targets, st.n_filters
+        a_cnt, t_cnt = params.counts()
+        self.NPAIR = int((a_cnt.astype(np.int64) * t_cnt).sum())  # (agent, target) pairs
         self.P = params.n_particles
         self.AM = params.max_agents
         self.NS = params.max_agents + params.max_targets
@@ -352,9 +354,9 @@ class Env:
     def debug(self) -> dict:
         v = _abi.DebugView()
         _check(lib.env_debug(self.h, ctypes.byref(v)), self.h, "env_debug")
-        F, FP, NA, AM = self.F, self.F * self.P, self.NA, self.AM
+        F, FP, NA, AM, NP = self.F, self.F * self.P, self.NA, self.AM, self.NPAIR
         return {
-            "range": device_view(v.range, (F,)), "valid": device_view(v.valid, (F,), torch.int32),
+            "range": device_view(v.range, (NP,)), "valid": device_view(v.valid, (NP,), torch.int32),
             "recv": device_view(v.recv, (NA * AM,), torch.int32), "meas": device_view(v.meas, (F, AM, 4)),
             "meas_n": device_view(v.meas_n, (F,), torch.int32),
             "pred_px": device_view(v.pred_px, (FP,)), "pred_py": device_view(v.pred_py, (FP,)),

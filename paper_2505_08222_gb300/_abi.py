@@ -7,7 +7,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libutrack.so")
 
-UT_ABI_VERSION = 5
+UT_ABI_VERSION = 6
 UT_FLAG_DEBUG = 1
 UT_FLAG_RING = 2
 
@@ -47,6 +47,7 @@ CONFIG_FIELDS = [
     ("id_env0", ctypes.c_uint32), ("id_agent0", ctypes.c_uint32), ("id_target0", ctypes.c_uint32),
     ("id_filter0", ctypes.c_uint32),
     ("d_model", ctypes.c_int32), ("n_layers", ctypes.c_int32), ("n_heads", ctypes.c_int32),
+    ("shared_filter", ctypes.c_int32), ("id_pair0", ctypes.c_uint32),
 ]
 
 

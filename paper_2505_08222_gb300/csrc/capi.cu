@@ -92,6 +92,7 @@ ut_status validate(const ut_config* c, std::string& why) {
   if (!(c->feature_scale > 0.0f)) return bad("feature_scale must be > 0");
   if (!(c->est_scale > 0.0f)) return bad("est_scale must be > 0");
   if (c->reward_type != 0 && c->reward_type != 1) return bad("reward_type must be 0 or 1");
+  if (c->shared_filter != 0 && c->shared_filter != 1) return bad("shared_filter must be 0 or 1");
   if (c->d_model < 0) return bad("d_model must be >= 0");
   if (c->d_model > 0) {
     if (c->n_heads < 1 || c->d_model % c->n_heads != 0) return bad("d_model % n_heads != 0");
@@ -102,8 +103,8 @@ ut_status validate(const ut_config* c, std::string& why) {
 
 // Host copy of the per-env counts and CSR offsets.
 struct Layout {
-  std::vector<int32_t> a, t, aoff, toff, foff, fagent, ftarget;
-  int64_t NA = 0, NT = 0, F = 0;
+  std::vector<int32_t> a, t, aoff, toff, foff, poff, fagent, ftarget;
+  int64_t NA = 0, NT = 0, F = 0, NPAIR = 0;
 };
 
 ut_status make_layout(const ut_config* c, Layout& L, std::string& why) {
@@ -121,34 +122,42 @@ ut_status make_layout(const ut_config* c, Layout& L, std::string& why) {
   L.aoff.assign(E + 1, 0);
   L.toff.assign(E + 1, 0);
   L.foff.assign(E + 1, 0);
-  int64_t na = 0, nt = 0, nf = 0;
+  L.poff.assign(E + 1, 0);
+  const bool shared = c->shared_filter != 0;
+  int64_t na = 0, nt = 0, nf = 0, np = 0;
   for (int e = 0; e < E; ++e) {
     L.aoff[e] = (int32_t)na;
     L.toff[e] = (int32_t)nt;
     L.foff[e] = (int32_t)nf;
+    L.poff[e] = (int32_t)np;
     na += L.a[e];
     nt += L.t[e];
-    nf += (int64_t)L.a[e] * L.t[e];
+    np += (int64_t)L.a[e] * L.t[e];
+    nf += shared ? L.t[e] : (int64_t)L.a[e] * L.t[e];
   }
-  if (nf >= (1ll << 31) - 1) {
+  if (np >= (1ll << 31) - 1) {
     why = "too many filters";
     return UT_ERR_INVALID;
   }
   L.aoff[E] = (int32_t)na;
   L.toff[E] = (int32_t)nt;
   L.foff[E] = (int32_t)nf;
+  L.poff[E] = (int32_t)np;
   L.NA = na;
   L.NT = nt;
   L.F = nf;
+  L.NPAIR = np;
   L.fagent.resize(nf);
   L.ftarget.resize(nf);
-  for (int e = 0; e < E; ++e)
-    for (int a = 0; a < L.a[e]; ++a)
-      for (int k = 0; k < L.t[e]; ++k) {
-        const int64_t f = L.foff[e] + (int64_t)a * L.t[e] + k;
-        L.fagent[f] = L.aoff[e] + a;
-        L.ftarget[f] = L.toff[e] + k;
-      }
+  for (int e = 0; e < E; ++e) {
+    const int nfe = L.foff[e + 1] - L.foff[e];
+    for (int j = 0; j < nfe; ++j) {
+      const int64_t f = L.foff[e] + j;
+      // per agent: filter j = a T + k; shared: filter j = k, anchored at agent 0
+      L.fagent[f] = L.aoff[e] + (shared ? 0 : j / L.t[e]);
+      L.ftarget[f] = L.toff[e] + (shared ? j : j % L.t[e]);
+    }
+  }
   return UT_OK;
 }
 
@@ -243,6 +252,10 @@ ut_status env_create(const ut_config* cfg, const ut_allocator* allocator, void* 
   d.gid_agent = cfg->id_agent0;
   d.gid_target = cfg->id_target0;
   d.gid_filter = cfg->id_filter0;
+  // pings are keyed by (agent, target) pair: per-agent filters are their pairs
+  d.gid_pair = cfg->shared_filter ? cfg->id_pair0 : cfg->id_filter0;
+  d.shared_filter = cfg->shared_filter ? 1 : 0;
+  d.NPAIR = (int)L.NPAIR;
   d.est_scale = cfg->est_scale;
   d.ring_on = (cfg->flags & UT_FLAG_RING) ? 1 : 0;
   d.debug_on = (cfg->flags & UT_FLAG_DEBUG) ? 1 : 0;
@@ -252,6 +265,8 @@ ut_status env_create(const ut_config* cfg, const ut_allocator* allocator, void* 
   int32_t* aoff = alloc_n<int32_t>(h, E + 1, ok);
   int32_t* toff = alloc_n<int32_t>(h, E + 1, ok);
   int32_t* foff = alloc_n<int32_t>(h, E + 1, ok);
+  int32_t* poff = alloc_n<int32_t>(h, E + 1, ok);
+  const size_t NPAIR = L.NPAIR;
   int32_t* fag = alloc_n<int32_t>(h, F, ok);
   int32_t* ftg = alloc_n<int32_t>(h, F, ok);
   d.ax = alloc_n<float>(h, NA, ok);
@@ -295,8 +310,8 @@ ut_status env_create(const ut_config* cfg, const ut_allocator* allocator, void* 
   d.metrics_u = alloc_n<unsigned long long>(h, 4, ok);
   d.status = alloc_n<int>(h, 1, ok);
   if (d.debug_on) {
-    d.range = alloc_n<float>(h, F, ok);
-    d.valid = alloc_n<int32_t>(h, F, ok);
+    d.range = alloc_n<float>(h, NPAIR, ok);
+    d.valid = alloc_n<int32_t>(h, NPAIR, ok);
     d.recv = alloc_n<int32_t>(h, NA * AM, ok);
     d.dbg_px = alloc_n<float>(h, FP, ok);
     d.dbg_py = alloc_n<float>(h, FP, ok);
@@ -315,12 +330,14 @@ ut_status env_create(const ut_config* cfg, const ut_allocator* allocator, void* 
   d.agent_off = aoff;
   d.target_off = toff;
   d.filter_off = foff;
+  d.pair_off = poff;
   d.filt_agent = fag;
   d.filt_target = ftg;
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMemcpyAsync(aoff, L.aoff.data(), (E + 1) * 4, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(toff, L.toff.data(), (E + 1) * 4, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(foff, L.foff.data(), (E + 1) * 4, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(poff, L.poff.data(), (E + 1) * 4, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess && F) e = cudaMemcpyAsync(fag, L.fagent.data(), F * 4, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess && F) e = cudaMemcpyAsync(ftg, L.ftarget.data(), F * 4, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

@@ -18,11 +18,14 @@ struct EnvDev {
   const int32_t* agent_off;   // [E+1]
   const int32_t* target_off;  // [E+1]
   const int32_t* filter_off;  // [E+1]
-  const int32_t* filt_agent;  // [F] global agent index of filter f
+  const int32_t* pair_off;    // [E+1] first (agent, target) pair of each env (= filter_off per agent)
+  int shared_filter;          // 1: one filter per (env, target), filter_off[e] + k
+  int NPAIR;                  // sum of A_e T_e
+  const int32_t* filt_agent;  // [F] global agent index of filter f (the env's first agent if shared)
   const int32_t* filt_target; // [F] global target index of filter f
   // constants
   uint64_t seed;
-  uint32_t gid_env, gid_agent, gid_target, gid_filter;  // global id offsets
+  uint32_t gid_env, gid_agent, gid_target, gid_filter, gid_pair;  // global id offsets
   float dt, agent_speed, heading_noise;
   float dpsi[8];              // heading change of each action (action_mode 2: of each rudder position)
   int rudder_mode;            // action_mode 2: actions move the rudder position

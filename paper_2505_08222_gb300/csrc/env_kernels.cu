@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) step_env_kernel(EnvDev d,
   const uint32_t g = d.counters[0] + 1u;
   const int a0 = d.agent_off[e], A = d.agent_off[e + 1] - a0;
   const int t0 = d.target_off[e], T = d.target_off[e + 1] - t0;
-  const int f0 = d.filter_off[e];
+  const int f0 = d.filter_off[e], q0 = d.pair_off[e];
 
   if (lane < A) {
     const int i = a0 + lane;
@@ -228,12 +228,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) step_env_kernel(EnvDev d,
   }
   __syncwarp();
 
-  // pings: filter index f = f0 + a * T + k
+  // pings of pair p = a * T + k (pair index q0 + p; the filter index with
+  // per-agent filters)
   for (int p = lane; p < A * T; p += 32) {
     const int a = p / T, k = p - a * T;
     const float dx = s_ax[wid][a] - s_tx[wid][k], dy = s_ay[wid][a] - s_ty[wid][k], dz = 0.0f - s_tz[wid][k];
     const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
-    Rand4 r = philox(d.gid_filter + (uint32_t)(f0 + p), 0u, g, TAG_PING, d.seed);
+    Rand4 r = philox(d.gid_pair + (uint32_t)(q0 + p), 0u, g, TAG_PING, d.seed);
     float n0, n1;
     box_muller(r.x[0], r.x[1], n0, n1);
     const int v = dist <= d.det_radius;
@@ -241,8 +242,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) step_env_kernel(EnvDev d,
     s_rng[wid][p] = rg;
     s_valid[wid][p] = v;
     if (d.debug_on) {
-      d.range[f0 + p] = rg;
-      d.valid[f0 + p] = v;
+      d.range[q0 + p] = rg;
+      d.valid[q0 + p] = v;
     }
   }
   // communication: agent a hears agent b
@@ -272,9 +273,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) step_env_kernel(EnvDev d,
   }
   __syncwarp();
 
-  // measurement list of each filter: received senders that heard target k
-  for (int p = lane; p < A * T; p += 32) {
-    const int a = p / T, k = p - a * T;
+  // measurement list of each filter: the received senders that heard target
+  // k (per-agent filter a T + k), or every agent that heard k (shared filter k)
+  const int nfe = d.shared_filter ? T : A * T;
+  for (int p = lane; p < nfe; p += 32) {
+    const int a = d.shared_filter ? 0 : p / T, k = d.shared_filter ? p : p - a * T;
     const int f = f0 + p;
     int n = 0;
     int head = 0, cnt = 0;
@@ -283,7 +286,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) step_env_kernel(EnvDev d,
       cnt = d.ring_count[f];
     }
     for (int b = 0; b < A; ++b) {
-      if (s_recv[wid][a * kMaxAgents + b] && s_valid[wid][b * T + k]) {
+      if ((d.shared_filter || s_recv[wid][a * kMaxAgents + b]) && s_valid[wid][b * T + k]) {
         const float qx = s_ax[wid][b], qy = s_ay[wid][b], r = s_rng[wid][b * T + k];
         d.meas[(long long)f * d.AM + n] = make_float4(qx, qy, 0.0f, r);
         ++n;
@@ -346,7 +349,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) obs_reward_kernel(EnvDev 
         v[7] = (float)(age < 16 ? age : 16) / 16.0f;
       } else if (slot < A + T) {
         const int k = slot - A;
-        const int f = f0 + a * T + k;
+        const int f = f0 + (d.shared_filter ? k : a * T + k);
         v[0] = (d.estx[f] - d.ax[ia]) / d.S;
         v[1] = (d.esty[f] - d.ay[ia]) / d.S;
         v[2] = d.tz[t0 + k] / d.S;
@@ -364,9 +367,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) obs_reward_kernel(EnvDev 
       if (lane < T) {
         const int k = lane;
         if (d.reward_type == 0) {
+          // agent-averaged error; a shared filter's error is every agent's
           float ek = 0.0f;
-          for (int a = 0; a < A; ++a) ek += d.err[f0 + a * T + k];
-          rk = tracking_reward(ek / (float)A, d.eps_min, d.eps_max);
+          if (d.shared_filter) {
+            ek = d.err[f0 + k];
+          } else {
+            for (int a = 0; a < A; ++a) ek += d.err[f0 + a * T + k];
+            ek /= (float)A;
+          }
+          rk = tracking_reward(ek, d.eps_min, d.eps_max);
         } else {
           float dk = INFINITY;
           for (int a = 0; a < A; ++a) {
@@ -387,7 +396,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) obs_reward_kernel(EnvDev 
       }
       cr = __any_sync(0xffffffffu, cr);
       double se = 0.0;
-      for (int p = lane; p < A * T; p += 32) {
+      const int nfe = d.filter_off[e + 1] - f0;
+      for (int p = lane; p < nfe; p += 32) {
         const double v = (double)d.err[f0 + p];
         se += v * v;
       }
@@ -400,7 +410,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) obs_reward_kernel(EnvDev 
       }
       sq = se;
       rw = (double)r;
-      n_err = (unsigned long long)(A * T);
+      n_err = (unsigned long long)nfe;
       n_crash = (unsigned long long)cr;
       n_agents = (unsigned long long)A;
     } else if (lane == 0) {

@@ -31,12 +31,17 @@ def _counts(params) -> Tuple[np.ndarray, np.ndarray]:
     return a, t
 
 
+def _filters(params, a, t) -> np.ndarray:
+    """Filters of each env: A_e T_e per-agent filters, or T_e shared ones."""
+    return t.copy() if getattr(params, "shared_filter", 0) else a * t
+
+
 def env_cost(params) -> np.ndarray:
     """Relative work of each env in one step: the particle filters dominate
-    (A_e * T_e filters of P particles), the agents' policy rows and kinematics
-    add a term per agent."""
+    (A_e T_e filters of P particles, T_e when shared), the agents' policy
+    rows and kinematics add a term per agent."""
     a, t = _counts(params)
-    return a * t * int(params.n_particles) + a * 64
+    return _filters(params, a, t) * int(params.n_particles) + a * 64
 
 
 def shard_bounds(params, world_size: int) -> List[Tuple[int, int]]:
@@ -69,8 +74,9 @@ def shard_bounds(params, world_size: int) -> List[Tuple[int, int]]:
 
 def shard_params(params, rank: int, world_size: int):
     """The parameters of rank ``rank``'s shard: its env count, its slice of a
-    ragged fleet and the global ids of its first env, agent, target and
-    filter (added to any offsets ``params`` already carries)."""
+    ragged fleet and the global ids of its first env, agent, target, filter
+    and (agent, target) pair (added to any offsets ``params`` already
+    carries)."""
     a, t = _counts(params)
     e0, e1 = shard_bounds(params, world_size)[rank]
     ragged = params.agents_per_env is not None or params.targets_per_env is not None
@@ -79,7 +85,8 @@ def shard_params(params, rank: int, world_size: int):
         id_env0=int(getattr(params, "id_env0", 0)) + e0,
         id_agent0=int(getattr(params, "id_agent0", 0)) + int(a[:e0].sum()),
         id_target0=int(getattr(params, "id_target0", 0)) + int(t[:e0].sum()),
-        id_filter0=int(getattr(params, "id_filter0", 0)) + int((a[:e0] * t[:e0]).sum()),
+        id_filter0=int(getattr(params, "id_filter0", 0)) + int(_filters(params, a[:e0], t[:e0]).sum()),
+        id_pair0=int(getattr(params, "id_pair0", 0)) + int((a[:e0] * t[:e0]).sum()),
     )
     if ragged:
         kw["agents_per_env"] = a[e0:e1].astype(np.int32)

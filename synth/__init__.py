@@ -82,6 +82,10 @@ class EnvParams:
     d_model: int = 0
     n_layers: int = 0
     n_heads: int = 0
+    # 1: one filter per (env, target) fed every ping of the target (C1's
+    # alternative); 0: one filter per (env, agent, target)
+    shared_filter: int = 0
+    id_pair0: int = 0  # global id of the first (agent, target) pair (sharded, shared filters)
 
     def counts(self):
         a = (np.full(self.n_envs, self.max_agents, np.int32) if self.agents_per_env is None

@@ -83,9 +83,10 @@ def test_resample_indices_bit_exact(P):
 
 
 # ---------------------------------------------------------------- reset
-@pytest.mark.parametrize("name,n_envs,P", [("small", 8, 1000), ("fleet5", 6, 256), ("ragged", 12, 100)])
-def test_reset_parity(name, n_envs, P):
-    p = preset(name, n_envs=n_envs).replace(n_particles=P)
+@pytest.mark.parametrize("name,n_envs,P,kw", [("small", 8, 1000, {}), ("fleet5", 6, 256, {}), ("ragged", 12, 100, {}),
+                                             ("fleet5", 6, 256, {"shared_filter": 1})])
+def test_reset_parity(name, n_envs, P, kw):
+    p = preset(name, n_envs=n_envs).replace(n_particles=P, **kw)
     env, o = _pair(p, seed=7)
     g = gpu_state(env)
     # spawn lies on a 2^-16 m lattice: bit-exact
@@ -182,7 +183,9 @@ def _compare_step(env, o, actions, check_tokens=True):
     ("fleet5", 4, 13, {"comm_drop": 0.3, "comm_radius": 300.0, "target_depth_max": 50.0}),
     ("fleet5", 4, 512, {"det_radius": 60.0}),
     ("fleet5", 6, 256, {"action_mode": 2, "n_rudder": 5, "n_actions": 3}),
+    ("fleet5", 6, 512, {"shared_filter": 1, "comm_drop": 0.3}),
     ("ragged", 24, 100, {}),
+    ("ragged", 16, 100, {"shared_filter": 1}),
     ("large", 2, 512, {}),
 ])
 def test_step_parity_from_injected_state(name, n_envs, P, kw):
@@ -199,9 +202,10 @@ def test_step_parity_from_injected_state(name, n_envs, P, kw):
 
 
 # ---------------------------------------------------------------- whole rollouts
-@pytest.mark.parametrize("name,n_envs,T,P", [("small", 1024, 200, 1000), ("fleet5", 64, 100, 2048),
-                                           ("ragged", 96, 60, 1024)])
-def test_rollout_rmse_matches_oracle(name, n_envs, T, P):
+@pytest.mark.parametrize("name,n_envs,T,P,kw", [("small", 1024, 200, 1000, {}), ("fleet5", 64, 100, 2048, {}),
+                                              ("ragged", 96, 60, 1024, {}),
+                                              ("fleet5", 256, 100, 1024, {"shared_filter": 1})])
+def test_rollout_rmse_matches_oracle(name, n_envs, T, P, kw):
     """Mean tracking RMSE of whole rollouts agrees within 2% (north-star
     bound).  'Mean tracking RMSE' = mean over filters of each filter's RMSE
     over the rollout.  Both sides draw the same random numbers, but float32
@@ -209,7 +213,7 @@ def test_rollout_rmse_matches_oracle(name, n_envs, T, P):
     CDF step now and then, after which the two filters are different (equally
     valid) realisations; a single agent's range-only posterior is bimodal, so
     the statistic needs about a thousand environments to settle within 2%."""
-    p = preset(name, n_envs=n_envs).replace(n_particles=P, d_model=0)
+    p = preset(name, n_envs=n_envs).replace(n_particles=P, d_model=0, **kw)
     env = ut.Env(p)
     env.reset(0)
     se_g = torch.zeros(env.F, dtype=torch.float64, device="cuda")

@@ -44,9 +44,10 @@ def _roll(env, steps, learned):
     return {k: st[k].clone() for k in KEYS}, torch.stack(rew)
 
 
-@pytest.mark.parametrize("kind,world,learned", [("fleet5", 3, False), ("ragged", 2, False), ("fleet5", 2, True)])
-def test_shards_reproduce_whole_batch(kind, world, learned):
-    p = preset(kind, n_envs=37, seed=4).replace(n_particles=256)
+@pytest.mark.parametrize("kind,world,learned,kw", [("fleet5", 3, False, {}), ("ragged", 2, False, {}),
+                                                  ("fleet5", 2, True, {}), ("ragged", 3, False, {"shared_filter": 1})])
+def test_shards_reproduce_whole_batch(kind, world, learned, kw):
+    p = preset(kind, n_envs=37, seed=4).replace(n_particles=256, **kw)
     env = _make(p, learned)
     v = env.pf_variant()
     whole, rew = _roll(env, 8, learned)

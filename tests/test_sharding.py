@@ -21,6 +21,8 @@ SEED = 17
 def _params(kind):
     if kind == "uniform":
         return preset("fleet5", n_envs=5).replace(n_particles=64, d_model=0)
+    if kind == "shared":  # one filter per (env, target), ragged counts
+        return preset("ragged", n_envs=7, seed=4).replace(n_particles=32, d_model=0, shared_filter=1)
     return preset("ragged", n_envs=7, seed=3).replace(n_particles=32, d_model=0)
 
 
@@ -60,7 +62,7 @@ def _worker(rank, world, port, kind, outdir):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("kind", ["uniform", "ragged"])
+@pytest.mark.parametrize("kind", ["uniform", "ragged", "shared"])
 def test_two_rank_shards_reproduce_whole_batch(kind):
     p = _params(kind)
     err_all, rew_all = _run(p)
@@ -97,4 +99,9 @@ def test_shard_ids_are_prefix_sums():
         e0 = sp.id_env0
         assert sp.id_agent0 == a[:e0].sum() and sp.id_target0 == t[:e0].sum()
         assert sp.id_filter0 == (a[:e0].astype(np.int64) * t[:e0]).sum()
+        assert sp.id_pair0 == (a[:e0].astype(np.int64) * t[:e0]).sum()
         np.testing.assert_array_equal(sp.agents_per_env, a[e0:e0 + sp.n_envs])
+        # shared filters: one per target (the cost, hence the bounds, change)
+        ss = shard.shard_params(p.replace(shared_filter=1), rank, 4)
+        s0 = ss.id_env0
+        assert ss.id_filter0 == t[:s0].sum() and ss.id_pair0 == (a[:s0].astype(np.int64) * t[:s0]).sum()
