@@ -297,6 +297,53 @@ def learned_form(args, p, K, W, rank):
                       "loss_last_per_round": losses, "train_ms": train_ms, "loss": "Huber, delta = 1 L"}}
 
 
+def shared_form(args, p, K, W, rank, env_main):
+    """The shared-filter form of the same workload: one filter per (env,
+    target) fed every ping of the target, its estimate used by every agent.
+    Timed like the main line (one graph of K steps after W warm-up steps);
+    pooled RMSE against the per-agent filters on the held-out seeds."""
+    import torch
+
+    import paper_2505_08222_gb300 as ut
+    import synth
+
+    T_eval = args.eval_steps
+    seeds = [9000 + rank, 9100 + rank]
+    ps = p.replace(shared_filter=1)
+    env = ut.Env(ps)
+    if p.d_model:
+        env.set_policy(synth.policy_params(synth.PolicyDims(p.d_model, p.n_layers, p.n_heads, p.n_actions)))
+    if env_main.pf_variant() in env.pf_variants():
+        env.set_pf_variant(env_main.pf_variant())
+
+    def rmse(e, seed):
+        e.reset(seed)
+        return e.rollout(T_eval)["rmse"]
+
+    sh = [rmse(env, s) for s in seeds]
+    pa = [rmse(env_main, s) for s in seeds]
+    env.reset(1000 + rank)
+    for _ in range(W):
+        env.step()
+    env.rollout_prepare(K)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    st = env.rollout(K)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    F = env.F
+    env.close()
+    sh_mean, pa_mean = sum(sh) / len(sh), sum(pa) / len(pa)
+    return {"value": st["agent_steps"] / (ms / 1e3), "unit": "agent-steps/s", "ms_per_step": ms / K,
+            "filters_per_gpu": F, "rmse_m": sh_mean, "per_agent_rmse_m": pa_mean, "rmse_ratio": sh_mean / pa_mean,
+            "eval": f"{len(seeds)} held-out seeds x {T_eval} steps, pooled RMSE per run, mean over seeds",
+            "tracker": "one particle filter per (env, target), every ping of the target (shared_filter 1)"}
+
+
 def run_reference(args):
     world, rank, _ = _dist_env()
     if rank != 0:
@@ -433,17 +480,19 @@ def run_ours(args):
     achieved = bytes_per_launch / (pf_avg_ms / 1e3) / 1e9
     traffic = _pf_traffic(env.pf_variant_name(), env.F * env.P)
 
-    # end to end through the C ABI, eager steps, every step's reward + done
-    # read back into pinned host memory: (1) the step as timed above (the
-    # on-device policy, or the device's random actions, picks the actions: the
-    # step has no host input); (2) a host controller's actions (pinned) copied
-    # in every step in place of the policy
+    # end to end through the C ABI, eager steps from the timed region's start,
+    # every step's reward + done read back into pinned host memory: (1) the
+    # step as timed above (the on-device policy, or the device's random
+    # actions, picks the actions: the step has no host input); (2) a host
+    # controller's actions (pinned) copied in every step in place of the policy
     NA, E = env.NA, env.E
     rew_host = torch.empty((K, E), dtype=torch.float32).pin_memory()
     done_host = torch.empty((K, E), dtype=torch.int32).pin_memory()
 
     def _e2e_loop(step_fn):
-        for _ in range(2):
+        # the same episode steps as the timed region: same seed, W warm-up steps
+        env.reset(1000)
+        for _ in range(W):
             step_fn(0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -505,6 +554,8 @@ def run_ours(args):
         }
         if not args.no_learned:
             line["learned"] = learned_form(args, p, K, W, rank)
+        if not args.no_shared:
+            line["shared_filter"] = shared_form(args, p, K, W, rank, env)
         if world == 1 and not args.no_cpu_baseline:
             os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
             line["cpu_baseline"] = cpu_baseline(args.workload)
@@ -527,6 +578,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--pf-variant", default=None, help="fixed filter launch variant (e.g. nt512x4m3), no autotune")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-estimator form")
+    ap.add_argument("--no-shared", action="store_true", help="skip the shared-filter form")
     ap.add_argument("--train-rows", type=int, default=20_000_000)
     ap.add_argument("--train-steps", type=int, default=3000, help="Adam steps on the filter-driven rows")
     ap.add_argument("--round-steps", type=int, default=800, help="Adam steps after each DAgger round")
