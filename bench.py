@@ -297,11 +297,13 @@ def learned_form(args, p, K, W, rank):
                       "loss_last_per_round": losses, "train_ms": train_ms, "loss": "Huber, delta = 1 L"}}
 
 
-def shared_form(args, p, K, W, rank, env_main):
-    """The shared-filter form of the same workload: one filter per (env,
-    target) fed every ping of the target, its estimate used by every agent.
-    Timed like the main line (one graph of K steps after W warm-up steps);
-    pooled RMSE against the per-agent filters on the held-out seeds."""
+def variant_form(args, p, K, W, rank, env_main, tracker, **kw):
+    """A tracker variant of the same workload (``kw`` replaces parameters:
+    shared_filter=1, one filter per (env, target) fed every ping of the
+    target; pf_ess_num=k, resampling only when the effective sample size
+    falls below k/16 of P).  Timed like the main line (one graph of K steps
+    after W warm-up steps); pooled RMSE against the main form on the
+    held-out seeds."""
     import torch
 
     import paper_2505_08222_gb300 as ut
@@ -309,7 +311,7 @@ def shared_form(args, p, K, W, rank, env_main):
 
     T_eval = args.eval_steps
     seeds = [9000 + rank, 9100 + rank]
-    ps = p.replace(shared_filter=1)
+    ps = p.replace(**kw)
     env = ut.Env(ps)
     if p.d_model:
         env.set_policy(synth.policy_params(synth.PolicyDims(p.d_model, p.n_layers, p.n_heads, p.n_actions)))
@@ -339,9 +341,9 @@ def shared_form(args, p, K, W, rank, env_main):
     env.close()
     sh_mean, pa_mean = sum(sh) / len(sh), sum(pa) / len(pa)
     return {"value": st["agent_steps"] / (ms / 1e3), "unit": "agent-steps/s", "ms_per_step": ms / K,
-            "filters_per_gpu": F, "rmse_m": sh_mean, "per_agent_rmse_m": pa_mean, "rmse_ratio": sh_mean / pa_mean,
+            "filters_per_gpu": F, "rmse_m": sh_mean, "main_form_rmse_m": pa_mean, "rmse_ratio": sh_mean / pa_mean,
             "eval": f"{len(seeds)} held-out seeds x {T_eval} steps, pooled RMSE per run, mean over seeds",
-            "tracker": "one particle filter per (env, target), every ping of the target (shared_filter 1)"}
+            "tracker": tracker}
 
 
 def run_reference(args):
@@ -555,7 +557,12 @@ def run_ours(args):
         if not args.no_learned:
             line["learned"] = learned_form(args, p, K, W, rank)
         if not args.no_shared:
-            line["shared_filter"] = shared_form(args, p, K, W, rank, env)
+            line["shared_filter"] = variant_form(
+                args, p, K, W, rank, env, "one particle filter per (env, target), every ping of the target "
+                "(shared_filter 1)", shared_filter=1)
+            line["ess_resampling"] = variant_form(
+                args, p, K, W, rank, env, "per-agent filters, weights carried across steps, resampling when "
+                "the effective sample size < P/2 (pf_ess_num 8)", pf_ess_num=8)
         if world == 1 and not args.no_cpu_baseline:
             os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
             line["cpu_baseline"] = cpu_baseline(args.workload)
@@ -578,7 +585,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--pf-variant", default=None, help="fixed filter launch variant (e.g. nt512x4m3), no autotune")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-estimator form")
-    ap.add_argument("--no-shared", action="store_true", help="skip the shared-filter form")
+    ap.add_argument("--no-shared", action="store_true", help="skip the shared-filter and ESS-resampling forms")
     ap.add_argument("--train-rows", type=int, default=20_000_000)
     ap.add_argument("--train-steps", type=int, default=3000, help="Adam steps on the filter-driven rows")
     ap.add_argument("--round-steps", type=int, default=800, help="Adam steps after each DAgger round")

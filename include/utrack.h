@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define UT_ABI_VERSION 6u
+#define UT_ABI_VERSION 7u
 #define UT_MAX_AGENTS 8      /* per environment */
 #define UT_MAX_TARGETS 8     /* per environment */
 #define UT_MAX_PARTICLES 4096
@@ -133,6 +133,13 @@ typedef struct ut_config {
    * by pair); used with shared_filter = 1, where pairs and filters differ.
    * With per-agent filters a pair is its filter and id_filter0 applies. */
   uint32_t id_pair0;
+  /* Resampling trigger: 0 resamples every step with a measurement (the
+   * paper's filter); k in 1..16 carries the weights across steps as
+   * per-particle log-weights and resamples only when the effective sample
+   * size falls below k/16 of P.  The decision is exact integer arithmetic on
+   * the max-normalised weights quantised to 15 bits, r = floor(w 2^15):
+   * resample iff 16 (sum r)^2 < k P sum r^2. */
+  int32_t pf_ess_num;
 } ut_config;
 
 typedef struct ut_env ut_env;
@@ -165,6 +172,8 @@ typedef struct ut_state_view {
   float* ring;                        /* estimator ring [F][16][4] (qx, qy, r, step) */
   int32_t *ring_head, *ring_count;    /* [F] */
   uint16_t* h;                        /* recurrent token bf16 [NA][d_model] (NULL without policy) */
+  float* pw;                          /* particle log-weights [F * P], log w - max log w, 0 after a
+                                         resample (NULL unless pf_ess_num > 0) */
   uint32_t step;                      /* global step counter g (random-stream position) */
   int32_t t_ep;                       /* steps since the last reset */
   int64_t n_agents, n_targets, n_filters; /* sizes, filled by env_get_state */

@@ -80,6 +80,7 @@ class OcConfig(ctypes.Structure):
         ("env0", ctypes.c_int32), ("agent0", ctypes.c_int32), ("target0", ctypes.c_int32),
         ("filter0", ctypes.c_int32), ("est_scale", ctypes.c_double),
         ("shared_filter", ctypes.c_int32), ("pair0", ctypes.c_int32), ("pair_off", _ip),
+        ("pf_ess_num", ctypes.c_int32),
     ]
 
 
@@ -89,7 +90,7 @@ class OcState(ctypes.Structure):
         ("lpage", _ip), ("estx", _dp), ("esty", _dp), ("prev_estx", _dp), ("prev_esty", _dp),
         ("prev2_estx", _dp), ("prev2_esty", _dp), ("velx", _dp), ("vely", _dp), ("rudder", _ip), ("ring", _dp),
         ("ring_head", _ip),
-        ("ring_count", _ip), ("step", ctypes.c_uint32), ("t_ep", ctypes.c_int32)]
+        ("ring_count", _ip), ("step", ctypes.c_uint32), ("t_ep", ctypes.c_int32), ("pw", _dp)]
 
 
 _OUT_FIELDS = [("range", _dp), ("valid", _ip), ("recv", _ip), ("meas", _dp), ("meas_n", _ip),
@@ -239,6 +240,9 @@ class OracleEnv:
             "ring": np.zeros(self.F * RING * 4), "ring_head": np.zeros(self.F, np.int32),
             "ring_count": np.zeros(self.F, np.int32),
         }
+        c.pf_ess_num = int(getattr(params, "pf_ess_num", 0))
+        if c.pf_ess_num > 0:  # carried particle log-weights
+            self.arr["pw"] = np.zeros(self.F * P)
         self.st = OcState()
         self._bind()
 

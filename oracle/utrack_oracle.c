@@ -100,6 +100,10 @@ typedef struct {
    * pairs are the filters and filter0 applies. */
   int32_t pair0;
   const int32_t* pair_off; /* [n_envs+1] */
+  /* Resampling trigger (reading C23): 0 resamples every step with a
+   * measurement; k in 1..16 carries log-weights across steps and resamples
+   * iff 16 (sum r)^2 < k P sum r^2, r = floor(w 2^38) >> 23. */
+  int32_t pf_ess_num;
 } oc_config;
 
 typedef struct {
@@ -117,6 +121,7 @@ typedef struct {
   int32_t *ring_head, *ring_count;          /* [F] */
   uint32_t step;                            /* global step counter g */
   int32_t t_ep;                             /* steps since reset */
+  double *pw;                               /* particle log-weights [F*P] (pf_ess_num > 0) */
 } oc_state;
 
 /* Per-step outputs and intermediates, all optional (NULL = not wanted). */
@@ -336,6 +341,7 @@ void oc_reset(const oc_config* c, oc_state* s, uint32_t g) {
           s->py[o] = s->ay[ia] + rho * sin(phi);
           s->pvx[o] = spd * cos(chi);
           s->pvy[o] = spd * sin(chi);
+          if (s->pw) s->pw[o] = 0.0; /* equal weights */
           sx += s->px[o];
           sy += s->py[o];
         }
@@ -617,13 +623,29 @@ void oc_pf_update(const oc_config* c, oc_state* s, uint32_t g, const double* mea
         double res = m[j * 4 + 3] - sqrt(dx * dx + dy * dy + dz * dz);
         acc += res * res;
       }
-      l[i] = -acc / (2.0 * c->range_sigma * c->range_sigma);
+      /* log-likelihood, plus the carried log-weight when resampling is
+       * triggered by the effective sample size (reading C23) */
+      l[i] = (c->pf_ess_num > 0 ? s->pw[(int64_t)f * P + i] : 0.0) - acc / (2.0 * c->range_sigma * c->range_sigma);
       if (l[i] > lmax) lmax = l[i];
     }
     double W = 0.0;
     for (int i = 0; i < P; ++i) {
       w[i] = exp(l[i] - lmax);
       W += w[i];
+    }
+    /* resample every step with a measurement, or (C23) only when
+     * 16 (sum r)^2 < k P sum r^2 with r = floor(w 2^38) >> 23; the carried
+     * log-weights become 0 after a resample, l - max l otherwise */
+    int resample = nm > 0;
+    if (c->pf_ess_num > 0) {
+      uint64_t s1 = 0, s2 = 0;
+      for (int i = 0; i < P; ++i) {
+        uint64_t r = (uint64_t)(int64_t)floor(w[i] * 274877906944.0) >> 23;
+        s1 += r;
+        s2 += r * r;
+      }
+      resample = resample && 16u * s1 * s1 < (uint64_t)c->pf_ess_num * (uint64_t)P * s2;
+      for (int i = 0; i < P; ++i) s->pw[(int64_t)f * P + i] = resample ? 0.0 : l[i] - lmax;
     }
     /* estimate (weighted mean; uniform weights when nothing was heard) */
     double ex = 0.0, ey = 0.0;
@@ -656,7 +678,7 @@ void oc_pf_update(const oc_config* c, oc_state* s, uint32_t g, const double* mea
     if (o && o->wmax)
       for (int i = 0; i < P; ++i) o->wmax[(int64_t)f * P + i] = w[i];
     /* resample */
-    if (nm > 0) {
+    if (resample) {
       uint32_t r[4];
       draw(c->seed, (uint32_t)(c->filter0 + f), 0, g, OC_TAG_RESAMPLE, r);
       uint64_t u64 = (uint64_t)r[0] | ((uint64_t)r[1] << 32);

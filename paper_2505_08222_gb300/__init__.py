@@ -325,7 +325,7 @@ class Env:
                   "lpx": (NA * AM,), "lpy": (NA * AM,), "lpage": (NA * AM,), "estx": (F,), "esty": (F,),
                   "prev_estx": (F,), "prev_esty": (F,), "prev2_estx": (F,), "prev2_esty": (F,),
                   "rudder": (NA,), "velx": (F,), "vely": (F,),
-                  "ring": (F, 16, 4), "ring_head": (F,), "ring_count": (F,)}
+                  "ring": (F, 16, 4), "ring_head": (F,), "ring_count": (F,), "pw": (FP,)}
         out = {}
         for k, shp in shapes.items():
             dt = torch.int32 if k in ("lpage", "ring_head", "ring_count", "rudder") else torch.float32

@@ -7,7 +7,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libutrack.so")
 
-UT_ABI_VERSION = 6
+UT_ABI_VERSION = 7
 UT_FLAG_DEBUG = 1
 UT_FLAG_RING = 2
 
@@ -47,7 +47,7 @@ CONFIG_FIELDS = [
     ("id_env0", ctypes.c_uint32), ("id_agent0", ctypes.c_uint32), ("id_target0", ctypes.c_uint32),
     ("id_filter0", ctypes.c_uint32),
     ("d_model", ctypes.c_int32), ("n_layers", ctypes.c_int32), ("n_heads", ctypes.c_int32),
-    ("shared_filter", ctypes.c_int32), ("id_pair0", ctypes.c_uint32),
+    ("shared_filter", ctypes.c_int32), ("id_pair0", ctypes.c_uint32), ("pf_ess_num", ctypes.c_int32),
 ]
 
 
@@ -62,7 +62,7 @@ class StepOut(ctypes.Structure):
 
 STATE_PTRS = ["ax", "ay", "apsi", "tx", "ty", "tz", "tpsi", "tspeed", "px", "py", "pvx", "pvy",
               "lpx", "lpy", "lpage", "estx", "esty", "prev_estx", "prev_esty", "prev2_estx", "prev2_esty",
-              "rudder", "velx", "vely", "ring", "ring_head", "ring_count", "h"]
+              "rudder", "velx", "vely", "ring", "ring_head", "ring_count", "h", "pw"]
 
 
 class StateView(ctypes.Structure):

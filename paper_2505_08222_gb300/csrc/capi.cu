@@ -93,6 +93,7 @@ ut_status validate(const ut_config* c, std::string& why) {
   if (!(c->est_scale > 0.0f)) return bad("est_scale must be > 0");
   if (c->reward_type != 0 && c->reward_type != 1) return bad("reward_type must be 0 or 1");
   if (c->shared_filter != 0 && c->shared_filter != 1) return bad("shared_filter must be 0 or 1");
+  if (c->pf_ess_num < 0 || c->pf_ess_num > 16) return bad("pf_ess_num must be in 0..16");
   if (c->d_model < 0) return bad("d_model must be >= 0");
   if (c->d_model > 0) {
     if (c->n_heads < 1 || c->d_model % c->n_heads != 0) return bad("d_model % n_heads != 0");
@@ -281,6 +282,8 @@ ut_status env_create(const ut_config* cfg, const ut_allocator* allocator, void* 
   d.py = alloc_n<float>(h, FP, ok);
   d.pvx = alloc_n<float>(h, FP, ok);
   d.pvy = alloc_n<float>(h, FP, ok);
+  d.pf_ess_num = cfg->pf_ess_num;
+  d.pw = cfg->pf_ess_num > 0 ? alloc_n<float>(h, FP, ok) : nullptr;
   d.lpx = alloc_n<float>(h, NA * AM, ok);
   d.lpy = alloc_n<float>(h, NA * AM, ok);
   d.lpage = alloc_n<int32_t>(h, NA * AM, ok);
@@ -658,6 +661,7 @@ ut_status env_get_state(const ut_env* hc, ut_state_view* out) {
   out->ring = d.ring_on ? d.ring : nullptr;
   out->ring_head = d.ring_head; out->ring_count = d.ring_count;
   out->h = extension_h(h);
+  out->pw = d.pw;
   uint32_t c[2];
   UT_CUDA(h, cudaMemcpyAsync(c, d.counters, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
   UT_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -689,6 +693,7 @@ ut_status env_set_state(ut_env* h, const ut_state_view* in) {
   UT_CUDA(h, cp(d.py, in->py, FP * 4));
   UT_CUDA(h, cp(d.pvx, in->pvx, FP * 4));
   UT_CUDA(h, cp(d.pvy, in->pvy, FP * 4));
+  if (d.pw) UT_CUDA(h, cp(d.pw, in->pw, FP * 4));
   UT_CUDA(h, cp(d.lpx, in->lpx, NA * AM * 4));
   UT_CUDA(h, cp(d.lpy, in->lpy, NA * AM * 4));
   UT_CUDA(h, cp(d.lpage, in->lpage, NA * AM * 4));

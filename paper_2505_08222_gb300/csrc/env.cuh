@@ -44,6 +44,8 @@ struct EnvDev {
   float *ax, *ay, *apsi;
   float *tx, *ty, *tz, *tpsi, *tspeed;
   float *px, *py, *pvx, *pvy;
+  float* pw;        // particle log-weights [F*P] (pf_ess_num > 0), else null
+  int pf_ess_num;   // resample when 16 (sum r)^2 < pf_ess_num P sum r^2; 0: every step
   float *lpx, *lpy;
   int32_t* lpage;
   float *estx, *esty, *err;

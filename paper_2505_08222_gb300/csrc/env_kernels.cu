@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(kInitThreads) reset_pf_kernel(EnvDev d, uint32
     d.py[base + i] = y;
     d.pvx[base + i] = spd * cchi;
     d.pvy[base + i] = spd * schi;
+    if (d.pw) d.pw[base + i] = 0.0f;  // equal weights
     sx += x;
     sy += y;
   }

@@ -75,6 +75,7 @@ struct ScanScratch {
   float fx[32], fy[32], fsum[2];
   int mtot[32];
   unsigned long long u64;  // the filter's resampling draw
+  unsigned long long e1[32], e2[32];  // per-warp ESS sums (resampling trigger)
 };
 
 // Warp maximum on the warp reduction unit (NaN inputs ignored, as by fmaxf).
@@ -94,6 +95,40 @@ __device__ __forceinline__ float block_max(float v, ScanScratch* sc) {
   if (lane == 0) sc->max[wid] = v;
   __syncthreads();
   return warp_max_redux(lane < NW ? sc->max[lane] : -INFINITY);
+}
+
+// Resampling trigger (pf_ess_num = k > 0): with r = floor(w 2^15) of the
+// max-normalised weights (the integer weight floor(w 2^38) shifted right by
+// 23), resample iff 16 (sum r)^2 < k P sum r^2, i.e. the effective sample
+// size (sum r)^2 / sum r^2 is below k/16 of P.  Exact integers: sum r <=
+// 2^27, sum r^2 <= 2^42, both sides below 2^59.  One exchange through shared
+// memory; every warp reduces the warp sums itself, so the decision is the
+// same in all of them.  sc->e1 / e2 are used once per CTA.
+template <int NT>
+__device__ __forceinline__ bool block_ess_trigger(unsigned long long s1, unsigned long long s2, int k, int P,
+                                                  ScanScratch* sc) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if (NW > 1) {
+    if (lane == 0) {
+      sc->e1[wid] = s1;
+      sc->e2[wid] = s2;
+    }
+    __syncthreads();
+    s1 = lane < NW ? sc->e1[lane] : 0ull;
+    s2 = lane < NW ? sc->e2[lane] : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+  }
+  return 16ull * s1 * s1 < (unsigned long long)k * (unsigned long long)P * s2;
 }
 
 // Exclusive block scan of the int64 v (returned; the block total in W),
@@ -296,8 +331,9 @@ struct Shared {
 };
 
 // MODE 0: any P (scalar loads); 1: P % 4 == 0 (float4 streams); 2: P equal
-// to NT * PPT (float4 streams, no slot is out of range).
-template <int NT, int PPT, int MINB, int MODE>
+// to NT * PPT (float4 streams, no slot is out of range).  ESS: weights carried
+// across steps as log-weights d.pw, resampling only when triggered.
+template <int NT, int PPT, int MINB, int MODE, bool ESS>
 __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
   static_assert(PPT % 4 == 0, "PPT must be a multiple of 4");
   constexpr bool VEC = MODE >= 1, FULL = MODE == 2;
@@ -405,6 +441,11 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
   // weight (log domain); measurements outer, particles inner
   const int nm = sh.nm;
   const float dz2 = sh.dz2;
+  float pwv[PPT];  // carried log-weights (ESS form)
+  if (ESS) {
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) pwv[q] = (FULL || base + q < P) ? d.pw[off + base + q] : 0.0f;
+  }
   float acc[PPT];
   {
     // particle pairs on the packed FP32 pipe: each lane rounds like the scalar
@@ -441,7 +482,8 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
   float lmax = -INFINITY;
 #pragma unroll
   for (int q = 0; q < PPT; ++q) {
-    acc[q] = -acc[q] * d.inv_two_s2;  // log-likelihood
+    // log-likelihood (plus the carried log-weight in the ESS form)
+    acc[q] = ESS ? fmaf(-acc[q], d.inv_two_s2, pwv[q]) : -acc[q] * d.inv_two_s2;
     if (FULL || base + q < P) lmax = fmaxf(lmax, acc[q]);
   }
   lmax = block_max<NT>(lmax, &sh.scan);
@@ -469,11 +511,28 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
       }
     }
   }
-  // nm is the same for the whole CTA, so both branches keep their barriers
-  // uniform; the particles are dead across the scan in the resampling branch
+  // ESS form: the trigger, then the new log-weights (0 after a resample,
+  // log w - max log w otherwise)
+  bool resample = nm > 0;
+  if (ESS) {
+    unsigned long long s1 = 0ull, s2 = 0ull;
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      const unsigned long long r = (unsigned long long)(qweight(w[q]) >> 23);
+      s1 += r;
+      s2 += r * r;
+    }
+    resample = block_ess_trigger<NT>(s1, s2, d.pf_ess_num, P, &sh.scan) && nm > 0;
+#pragma unroll
+    for (int q = 0; q < PPT; ++q)
+      if (FULL || base + q < P) d.pw[off + base + q] = resample ? 0.0f : acc[q] - lmax;
+  }
+  // the branch condition is the same for the whole CTA, so both branches
+  // keep their barriers uniform; the particles are dead across the scan in
+  // the resampling branch
   long long W;
   int idx[PPT];
-  if (nm > 0) {
+  if (resample) {
 #pragma unroll
     for (int q = 0; q < PPT; ++q) s_part[q * NT + tid] = make_float4(x[q], y[q], vx[q], vy[q]);
     init_markers<PPT>(s_mark, base);
@@ -604,11 +663,11 @@ cudaError_t ensure_smem(K k, size_t smem, int& done) {
   return e;
 }
 
-template <int NT, int PPT, int MINB, int MODE>
+template <int NT, int PPT, int MINB, int MODE, bool ESS>
 cudaError_t launch_mode(const EnvDev& d, cudaStream_t s) {
   static int ready = 0;
   const size_t smem = step_smem_bytes(NT, PPT);
-  auto k = pf_step_kernel<NT, PPT, MINB, MODE>;
+  auto k = pf_step_kernel<NT, PPT, MINB, MODE, ESS>;
   cudaError_t e = ensure_smem(k, smem, ready);
   if (e != cudaSuccess) return e;
   if (d.F > 0) k<<<d.F, NT, smem, s>>>(d);
@@ -619,9 +678,14 @@ cudaError_t launch_mode(const EnvDev& d, cudaStream_t s) {
 template <int NT, int PPT, int MINB>
 cudaError_t launch_step(const EnvDev& d, cudaStream_t s) {
   if (d.P > NT * PPT) return cudaErrorInvalidValue;
-  if (d.P == NT * PPT) return launch_mode<NT, PPT, MINB, 2>(d, s);
-  if (d.P % 4 == 0) return launch_mode<NT, PPT, MINB, 1>(d, s);
-  return launch_mode<NT, PPT, MINB, 0>(d, s);
+  if (d.pw) {
+    if (d.P == NT * PPT) return launch_mode<NT, PPT, MINB, 2, true>(d, s);
+    if (d.P % 4 == 0) return launch_mode<NT, PPT, MINB, 1, true>(d, s);
+    return launch_mode<NT, PPT, MINB, 0, true>(d, s);
+  }
+  if (d.P == NT * PPT) return launch_mode<NT, PPT, MINB, 2, false>(d, s);
+  if (d.P % 4 == 0) return launch_mode<NT, PPT, MINB, 1, false>(d, s);
+  return launch_mode<NT, PPT, MINB, 0, false>(d, s);
 }
 
 }  // namespace pf

@@ -86,6 +86,8 @@ class EnvParams:
     # alternative); 0: one filter per (env, agent, target)
     shared_filter: int = 0
     id_pair0: int = 0  # global id of the first (agent, target) pair (sharded, shared filters)
+    # resampling trigger: 0 every step with a measurement; k in 1..16: when ESS < k/16 P
+    pf_ess_num: int = 0
 
     def counts(self):
         a = (np.full(self.n_envs, self.max_agents, np.int32) if self.agents_per_env is None

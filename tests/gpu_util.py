@@ -16,7 +16,7 @@ def gpu_state(env) -> dict:
     torch.cuda.synchronize()
     st = env.state()
     out = {}
-    for k in STATE_KEYS_F + STATE_KEYS_I + ["ring", "ring_head", "ring_count"]:
+    for k in STATE_KEYS_F + STATE_KEYS_I + ["ring", "ring_head", "ring_count", "pw"]:
         v = st.get(k)
         if v is not None:
             out[k] = v.detach().cpu().numpy().copy()
@@ -27,6 +27,8 @@ def gpu_state(env) -> dict:
 def oracle_state_f32(o: oracle.OracleEnv) -> dict:
     """The oracle's state rounded to float32 (what a GPU handle can hold)."""
     out = {k: o.arr[k].astype(np.float32) for k in STATE_KEYS_F}
+    if "pw" in o.arr:  # carried log-weights (resampling triggered by the effective sample size)
+        out["pw"] = o.arr["pw"].astype(np.float32)
     out["lpage"] = o.arr["lpage"].copy()
     out["rudder"] = o.arr["rudder"].copy()
     return out
@@ -48,6 +50,14 @@ def rel_close(a, b, rel, floor=1.0):
 
 def angle_diff(a, b):
     return np.abs(np.angle(np.exp(1j * (np.asarray(a, np.float64) - np.asarray(b, np.float64)))))
+
+
+def ess_trigger(wmax, k: int, P: int) -> bool:
+    """The filter's resampling trigger on its own max-normalised weights:
+    16 (sum r)^2 < k P sum r^2 with r = floor(w 2^38) >> 23."""
+    r = np.floor(np.asarray(wmax, np.float64) * 2.0 ** 38).astype(np.int64) >> 23
+    s1, s2 = int(r.sum()), int((r * r).sum())
+    return 16 * s1 * s1 < k * P * s2
 
 
 def resample_u64(seed: int, filt_global: int, g: int) -> int:

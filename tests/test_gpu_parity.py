@@ -24,7 +24,8 @@ import torch
 import oracle
 from synth import preset
 
-from gpu_util import angle_diff, bf16_to_f32, gpu_state, inject, oracle_state_f32, rel_close, resample_u64
+from gpu_util import (angle_diff, bf16_to_f32, ess_trigger, gpu_state, inject, oracle_state_f32, rel_close,
+                      resample_u64)
 
 pytestmark = pytest.mark.gpu
 
@@ -149,12 +150,25 @@ def _compare_step(env, o, actions, check_tokens=True):
     # resample map: bit-exact against the definition applied to the kernel's own weights
     wmax = dbg["wmax"].reshape(-1, P)
     idx = dbg["idx"].reshape(-1, P)
+    k_ess = int(getattr(p, "pf_ess_num", 0))
     for f in range(o.F):
-        if dbg["meas_n"][f] > 0:
+        if dbg["meas_n"][f] > 0 and (k_ess == 0 or ess_trigger(wmax[f], k_ess, P)):
             want = oracle.systematic_resample(wmax[f].astype(np.float64), resample_u64(o.seed, f, g_next))
             np.testing.assert_array_equal(idx[f], want)
         else:
             np.testing.assert_array_equal(idx[f], np.arange(P))
+    # carried log-weights (ESS form): 0 where the kernel resampled, else
+    # log w - max log w, against the oracle's where both took the same decision
+    if k_ess:
+        trig_g = np.array([dbg["meas_n"][f] > 0 and ess_trigger(wmax[f], k_ess, P) for f in range(o.F)])
+        wo_max = ref["wmax"].reshape(-1, P)
+        trig_o = np.array([ref["meas_n"][f] > 0 and ess_trigger(wo_max[f], k_ess, P) for f in range(o.F)])
+        pw_g, pw_o = g["pw"].reshape(-1, P), o.arr["pw"].reshape(-1, P)
+        assert np.all(pw_g[trig_g] == 0.0)
+        same = (trig_g == trig_o) & sel
+        assert np.mean(trig_g == trig_o) > 0.99
+        keep = same & ~trig_g
+        assert np.all(np.abs(pw_g[keep] - pw_o[keep]) <= 2e-3 + 1e-4 * np.abs(pw_o[keep]))
     # gather: new particles are the predicted ones at the resample indices
     for k, pk in (("px", "pred_px"), ("py", "pred_py"), ("pvx", "pred_pvx"), ("pvy", "pred_pvy")):
         np.testing.assert_array_equal(g[k].reshape(-1, P), np.take_along_axis(dbg[pk].reshape(-1, P), idx, 1))
@@ -186,6 +200,8 @@ def _compare_step(env, o, actions, check_tokens=True):
     ("fleet5", 6, 512, {"shared_filter": 1, "comm_drop": 0.3}),
     ("ragged", 24, 100, {}),
     ("ragged", 16, 100, {"shared_filter": 1}),
+    ("fleet5", 6, 512, {"pf_ess_num": 8, "range_sigma": 30.0}),
+    ("fleet5", 4, 2048, {"pf_ess_num": 4}),
     ("large", 2, 512, {}),
 ])
 def test_step_parity_from_injected_state(name, n_envs, P, kw):
@@ -204,7 +220,8 @@ def test_step_parity_from_injected_state(name, n_envs, P, kw):
 # ---------------------------------------------------------------- whole rollouts
 @pytest.mark.parametrize("name,n_envs,T,P,kw", [("small", 1024, 200, 1000, {}), ("fleet5", 64, 100, 2048, {}),
                                               ("ragged", 96, 60, 1024, {}),
-                                              ("fleet5", 256, 100, 1024, {"shared_filter": 1})])
+                                              ("fleet5", 256, 100, 1024, {"shared_filter": 1}),
+                                              ("fleet5", 128, 100, 1024, {"pf_ess_num": 8})])
 def test_rollout_rmse_matches_oracle(name, n_envs, T, P, kw):
     """Mean tracking RMSE of whole rollouts agrees within 2% (north-star
     bound).  'Mean tracking RMSE' = mean over filters of each filter's RMSE
@@ -237,6 +254,25 @@ def test_rollout_rmse_matches_oracle(name, n_envs, T, P, kw):
     print(f"{name}: mean RMSE gpu {mean_rmse_g:.3f} oracle {mean_rmse_o:.3f}; pooled gpu {stats['rmse']:.3f} "
           f"oracle {pooled_o:.3f}; reward gpu {stats['reward_sum']:.1f} oracle {rw:.1f}")
     assert abs(stats["reward_sum"] - rw) <= 0.05 * abs(rw) + 1.0
+
+
+def test_ess_k16_is_the_every_step_filter():
+    """With k = 16 the trigger fires unless all quantised weights are equal,
+    so the carried-weight filter runs the every-step filter's computation:
+    the two handles' states agree bit for bit."""
+    p = preset("fleet5", n_envs=16).replace(n_particles=512, d_model=0)
+    a, b = ut.Env(p), ut.Env(p.replace(pf_ess_num=16))
+    v = a.pf_variant()
+    b.set_pf_variant(v)
+    a.reset(4)
+    b.reset(4)
+    for _ in range(6):
+        a.step()
+        b.step()
+    sa, sb = gpu_state(a), gpu_state(b)
+    for k in ("px", "py", "pvx", "pvy", "estx", "esty"):
+        np.testing.assert_array_equal(sa[k], sb[k], err_msg=k)
+    assert np.all(sb["pw"] == 0.0)
 
 
 def test_rollout_graph_metrics():
