@@ -526,6 +526,37 @@ def run_ours(args):
 
     e2e_host = _e2e_loop(_host_actions)
 
+    # roofline of the transformer agent (it dominates the large workload): its
+    # forward over this batch's tokens through the stand-alone entry (the same
+    # device code as the step's), CUDA events over K launches on the stream;
+    # algorithmic tensor FLOPs 2 * 128 * 12 d^2 L per 128-row tile
+    pol_roof = None
+    if policy_on:
+        tok = env.step(None)["obs"].view(torch.bfloat16)
+        a_cnt, t_cnt = p.counts()
+        n_ent = torch.from_numpy(np.repeat(a_cnt + t_cnt, a_cnt).astype(np.int32)).cuda()
+        h_tmp = torch.zeros((NA, p.d_model), dtype=torch.bfloat16, device="cuda")
+        for _ in range(3):
+            env.policy_forward(tok, n_ent, h_tmp)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            env.policy_forward(tok, n_ent, h_tmp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pol_ms = e0.elapsed_time(e1) / K
+        apt = 128 // (1 + p.max_agents + p.max_targets)
+        tiles = -(-NA // apt)
+        flops = tiles * 2 * 128 * 12 * p.d_model ** 2 * p.n_layers
+        pol_tf = flops / (pol_ms / 1e3) / 1e12
+        pol_roof = {"bound": "tensor", "achieved": pol_tf, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                    "frac": pol_tf / peaks["bf16_tflops"], "traffic": None, "kernel": "policy_fwd_kernel",
+                    "avg_launch_ms": pol_ms, "launches": K, "tiles": tiles, "flops_per_launch": flops,
+                    "peak_kind": f"{peak_kind} cuBLAS bf16 GEMM (burst)",
+                    "timing": "CUDA events over K stand-alone launches on the batch's tokens"}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "agent-steps/s", "n_gpus": world, "steps": K, "warmup": W,
@@ -551,6 +582,7 @@ def run_ours(args):
                     "host_actions": {"value": e2e_host, "h2d_bytes_per_step": NA * 4, "d2h_bytes_per_step": E * 8,
                                      "note": "a host controller's actions copied in every step in place of the policy"}},
             "gpu_launches": stats["kernel_launches"],
+            "policy_roofline": pol_roof,
             "clocks": clock_info,
             "rmse_m": stats["rmse"],
         }
@@ -586,13 +618,17 @@ def main():
     ap.add_argument("--pf-variant", default=None, help="fixed filter launch variant (e.g. nt512x4m3), no autotune")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-estimator form")
     ap.add_argument("--no-shared", action="store_true", help="skip the shared-filter and ESS-resampling forms")
-    ap.add_argument("--train-rows", type=int, default=20_000_000)
+    ap.add_argument("--train-rows", type=int, default=None,
+                    help="recorded estimator rows (default 20M; 64M for the large workload, whose 4.2M filters "
+                         "per step would otherwise give too few recorded episodes)")
     ap.add_argument("--train-steps", type=int, default=3000, help="Adam steps on the filter-driven rows")
     ap.add_argument("--round-steps", type=int, default=800, help="Adam steps after each DAgger round")
     ap.add_argument("--eval-steps", type=int, default=100)
     ap.add_argument("--est-candidates", type=int, default=3, help="estimator trainings to choose from")
     ap.add_argument("--envs", type=int, default=None, help="override the env count (profiling cases)")
     args = ap.parse_args()
+    if args.train_rows is None:
+        args.train_rows = 64_000_000 if args.workload == "large" else 20_000_000
     global _ENVS
     _ENVS = args.envs
     if args.warmup < 3:

@@ -20,8 +20,8 @@
  *     by measurement likelihoods, resampled): Sec. II-A;
  *   - transformer agent (entity tokens + recurrent token, self-attention,
  *     LayerNorm, MLP head on the recurrent token): Sec. III-B.1, Fig. 3.
- * Where the paper is silent the readings taken are listed in the design doc
- * (readings C1-C18); every such constant is a field of oc_config.
+ * Where the paper is silent a reading is taken (numbered C1-C23 where it is
+ * used below); every such constant is a field of oc_config.
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
  * numbers: as easy as 1, 2, 3", SC'11), keyed by the seed, counter =
