@@ -125,7 +125,7 @@ def cpu_baseline(workload: str, budget_s: float = 12.0, n_envs: int = 64):
     p = preset(workload, n_envs=n_envs)
     o = oracle.OracleEnv(p, 0)
     o.reset(0)
-    cores = os.cpu_count() or 1
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     use_policy = p.d_model > 0
     if use_policy:
         dims = synth.PolicyDims(p.d_model, p.n_layers, p.n_heads, p.n_actions)
@@ -150,8 +150,24 @@ def cpu_baseline(workload: str, budget_s: float = 12.0, n_envs: int = 64):
             break
     dt = time.perf_counter() - t0
     value = steps * o.NA / dt
-    return {"value": value, "unit": "agent-steps/s", "cores": cores, "kind": "oracle",
+    return {"value": value, "unit": "agent-steps/s", "cores": cores, "kind": "oracle", "per_core": value / cores,
             "sample": f"{n_envs} envs of the {workload} workload x {steps} steps ({dt:.1f} s, FP64, OpenMP)"}
+
+
+def cpu_baseline_one_thread(workload: str, budget_s: float = 5.0):
+    """The same oracle sample on one host thread (a child process, so that
+    OpenMP starts with one thread)."""
+    import subprocess
+    import sys
+
+    code = ("import json, bench; print(json.dumps(bench.cpu_baseline(%r, budget_s=%r)))" % (workload, budget_s))
+    env = dict(os.environ, OMP_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       cwd=os.path.dirname(os.path.abspath(__file__)), timeout=600)
+    try:
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except (IndexError, ValueError):
+        return {"error": (r.stderr or "no output").strip().splitlines()[-1:]}
 
 
 def learned_form(args, p, K, W, rank):
@@ -461,6 +477,26 @@ def run_ours(args):
         ms = float(t.item())
         dist.barrier()
     agent_steps = float(shard.reduce_sums([stats["agent_steps"]])[0])
+
+    # the same timed rollout (same graph, W warm-up steps) from seeds 0..4
+    sweep = []
+    for sd in range(5):
+        env.reset(sd)
+        for _ in range(W):
+            env.step()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ev0.record(stream)
+        st_sd = env.rollout(K)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_sd = ev0.elapsed_time(ev1)
+        if world > 1:
+            t = torch.tensor([ms_sd], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms_sd = float(t.item())
+        sweep.append(float(shard.reduce_sums([st_sd["agent_steps"]])[0]) / (ms_sd / 1e3))
     # dominant-kernel duration: CUDA events around each particle-filter launch
     # on its stream (events recorded by graph nodes cannot be timed), over an
     # eager replay of the timed steps: same seed, W untimed steps, then the
@@ -582,6 +618,8 @@ def run_ours(args):
                     "host_actions": {"value": e2e_host, "h2d_bytes_per_step": NA * 4, "d2h_bytes_per_step": E * 8,
                                      "note": "a host controller's actions copied in every step in place of the policy"}},
             "gpu_launches": stats["kernel_launches"],
+            "seeds_0_4": {"values": sweep, "mean": sum(sweep) / len(sweep), "min": min(sweep), "max": max(sweep),
+                          "note": "the timed rollout repeated from env_reset(seed), seeds 0..4"},
             "policy_roofline": pol_roof,
             "clocks": clock_info,
             "rmse_m": stats["rmse"],
@@ -598,6 +636,7 @@ def run_ours(args):
         if world == 1 and not args.no_cpu_baseline:
             os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
             line["cpu_baseline"] = cpu_baseline(args.workload)
+            line["cpu_baseline"]["one_thread"] = cpu_baseline_one_thread(args.workload)
         print(json.dumps(line), flush=True)
     env.close()
     if world > 1:
