@@ -63,7 +63,8 @@ def _cfg(**kw):
 @pytest.mark.parametrize("kw", [
     {"n_envs": 0}, {"max_agents": 9}, {"max_targets": 0}, {"n_particles": 0}, {"n_particles": 4097},
     {"range_sigma": 0.0}, {"n_heads": 3}, {"n_actions": 9}, {"reward_type": 2}, {"spawn_tries": 65},
-    {"action_mode": 3}, {"shared_filter": 2}, {"action_mode": 2, "n_actions": 7}, {"action_mode": 2, "n_actions": 3, "n_rudder": 1},
+    {"action_mode": 3}, {"shared_filter": 2}, {"shared_filter": -1}, {"pf_ess_num": 17}, {"pf_ess_num": -1},
+    {"action_mode": 2, "n_actions": 7}, {"action_mode": 2, "n_actions": 3, "n_rudder": 1},
     {"action_mode": 2, "n_actions": 3, "n_rudder": 9},
 ])
 def test_create_rejects_invalid_config(lib, kw):

@@ -379,14 +379,16 @@ def test_learned_step_matches_oracle(mode):
         env.close()
 
 
-def test_ls_step_matches_oracle():
+@pytest.mark.parametrize("shared", [0, 1])
+def test_ls_step_matches_oracle(shared):
     """Least-squares tracker (est_set_mode 4): one step from an injected oracle
     state, GPU (FP32, positions relative to the previous estimate) against the
-    oracle (FP64).  Filters whose normal matrix sits within a factor 2 of the
-    degeneracy threshold may take the other branch in FP32 and are left out;
-    elsewhere the bound is 1 m (FP32 rounding of a = |q|^2 - rho^2 on
-    kilometre baselines, amplified by at most the 1e3 condition limit)."""
-    env, p = _env(n_envs=8, comm_drop=0.2, target_depth_max=40.0)
+    oracle (FP64), with per-agent and with shared filters.  Filters whose
+    normal matrix sits within a factor 2 of the degeneracy threshold may take
+    the other branch in FP32 and are left out; elsewhere the bound is 1 m
+    (FP32 rounding of a = |q|^2 - rho^2 on kilometre baselines, amplified by
+    at most the 1e3 condition limit)."""
+    env, p = _env(n_envs=8, comm_drop=0.2, target_depth_max=40.0, shared_filter=shared)
     env.reset(8)
     o = oracle.OracleEnv(p, 8)
     o.reset(0)
