@@ -14,6 +14,35 @@
 
 namespace ut {
 
+// Programmatic dependent launch between the kernels of one environment step:
+// every step kernel waits for its predecessor's completion and memory before
+// its first global access (pdl_wait); the small single-wave kernels also let
+// the next kernel launch as soon as all of their own CTAs are running
+// (pdl_trigger), the many-wave ones (filter, policy, estimator) let it launch
+// as their CTAs exit, so that no waiting CTA holds an SM during their last
+// wave.  Both are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch with programmatic stream serialization: the kernel may start while
+// the previous kernel in the stream is still running, so it must call
+// pdl_wait() before touching memory that kernel writes.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Stream tags (counter word 3).
 enum : uint32_t {
   TAG_SPAWN = 1,

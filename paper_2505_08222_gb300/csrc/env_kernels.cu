@@ -159,6 +159,8 @@ __global__ void reset_counters_kernel(EnvDev d) {
 // One warp per environment.
 // -------------------------------------------------------------------------
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) step_env_kernel(EnvDev d, const int32_t* __restrict__ act_in) {
+  pdl_wait();
+  pdl_trigger();
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int e = blockIdx.x * kWarpsPerBlock + wid;
   __shared__ float s_ax[kWarpsPerBlock][kMaxAgents], s_ay[kWarpsPerBlock][kMaxAgents];
@@ -323,6 +325,8 @@ __device__ __forceinline__ float tracking_reward(float err, float emin, float em
 // metrics.  One warp per environment.
 // -------------------------------------------------------------------------
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) obs_reward_kernel(EnvDev d, int after_reset) {
+  pdl_wait();
+  pdl_trigger();
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int e = blockIdx.x * kWarpsPerBlock + wid;
   __shared__ double s_sq[kWarpsPerBlock], s_rw[kWarpsPerBlock];
@@ -445,6 +449,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) obs_reward_kernel(EnvDev 
 }
 
 __global__ void advance_kernel(EnvDev d) {
+  pdl_wait();
+  pdl_trigger();
   if (threadIdx.x == 0) {
     d.counters[0] += 1u;
     d.counters[1] += 1u;
@@ -471,18 +477,17 @@ cudaError_t launch_reset(const EnvDev& d, cudaStream_t s) {
 }
 
 cudaError_t launch_step_env(const EnvDev& d, const int32_t* act_in, cudaStream_t s) {
-  step_env_kernel<<<(d.E + kWarpsPerBlock - 1) / kWarpsPerBlock, kWarpsPerBlock * 32, 0, s>>>(d, act_in);
-  return cudaGetLastError();
+  return launch_pdl(step_env_kernel, dim3((d.E + kWarpsPerBlock - 1) / kWarpsPerBlock), dim3(kWarpsPerBlock * 32), 0,
+                    s, d, act_in);
 }
 
 cudaError_t launch_obs_reward(const EnvDev& d, int after_reset, cudaStream_t s) {
-  obs_reward_kernel<<<(d.E + kWarpsPerBlock - 1) / kWarpsPerBlock, kWarpsPerBlock * 32, 0, s>>>(d, after_reset);
-  return cudaGetLastError();
+  return launch_pdl(obs_reward_kernel, dim3((d.E + kWarpsPerBlock - 1) / kWarpsPerBlock), dim3(kWarpsPerBlock * 32), 0,
+                    s, d, after_reset);
 }
 
 cudaError_t launch_advance(const EnvDev& d, cudaStream_t s) {
-  advance_kernel<<<1, 32, 0, s>>>(d);
-  return cudaGetLastError();
+  return launch_pdl(advance_kernel, dim3(1), dim3(32), 0, s, d);
 }
 
 cudaError_t launch_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n, cudaStream_t s) {

@@ -232,6 +232,7 @@ __device__ __forceinline__ void env_stage(int s, size_t& off, uint32_t& bytes) {
 }
 
 __global__ void __launch_bounds__(kTE, 1) fwd_env_kernel(Net net, EnvDev d, int stale) {
+  pdl_wait();  // (dependents launch as this grid's CTAs exit)
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;           // features hi | lo [2 x 128 x 96], then hidden activations [128 x 256]
   unsigned char* sW = smem + 65536;   // two weight slots
@@ -730,7 +731,7 @@ cudaError_t launch_forward_env(const Net& net, const EnvDev& d, int stale, cudaS
   cudaError_t e = smem_optin(fwd_env_kernel, kEnvSmem, ready);
   if (e != cudaSuccess) return e;
   if (d.F <= 0) return cudaSuccess;
-  fwd_env_kernel<<<(d.F + 127) / 128, kTE, kEnvSmem, s>>>(net, d, stale);
+  launch_pdl(fwd_env_kernel, dim3((d.F + 127) / 128), dim3(kTE), kEnvSmem, s, net, d, stale);
   return cudaGetLastError();
 }
 

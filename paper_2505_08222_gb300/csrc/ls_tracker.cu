@@ -22,6 +22,7 @@ namespace {
 constexpr float kLsMinDetRatio = 1e-3f;
 
 __global__ void ls_update_kernel(EnvDev d) {
+  pdl_wait();  // (dependents launch as this grid's CTAs exit)
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= d.F) return;
   const int it = d.filt_target[f];
@@ -87,8 +88,7 @@ __global__ void ls_update_kernel(EnvDev d) {
 
 cudaError_t launch_ls_update(const EnvDev& d, cudaStream_t s) {
   if (d.F <= 0) return cudaSuccess;
-  ls_update_kernel<<<(d.F + 127) / 128, 128, 0, s>>>(d);
-  return cudaGetLastError();
+  return launch_pdl(ls_update_kernel, dim3((d.F + 127) / 128), dim3(128), 0, s, d);
 }
 
 }  // namespace ut

@@ -335,6 +335,7 @@ struct Shared {
 // across steps as log-weights d.pw, resampling only when triggered.
 template <int NT, int PPT, int MINB, int MODE, bool ESS>
 __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
+  pdl_wait();  // (dependents launch as this grid's CTAs exit: no early trigger in a many-wave kernel)
   static_assert(PPT % 4 == 0, "PPT must be a multiple of 4");
   constexpr bool VEC = MODE >= 1, FULL = MODE == 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -670,8 +671,8 @@ cudaError_t launch_mode(const EnvDev& d, cudaStream_t s) {
   auto k = pf_step_kernel<NT, PPT, MINB, MODE, ESS>;
   cudaError_t e = ensure_smem(k, smem, ready);
   if (e != cudaSuccess) return e;
-  if (d.F > 0) k<<<d.F, NT, smem, s>>>(d);
-  return cudaGetLastError();
+  if (d.F > 0) return launch_pdl(k, dim3(d.F), dim3(NT), smem, s, d);
+  return cudaSuccess;
 }
 
 // Requires NT * PPT >= P (the variant check).

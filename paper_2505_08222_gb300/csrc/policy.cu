@@ -382,6 +382,7 @@ __device__ __forceinline__ void attend_warp(uint32_t aQ, uint32_t aK, uint32_t a
 
 template <int D>
 __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_kernel(PolicyDev p) {
+  pdl_wait();  // (dependents launch as this grid's CTAs exit: no early trigger in a many-wave kernel)
   using G = Geo<D>;
   constexpr int COLS = G::COLS, kThreads = G::THREADS;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -678,7 +679,11 @@ cudaError_t launch_policy_t(const PolicyDev& p, cudaStream_t s) {
     ready = 1;
   }
   const long long tiles = (p.NA + p.apt - 1) / p.apt;
-  if (tiles > 0) policy_fwd_kernel<D><<<(unsigned)tiles, Geo<D>::THREADS, Geo<D>::SMEM, s>>>(p);
+  if (tiles > 0) {
+    const cudaError_t e =
+        launch_pdl(policy_fwd_kernel<D>, dim3((unsigned)tiles), dim3(Geo<D>::THREADS), Geo<D>::SMEM, s, p);
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 
