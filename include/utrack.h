@@ -449,7 +449,8 @@ ut_status tc_gemm_bf16(const uint16_t* A_dev, const uint16_t* B_dev, float* C_de
  * target) filter — the same rules and random draws as env_step at global step
  * `step` (>= 1) with `seed`.  Uniform fleets only: cfg->n_envs environments of
  * cfg->max_agents agents and cfg->max_targets targets (the per-env count
- * pointers must be NULL); cfg supplies the constants.
+ * pointers must be NULL), per-agent filters resampled every step
+ * (shared_filter and pf_ess_num 0); cfg supplies the constants.
  *   ax/ay_dev [E*A], tx/ty/tz_dev [E*T]: positions (read);
  *   px/py/pvx/pvy_dev [E*A*T*P]: particles, updated in place;
  *   estx/esty/err_dev [E*A*T]: estimate and its 2-D error (written).

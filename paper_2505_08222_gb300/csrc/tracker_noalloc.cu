@@ -168,8 +168,11 @@ extern "C" ut_status tracker_update_noalloc(const ut_config* cfg, uint64_t seed,
   if (!cfg || cfg->abi_version != UT_ABI_VERSION) return UT_ERR_INVALID;
   const int E = cfg->n_envs, A = cfg->max_agents, T = cfg->max_targets, P = cfg->n_particles;
   if (E < 1 || A < 1 || A > UT_MAX_AGENTS || T < 1 || T > UT_MAX_TARGETS || P < 1 || P > UT_MAX_PARTICLES ||
-      cfg->agents_per_env_host || cfg->targets_per_env_host || !(cfg->range_sigma > 0.0f) || step < 1u) {
-    std::fprintf(stderr, "tracker_update_noalloc: invalid configuration (uniform fleets only, step >= 1)\n");
+      cfg->agents_per_env_host || cfg->targets_per_env_host || !(cfg->range_sigma > 0.0f) || step < 1u ||
+      cfg->shared_filter != 0 || cfg->pf_ess_num != 0) {
+    std::fprintf(stderr,
+                 "tracker_update_noalloc: invalid configuration (uniform fleets, per-agent filters resampled "
+                 "every step, step >= 1)\n");
     return UT_ERR_INVALID;
   }
   const long long F = (long long)E * A * T;

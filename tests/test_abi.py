@@ -87,6 +87,19 @@ def test_create_rejects_bad_ragged_counts_and_abi(lib):
     assert ut.lib.env_create(ctypes.byref(cfg), None, None, ctypes.byref(h)) == 1
 
 
+def test_noalloc_rejects_layouts_it_does_not_run(lib):
+    """The allocation-free tracker runs per-agent filters resampled every
+    step on uniform fleets; other configurations are refused before any
+    device work (so this runs without a GPU)."""
+    import paper_2505_08222_gb300 as ut
+    dummy = [ctypes.c_void_p(16)] * 12
+    for kw in ({"shared_filter": 1}, {"pf_ess_num": 8}, {"n_envs": 0}):
+        cfg, keep = _cfg(**kw)
+        assert ut.lib.tracker_update_noalloc(ctypes.byref(cfg), ctypes.c_uint64(1), 1, *dummy, None) == 1
+    cfg, keep = _cfg()
+    assert ut.lib.tracker_update_noalloc(ctypes.byref(cfg), ctypes.c_uint64(1), 0, *dummy, None) == 1
+
+
 def test_standalone_ops_validate_arguments(lib):
     import paper_2505_08222_gb300 as ut
     assert ut.lib.pf_resample(None, None, -1, 16, None, None) == 1
