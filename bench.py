@@ -479,7 +479,7 @@ def run_ours(args):
     agent_steps = float(shard.reduce_sums([stats["agent_steps"]])[0])
 
     # the same timed rollout (same graph, W warm-up steps) from seeds 0..4
-    sweep = []
+    sweep, sweep_rmse = [], []
     for sd in range(5):
         env.reset(sd)
         for _ in range(W):
@@ -497,6 +497,8 @@ def run_ours(args):
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             ms_sd = float(t.item())
         sweep.append(float(shard.reduce_sums([st_sd["agent_steps"]])[0]) / (ms_sd / 1e3))
+        sq = shard.reduce_sums([st_sd["sum_sq_err"], st_sd["n_err"]])
+        sweep_rmse.append(float((sq[0] / max(sq[1], 1.0)) ** 0.5))
     # dominant-kernel duration: CUDA events around each particle-filter launch
     # on its stream (events recorded by graph nodes cannot be timed), over an
     # eager replay of the timed steps: same seed, W untimed steps, then the
@@ -619,7 +621,10 @@ def run_ours(args):
                                      "note": "a host controller's actions copied in every step in place of the policy"}},
             "gpu_launches": stats["kernel_launches"],
             "seeds_0_4": {"values": sweep, "mean": sum(sweep) / len(sweep), "min": min(sweep), "max": max(sweep),
-                          "note": "the timed rollout repeated from env_reset(seed), seeds 0..4"},
+                          "median": sorted(sweep)[len(sweep) // 2],
+                          "rmse_m": sweep_rmse, "rmse_mean_m": sum(sweep_rmse) / len(sweep_rmse),
+                          "note": "the timed rollout repeated from env_reset(seed), seeds 0..4 (pooled RMSE over "
+                                  "the K steps per seed)"},
             "policy_roofline": pol_roof,
             "clocks": clock_info,
             "rmse_m": stats["rmse"],
