@@ -202,6 +202,9 @@ def _compare_step(env, o, actions, check_tokens=True):
     ("ragged", 16, 100, {"shared_filter": 1}),
     ("fleet5", 6, 512, {"pf_ess_num": 8, "range_sigma": 30.0}),
     ("fleet5", 4, 2048, {"pf_ess_num": 4}),
+    ("ragged", 12, 13, {"pf_ess_num": 8, "range_sigma": 20.0}),
+    ("small", 3, 4096, {"pf_ess_num": 12, "range_sigma": 40.0}),
+    ("fleet5", 4, 256, {"shared_filter": 1, "pf_ess_num": 8, "range_sigma": 25.0}),
     ("large", 2, 512, {}),
 ])
 def test_step_parity_from_injected_state(name, n_envs, P, kw):

@@ -12,6 +12,7 @@ filter, reading C23) in the oracle, pinned by reductions and brute force.
   weights; when it fires, the resample map is the systematic map of those
   weights, else the identity."""
 import numpy as np
+import pytest
 
 import oracle
 from synth import preset
@@ -23,8 +24,10 @@ def _trigger(wmax, k, P):
     return 16 * s1 * s1 < k * P * s2
 
 
-def test_k16_is_the_every_step_filter():
-    p = preset("fleet5", n_envs=3).replace(n_particles=64, d_model=0, comm_drop=0.2, det_radius=300.0)
+@pytest.mark.parametrize("shared", [0, 1])
+def test_k16_is_the_every_step_filter(shared):
+    p = preset("fleet5", n_envs=3).replace(n_particles=64, d_model=0, comm_drop=0.2, det_radius=300.0,
+                                           shared_filter=shared)
     a = oracle.OracleEnv(p, 31)
     b = oracle.OracleEnv(p.replace(pf_ess_num=16), 31)
     a.reset(0)
