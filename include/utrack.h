@@ -54,7 +54,7 @@ typedef enum {
   UT_ERR_CUDA = 3,        /* CUDA runtime error (message in env_last_error) */
   UT_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
   UT_ERR_STATE = 5,       /* call not valid in the handle's current state */
-  UT_ERR_UNSUPPORTED = 6  /* feature not available in this build/config */
+  UT_ERR_UNSUPPORTED = 6  /* feature not available in this library or configuration */
 } ut_status;
 
 /* Caller-supplied device allocator.  alloc(bytes, stream, ctx) returns a
