@@ -288,8 +288,9 @@ def test_rollout_graph_metrics():
     assert 0 < s["rmse"] < 1000 and math.isfinite(s["reward_sum"])
 
 
-def test_eager_steps_equal_graph_rollout():
-    p = preset("fleet5", n_envs=16).replace(n_particles=256, d_model=0)
+@pytest.mark.parametrize("kw", [{}, {"shared_filter": 1}, {"pf_ess_num": 8, "range_sigma": 30.0}])
+def test_eager_steps_equal_graph_rollout(kw):
+    p = preset("fleet5", n_envs=16).replace(n_particles=256, d_model=0, **kw)
     a = ut.Env(p)
     a.reset(5)
     for _ in range(10):
