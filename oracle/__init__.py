@@ -6,7 +6,9 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 
 The arithmetic lives in ``utrack_oracle.c`` (environment, particle filter,
 reward, observations) and ``utrack_oracle_nn.c`` (transformer agent,
-estimator MLP, Adam), compiled with gcc into ``_build/liboracle.so``.  This
+estimator MLP, Adam) and ``utrack_oracle_ppo.c`` (TransfMAPPO: the
+actor's and critic's loss gradients, GAE, the critic's state tokens),
+compiled with gcc into ``_build/liboracle.so``.  This
 module only marshals numpy arrays through ctypes.
 """
 from __future__ import annotations
@@ -19,7 +21,8 @@ from typing import Optional
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = [os.path.join(_HERE, "utrack_oracle.c"), os.path.join(_HERE, "utrack_oracle_nn.c")]
+_SRC = [os.path.join(_HERE, "utrack_oracle.c"), os.path.join(_HERE, "utrack_oracle_nn.c"),
+        os.path.join(_HERE, "utrack_oracle_ppo.c")]
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 
@@ -136,6 +139,18 @@ def _declare(L):
     L.oc_mlp_loss_grad.restype = ctypes.c_double
     L.oc_adam.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, ctypes.c_int32, ctypes.c_double,
                           ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    L.oc_tfm_param_count.argtypes = [ctypes.POINTER(OcPolicyDims)]
+    L.oc_tfm_param_count.restype = ctypes.c_int64
+    L.oc_tfm_forward.argtypes = [ctypes.POINTER(OcPolicyDims), _dp, ctypes.c_int32, ctypes.c_int32, _dp, _ip,
+                                 _dp, _dp, _dp]
+    L.oc_tfm_loss_grad.argtypes = [ctypes.POINTER(OcPolicyDims), _dp, ctypes.c_int32, ctypes.c_int32, _dp, _ip,
+                                   _dp, ctypes.c_int32, _ip, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp,
+                                   _dp, _dp]
+    L.oc_tfm_loss_grad.restype = ctypes.c_double
+    L.oc_gae.argtypes = [ctypes.c_int32, ctypes.c_int32, _dp, _dp, _ip, ctypes.c_double, ctypes.c_double,
+                         _dp, _dp]
+    L.oc_state_tokens.argtypes = [ctypes.c_int32, _ip, _ip, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                  _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _ip]
     return v
 
 
@@ -407,3 +422,71 @@ def adam(theta, m, v, grad, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     th, mm, vv, gg = _f64(theta).copy(), _f64(m).copy(), _f64(v).copy(), _f64(grad)
     lib().oc_adam(len(th), _p(th), _p(mm), _p(vv), _p(gg), t, lr, beta1, beta2, eps)
     return th, mm, vv
+
+
+# --------------------------------------------------------------------------
+# TransfMAPPO training (actor and critic losses, GAE, critic tokens)
+# --------------------------------------------------------------------------
+ACTOR, CRITIC = 0, 1
+
+
+def tfm_param_count(d, n_layers, n_heads, n_out, n_in=8) -> int:
+    return int(lib().oc_tfm_param_count(ctypes.byref(OcPolicyDims(d, n_layers, n_heads, n_out, n_in))))
+
+
+def tfm_forward(params, d, n_layers, n_heads, n_out, tokens, n_ent, h_in):
+    """out [n, n_out], h_out [n, d] of the transformer (actor or critic)."""
+    if n_layers > 8:
+        raise ValueError("at most 8 blocks")
+    dims = OcPolicyDims(d, n_layers, n_heads, n_out, 8)
+    prm, tok, ne, h = _f64(params), _f64(tokens), _i32(n_ent), _f64(h_in)
+    n, ns, _ = tok.shape
+    out = np.zeros((n, n_out))
+    h_out = np.zeros((n, d))
+    lib().oc_tfm_forward(ctypes.byref(dims), _p(prm), n, ns, _p(tok), _p(ne, _ip), _p(h), _p(out), _p(h_out))
+    return out, h_out
+
+
+def tfm_loss_grad(params, d, n_layers, n_heads, n_out, kind, tokens, n_ent, h_in, actions=None, logp_old=None,
+                  adv=None, clip_eps=0.2, ent_coef=0.0, returns=None, want_grad=True):
+    """Mean loss, its gradient (or None) and the mean stats [loss, entropy
+    (actor) / V (critic), clipped fraction, approximate KL]."""
+    if n_layers > 8 or n_out > 64:
+        raise ValueError("at most 8 blocks and 64 outputs")
+    dims = OcPolicyDims(d, n_layers, n_heads, n_out, 8)
+    prm, tok, ne, h = _f64(params), _f64(tokens), _i32(n_ent), _f64(h_in)
+    n, ns, _ = tok.shape
+    act = None if actions is None else _i32(actions)
+    lo = None if logp_old is None else _f64(logp_old)
+    ad = None if adv is None else _f64(adv)
+    rt = None if returns is None else _f64(returns)
+    g = np.zeros_like(prm) if want_grad else None
+    st = np.zeros(4)
+    loss = lib().oc_tfm_loss_grad(ctypes.byref(dims), _p(prm), n, ns, _p(tok), _p(ne, _ip), _p(h), int(kind),
+                                  _p(act, _ip), _p(lo), _p(ad), float(clip_eps), float(ent_coef), _p(rt), _p(g),
+                                  _p(st))
+    return loss, g, st
+
+
+def gae(reward, value, done, gamma, lam):
+    """adv, ret [T, E] from reward, done [T, E] and value [T + 1, E]."""
+    r, v, dn = _f64(reward), _f64(value), _i32(done)
+    T, E = r.shape
+    assert v.shape == (T + 1, E) and dn.shape == (T, E)
+    adv, ret = np.zeros((T, E)), np.zeros((T, E))
+    lib().oc_gae(T, E, _p(r), _p(v), _p(dn, _ip), float(gamma), float(lam), _p(adv), _p(ret))
+    return adv, ret
+
+
+def state_tokens(env: "OracleEnv", n_slots=None):
+    """Critic tokens [E, n_slots, 8] and n_ent [E] from the env's true state."""
+    c = env.cfg
+    ns = n_slots or (c.max_agents + c.max_targets)
+    E = c.n_envs
+    tok = np.zeros((E, ns, 8))
+    ne = np.zeros(E, np.int32)
+    a = env.arr
+    lib().oc_state_tokens(E, _p(env.agent_off, _ip), _p(env.target_off, _ip), ns, float(c.feature_scale),
+                          float(c.agent_speed), _p(a["ax"]), _p(a["ay"]), _p(a["apsi"]), _p(a["tx"]), _p(a["ty"]),
+                          _p(a["tz"]), _p(a["tpsi"]), _p(a["tspeed"]), _p(tok), _p(ne, _ip))
+    return tok, ne
