@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define UT_ABI_VERSION 7u
+#define UT_ABI_VERSION 8u
 #define UT_MAX_AGENTS 8      /* per environment */
 #define UT_MAX_TARGETS 8     /* per environment */
 #define UT_MAX_PARTICLES 4096
@@ -467,6 +467,136 @@ ut_status tracker_update_noalloc(const ut_config* cfg, uint64_t seed, uint32_t s
                                  const float* ay_dev, const float* tx_dev, const float* ty_dev, const float* tz_dev,
                                  float* px_dev, float* py_dev, float* pvx_dev, float* pvy_dev, float* estx_dev,
                                  float* esty_dev, float* err_dev, void* cuda_stream);
+
+/* ---------------------------------------------------------------------- */
+/* TransfMAPPO training (Sec. II-B: MAPPO, PPO's clipped surrogate for the  */
+/* actors and one centralized critic V(S) on the global state; Sec. III-B.1 */
+/* and Fig. 3: TransformerAgent and TransformerCritic, one architecture,    */
+/* the critic fed the true position, velocity and heading of every entity   */
+/* and keeping its own recurrent embedding).                               */
+/*                                                                          */
+/* A ut_tfm handle holds one transformer in FP32 for training — the actor  */
+/* (n_out = n_actions, same parameter layout as env_set_policy) or the      */
+/* critic (n_out = 1) — with its Adam moments and the activation buffers of */
+/* up to max_batch samples.  A sample is n_slots entity tokens of 8 values  */
+/* (the first n_ent of them in use) plus a recurrent embedding h of d_model */
+/* floats at token 0; the network is the agent's (pre-LN blocks, FFN 4d     */
+/* with erf-GELU, LayerNorm epsilon 1e-5, final LayerNorm and a linear head */
+/* on token 0).  Readings: the recurrent input is data (no backpropagation  */
+/* through time); PPO per sample L = -min(r A, clip(r, 1-eps, 1+eps) A)     */
+/* - ent_coef H(pi) with r = exp(log pi(a) - log pi_old(a)) (Schulman et    */
+/* al. 2017, Eq. 7 and 9); value loss (V - R)^2; batch losses are means.    */
+/* Calls are enqueued on the handle's stream; those that return statistics */
+/* to a host pointer synchronise.  Not thread-safe.                         */
+/* ---------------------------------------------------------------------- */
+typedef struct ut_tfm ut_tfm;
+
+typedef struct ut_tfm_config {
+  uint32_t abi_version;  /* must be UT_ABI_VERSION */
+  int32_t d_model;       /* 32, 64, 96 or 128 */
+  int32_t n_layers;      /* 1 .. 8 */
+  int32_t n_heads;       /* head width d_model / n_heads in {8, 16, 32} */
+  int32_t n_out;         /* 1 .. 16 head outputs */
+  int32_t n_slots;       /* entity token slots per sample, 1 .. UT_MAX_AGENTS + UT_MAX_TARGETS */
+  int32_t tokens_bf16;   /* 1: tokens are BF16 (the observation tokens), 0: FP32 */
+  int32_t reserved;
+  int64_t max_batch;     /* samples per call, 1 .. 2^22 */
+} ut_tfm_config;
+
+/* Number of parameters of the configuration (canonical order of
+ * env_set_policy with n_actions = n_out), or -1 if it is invalid. */
+int64_t tfm_param_count(const ut_tfm_config* cfg);
+
+/* Creates the handle on cuda_stream with a copy of params_host (n_params
+ * floats, canonical order) as the FP32 master weights and zero Adam moments.
+ * Device memory: about (16 d + 8) x 4 bytes per token row per block plus
+ * the backward buffers, for max_batch x (1 + n_slots) rows.
+ * Errors: UT_ERR_INVALID (configuration or count), UT_ERR_NOMEM, UT_ERR_CUDA. */
+ut_status tfm_create(const ut_tfm_config* cfg, const float* params_host, int64_t n_params, void* cuda_stream,
+                     ut_tfm** out);
+void tfm_destroy(ut_tfm* t);
+const char* tfm_last_error(const ut_tfm* t);
+
+/* Borrowed device pointer to the FP32 master weights (n_params floats),
+ * valid until tfm_destroy; writes through it change the network. */
+ut_status tfm_params(ut_tfm* t, float** params_dev);
+
+/* Forward of n samples (1 .. max_batch).  Sample s reads batch row
+ * b = sel_dev ? sel_dev[s] : s of: tokens_dev [.][n_slots][8] (FP32, or BF16
+ * when tokens_bf16), n_ent_dev [.] (clamped to 0 .. n_slots) and h_dev
+ * [.][d_model] FP32.  Writes out_dev [n][n_out] and, if h_out_dev is not
+ * NULL, h_out_dev [n][d_model] = the residual stream at token 0 after the
+ * last block (the next recurrent embedding).  h_out_dev may equal h_dev
+ * when sel_dev is NULL.  Errors: UT_ERR_INVALID, UT_ERR_CUDA. */
+ut_status tfm_forward(ut_tfm* t, const void* tokens_dev, const int32_t* n_ent_dev, const float* h_dev,
+                      const int32_t* sel_dev, int64_t n, float* out_dev, float* h_out_dev);
+
+/* PPO actor loss over n samples (rows selected as in tfm_forward) and its
+ * gradient: actions_dev [.] in 0 .. n_out-1, logp_old_dev [.] the behaviour
+ * policy's log-probability of the action, adv_dev [.] advantages;
+ * clip_eps > 0, ent_coef >= 0.  grad_dev [n_params] is overwritten with the
+ * gradient of the mean loss.  stats_host (optional; NULL keeps the call
+ * asynchronous) receives the means of [loss, entropy, clipped fraction
+ * (|r - 1| > eps), log pi_old - log pi].  Errors: UT_ERR_INVALID (also for
+ * a handle with n_out < 2), UT_ERR_CUDA. */
+ut_status tfm_ppo_actor_grad(ut_tfm* t, const void* tokens_dev, const int32_t* n_ent_dev, const float* h_dev,
+                             const int32_t* sel_dev, int64_t n, const int32_t* actions_dev,
+                             const float* logp_old_dev, const float* adv_dev, float clip_eps, float ent_coef,
+                             float* grad_dev, double* stats_host);
+
+/* Critic loss mean (V - R)^2 over n samples against returns_dev [.] and its
+ * gradient (grad_dev [n_params], overwritten).  stats_host (optional)
+ * receives the means of [loss, V, 0, 0].  Errors: UT_ERR_INVALID (also for a
+ * handle with n_out != 1), UT_ERR_CUDA. */
+ut_status tfm_value_grad(ut_tfm* t, const void* tokens_dev, const int32_t* n_ent_dev, const float* h_dev,
+                         const int32_t* sel_dev, int64_t n, const float* returns_dev, float* grad_dev,
+                         double* stats_host);
+
+/* One Adam step (Kingma & Ba 2015, Algorithm 1, with bias correction) on the
+ * master weights from grad_dev [n_params]: lr >= 0, beta1 and beta2 in
+ * [0, 1), eps > 0.  Errors: UT_ERR_INVALID, UT_ERR_CUDA. */
+ut_status tfm_adam_step(ut_tfm* t, const float* grad_dev, float lr, float beta1, float beta2, float eps);
+
+/* Copies the actor's master weights into env's transformer agent (as
+ * env_set_policy: matrices rounded to BF16 and packed); the configuration
+ * must match the env's (d_model, n_layers, n_heads, n_out = n_actions).
+ * Synchronises both streams.  Errors: UT_ERR_INVALID, UT_ERR_STATE,
+ * UT_ERR_UNSUPPORTED (as env_set_policy), UT_ERR_CUDA. */
+ut_status tfm_sync_policy(ut_tfm* t, ut_env* env);
+
+/* Generalized advantage estimation (Schulman et al. 2016, Eq. 16) by the
+ * backward recursion A_t = delta_t + gamma lambda (1 - done_t) A_{t+1},
+ * delta_t = r_t + gamma (1 - done_t) V_{t+1} - V_t, and R_t = A_t + V_t:
+ * reward_dev, done_dev [T][E] (done_t = 1 when step t ended an episode),
+ * value_dev [T+1][E] (the last row bootstraps); adv_dev, ret_dev [T][E].
+ * If agent_env_dev [NA] (the env of each agent) and adv_agent_dev [T][NA]
+ * are given, the env's advantage is also written for each of its agents.
+ * FP32 arithmetic, one thread per env.  Enqueued on cuda_stream.
+ * Errors: UT_ERR_INVALID, UT_ERR_CUDA. */
+ut_status ppo_gae(const float* reward_dev, const float* value_dev, const int32_t* done_dev, int32_t T, int64_t E,
+                  float gamma, float lam, float* adv_dev, float* ret_dev, const int32_t* agent_env_dev, int64_t NA,
+                  float* adv_agent_dev, void* cuda_stream);
+
+/* Critic tokens of every env from the true state (Sec. III-A: the global
+ * state holds the true 3-D position, velocity and direction of each
+ * entity): tokens_dev [E][A_max + T_max][8] FP32, agents then targets packed
+ * from slot 0, each [x/S, y/S, z/S, vx, vy, cos psi, sin psi, kind] with S =
+ * feature_scale, velocity in m/s (agents at depth 0 moving at agent_speed)
+ * and kind 1 for an agent, 0 for a target; zero padding; n_ent_dev [E] =
+ * A_e + T_e.  Enqueued on the env's stream.  Errors: UT_ERR_INVALID. */
+ut_status env_state_tokens(ut_env* env, float* tokens_dev, int32_t* n_ent_dev);
+
+/* Rollout recording for the PPO batch, on the env's stream.
+ * env_ppo_snapshot, before env_step: the agents' current observation
+ * tokens (the policy's input) to tokens_dev [NA][A_max + T_max][8] BF16,
+ * their entity counts to n_ent_dev [NA] and the recurrent embedding (BF16)
+ * to h_dev [NA][d_model] FP32.  env_ppo_record, after an env_step whose
+ * actions the transformer agent drew: actions_dev [NA], logp_dev [NA] =
+ * log-softmax of the agent's logits at its action, reward_dev [E],
+ * done_dev [E].  Each pointer may be NULL (not recorded).
+ * Errors: UT_ERR_STATE (no transformer agent), UT_ERR_INVALID, UT_ERR_CUDA. */
+ut_status env_ppo_snapshot(ut_env* env, uint16_t* tokens_dev, int32_t* n_ent_dev, float* h_dev);
+ut_status env_ppo_record(ut_env* env, int32_t* actions_dev, float* logp_dev, float* reward_dev, int32_t* done_dev);
 
 #ifdef __cplusplus
 }

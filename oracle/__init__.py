@@ -478,15 +478,22 @@ def gae(reward, value, done, gamma, lam):
     return adv, ret
 
 
+def state_tokens_arrays(agent_off, target_off, n_slots, S, agent_speed, ax, ay, apsi, tx, ty, tz, tpsi, tspeed):
+    """Critic tokens [E, n_slots, 8] and n_ent [E] from state arrays."""
+    ao, to = _i32(agent_off), _i32(target_off)
+    E = len(ao) - 1
+    arrs = [_f64(a) for a in (ax, ay, apsi, tx, ty, tz, tpsi, tspeed)]
+    tok = np.zeros((E, n_slots, 8))
+    ne = np.zeros(E, np.int32)
+    lib().oc_state_tokens(E, _p(ao, _ip), _p(to, _ip), n_slots, float(S), float(agent_speed),
+                          *[_p(a) for a in arrs], _p(tok), _p(ne, _ip))
+    return tok, ne
+
+
 def state_tokens(env: "OracleEnv", n_slots=None):
     """Critic tokens [E, n_slots, 8] and n_ent [E] from the env's true state."""
     c = env.cfg
-    ns = n_slots or (c.max_agents + c.max_targets)
-    E = c.n_envs
-    tok = np.zeros((E, ns, 8))
-    ne = np.zeros(E, np.int32)
     a = env.arr
-    lib().oc_state_tokens(E, _p(env.agent_off, _ip), _p(env.target_off, _ip), ns, float(c.feature_scale),
-                          float(c.agent_speed), _p(a["ax"]), _p(a["ay"]), _p(a["apsi"]), _p(a["tx"]), _p(a["ty"]),
-                          _p(a["tz"]), _p(a["tpsi"]), _p(a["tspeed"]), _p(tok), _p(ne, _ip))
-    return tok, ne
+    return state_tokens_arrays(env.agent_off, env.target_off, n_slots or (c.max_agents + c.max_targets),
+                               c.feature_scale, c.agent_speed, a["ax"], a["ay"], a["apsi"], a["tx"], a["ty"],
+                               a["tz"], a["tpsi"], a["tspeed"])

@@ -432,38 +432,41 @@ double oc_tfm_loss_grad(const oc_tfm_dims* p, const double* params, int32_t n, i
                         const double* logp_old, const double* adv, double clip_eps, double ent_coef,
                         const double* ret, double* grad, double* stats) {
   const int64_t np = oc_tfm_param_count(p);
+  enum { BLK = 16 };
   tfm_view v = tfm_split(p, params);
-  double* gpart = grad ? (double*)xmalloc(sizeof(double) * np * n) : NULL;
-  double* st = (double*)xmalloc(sizeof(double) * 4 * n);
+  /* per-sample gradients of blocks of BLK samples, added in sample order */
+  double* gpart = grad ? (double*)xmalloc(sizeof(double) * np * BLK) : NULL;
+  double* st = (double*)xmalloc(sizeof(double) * 4 * (n > 0 ? n : 1));
+  if (grad) memset(grad, 0, sizeof(double) * np);
+  for (int i0 = 0; i0 < n; i0 += BLK) {
+    const int i1 = i0 + BLK < n ? i0 + BLK : n;
+    if (gpart) memset(gpart, 0, sizeof(double) * np * BLK);
 #pragma omp parallel for schedule(dynamic, 1)
-  for (int i = 0; i < n; ++i) {
-    tfm_cache c;
-    double dout[64];
-    int ne = n_ent[i] < 0 ? 0 : (n_ent[i] > n_slots ? n_slots : n_ent[i]);
-    const double* tok = tokens + (int64_t)i * n_slots * p->n_in;
-    cache_alloc(p, 1 + ne, &c);
-    tfm_fwd(p, &v, tok, h_in + (int64_t)i * p->d, &c);
-    head_loss(kind, p->n_out, c.out, actions ? actions[i] : 0, logp_old ? logp_old[i] : 0.0, adv ? adv[i] : 0.0,
-              clip_eps, ent_coef, ret ? ret[i] : 0.0, dout, st + 4 * i);
-    if (gpart) {
-      for (int j = 0; j < p->n_out; ++j) dout[j] /= n;
-      tfm_gview g = tfm_gsplit(p, gpart + (int64_t)i * np);
-      tfm_bwd(p, &v, tok, &c, dout, &g);
+    for (int i = i0; i < i1; ++i) {
+      tfm_cache c;
+      double dout[64];
+      int ne = n_ent[i] < 0 ? 0 : (n_ent[i] > n_slots ? n_slots : n_ent[i]);
+      const double* tok = tokens + (int64_t)i * n_slots * p->n_in;
+      cache_alloc(p, 1 + ne, &c);
+      tfm_fwd(p, &v, tok, h_in + (int64_t)i * p->d, &c);
+      head_loss(kind, p->n_out, c.out, actions ? actions[i] : 0, logp_old ? logp_old[i] : 0.0, adv ? adv[i] : 0.0,
+                clip_eps, ent_coef, ret ? ret[i] : 0.0, dout, st + 4 * i);
+      if (gpart) {
+        for (int j = 0; j < p->n_out; ++j) dout[j] /= n;
+        tfm_gview g = tfm_gsplit(p, gpart + (int64_t)(i - i0) * np);
+        tfm_bwd(p, &v, tok, &c, dout, &g);
+      }
+      cache_free(p, &c);
     }
-    cache_free(p, &c);
+    if (grad)
+      for (int i = i0; i < i1; ++i)
+        for (int64_t j = 0; j < np; ++j) grad[j] += gpart[(int64_t)(i - i0) * np + j];
   }
+  free(gpart);
   /* sums in sample order (deterministic) */
   double acc[4] = {0, 0, 0, 0};
   for (int i = 0; i < n; ++i)
     for (int k = 0; k < 4; ++k) acc[k] += st[4 * i + k];
-  if (grad) {
-    for (int64_t j = 0; j < np; ++j) {
-      double s = 0.0;
-      for (int i = 0; i < n; ++i) s += gpart[(int64_t)i * np + j];
-      grad[j] = s;
-    }
-    free(gpart);
-  }
   free(st);
   if (stats)
     for (int k = 0; k < 4; ++k) stats[k] = acc[k] / n;

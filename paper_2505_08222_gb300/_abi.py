@@ -7,7 +7,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libutrack.so")
 
-UT_ABI_VERSION = 7
+UT_ABI_VERSION = 8
 UT_FLAG_DEBUG = 1
 UT_FLAG_RING = 2
 
@@ -90,6 +90,12 @@ class EstTrainStats(ctypes.Structure):
                 ("rows_seen", ctypes.c_int64)]
 
 
+class TfmConfig(ctypes.Structure):
+    _fields_ = [("abi_version", ctypes.c_uint32), ("d_model", ctypes.c_int32), ("n_layers", ctypes.c_int32),
+                ("n_heads", ctypes.c_int32), ("n_out", ctypes.c_int32), ("n_slots", ctypes.c_int32),
+                ("tokens_bf16", ctypes.c_int32), ("reserved", ctypes.c_int32), ("max_batch", ctypes.c_int64)]
+
+
 class RolloutStats(ctypes.Structure):
     _fields_ = [("sum_sq_err", ctypes.c_double), ("n_err", ctypes.c_int64), ("rmse", ctypes.c_double),
                 ("reward_sum", ctypes.c_double), ("crash_count", ctypes.c_int64),
@@ -138,6 +144,23 @@ SIGNATURES = {
     "tc_gemm_bf16": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp]),
     "tracker_update_noalloc": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_uint64, ctypes.c_uint32] + [_vp] * 13),
     "pf_resample": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_int32, _vp, _vp]),
+    "tfm_param_count": (ctypes.c_int64, [ctypes.POINTER(TfmConfig)]),
+    "tfm_create": (ctypes.c_int, [ctypes.POINTER(TfmConfig), _vp, ctypes.c_int64, _vp, ctypes.POINTER(_vp)]),
+    "tfm_destroy": (None, [_vp]),
+    "tfm_last_error": (ctypes.c_char_p, [_vp]),
+    "tfm_params": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
+    "tfm_forward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp]),
+    "tfm_ppo_actor_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp, ctypes.c_float,
+                                          ctypes.c_float, _vp, ctypes.POINTER(ctypes.c_double)]),
+    "tfm_value_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp,
+                                      ctypes.POINTER(ctypes.c_double)]),
+    "tfm_adam_step": (ctypes.c_int, [_vp, _vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+    "tfm_sync_policy": (ctypes.c_int, [_vp, _vp]),
+    "ppo_gae": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_float, _vp,
+                               _vp, _vp, ctypes.c_int64, _vp, _vp]),
+    "env_state_tokens": (ctypes.c_int, [_vp, _vp, _vp]),
+    "env_ppo_snapshot": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "env_ppo_record": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
 }
 
 _lib = None

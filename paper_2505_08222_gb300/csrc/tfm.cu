@@ -1,0 +1,1221 @@
+// Transformer actor and critic in FP32 for the TransfMAPPO update (Sec. II-B,
+// Sec. III-B.1, Fig. 3): the forward pass with stored activations, the PPO
+// clipped-surrogate and value losses, the backward pass, Adam, and
+// generalized advantage estimation.
+//
+// Layout: sample s of a call occupies token rows s*T .. s*T+T-1 (T = 1 +
+// n_slots, row 0 its recurrent embedding); every activation is row-major
+// [rows][width].  Rows past a sample's entity count are computed (from the
+// embedding bias alone) but no row attends to them, so they receive exactly
+// zero gradient and add nothing to the weight gradients.
+//
+// The dense contractions run on CUDA cores in FP32 (a 64 x 64 register-tiled
+// GEMM); the weight gradients are split along the token rows into partial
+// slabs summed in a fixed order, so every result is deterministic.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/utrack.h"
+#include "common.cuh"
+
+namespace ut {
+namespace tfm {
+
+constexpr int kMaxT = 1 + UT_MAX_AGENTS + UT_MAX_TARGETS;  // tokens per sample
+constexpr int kRowBlocks = 304;                             // blocks of the warp-per-row kernels
+constexpr int kRowWarps = kRowBlocks * 8;                   // warps writing partial sums
+
+enum { EPI_STORE = 0, EPI_BIAS = 1, EPI_BIAS_RES = 2, EPI_BIAS_GELU = 3, EPI_GELU_GRAD = 4, EPI_PARTIAL = 5 };
+
+// C = op(A) op(B) with an epilogue.  A(m, k) is A[m * lda + k] when AK (k
+// contiguous), else A[k * lda + m]; B(k, n) is B[n * ldb + k] when BK, else
+// B[k * ldb + n].  blockIdx.z takes K range [z * kchunk, (z + 1) * kchunk).
+struct Gemm {
+  const float* A;
+  long long lda;
+  const float* B;
+  long long ldb;
+  float* C;
+  long long ldc;
+  long long M, K, kchunk;
+  int N, epi;
+  const float* bias;   // [N] (EPI_BIAS*)
+  const float* R;      // residual added (EPI_BIAS_RES), ld = ldc
+  float* C2;           // GELU of the output (EPI_BIAS_GELU), ld = ldc
+  const float* aux;    // pre-activation whose GELU derivative scales the output (EPI_GELU_GRAD), ld = ldc
+};
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// 64 x 64 output tile per CTA of 256 threads, 4 x 4 outputs per thread,
+// K staged 16 at a time through shared memory.
+template <bool AK, bool BK>
+__global__ void __launch_bounds__(256) sgemm_kernel(Gemm g) {
+  __shared__ __align__(16) float As[16][68];
+  __shared__ __align__(16) float Bs[16][68];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const long long m0 = (long long)blockIdx.x * 64;
+  const int n0 = blockIdx.y * 64;
+  const long long kb = (long long)blockIdx.z * g.kchunk;
+  const long long ke = kb + g.kchunk < g.K ? kb + g.kchunk : g.K;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+  for (long long k0 = kb; k0 < ke; k0 += 16) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = tid + r * 256;
+      const int mm = AK ? (i >> 4) : (i & 63), kk = AK ? (i & 15) : (i >> 6);
+      const long long m = m0 + mm, k = k0 + kk;
+      float v = 0.0f;
+      if (m < g.M && k < ke) v = AK ? g.A[m * g.lda + k] : g.A[k * g.lda + m];
+      As[kk][mm] = v;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = tid + r * 256;
+      const int nn = BK ? (i >> 4) : (i & 63), kk = BK ? (i & 15) : (i >> 6);
+      const long long k = k0 + kk;
+      const int n = n0 + nn;
+      float v = 0.0f;
+      if (n < g.N && k < ke) v = BK ? g.B[(long long)n * g.ldb + k] : g.B[k * g.ldb + n];
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const long long m = m0 + ty * 4 + i;
+    if (m >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx * 4 + j;
+      if (n >= g.N) continue;
+      float v = acc[i][j];
+      const long long o = m * g.ldc + n;
+      switch (g.epi) {
+        case EPI_BIAS:
+          g.C[o] = v + g.bias[n];
+          break;
+        case EPI_BIAS_RES:
+          g.C[o] = v + g.bias[n] + g.R[o];
+          break;
+        case EPI_BIAS_GELU:
+          v += g.bias[n];
+          g.C[o] = v;
+          g.C2[o] = gelu_f(v);
+          break;
+        case EPI_GELU_GRAD:
+          g.C[o] = v * gelu_grad_f(g.aux[o]);
+          break;
+        case EPI_PARTIAL:
+          g.C[((long long)blockIdx.z * g.M + m) * g.N + n] = v;
+          break;
+        default:
+          g.C[o] = v;
+      }
+    }
+  }
+}
+
+// Embedding of the entity tokens; token 0 of each sample is its recurrent
+// embedding.  One thread per output value.
+template <typename TokT>
+__global__ void embed_kernel(const TokT* __restrict__ tok, const int32_t* __restrict__ n_ent,
+                             const float* __restrict__ h, const int32_t* __restrict__ sel,
+                             const float* __restrict__ W, const float* __restrict__ b, float* __restrict__ X,
+                             long long n, int T, int NS, int d) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * T * d) return;
+  const int j = (int)(i % d);
+  const long long row = i / d;
+  const long long s = row / T;
+  const int t = (int)(row - s * T);
+  const long long bs = sel ? (long long)sel[s] : s;
+  if (t == 0) {
+    X[i] = h[bs * d + j];
+    return;
+  }
+  int ne = n_ent[bs];
+  ne = ne < 0 ? 0 : (ne > NS ? NS : ne);
+  float acc = b[j];
+  if (t <= ne) {
+    const TokT* q = tok + (bs * NS + (t - 1)) * 8;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc = fmaf(W[j * 8 + k], (float)q[k], acc);
+  }
+  X[i] = acc;
+}
+
+// LayerNorm forward, one warp per row: Y = (X - mean) rstd g + b and the row's
+// (mean, rstd).
+template <int DJ>
+__global__ void ln_fwd_kernel(const float* __restrict__ X, const float* __restrict__ gam,
+                              const float* __restrict__ bet, float* __restrict__ Y, float* __restrict__ stat,
+                              long long rows) {
+  constexpr int d = 32 * DJ;
+  const int lane = threadIdx.x & 31;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long r = w0; r < rows; r += nw) {
+    float x[DJ], s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < DJ; ++i) {
+      x[i] = X[r * d + lane + 32 * i];
+      s += x[i];
+    }
+    const float mean = warp_sum(s) * (1.0f / d);
+    float v = 0.0f;
+#pragma unroll
+    for (int i = 0; i < DJ; ++i) v += (x[i] - mean) * (x[i] - mean);
+    const float rstd = 1.0f / sqrtf(warp_sum(v) * (1.0f / d) + 1e-5f);
+#pragma unroll
+    for (int i = 0; i < DJ; ++i) {
+      const int j = lane + 32 * i;
+      Y[r * d + j] = (x[i] - mean) * rstd * gam[j] + bet[j];
+    }
+    if (lane == 0) {
+      stat[2 * r] = mean;
+      stat[2 * r + 1] = rstd;
+    }
+  }
+}
+
+// LayerNorm backward, one warp per row: out = base + dL/dX from dY (the
+// gradient at the LayerNorm output), and per-warp partial sums of dL/dg
+// (sum dY xh) and dL/db (sum dY) into part[warp][2d].  out may equal base.
+template <int DJ>
+__global__ void ln_bwd_kernel(const float* __restrict__ dY, const float* __restrict__ X,
+                              const float* __restrict__ stat, const float* __restrict__ gam, const float* base,
+                              float* out, float* __restrict__ part, long long rows) {
+  constexpr int d = 32 * DJ;
+  const int lane = threadIdx.x & 31;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  float pg[DJ], pb[DJ];
+#pragma unroll
+  for (int i = 0; i < DJ; ++i) pg[i] = pb[i] = 0.0f;
+  for (long long r = w0; r < rows; r += nw) {
+    const float mean = stat[2 * r], rstd = stat[2 * r + 1];
+    float xh[DJ], dxh[DJ], m1 = 0.0f, m2 = 0.0f;
+#pragma unroll
+    for (int i = 0; i < DJ; ++i) {
+      const int j = lane + 32 * i;
+      const float dy = dY[r * d + j];
+      xh[i] = (X[r * d + j] - mean) * rstd;
+      dxh[i] = dy * gam[j];
+      pg[i] = fmaf(dy, xh[i], pg[i]);
+      pb[i] += dy;
+      m1 += dxh[i];
+      m2 = fmaf(dxh[i], xh[i], m2);
+    }
+    m1 = warp_sum(m1) * (1.0f / d);
+    m2 = warp_sum(m2) * (1.0f / d);
+#pragma unroll
+    for (int i = 0; i < DJ; ++i) {
+      const long long o = r * d + lane + 32 * i;
+      out[o] = base[o] + rstd * (dxh[i] - m1 - xh[i] * m2);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < DJ; ++i) {
+    part[w0 * 2 * d + lane + 32 * i] = pg[i];
+    part[w0 * 2 * d + d + lane + 32 * i] = pb[i];
+  }
+}
+
+// Self-attention of one (sample, head) per warp, lane t = query token t:
+// P[s][head][t][u] (zero for masked keys u > n_ent) and O = P V.
+template <int DH>
+__global__ void attn_fwd_kernel(const float* __restrict__ QKV, const int32_t* __restrict__ n_ent,
+                                const int32_t* __restrict__ sel, float* __restrict__ P, float* __restrict__ O,
+                                long long n, int T, int NS, int H, float scale) {
+  const int lane = threadIdx.x & 31;
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= n * H) return;
+  const long long s = w / H;
+  const int hh = (int)(w - s * H);
+  const int d = DH * H, ld = 3 * d;
+  int ne = n_ent[sel ? (long long)sel[s] : s];
+  ne = ne < 0 ? 0 : (ne > NS ? NS : ne);
+  if (lane >= T) return;
+  const float* base = QKV + s * T * ld + hh * DH;
+  float q[DH];
+#pragma unroll
+  for (int j = 0; j < DH; ++j) q[j] = base[lane * ld + j];
+  float sc[kMaxT];
+  float mx = -INFINITY;
+#pragma unroll
+  for (int u = 0; u < kMaxT; ++u) {
+    sc[u] = -INFINITY;
+    if (u < T && u <= ne) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int j = 0; j < DH; ++j) acc = fmaf(q[j], base[u * ld + d + j], acc);
+      sc[u] = acc * scale;
+      mx = fmaxf(mx, sc[u]);
+    }
+  }
+  float z = 0.0f;
+#pragma unroll
+  for (int u = 0; u < kMaxT; ++u) {
+    const float e = (u < T && u <= ne) ? expf(sc[u] - mx) : 0.0f;
+    sc[u] = e;
+    z += e;
+  }
+  const float iz = 1.0f / z;
+  float o[DH];
+#pragma unroll
+  for (int j = 0; j < DH; ++j) o[j] = 0.0f;
+  float* Pr = P + ((s * H + hh) * T + lane) * T;
+#pragma unroll
+  for (int u = 0; u < kMaxT; ++u) {
+    if (u < T) {
+      const float p = sc[u] * iz;
+      Pr[u] = p;
+      if (u <= ne) {
+#pragma unroll
+        for (int j = 0; j < DH; ++j) o[j] = fmaf(p, base[u * ld + 2 * d + j], o[j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < DH; ++j) O[(s * T + lane) * d + hh * DH + j] = o[j];
+}
+
+// Attention backward of one (sample, head) per warp: from dO and the stored
+// P, dS = P (dP - rowsum(P dP)) scale with dP = dO V^T; lane t writes dQ_t,
+// then lane u writes dK_u = sum_t dS_tu Q_t and dV_u = sum_t P_tu dO_t.
+template <int DH>
+__global__ void __launch_bounds__(256) attn_bwd_kernel(const float* __restrict__ QKV, const float* __restrict__ P,
+                                                       const float* __restrict__ dO, float* __restrict__ dQKV,
+                                                       long long n, int T, int H, float scale) {
+  __shared__ float sdS[8][kMaxT * kMaxT];
+  __shared__ float sP[8][kMaxT * kMaxT];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= n * H) return;  // whole warps leave together
+  const long long s = w / H;
+  const int hh = (int)(w - s * H);
+  const int d = DH * H, ld = 3 * d;
+  const float* base = QKV + s * T * ld + hh * DH;
+  const float* dOb = dO + s * T * d + hh * DH;
+  float* out = dQKV + s * T * ld + hh * DH;
+  const float* Pb = P + (s * H + hh) * T * T;
+  if (lane < T) {
+    float g[DH];
+#pragma unroll
+    for (int j = 0; j < DH; ++j) g[j] = dOb[lane * d + j];
+    float p[kMaxT], dp[kMaxT], dot = 0.0f;
+#pragma unroll
+    for (int u = 0; u < kMaxT; ++u) {
+      p[u] = dp[u] = 0.0f;
+      if (u < T) {
+        p[u] = Pb[lane * T + u];
+        sP[wl][lane * T + u] = p[u];
+        float acc = 0.0f;
+#pragma unroll
+        for (int j = 0; j < DH; ++j) acc = fmaf(g[j], base[u * ld + 2 * d + j], acc);
+        dp[u] = acc;
+        dot = fmaf(p[u], acc, dot);
+      }
+    }
+    float dq[DH];
+#pragma unroll
+    for (int j = 0; j < DH; ++j) dq[j] = 0.0f;
+#pragma unroll
+    for (int u = 0; u < kMaxT; ++u) {
+      if (u < T) {
+        const float ds = p[u] * (dp[u] - dot) * scale;
+        sdS[wl][lane * T + u] = ds;
+#pragma unroll
+        for (int j = 0; j < DH; ++j) dq[j] = fmaf(ds, base[u * ld + d + j], dq[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < DH; ++j) out[lane * ld + j] = dq[j];
+  }
+  __syncwarp();
+  if (lane < T) {
+    float dk[DH], dv[DH];
+#pragma unroll
+    for (int j = 0; j < DH; ++j) dk[j] = dv[j] = 0.0f;
+    for (int t = 0; t < T; ++t) {
+      const float ds = sdS[wl][t * T + lane], p = sP[wl][t * T + lane];
+#pragma unroll
+      for (int j = 0; j < DH; ++j) {
+        dk[j] = fmaf(ds, base[t * ld + j], dk[j]);
+        dv[j] = fmaf(p, dOb[t * d + j], dv[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < DH; ++j) {
+      out[lane * ld + d + j] = dk[j];
+      out[lane * ld + 2 * d + j] = dv[j];
+    }
+  }
+}
+
+struct HeadArgs {
+  const float* XL;  // [rows][d] residual stream after the last block
+  long long n;
+  int T, n_out, mode;  // mode 0: forward, 1: PPO actor loss, 2: value loss
+  const float *lnf_g, *lnf_b, *Wh, *bh;
+  float* out;        // [n][n_out] (mode 0)
+  float* h_out;      // [n][d] (mode 0, optional)
+  const int32_t* sel;
+  const int32_t* actions;
+  const float *logp_old, *adv, *ret;
+  float clip_eps, ent_coef, inv_n;
+  float* dXL;        // [rows][d] (modes 1, 2): token 0 gets the gradient, the other rows zero
+  float* part;       // [warps][2d + n_out d + n_out]: lnf_g, lnf_b, Wh, bh partial gradients
+  double* spart;     // [warps][4] partial sums of the per-sample statistics
+};
+
+// Final LayerNorm and head on token 0, one warp per sample; in the loss modes
+// also the loss, dL/d(head output), the head's and final LayerNorm's
+// backward, and per-warp partial sums of their parameter gradients.
+template <int DJ, int NO>
+__global__ void __launch_bounds__(256) head_kernel(HeadArgs a) {
+  constexpr int d = 32 * DJ;
+  const int lane = threadIdx.x & 31;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int no = a.n_out;
+  float gW[NO][DJ], gB[NO], gg[DJ], gb[DJ];
+#pragma unroll
+  for (int o = 0; o < NO; ++o) {
+    gB[o] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < DJ; ++i) gW[o][i] = 0.0f;
+  }
+#pragma unroll
+  for (int i = 0; i < DJ; ++i) gg[i] = gb[i] = 0.0f;
+  double st[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long long s = w0; s < a.n; s += nw) {
+    const float* x0 = a.XL + s * a.T * d;
+    float x[DJ], xh[DJ], U[DJ], sum = 0.0f;
+#pragma unroll
+    for (int i = 0; i < DJ; ++i) {
+      x[i] = x0[lane + 32 * i];
+      sum += x[i];
+    }
+    const float mean = warp_sum(sum) * (1.0f / d);
+    float v = 0.0f;
+#pragma unroll
+    for (int i = 0; i < DJ; ++i) v += (x[i] - mean) * (x[i] - mean);
+    const float rstd = 1.0f / sqrtf(warp_sum(v) * (1.0f / d) + 1e-5f);
+#pragma unroll
+    for (int i = 0; i < DJ; ++i) {
+      const int j = lane + 32 * i;
+      xh[i] = (x[i] - mean) * rstd;
+      U[i] = xh[i] * a.lnf_g[j] + a.lnf_b[j];
+    }
+    float z[NO];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      z[o] = 0.0f;
+      if (o < no) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int i = 0; i < DJ; ++i) acc = fmaf(a.Wh[o * d + lane + 32 * i], U[i], acc);
+        z[o] = warp_sum(acc) + a.bh[o];
+      }
+    }
+    if (a.mode == 0) {
+      if (lane < no) {
+#pragma unroll
+        for (int o = 0; o < NO; ++o)
+          if (o == lane) a.out[s * no + o] = z[o];
+      }
+      if (a.h_out)
+#pragma unroll
+        for (int i = 0; i < DJ; ++i) a.h_out[s * d + lane + 32 * i] = x[i];
+      continue;
+    }
+    const long long bs = a.sel ? (long long)a.sel[s] : s;
+    float dz[NO];
+    if (a.mode == 2) {
+      const float e = z[0] - a.ret[bs];
+#pragma unroll
+      for (int o = 0; o < NO; ++o) dz[o] = 0.0f;
+      dz[0] = 2.0f * e * a.inv_n;
+      st[0] += (double)e * e;
+      st[1] += (double)z[0];
+    } else {
+      float mx = -INFINITY;
+#pragma unroll
+      for (int o = 0; o < NO; ++o)
+        if (o < no) mx = fmaxf(mx, z[o]);
+      float zs = 0.0f;
+#pragma unroll
+      for (int o = 0; o < NO; ++o)
+        if (o < no) zs += expf(z[o] - mx);
+      const float lse = mx + logf(zs);
+      const int act = a.actions[bs];
+      float ent = 0.0f, lpa = 0.0f;
+#pragma unroll
+      for (int o = 0; o < NO; ++o)
+        if (o < no) {
+          const float lp = z[o] - lse;
+          ent -= expf(lp) * lp;
+          if (o == act) lpa = lp;
+        }
+      const float A = a.adv[bs], lo = a.logp_old[bs];
+      const float r = expf(lpa - lo);
+      const float rc = fminf(fmaxf(r, 1.0f - a.clip_eps), 1.0f + a.clip_eps);
+      const float s1 = r * A, s2 = rc * A;
+      const float gl = s1 <= s2 ? -A * r : 0.0f;  // ties: the unclipped term carries the gradient
+#pragma unroll
+      for (int o = 0; o < NO; ++o) {
+        dz[o] = 0.0f;
+        if (o < no) {
+          const float lp = z[o] - lse, p = expf(lp);
+          dz[o] = (gl * ((o == act ? 1.0f : 0.0f) - p) + a.ent_coef * p * (lp + ent)) * a.inv_n;
+        }
+      }
+      st[0] += (double)(-fminf(s1, s2) - a.ent_coef * ent);
+      st[1] += (double)ent;
+      st[2] += fabsf(r - 1.0f) > a.clip_eps ? 1.0 : 0.0;
+      st[3] += (double)(lo - lpa);
+    }
+    float dU[DJ];
+#pragma unroll
+    for (int i = 0; i < DJ; ++i) dU[i] = 0.0f;
+#pragma unroll
+    for (int o = 0; o < NO; ++o)
+      if (o < no) {
+        gB[o] += dz[o];
+#pragma unroll
+        for (int i = 0; i < DJ; ++i) {
+          gW[o][i] = fmaf(dz[o], U[i], gW[o][i]);
+          dU[i] = fmaf(a.Wh[o * d + lane + 32 * i], dz[o], dU[i]);
+        }
+      }
+    float dxh[DJ], m1 = 0.0f, m2 = 0.0f;
+#pragma unroll
+    for (int i = 0; i < DJ; ++i) {
+      const int j = lane + 32 * i;
+      dxh[i] = dU[i] * a.lnf_g[j];
+      gg[i] = fmaf(dU[i], xh[i], gg[i]);
+      gb[i] += dU[i];
+      m1 += dxh[i];
+      m2 = fmaf(dxh[i], xh[i], m2);
+    }
+    m1 = warp_sum(m1) * (1.0f / d);
+    m2 = warp_sum(m2) * (1.0f / d);
+    float* dx0 = a.dXL + s * a.T * d;
+#pragma unroll
+    for (int i = 0; i < DJ; ++i) dx0[lane + 32 * i] = rstd * (dxh[i] - m1 - xh[i] * m2);
+    for (int t = 1; t < a.T; ++t)
+#pragma unroll
+      for (int i = 0; i < DJ; ++i) dx0[t * d + lane + 32 * i] = 0.0f;
+  }
+  if (a.mode == 0) return;
+  const long long plen = 2 * d + (long long)no * d + no;
+  float* pp = a.part + w0 * plen;
+#pragma unroll
+  for (int i = 0; i < DJ; ++i) {
+    pp[lane + 32 * i] = gg[i];
+    pp[d + lane + 32 * i] = gb[i];
+  }
+#pragma unroll
+  for (int o = 0; o < NO; ++o)
+    if (o < no) {
+#pragma unroll
+      for (int i = 0; i < DJ; ++i) pp[2 * d + o * d + lane + 32 * i] = gW[o][i];
+      if (lane == 0) pp[2 * d + no * d + o] = gB[o];
+    }
+  if (lane == 0)
+    for (int k = 0; k < 4; ++k) a.spart[w0 * 4 + k] = st[k];
+}
+
+// Embedding weight gradients, one warp per sample: per-warp partial sums of
+// dW_emb[j][k] = sum dX[row][j] tok[row][k] and db_emb[j] over the sample's
+// entity rows, into part[warp][9d] (W_emb then b_emb).
+template <typename TokT, int DJ>
+__global__ void __launch_bounds__(256) embed_grad_kernel(const TokT* __restrict__ tok,
+                                                         const int32_t* __restrict__ n_ent,
+                                                         const int32_t* __restrict__ sel,
+                                                         const float* __restrict__ dX, float* __restrict__ part,
+                                                         long long n, int T, int NS) {
+  constexpr int d = 32 * DJ;
+  const int lane = threadIdx.x & 31;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  float gW[DJ][8], gb[DJ];
+#pragma unroll
+  for (int i = 0; i < DJ; ++i) {
+    gb[i] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) gW[i][k] = 0.0f;
+  }
+  for (long long s = w0; s < n; s += nw) {
+    const long long bs = sel ? (long long)sel[s] : s;
+    int ne = n_ent[bs];
+    ne = ne < 0 ? 0 : (ne > NS ? NS : ne);
+    for (int t = 1; t <= ne; ++t) {
+      const TokT* q = tok + (bs * NS + (t - 1)) * 8;
+      float tk[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) tk[k] = (float)q[k];
+#pragma unroll
+      for (int i = 0; i < DJ; ++i) {
+        const float g = dX[(s * T + t) * d + lane + 32 * i];
+        gb[i] += g;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) gW[i][k] = fmaf(g, tk[k], gW[i][k]);
+      }
+    }
+  }
+  float* pp = part + w0 * 9 * d;
+#pragma unroll
+  for (int i = 0; i < DJ; ++i) {
+    const int j = lane + 32 * i;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) pp[j * 8 + k] = gW[i][k];
+    pp[8 * d + j] = gb[i];
+  }
+}
+
+// Column sums of A [rows][N] (leading dimension lda): block (x, y) sums
+// columns 32x .. 32x+31 over its share of the rows into part[y][N].
+__global__ void __launch_bounds__(256) colsum_kernel(const float* __restrict__ A, long long lda, long long rows,
+                                                     int N, float* __restrict__ part) {
+  __shared__ float red[8][33];
+  const int c = blockIdx.x * 32 + (threadIdx.x & 31), rg = threadIdx.x >> 5;
+  const long long chunk = (rows + gridDim.y - 1) / gridDim.y;
+  const long long r0 = (long long)blockIdx.y * chunk;
+  const long long r1 = r0 + chunk < rows ? r0 + chunk : rows;
+  float acc = 0.0f;
+  if (c < N)
+    for (long long r = r0 + rg; r < r1; r += 8) acc += A[r * lda + c];
+  red[rg][threadIdx.x & 31] = acc;
+  __syncthreads();
+  if (rg == 0 && c < N) {
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += red[k][threadIdx.x & 31];
+    part[(long long)blockIdx.y * N + c] = s;
+  }
+}
+
+// out[i] = sum over p of part[p * stride + i], in order of p.
+__global__ void reduce_kernel(const float* __restrict__ part, int nparts, long long len, long long stride,
+                              float* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= len) return;
+  float s = 0.0f;
+  for (int p = 0; p < nparts; ++p) s += part[p * stride + i];
+  out[i] = s;
+}
+
+// Statistics: sums of the per-warp partials, in warp order, times inv_n.
+__global__ void reduce_stats_kernel(const double* __restrict__ spart, int nparts, double inv_n,
+                                    double* __restrict__ out) {
+  const int k = threadIdx.x;
+  if (k >= 4) return;
+  double s = 0.0;
+  for (int p = 0; p < nparts; ++p) s += spart[p * 4 + k];
+  out[k] = s * inv_n;
+}
+
+// Adam with bias correction (Kingma & Ba 2015, Algorithm 1); bc1 = 1 -
+// beta1^t and bc2 = 1 - beta2^t are computed on the host in double.
+__global__ void adam_kernel(float* __restrict__ th, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ g, long long n, float lr, float b1, float b2, float eps,
+                            float bc1, float bc2) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.0f - b1) * gi;
+  const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  th[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+}
+
+// GAE by the backward recursion, one thread per env.
+__global__ void gae_kernel(const float* __restrict__ r, const float* __restrict__ v, const int32_t* __restrict__ done,
+                           int T, long long E, float gamma, float lam, float* __restrict__ adv,
+                           float* __restrict__ ret) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  float a = 0.0f;
+  for (int t = T - 1; t >= 0; --t) {
+    const long long i = (long long)t * E + e;
+    const float nd = done[i] ? 0.0f : 1.0f;
+    const float delta = r[i] + gamma * nd * v[i + E] - v[i];
+    a = delta + gamma * lam * nd * a;
+    adv[i] = a;
+    ret[i] = a + v[i];
+  }
+}
+
+__global__ void gae_agents_kernel(const float* __restrict__ adv, const int32_t* __restrict__ agent_env, int T,
+                                  long long E, long long NA, float* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)T * NA) return;
+  const long long t = i / NA, a = i - t * NA;
+  out[i] = adv[t * E + agent_env[a]];
+}
+
+}  // namespace tfm
+}  // namespace ut
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+#include "runtime.cuh"
+
+struct ut_tfm {
+  ut_tfm_config cfg{};
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int d = 0, L = 0, H = 0, dh = 0, n_out = 0, NS = 0, T = 0, f = 0;
+  int64_t n_params = 0, max_rows = 0;
+  std::vector<void*> allocs;
+  float *prm = nullptr, *am = nullptr, *av = nullptr;
+  int adam_t = 0;
+  // activations: X [(L+1)][max_rows][d]; per block l: Y1, O, M, Y2 [rows][d],
+  // S1, S2 [rows][2], QKV [rows][3d], P [samples][H][T][T], Z, G [rows][4d]
+  float *X = nullptr, *Y1 = nullptr, *Y2 = nullptr, *S1 = nullptr, *S2 = nullptr, *QKV = nullptr, *P = nullptr,
+        *O = nullptr, *M = nullptr, *Z = nullptr, *G = nullptr;
+  // backward buffers
+  float *dX = nullptr, *dM = nullptr, *dY = nullptr, *dO = nullptr, *dBig = nullptr;
+  float* part = nullptr;  // partial sums of the parameter gradients
+  double *spart = nullptr, *stats_d = nullptr;
+  std::vector<int64_t> off;  // canonical tensor offsets
+};
+
+namespace ut {
+namespace tfm {
+namespace {
+
+// Tensor offsets in the canonical order: 0 W_emb, 1 b_emb, per block l at
+// 2 + 12 l: ln1_g, ln1_b, Wqkv, bqkv, Wo, bo, ln2_g, ln2_b, W1, b1, W2, b2;
+// then lnf_g, lnf_b, Wh, bh and the end.
+enum { T_LN1G = 0, T_LN1B, T_WQKV, T_BQKV, T_WO, T_BO, T_LN2G, T_LN2B, T_W1, T_B1, T_W2, T_B2 };
+
+std::vector<int64_t> offsets(int d, int L, int n_out) {
+  std::vector<int64_t> o;
+  int64_t p = 0;
+  auto add = [&](int64_t n) {
+    o.push_back(p);
+    p += n;
+  };
+  const int64_t D = d, F = 4 * (int64_t)d;
+  add(D * 8);
+  add(D);
+  for (int l = 0; l < L; ++l) {
+    add(D); add(D); add(3 * D * D); add(3 * D); add(D * D); add(D);
+    add(D); add(D); add(F * D); add(F); add(D * F); add(D);
+  }
+  add(D); add(D); add((int64_t)n_out * D); add(n_out);
+  o.push_back(p);
+  return o;
+}
+
+bool valid_config(const ut_tfm_config* c) {
+  if (!c || c->abi_version != UT_ABI_VERSION) return false;
+  const int d = c->d_model;
+  if (d != 32 && d != 64 && d != 96 && d != 128) return false;
+  if (c->n_layers < 1 || c->n_layers > 8 || c->n_heads < 1 || d % c->n_heads) return false;
+  const int dh = d / c->n_heads;
+  if (dh != 8 && dh != 16 && dh != 32) return false;
+  if (c->n_out < 1 || c->n_out > 16) return false;
+  if (c->n_slots < 1 || c->n_slots > UT_MAX_AGENTS + UT_MAX_TARGETS) return false;
+  if (c->tokens_bf16 != 0 && c->tokens_bf16 != 1) return false;
+  return c->max_batch >= 1 && c->max_batch <= (1ll << 22);
+}
+
+inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+// kind 0: forward (A row-major, B = W [N][K]); 1: input gradient (A
+// row-major, B = W [K][N]); 2: weight gradient (A and B indexed [k][.]).
+cudaError_t gemm(int kind, const Gemm& g, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
+  const long long kc = g.kchunk > 0 ? g.kchunk : g.K;
+  dim3 grid((unsigned)((g.M + 63) / 64), (unsigned)((g.N + 63) / 64), (unsigned)((g.K + kc - 1) / kc));
+  Gemm a = g;
+  a.kchunk = kc;
+  if (kind == 0)
+    sgemm_kernel<true, true><<<grid, 256, 0, s>>>(a);
+  else if (kind == 1)
+    sgemm_kernel<true, false><<<grid, 256, 0, s>>>(a);
+  else
+    sgemm_kernel<false, false><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+Gemm mk(const float* A, long long lda, const float* B, long long ldb, float* C, long long ldc, long long M, int N,
+        long long K, int epi) {
+  Gemm g;
+  std::memset(&g, 0, sizeof(g));
+  g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
+  g.M = M; g.N = N; g.K = K; g.kchunk = K; g.epi = epi;
+  return g;
+}
+
+cudaError_t reduce(const float* part, int nparts, long long len, long long stride, float* out, cudaStream_t s) {
+  reduce_kernel<<<blocks_for(len, 256), 256, 0, s>>>(part, nparts, len, stride, out);
+  return cudaGetLastError();
+}
+
+// dW[o][i] = sum_r dOut[r][o] In[r][i] and db[o] = sum_r dOut[r][o] over rows
+// r, split along the rows into partial slabs summed in order.
+cudaError_t wgrad(ut_tfm* t, const float* dOut, int n_o, const float* In, int n_i, long long rows, float* gW,
+                  float* gb, cudaStream_t s) {
+  Gemm g = mk(dOut, n_o, In, n_i, t->part, n_i, n_o, n_i, rows, EPI_PARTIAL);
+  const long long tiles = (long long)((n_o + 63) / 64) * ((n_i + 63) / 64);
+  long long splits = (608 + tiles - 1) / tiles;
+  splits = splits < 1 ? 1 : (splits > 128 ? 128 : splits);
+  const long long max_split = (rows + 63) / 64;
+  if (splits > max_split) splits = max_split;
+  long long kc = (rows + splits - 1) / splits;
+  kc = (kc + 15) / 16 * 16;
+  splits = (rows + kc - 1) / kc;
+  g.kchunk = kc;
+  cudaError_t e = gemm(2, g, s);
+  if (e == cudaSuccess) e = reduce(t->part, (int)splits, (long long)n_o * n_i, (long long)n_o * n_i, gW, s);
+  if (e != cudaSuccess) return e;
+  long long nblk = (rows + 63) / 64;
+  nblk = nblk < 1 ? 1 : (nblk > 256 ? 256 : nblk);
+  colsum_kernel<<<dim3((unsigned)((n_o + 31) / 32), (unsigned)nblk), 256, 0, s>>>(dOut, n_o, rows, n_o, t->part);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = reduce(t->part, (int)nblk, n_o, n_o, gb, s);
+  return e;
+}
+
+template <int DJ>
+cudaError_t ln_fwd(const float* X, const float* g, const float* b, float* Y, float* st, long long rows, cudaStream_t s) {
+  ln_fwd_kernel<DJ><<<kRowBlocks, 256, 0, s>>>(X, g, b, Y, st, rows);
+  return cudaGetLastError();
+}
+
+template <int DJ>
+cudaError_t ln_bwd(ut_tfm* t, const float* dY, const float* X, const float* st, const float* g, const float* base,
+                   float* out, float* grad_gb, long long rows, cudaStream_t s) {
+  ln_bwd_kernel<DJ><<<kRowBlocks, 256, 0, s>>>(dY, X, st, g, base, out, t->part, rows);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = reduce(t->part, kRowWarps, 2 * 32 * DJ, 2 * 32 * DJ, grad_gb, s);
+  return e;
+}
+
+template <int DH>
+cudaError_t attn_fwd(const float* QKV, const int32_t* ne, const int32_t* sel, float* P, float* O, long long n, int T,
+                     int NS, int H, cudaStream_t s) {
+  attn_fwd_kernel<DH><<<blocks_for(n * H * 32, 256), 256, 0, s>>>(QKV, ne, sel, P, O, n, T, NS, H,
+                                                                   1.0f / sqrtf((float)DH));
+  return cudaGetLastError();
+}
+
+template <int DH>
+cudaError_t attn_bwd(const float* QKV, const float* P, const float* dO, float* dQKV, long long n, int T, int H,
+                     cudaStream_t s) {
+  attn_bwd_kernel<DH><<<blocks_for(n * H * 32, 256), 256, 0, s>>>(QKV, P, dO, dQKV, n, T, H, 1.0f / sqrtf((float)DH));
+  return cudaGetLastError();
+}
+
+struct Call {
+  const void* tok;
+  const int32_t* ne;
+  const float* h;
+  const int32_t* sel;
+  long long n;
+};
+
+template <int DJ, int DH, typename TokT>
+cudaError_t forward(ut_tfm* t, const Call& c, cudaStream_t s) {
+  constexpr int d = 32 * DJ;
+  const long long rows = c.n * t->T, MR = t->max_rows;
+  const float* w = t->prm;
+  const auto& o = t->off;
+  embed_kernel<TokT><<<blocks_for(rows * d, 256), 256, 0, s>>>((const TokT*)c.tok, c.ne, c.h, c.sel, w + o[0],
+                                                              w + o[1], t->X, c.n, t->T, t->NS, d);
+  cudaError_t e = cudaGetLastError();
+  for (int l = 0; l < t->L && e == cudaSuccess; ++l) {
+    const int64_t* ol = o.data() + 2 + 12 * l;
+    float* Xl = t->X + l * MR * d;
+    float* Xn = t->X + (l + 1) * MR * d;
+    float* Y1 = t->Y1 + l * MR * d;
+    float* Y2 = t->Y2 + l * MR * d;
+    float* S1 = t->S1 + l * MR * 2;
+    float* S2 = t->S2 + l * MR * 2;
+    float* QKV = t->QKV + l * MR * 3 * d;
+    float* P = t->P + (long long)l * t->cfg.max_batch * t->H * t->T * t->T;
+    float* O = t->O + l * MR * d;
+    float* M = t->M + l * MR * d;
+    float* Z = t->Z + l * MR * 4 * d;
+    float* G = t->G + l * MR * 4 * d;
+    e = ln_fwd<DJ>(Xl, w + ol[T_LN1G], w + ol[T_LN1B], Y1, S1, rows, s);
+    if (e != cudaSuccess) break;
+    Gemm g = mk(Y1, d, w + ol[T_WQKV], d, QKV, 3 * d, rows, 3 * d, d, EPI_BIAS);
+    g.bias = w + ol[T_BQKV];
+    e = gemm(0, g, s);
+    if (e == cudaSuccess) e = attn_fwd<DH>(QKV, c.ne, c.sel, P, O, c.n, t->T, t->NS, t->H, s);
+    if (e != cudaSuccess) break;
+    g = mk(O, d, w + ol[T_WO], d, M, d, rows, d, d, EPI_BIAS_RES);
+    g.bias = w + ol[T_BO];
+    g.R = Xl;
+    e = gemm(0, g, s);
+    if (e == cudaSuccess) e = ln_fwd<DJ>(M, w + ol[T_LN2G], w + ol[T_LN2B], Y2, S2, rows, s);
+    if (e != cudaSuccess) break;
+    g = mk(Y2, d, w + ol[T_W1], d, Z, 4 * d, rows, 4 * d, d, EPI_BIAS_GELU);
+    g.bias = w + ol[T_B1];
+    g.C2 = G;
+    e = gemm(0, g, s);
+    if (e != cudaSuccess) break;
+    g = mk(G, 4 * d, w + ol[T_W2], 4 * d, Xn, d, rows, d, 4 * d, EPI_BIAS_RES);
+    g.bias = w + ol[T_B2];
+    g.R = M;
+    e = gemm(0, g, s);
+  }
+  return e;
+}
+
+template <int DJ, int DH, typename TokT>
+cudaError_t backward(ut_tfm* t, const Call& c, float* grad, cudaStream_t s) {
+  constexpr int d = 32 * DJ;
+  const long long rows = c.n * t->T, MR = t->max_rows;
+  const float* w = t->prm;
+  const auto& o = t->off;
+  cudaError_t e = cudaSuccess;
+  for (int l = t->L - 1; l >= 0 && e == cudaSuccess; --l) {
+    const int64_t* ol = o.data() + 2 + 12 * l;
+    const float* Xl = t->X + l * MR * d;
+    const float* Y1 = t->Y1 + l * MR * d;
+    const float* Y2 = t->Y2 + l * MR * d;
+    const float* S1 = t->S1 + l * MR * 2;
+    const float* S2 = t->S2 + l * MR * 2;
+    const float* QKV = t->QKV + l * MR * 3 * d;
+    const float* P = t->P + (long long)l * t->cfg.max_batch * t->H * t->T * t->T;
+    const float* O = t->O + l * MR * d;
+    const float* M = t->M + l * MR * d;
+    const float* Z = t->Z + l * MR * 4 * d;
+    const float* G = t->G + l * MR * 4 * d;
+    // feed-forward sub-block: X' = M + W2 gelu(W1 LN2(M) + b1) + b2
+    Gemm g = mk(t->dX, d, w + ol[T_W2], 4 * d, t->dBig, 4 * d, rows, 4 * d, d, EPI_GELU_GRAD);
+    g.aux = Z;
+    e = gemm(1, g, s);
+    if (e == cudaSuccess) e = wgrad(t, t->dX, d, G, 4 * d, rows, grad + ol[T_W2], grad + ol[T_B2], s);
+    if (e == cudaSuccess) e = gemm(1, mk(t->dBig, 4 * d, w + ol[T_W1], d, t->dY, d, rows, d, 4 * d, EPI_STORE), s);
+    if (e == cudaSuccess) e = wgrad(t, t->dBig, 4 * d, Y2, d, rows, grad + ol[T_W1], grad + ol[T_B1], s);
+    if (e == cudaSuccess) e = ln_bwd<DJ>(t, t->dY, M, S2, w + ol[T_LN2G], t->dX, t->dM, grad + ol[T_LN2G], rows, s);
+    // attention sub-block: M = X + Wo attn(LN1(X)) + bo
+    if (e == cudaSuccess) e = gemm(1, mk(t->dM, d, w + ol[T_WO], d, t->dO, d, rows, d, d, EPI_STORE), s);
+    if (e == cudaSuccess) e = wgrad(t, t->dM, d, O, d, rows, grad + ol[T_WO], grad + ol[T_BO], s);
+    if (e == cudaSuccess) e = attn_bwd<DH>(QKV, P, t->dO, t->dBig, c.n, t->T, t->H, s);
+    if (e == cudaSuccess) e = gemm(1, mk(t->dBig, 3 * d, w + ol[T_WQKV], d, t->dY, d, rows, d, 3 * d, EPI_STORE), s);
+    if (e == cudaSuccess) e = wgrad(t, t->dBig, 3 * d, Y1, d, rows, grad + ol[T_WQKV], grad + ol[T_BQKV], s);
+    if (e == cudaSuccess) e = ln_bwd<DJ>(t, t->dY, Xl, S1, w + ol[T_LN1G], t->dM, t->dX, grad + ol[T_LN1G], rows, s);
+  }
+  if (e != cudaSuccess) return e;
+  embed_grad_kernel<TokT, DJ><<<kRowBlocks, 256, 0, s>>>((const TokT*)c.tok, c.ne, c.sel, t->dX, t->part, c.n, t->T,
+                                                         t->NS);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = reduce(t->part, kRowWarps, 9 * d, 9 * d, grad + o[0], s);
+  return e;
+}
+
+// mode 0: forward (out, h_out); 1: PPO actor loss + gradient; 2: value loss +
+// gradient.
+template <int DJ, int DH, typename TokT>
+cudaError_t run(ut_tfm* t, const Call& c, int mode, const HeadArgs& ha_in, float* grad, cudaStream_t s) {
+  constexpr int d = 32 * DJ;
+  cudaError_t e = forward<DJ, DH, TokT>(t, c, s);
+  if (e != cudaSuccess) return e;
+  const auto& o = t->off;
+  const int idx = 2 + 12 * t->L;
+  HeadArgs ha = ha_in;
+  ha.XL = t->X + (long long)t->L * t->max_rows * d;
+  ha.n = c.n;
+  ha.T = t->T;
+  ha.n_out = t->n_out;
+  ha.mode = mode;
+  ha.lnf_g = t->prm + o[idx];
+  ha.lnf_b = t->prm + o[idx + 1];
+  ha.Wh = t->prm + o[idx + 2];
+  ha.bh = t->prm + o[idx + 3];
+  ha.sel = c.sel;
+  ha.inv_n = 1.0f / (float)c.n;
+  ha.dXL = t->dX;
+  ha.part = t->part;
+  ha.spart = t->spart;
+  if (t->n_out == 1)
+    head_kernel<DJ, 1><<<kRowBlocks, 256, 0, s>>>(ha);
+  else
+    head_kernel<DJ, 16><<<kRowBlocks, 256, 0, s>>>(ha);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || mode == 0) return e;
+  const long long plen = 2 * d + (long long)t->n_out * d + t->n_out;
+  e = reduce(t->part, kRowWarps, plen, plen, grad + o[idx], s);
+  if (e != cudaSuccess) return e;
+  reduce_stats_kernel<<<1, 32, 0, s>>>(t->spart, kRowWarps, 1.0 / (double)c.n, t->stats_d);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return backward<DJ, DH, TokT>(t, c, grad, s);
+}
+
+template <int DJ, int DH>
+cudaError_t run_tok(ut_tfm* t, const Call& c, int mode, const HeadArgs& ha, float* grad, cudaStream_t s) {
+  return t->cfg.tokens_bf16 ? run<DJ, DH, __nv_bfloat16>(t, c, mode, ha, grad, s)
+                            : run<DJ, DH, float>(t, c, mode, ha, grad, s);
+}
+
+template <int DJ>
+cudaError_t run_dh(ut_tfm* t, const Call& c, int mode, const HeadArgs& ha, float* grad, cudaStream_t s) {
+  switch (t->dh) {
+    case 8: return run_tok<DJ, 8>(t, c, mode, ha, grad, s);
+    case 16: return run_tok<DJ, 16>(t, c, mode, ha, grad, s);
+    default: return run_tok<DJ, 32>(t, c, mode, ha, grad, s);
+  }
+}
+
+cudaError_t dispatch(ut_tfm* t, const Call& c, int mode, const HeadArgs& ha, float* grad) {
+  switch (t->d) {
+    case 32: return run_dh<1>(t, c, mode, ha, grad, t->stream);
+    case 64: return run_dh<2>(t, c, mode, ha, grad, t->stream);
+    case 96: return run_dh<3>(t, c, mode, ha, grad, t->stream);
+    default: return run_dh<4>(t, c, mode, ha, grad, t->stream);
+  }
+}
+
+ut_status fail(ut_tfm* t, ut_status st, const std::string& msg) {
+  t->err = msg;
+  return st;
+}
+
+void* dalloc(ut_tfm* t, size_t bytes) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) return nullptr;
+  t->allocs.push_back(p);
+  return p;
+}
+
+bool call_ok(const ut_tfm* t, const void* tok, const int32_t* ne, const float* h, int64_t n) {
+  return tok && ne && h && n >= 1 && n <= t->cfg.max_batch;
+}
+
+}  // namespace
+}  // namespace tfm
+}  // namespace ut
+
+using namespace ut::tfm;
+
+extern "C" int64_t tfm_param_count(const ut_tfm_config* cfg) {
+  if (!valid_config(cfg)) return -1;
+  return offsets(cfg->d_model, cfg->n_layers, cfg->n_out).back();
+}
+
+extern "C" ut_status tfm_create(const ut_tfm_config* cfg, const float* params_host, int64_t n_params,
+                                void* cuda_stream, ut_tfm** out) {
+  if (!out) return UT_ERR_INVALID;
+  *out = nullptr;
+  if (!valid_config(cfg) || !params_host || n_params != tfm_param_count(cfg)) return UT_ERR_INVALID;
+  ut_tfm* t = new ut_tfm();
+  t->cfg = *cfg;
+  t->stream = (cudaStream_t)cuda_stream;
+  t->d = cfg->d_model;
+  t->L = cfg->n_layers;
+  t->H = cfg->n_heads;
+  t->dh = t->d / t->H;
+  t->n_out = cfg->n_out;
+  t->NS = cfg->n_slots;
+  t->T = 1 + cfg->n_slots;
+  t->f = 4 * t->d;
+  t->n_params = n_params;
+  t->off = offsets(t->d, t->L, t->n_out);
+  t->max_rows = cfg->max_batch * t->T;
+  const size_t R = (size_t)t->max_rows, d = (size_t)t->d, L = (size_t)t->L;
+  const size_t Pn = (size_t)cfg->max_batch * t->H * t->T * t->T;
+  size_t part = (size_t)128 * 4 * d * d;
+  part = std::max(part, (size_t)256 * 4 * d);
+  part = std::max(part, (size_t)kRowWarps * (2 * d + (size_t)t->n_out * d + t->n_out));
+  part = std::max(part, (size_t)kRowWarps * 9 * d);
+  bool ok = true;
+  auto A = [&](size_t n) -> float* {
+    float* p = (float*)dalloc(t, n * 4);
+    ok = ok && p;
+    return p;
+  };
+  t->prm = A(n_params);
+  t->am = A(n_params);
+  t->av = A(n_params);
+  t->X = A((L + 1) * R * d);
+  t->Y1 = A(L * R * d);
+  t->Y2 = A(L * R * d);
+  t->S1 = A(L * R * 2);
+  t->S2 = A(L * R * 2);
+  t->QKV = A(L * R * 3 * d);
+  t->P = A(L * Pn);
+  t->O = A(L * R * d);
+  t->M = A(L * R * d);
+  t->Z = A(L * R * 4 * d);
+  t->G = A(L * R * 4 * d);
+  t->dX = A(R * d);
+  t->dM = A(R * d);
+  t->dY = A(R * d);
+  t->dO = A(R * d);
+  t->dBig = A(R * 4 * d);
+  t->part = A(part);
+  t->spart = (double*)dalloc(t, (size_t)kRowWarps * 4 * 8);
+  t->stats_d = (double*)dalloc(t, 4 * 8);
+  ok = ok && t->spart && t->stats_d;
+  if (!ok) {
+    tfm_destroy(t);
+    return UT_ERR_NOMEM;
+  }
+  cudaError_t e = cudaMemcpyAsync(t->prm, params_host, (size_t)n_params * 4, cudaMemcpyHostToDevice, t->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->am, 0, (size_t)n_params * 4, t->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->av, 0, (size_t)n_params * 4, t->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(t->stream);
+  if (e != cudaSuccess) {
+    tfm_destroy(t);
+    return UT_ERR_CUDA;
+  }
+  *out = t;
+  return UT_OK;
+}
+
+extern "C" void tfm_destroy(ut_tfm* t) {
+  if (!t) return;
+  if (t->stream) cudaStreamSynchronize(t->stream);
+  for (void* p : t->allocs) cudaFree(p);
+  delete t;
+}
+
+extern "C" const char* tfm_last_error(const ut_tfm* t) { return t ? t->err.c_str() : "null handle"; }
+
+extern "C" ut_status tfm_params(ut_tfm* t, float** params_dev) {
+  if (!t || !params_dev) return UT_ERR_INVALID;
+  *params_dev = t->prm;
+  return UT_OK;
+}
+
+extern "C" ut_status tfm_forward(ut_tfm* t, const void* tokens_dev, const int32_t* n_ent_dev, const float* h_dev,
+                                 const int32_t* sel_dev, int64_t n, float* out_dev, float* h_out_dev) {
+  if (!t) return UT_ERR_INVALID;
+  if (!call_ok(t, tokens_dev, n_ent_dev, h_dev, n) || !out_dev || (h_out_dev == h_dev && sel_dev))
+    return fail(t, UT_ERR_INVALID, "tfm_forward: invalid arguments");
+  HeadArgs ha;
+  std::memset(&ha, 0, sizeof(ha));
+  ha.out = out_dev;
+  ha.h_out = h_out_dev;
+  const cudaError_t e = dispatch(t, Call{tokens_dev, n_ent_dev, h_dev, sel_dev, n}, 0, ha, nullptr);
+  return e == cudaSuccess ? UT_OK : fail(t, UT_ERR_CUDA, std::string("tfm_forward: ") + cudaGetErrorString(e));
+}
+
+static ut_status finish_stats(ut_tfm* t, double* stats_host, const char* name) {
+  if (!stats_host) return UT_OK;
+  cudaError_t e = cudaMemcpyAsync(stats_host, t->stats_d, 4 * 8, cudaMemcpyDeviceToHost, t->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(t->stream);
+  return e == cudaSuccess ? UT_OK : fail(t, UT_ERR_CUDA, std::string(name) + ": " + cudaGetErrorString(e));
+}
+
+extern "C" ut_status tfm_ppo_actor_grad(ut_tfm* t, const void* tokens_dev, const int32_t* n_ent_dev,
+                                        const float* h_dev, const int32_t* sel_dev, int64_t n,
+                                        const int32_t* actions_dev, const float* logp_old_dev, const float* adv_dev,
+                                        float clip_eps, float ent_coef, float* grad_dev, double* stats_host) {
+  if (!t) return UT_ERR_INVALID;
+  if (!call_ok(t, tokens_dev, n_ent_dev, h_dev, n) || !actions_dev || !logp_old_dev || !adv_dev || !grad_dev ||
+      !(clip_eps > 0.0f) || !(ent_coef >= 0.0f) || t->n_out < 2)
+    return fail(t, UT_ERR_INVALID, "tfm_ppo_actor_grad: invalid arguments");
+  HeadArgs ha;
+  std::memset(&ha, 0, sizeof(ha));
+  ha.actions = actions_dev;
+  ha.logp_old = logp_old_dev;
+  ha.adv = adv_dev;
+  ha.clip_eps = clip_eps;
+  ha.ent_coef = ent_coef;
+  const cudaError_t e = dispatch(t, Call{tokens_dev, n_ent_dev, h_dev, sel_dev, n}, 1, ha, grad_dev);
+  if (e != cudaSuccess) return fail(t, UT_ERR_CUDA, std::string("tfm_ppo_actor_grad: ") + cudaGetErrorString(e));
+  return finish_stats(t, stats_host, "tfm_ppo_actor_grad");
+}
+
+extern "C" ut_status tfm_value_grad(ut_tfm* t, const void* tokens_dev, const int32_t* n_ent_dev, const float* h_dev,
+                                    const int32_t* sel_dev, int64_t n, const float* returns_dev, float* grad_dev,
+                                    double* stats_host) {
+  if (!t) return UT_ERR_INVALID;
+  if (!call_ok(t, tokens_dev, n_ent_dev, h_dev, n) || !returns_dev || !grad_dev || t->n_out != 1)
+    return fail(t, UT_ERR_INVALID, "tfm_value_grad: invalid arguments");
+  HeadArgs ha;
+  std::memset(&ha, 0, sizeof(ha));
+  ha.ret = returns_dev;
+  const cudaError_t e = dispatch(t, Call{tokens_dev, n_ent_dev, h_dev, sel_dev, n}, 2, ha, grad_dev);
+  if (e != cudaSuccess) return fail(t, UT_ERR_CUDA, std::string("tfm_value_grad: ") + cudaGetErrorString(e));
+  return finish_stats(t, stats_host, "tfm_value_grad");
+}
+
+extern "C" ut_status tfm_adam_step(ut_tfm* t, const float* grad_dev, float lr, float beta1, float beta2, float eps) {
+  if (!t) return UT_ERR_INVALID;
+  if (!grad_dev || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) ||
+      !(eps > 0.0f))
+    return fail(t, UT_ERR_INVALID, "tfm_adam_step: invalid arguments");
+  t->adam_t += 1;
+  const float bc1 = (float)(1.0 - std::pow((double)beta1, t->adam_t));
+  const float bc2 = (float)(1.0 - std::pow((double)beta2, t->adam_t));
+  adam_kernel<<<blocks_for(t->n_params, 256), 256, 0, t->stream>>>(t->prm, t->am, t->av, grad_dev, t->n_params, lr,
+                                                                   beta1, beta2, eps, bc1, bc2);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? UT_OK : fail(t, UT_ERR_CUDA, std::string("tfm_adam_step: ") + cudaGetErrorString(e));
+}
+
+extern "C" ut_status tfm_sync_policy(ut_tfm* t, ut_env* env) {
+  if (!t || !env) return UT_ERR_INVALID;
+  const ut_config& c = env->cfg;
+  if (c.d_model != t->d || c.n_layers != t->L || c.n_heads != t->H || c.n_actions != t->n_out)
+    return fail(t, UT_ERR_INVALID, "tfm_sync_policy: the env's transformer agent has another configuration");
+  std::vector<float> host((size_t)t->n_params);
+  cudaError_t e = cudaMemcpyAsync(host.data(), t->prm, host.size() * 4, cudaMemcpyDeviceToHost, t->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(t->stream);
+  if (e != cudaSuccess) return fail(t, UT_ERR_CUDA, std::string("tfm_sync_policy: ") + cudaGetErrorString(e));
+  const ut_status st = env_set_policy(env, host.data(), t->n_params);
+  if (st != UT_OK) t->err = std::string("tfm_sync_policy: ") + env_last_error(env);
+  return st;
+}
+
+extern "C" ut_status ppo_gae(const float* reward_dev, const float* value_dev, const int32_t* done_dev, int32_t T,
+                             int64_t E, float gamma, float lam, float* adv_dev, float* ret_dev,
+                             const int32_t* agent_env_dev, int64_t NA, float* adv_agent_dev, void* cuda_stream) {
+  if (!reward_dev || !value_dev || !done_dev || !adv_dev || !ret_dev || T < 1 || E < 1 || !(gamma >= 0.0f) ||
+      !(gamma <= 1.0f) || !(lam >= 0.0f) || !(lam <= 1.0f))
+    return UT_ERR_INVALID;
+  if ((agent_env_dev == nullptr) != (adv_agent_dev == nullptr) || (adv_agent_dev && NA < 1)) return UT_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  gae_kernel<<<blocks_for(E, 256), 256, 0, s>>>(reward_dev, value_dev, done_dev, T, E, gamma, lam, adv_dev, ret_dev);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && adv_agent_dev) {
+    gae_agents_kernel<<<blocks_for((long long)T * NA, 256), 256, 0, s>>>(adv_dev, agent_env_dev, T, E, NA,
+                                                                        adv_agent_dev);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? UT_OK : UT_ERR_CUDA;
+}

@@ -111,3 +111,45 @@ def test_estimator_entry_points_reject_null_handles(lib):
     import paper_2505_08222_gb300 as ut
     assert ut.lib.est_set_mode(None, 1) == 1
     assert ut.lib.est_set_mode(None, 4) == 1
+
+
+def test_tfm_param_count_validates_the_configuration(lib):
+    from paper_2505_08222_gb300 import _abi
+    import oracle
+
+    f = lib.tfm_param_count
+    f.restype = ctypes.c_int64
+    f.argtypes = [ctypes.POINTER(_abi.TfmConfig)]
+
+    def cfg(**kw):
+        base = dict(abi_version=_abi.UT_ABI_VERSION, d_model=64, n_layers=2, n_heads=4, n_out=7, n_slots=10,
+                    tokens_bf16=1, reserved=0, max_batch=1024)
+        base.update(kw)
+        return _abi.TfmConfig(**base)
+
+    for d, L, H, no in ((64, 2, 4, 7), (128, 3, 8, 7), (32, 1, 4, 1), (96, 2, 3, 5)):
+        assert f(ctypes.byref(cfg(d_model=d, n_layers=L, n_heads=H, n_out=no))) == oracle.tfm_param_count(d, L, H, no)
+    for bad in (dict(d_model=48), dict(d_model=256), dict(n_heads=1), dict(n_heads=16), dict(n_heads=5), dict(n_layers=0),
+                dict(n_layers=9), dict(n_out=0), dict(n_out=17), dict(n_slots=0), dict(n_slots=17),
+                dict(tokens_bf16=2), dict(max_batch=0), dict(max_batch=(1 << 22) + 1), dict(abi_version=1)):
+        assert f(ctypes.byref(cfg(**bad))) == -1, bad
+
+
+def test_training_calls_reject_bad_arguments_before_any_cuda_call(lib):
+    from paper_2505_08222_gb300 import _abi
+
+    for name, (res, args) in _abi.SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype, fn.argtypes = res, args
+    one = ctypes.c_void_p(16)
+    assert lib.tfm_create(None, None, 0, None, ctypes.byref(ctypes.c_void_p())) == 1
+    c = _abi.TfmConfig(_abi.UT_ABI_VERSION, 64, 2, 4, 7, 10, 1, 0, 8)
+    assert lib.tfm_create(ctypes.byref(c), one, 5, None, ctypes.byref(ctypes.c_void_p())) == 1  # count mismatch
+    # GAE: bad sizes, discount outside [0, 1], agent map without output
+    assert lib.ppo_gae(one, one, one, 0, 4, 0.99, 0.95, one, one, None, 0, None, None) == 1
+    assert lib.ppo_gae(one, one, one, 4, 4, 1.5, 0.95, one, one, None, 0, None, None) == 1
+    assert lib.ppo_gae(one, one, one, 4, 4, 0.99, -0.1, one, one, None, 0, None, None) == 1
+    assert lib.ppo_gae(one, one, one, 4, 4, 0.99, 0.95, one, one, one, 8, None, None) == 1
+    assert lib.tfm_forward(None, one, one, one, None, 1, one, None) == 1
+    assert lib.tfm_sync_policy(None, None) == 1
+    assert lib.env_ppo_record(None, None, None, None, None) == 1
