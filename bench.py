@@ -313,6 +313,94 @@ def learned_form(args, p, K, W, rank):
                       "loss_last_per_round": losses, "train_ms": train_ms, "loss": "Huber, delta = 1 L"}}
 
 
+def fp32_simt_peak_tflops(sm_mhz: float) -> float:
+    """FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x SM clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def ppo_flops_per_sample(d: int, L: int, n_tok: int, n_out: int) -> float:
+    """Algorithmic FLOPs of one sample's forward + backward: the block GEMMs
+    (QKV 3d^2, O d^2, FFN 8d^2 per token) three times (forward, input and
+    weight gradients), attention (QK^T and PV, 2 n_tok^2 d each) three times,
+    embedding and head."""
+    gemm = 3 * 2 * n_tok * L * 12 * d * d
+    attn = 3 * 2 * 2 * n_tok * n_tok * d * L
+    return float(gemm + attn + 3 * 2 * (n_tok - 1) * 8 * d + 3 * 2 * d * n_out)
+
+
+def ppo_update(args, p, rank):
+    """TransfMAPPO update (Sec. II-B) on one batch collected by the env with
+    the transformer agent acting: T steps, the batch split into 4 minibatches
+    for the actor (agent-steps) and the critic (env-steps), one epoch, each
+    minibatch one PPO gradient + Adam step of both networks, then the copy of
+    the actor's weights into the env's agent."""
+    import torch
+
+    import paper_2505_08222_gb300 as ut
+    import synth
+    from paper_2505_08222_gb300 import ppo
+
+    T = args.ppo_steps
+    env = ut.Env(p)
+    dims = synth.PolicyDims(p.d_model, p.n_layers, p.n_heads, p.n_actions)
+    prm = synth.policy_params(dims, seed=1234)
+    crit = synth.policy_params(synth.PolicyDims(p.d_model, p.n_layers, p.n_heads, 1), seed=4321)
+    env.set_policy(prm)
+    tr = ppo.Trainer(env, prm, crit, ppo.PPOConfig(T=T, epochs=1, minibatches=4))
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    tr.collect(1000)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    collect_ms = e0.elapsed_time(e1)
+    for w in range(2):  # warm-up updates on the batch
+        tr.update(w)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    stats = tr.update(7)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    update_ms = e0.elapsed_time(e1)
+    # the actor's gradient step alone, K minibatches of the same size
+    NA, NS, d = tr.NA, tr.NS, tr.d
+    tok, ne, h = tr.tok.view(T * NA, NS, 8), tr.ne.view(T * NA), tr.h.view(T * NA, d)
+    sel = torch.randperm(T * NA, device="cuda")[:tr.mb_actor].to(torch.int32)
+    act, logp, adv = tr.act.view(-1), tr.logp.view(-1), tr.adv_a.view(-1)
+    reps = 6
+    for _ in range(2):
+        tr.actor.actor_grad(tok, ne, h, act, logp, adv, sel=sel, stats=False)
+    e0.record(stream)
+    for _ in range(reps):
+        torch.cuda.nvtx.range_push("ppo_actor_step")
+        tr.actor.actor_grad(tok, ne, h, act, logp, adv, sel=sel, stats=False)
+        torch.cuda.nvtx.range_pop()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / reps
+    n_tok = 1 + NS
+    fps = ppo_flops_per_sample(d, p.n_layers, n_tok, p.n_actions)
+    achieved = fps * tr.mb_actor / (step_ms * 1e-3) / 1e12
+    peak = fp32_simt_peak_tflops(2070.0)
+    env.close()
+    return {
+        "metric": "PPO update throughput", "value": T * NA / (update_ms * 1e-3), "unit": "agent-samples/s",
+        "ms_per_update": update_ms, "collect_ms": collect_ms,
+        "iteration_agent_steps_per_s": T * NA / ((collect_ms + update_ms) * 1e-3),
+        "T": T, "epochs": 1, "minibatches": 4, "actor_minibatch": tr.mb_actor, "critic_minibatch": tr.mb_critic,
+        "dtype": "f32",
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "scope": "actor PPO gradient step (forward, loss, backward: all kernels)",
+                     "avg_step_ms": step_ms, "flops_per_sample": fps,
+                     "peak_kind": "derived FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz",
+                     "timing": "CUDA events around 6 gradient calls on one minibatch"},
+        "stats_last_minibatch": stats,
+        "note": ("FP32 transformer training path on CUDA cores; the batch is a real collection (env_reset(1000), "
+                 "T steps with the agent acting), the critic fed the true state"),
+    }
+
+
 def variant_form(args, p, K, W, rank, env_main, tracker, **kw):
     """A tracker variant of the same workload (``kw`` replaces parameters:
     shared_filter=1, one filter per (env, target) fed every ping of the
@@ -428,6 +516,12 @@ def run_ours(args):
     from paper_2505_08222_gb300 import shard
 
     p = _workload(args.workload)
+    if args.ppo_only:
+        # the TransfMAPPO update measurement alone (profiling case)
+        if rank == 0:
+            print(json.dumps({"workload": args.workload, "n_envs": p.n_envs, "ppo": ppo_update(args, p, rank)}),
+                  flush=True)
+        return 0
     if world > 1:
         # weak scaling: the job is one batch of world x n_envs envs; rank r
         # steps its contiguous shard, random draws keyed by global ids
@@ -638,6 +732,8 @@ def run_ours(args):
             line["ess_resampling"] = variant_form(
                 args, p, K, W, rank, env, "per-agent filters, weights carried across steps, resampling when "
                 "the effective sample size < P/2 (pf_ess_num 8)", pf_ess_num=8)
+        if not args.no_ppo and getattr(p, "d_model", 0):
+            line["ppo"] = ppo_update(args, p, rank)
         if world == 1 and not args.no_cpu_baseline:
             os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
             line["cpu_baseline"] = cpu_baseline(args.workload)
@@ -662,6 +758,9 @@ def main():
     ap.add_argument("--pf-variant", default=None, help="fixed filter launch variant (e.g. nt512x4m3), no autotune")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-estimator form")
     ap.add_argument("--no-shared", action="store_true", help="skip the shared-filter and ESS-resampling forms")
+    ap.add_argument("--no-ppo", action="store_true", help="skip the TransfMAPPO update measurement")
+    ap.add_argument("--ppo-steps", type=int, default=32, help="steps collected for the PPO batch")
+    ap.add_argument("--ppo-only", action="store_true", help="only the TransfMAPPO update measurement")
     ap.add_argument("--train-rows", type=int, default=None,
                     help="recorded estimator rows (default 20M; 64M for the large workload, whose 4.2M filters "
                          "per step would otherwise give too few recorded episodes)")

@@ -145,6 +145,145 @@ __global__ void __launch_bounds__(256) sgemm_kernel(Gemm g) {
   }
 }
 
+// The same product with a 128 x 64 tile, 8 x 4 outputs per thread, float4
+// global loads and the next K slice prefetched into registers while the
+// current one is multiplied.  Preconditions (checked on the host): the
+// contiguous dimension of each operand is read in aligned float4 (leading
+// dimensions and base addresses multiples of 4 floats; M, N multiples of 4
+// where they are contiguous), and with k-contiguous operands the K range is
+// a multiple of 16.
+template <bool AK, bool BK>
+__global__ void __launch_bounds__(256) sgemm128_kernel(Gemm g) {
+  __shared__ __align__(16) float As[2][16][132];
+  __shared__ __align__(16) float Bs[2][16][68];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const long long m0 = (long long)blockIdx.x * 128;
+  const int n0 = blockIdx.y * 64;
+  const long long kb = (long long)blockIdx.z * g.kchunk;
+  const long long ke = kb + g.kchunk < g.K ? kb + g.kchunk : g.K;
+  float4 ra[2], rb;
+  // A slice: 128 (m) x 16 (k) as 512 float4, two per thread
+  auto load_a = [&](long long k0) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int i = tid + r * 256;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (AK) {
+        const long long m = m0 + (i >> 2), k = k0 + (i & 3) * 4;
+        if (m < g.M && k < ke) v = *reinterpret_cast<const float4*>(g.A + m * g.lda + k);
+      } else {
+        const long long k = k0 + (i >> 5), m = m0 + (i & 31) * 4;
+        if (m < g.M && k < ke) v = *reinterpret_cast<const float4*>(g.A + k * g.lda + m);
+      }
+      ra[r] = v;
+    }
+  };
+  // B slice: 16 (k) x 64 (n) as 256 float4, one per thread
+  auto load_b = [&](long long k0) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (BK) {
+      const int n = n0 + (tid >> 2);
+      const long long k = k0 + (tid & 3) * 4;
+      if (n < g.N && k < ke) v = *reinterpret_cast<const float4*>(g.B + (long long)n * g.ldb + k);
+    } else {
+      const long long k = k0 + (tid >> 4);
+      const int n = n0 + (tid & 15) * 4;
+      if (n < g.N && k < ke) v = *reinterpret_cast<const float4*>(g.B + k * g.ldb + n);
+    }
+    rb = v;
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int i = tid + r * 256;
+      if (AK) {
+        const int mm = i >> 2, kk = (i & 3) * 4;
+        As[buf][kk][mm] = ra[r].x;
+        As[buf][kk + 1][mm] = ra[r].y;
+        As[buf][kk + 2][mm] = ra[r].z;
+        As[buf][kk + 3][mm] = ra[r].w;
+      } else {
+        *reinterpret_cast<float4*>(&As[buf][i >> 5][(i & 31) * 4]) = ra[r];
+      }
+    }
+    if (BK) {
+      const int nn = tid >> 2, kk = (tid & 3) * 4;
+      Bs[buf][kk][nn] = rb.x;
+      Bs[buf][kk + 1][nn] = rb.y;
+      Bs[buf][kk + 2][nn] = rb.z;
+      Bs[buf][kk + 3][nn] = rb.w;
+    } else {
+      *reinterpret_cast<float4*>(&Bs[buf][tid >> 4][(tid & 15) * 4]) = rb;
+    }
+  };
+  float acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+  int buf = 0;
+  if (kb < ke) {
+    load_a(kb);
+    load_b(kb);
+    store(0);
+  }
+  __syncthreads();
+  for (long long k0 = kb; k0 < ke; k0 += 16) {
+    const bool more = k0 + 16 < ke;
+    if (more) {
+      load_a(k0 + 16);
+      load_b(k0 + 16);
+    }
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 8 + 4]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    if (more) store(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const long long m = m0 + ty * 8 + i;
+    if (m >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx * 4 + j;
+      if (n >= g.N) continue;
+      float v = acc[i][j];
+      const long long o = m * g.ldc + n;
+      switch (g.epi) {
+        case EPI_BIAS:
+          g.C[o] = v + g.bias[n];
+          break;
+        case EPI_BIAS_RES:
+          g.C[o] = v + g.bias[n] + g.R[o];
+          break;
+        case EPI_BIAS_GELU:
+          v += g.bias[n];
+          g.C[o] = v;
+          g.C2[o] = gelu_f(v);
+          break;
+        case EPI_GELU_GRAD:
+          g.C[o] = v * gelu_grad_f(g.aux[o]);
+          break;
+        case EPI_PARTIAL:
+          g.C[((long long)blockIdx.z * g.M + m) * g.N + n] = v;
+          break;
+        default:
+          g.C[o] = v;
+      }
+    }
+  }
+}
+
 // Embedding of the entity tokens; token 0 of each sample is its recurrent
 // embedding.  One thread per output value.
 template <typename TokT>
@@ -252,21 +391,32 @@ __global__ void ln_bwd_kernel(const float* __restrict__ dY, const float* __restr
 }
 
 // Self-attention of one (sample, head) per warp, lane t = query token t:
-// P[s][head][t][u] (zero for masked keys u > n_ent) and O = P V.
+// P[s][head][t][u] (zero for masked keys u > n_ent) and O = P V.  The warp
+// first copies the head's K and V rows of its sample to shared memory.
 template <int DH>
-__global__ void attn_fwd_kernel(const float* __restrict__ QKV, const int32_t* __restrict__ n_ent,
-                                const int32_t* __restrict__ sel, float* __restrict__ P, float* __restrict__ O,
-                                long long n, int T, int NS, int H, float scale) {
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(256) attn_fwd_kernel(const float* __restrict__ QKV,
+                                                       const int32_t* __restrict__ n_ent,
+                                                       const int32_t* __restrict__ sel, float* __restrict__ P,
+                                                       float* __restrict__ O, long long n, int T, int NS, int H,
+                                                       float scale) {
+  __shared__ float sk[8][kMaxT * DH];
+  __shared__ float sv[8][kMaxT * DH];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (w >= n * H) return;
+  if (w >= n * H) return;  // whole warps leave together
   const long long s = w / H;
   const int hh = (int)(w - s * H);
   const int d = DH * H, ld = 3 * d;
   int ne = n_ent[sel ? (long long)sel[s] : s];
   ne = ne < 0 ? 0 : (ne > NS ? NS : ne);
-  if (lane >= T) return;
   const float* base = QKV + s * T * ld + hh * DH;
+  for (int i = lane; i < T * DH; i += 32) {
+    const int u = i / DH, j = i - u * DH;
+    sk[wl][i] = base[u * ld + d + j];
+    sv[wl][i] = base[u * ld + 2 * d + j];
+  }
+  __syncwarp();
+  if (lane >= T) return;
   float q[DH];
 #pragma unroll
   for (int j = 0; j < DH; ++j) q[j] = base[lane * ld + j];
@@ -278,7 +428,7 @@ __global__ void attn_fwd_kernel(const float* __restrict__ QKV, const int32_t* __
     if (u < T && u <= ne) {
       float acc = 0.0f;
 #pragma unroll
-      for (int j = 0; j < DH; ++j) acc = fmaf(q[j], base[u * ld + d + j], acc);
+      for (int j = 0; j < DH; ++j) acc = fmaf(q[j], sk[wl][u * DH + j], acc);
       sc[u] = acc * scale;
       mx = fmaxf(mx, sc[u]);
     }
@@ -302,7 +452,7 @@ __global__ void attn_fwd_kernel(const float* __restrict__ QKV, const int32_t* __
       Pr[u] = p;
       if (u <= ne) {
 #pragma unroll
-        for (int j = 0; j < DH; ++j) o[j] = fmaf(p, base[u * ld + 2 * d + j], o[j]);
+        for (int j = 0; j < DH; ++j) o[j] = fmaf(p, sv[wl][u * DH + j], o[j]);
       }
     }
   }
@@ -310,15 +460,20 @@ __global__ void attn_fwd_kernel(const float* __restrict__ QKV, const int32_t* __
   for (int j = 0; j < DH; ++j) O[(s * T + lane) * d + hh * DH + j] = o[j];
 }
 
-// Attention backward of one (sample, head) per warp: from dO and the stored
-// P, dS = P (dP - rowsum(P dP)) scale with dP = dO V^T; lane t writes dQ_t,
-// then lane u writes dK_u = sum_t dS_tu Q_t and dV_u = sum_t P_tu dO_t.
+// Attention backward of one (sample, head) per warp (4 warps per block): from
+// dO and the stored P, dS = P (dP - rowsum(P dP)) scale with dP = dO V^T;
+// lane t writes dQ_t, then lane u writes dK_u = sum_t dS_tu Q_t and
+// dV_u = sum_t P_tu dO_t.  Q, K, V and dO rows are staged in shared memory.
 template <int DH>
-__global__ void __launch_bounds__(256) attn_bwd_kernel(const float* __restrict__ QKV, const float* __restrict__ P,
+__global__ void __launch_bounds__(128) attn_bwd_kernel(const float* __restrict__ QKV, const float* __restrict__ P,
                                                        const float* __restrict__ dO, float* __restrict__ dQKV,
                                                        long long n, int T, int H, float scale) {
-  __shared__ float sdS[8][kMaxT * kMaxT];
-  __shared__ float sP[8][kMaxT * kMaxT];
+  __shared__ float sq[4][kMaxT * DH];
+  __shared__ float sk[4][kMaxT * DH];
+  __shared__ float sv[4][kMaxT * DH];
+  __shared__ float sg[4][kMaxT * DH];
+  __shared__ float sdS[4][kMaxT * kMaxT];
+  __shared__ float sP[4][kMaxT * kMaxT];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= n * H) return;  // whole warps leave together
@@ -329,22 +484,26 @@ __global__ void __launch_bounds__(256) attn_bwd_kernel(const float* __restrict__
   const float* dOb = dO + s * T * d + hh * DH;
   float* out = dQKV + s * T * ld + hh * DH;
   const float* Pb = P + (s * H + hh) * T * T;
+  for (int i = lane; i < T * DH; i += 32) {
+    const int u = i / DH, j = i - u * DH;
+    sq[wl][i] = base[u * ld + j];
+    sk[wl][i] = base[u * ld + d + j];
+    sv[wl][i] = base[u * ld + 2 * d + j];
+    sg[wl][i] = dOb[u * d + j];
+  }
+  for (int i = lane; i < T * T; i += 32) sP[wl][i] = Pb[i];
+  __syncwarp();
   if (lane < T) {
-    float g[DH];
-#pragma unroll
-    for (int j = 0; j < DH; ++j) g[j] = dOb[lane * d + j];
-    float p[kMaxT], dp[kMaxT], dot = 0.0f;
+    float dp[kMaxT], dot = 0.0f;
 #pragma unroll
     for (int u = 0; u < kMaxT; ++u) {
-      p[u] = dp[u] = 0.0f;
+      dp[u] = 0.0f;
       if (u < T) {
-        p[u] = Pb[lane * T + u];
-        sP[wl][lane * T + u] = p[u];
         float acc = 0.0f;
 #pragma unroll
-        for (int j = 0; j < DH; ++j) acc = fmaf(g[j], base[u * ld + 2 * d + j], acc);
+        for (int j = 0; j < DH; ++j) acc = fmaf(sg[wl][lane * DH + j], sv[wl][u * DH + j], acc);
         dp[u] = acc;
-        dot = fmaf(p[u], acc, dot);
+        dot = fmaf(sP[wl][lane * T + u], acc, dot);
       }
     }
     float dq[DH];
@@ -353,10 +512,10 @@ __global__ void __launch_bounds__(256) attn_bwd_kernel(const float* __restrict__
 #pragma unroll
     for (int u = 0; u < kMaxT; ++u) {
       if (u < T) {
-        const float ds = p[u] * (dp[u] - dot) * scale;
+        const float ds = sP[wl][lane * T + u] * (dp[u] - dot) * scale;
         sdS[wl][lane * T + u] = ds;
 #pragma unroll
-        for (int j = 0; j < DH; ++j) dq[j] = fmaf(ds, base[u * ld + d + j], dq[j]);
+        for (int j = 0; j < DH; ++j) dq[j] = fmaf(ds, sk[wl][u * DH + j], dq[j]);
       }
     }
 #pragma unroll
@@ -371,8 +530,8 @@ __global__ void __launch_bounds__(256) attn_bwd_kernel(const float* __restrict__
       const float ds = sdS[wl][t * T + lane], p = sP[wl][t * T + lane];
 #pragma unroll
       for (int j = 0; j < DH; ++j) {
-        dk[j] = fmaf(ds, base[t * ld + j], dk[j]);
-        dv[j] = fmaf(p, dOb[t * d + j], dv[j]);
+        dk[j] = fmaf(ds, sq[wl][t * DH + j], dk[j]);
+        dv[j] = fmaf(p, sg[wl][t * DH + j], dv[j]);
       }
     }
 #pragma unroll
@@ -627,24 +786,43 @@ __global__ void __launch_bounds__(256) colsum_kernel(const float* __restrict__ A
   }
 }
 
-// out[i] = sum over p of part[p * stride + i], in order of p.
-__global__ void reduce_kernel(const float* __restrict__ part, int nparts, long long len, long long stride,
-                              float* __restrict__ out) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= len) return;
+// out[i] = sum over p of part[p * stride + i]: block x sums columns
+// 32x .. 32x+31, thread row g the parts p = g (mod 8) in increasing p, then
+// the 8 row sums in order of g (a fixed association: deterministic).
+__global__ void __launch_bounds__(256) reduce_kernel(const float* __restrict__ part, int nparts, long long len,
+                                                     long long stride, float* __restrict__ out) {
+  __shared__ float red[8][33];
+  const int c = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const long long i = (long long)blockIdx.x * 32 + c;
   float s = 0.0f;
-  for (int p = 0; p < nparts; ++p) s += part[p * stride + i];
-  out[i] = s;
+  if (i < len)
+    for (int p = g; p < nparts; p += 8) s += part[p * stride + i];
+  red[g][c] = s;
+  __syncthreads();
+  if (g == 0 && i < len) {
+    float t = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += red[k][c];
+    out[i] = t;
+  }
 }
 
-// Statistics: sums of the per-warp partials, in warp order, times inv_n.
-__global__ void reduce_stats_kernel(const double* __restrict__ spart, int nparts, double inv_n,
-                                    double* __restrict__ out) {
-  const int k = threadIdx.x;
-  if (k >= 4) return;
+// Statistics: sums of the per-warp partials times inv_n; thread j of 256
+// sums parts p = j (mod 64) of statistic j / 64, then 64 partial sums are
+// added in order.
+__global__ void __launch_bounds__(256) reduce_stats_kernel(const double* __restrict__ spart, int nparts,
+                                                           double inv_n, double* __restrict__ out) {
+  __shared__ double red[4][64];
+  const int k = threadIdx.x >> 6, j = threadIdx.x & 63;
   double s = 0.0;
-  for (int p = 0; p < nparts; ++p) s += spart[p * 4 + k];
-  out[k] = s * inv_n;
+  for (int p = j; p < nparts; p += 64) s += spart[p * 4 + k];
+  red[k][j] = s;
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0.0;
+    for (int q = 0; q < 64; ++q) t += red[threadIdx.x][q];
+    out[threadIdx.x] = t * inv_n;
+  }
 }
 
 // Adam with bias correction (Kingma & Ba 2015, Algorithm 1); bc1 = 1 -
@@ -766,6 +944,22 @@ cudaError_t gemm(int kind, const Gemm& g, cudaStream_t s) {
   dim3 grid((unsigned)((g.M + 63) / 64), (unsigned)((g.N + 63) / 64), (unsigned)((g.K + kc - 1) / kc));
   Gemm a = g;
   a.kchunk = kc;
+  // aligned float4 operands: the 128 x 64 kernel
+  auto al = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+  const bool ak = kind != 2, bk = kind == 0;
+  bool fast = al(g.A) && al(g.B) && g.lda % 4 == 0 && g.ldb % 4 == 0;
+  fast = fast && (ak ? (kc % 16 == 0 && g.K % 16 == 0) : g.M % 4 == 0);
+  fast = fast && (bk ? (kc % 16 == 0 && g.K % 16 == 0) : g.N % 4 == 0);
+  if (fast) {
+    dim3 grid2((unsigned)((g.M + 127) / 128), (unsigned)((g.N + 63) / 64), (unsigned)((g.K + kc - 1) / kc));
+    if (kind == 0)
+      sgemm128_kernel<true, true><<<grid2, 256, 0, s>>>(a);
+    else if (kind == 1)
+      sgemm128_kernel<true, false><<<grid2, 256, 0, s>>>(a);
+    else
+      sgemm128_kernel<false, false><<<grid2, 256, 0, s>>>(a);
+    return cudaGetLastError();
+  }
   if (kind == 0)
     sgemm_kernel<true, true><<<grid, 256, 0, s>>>(a);
   else if (kind == 1)
@@ -785,7 +979,7 @@ Gemm mk(const float* A, long long lda, const float* B, long long ldb, float* C, 
 }
 
 cudaError_t reduce(const float* part, int nparts, long long len, long long stride, float* out, cudaStream_t s) {
-  reduce_kernel<<<blocks_for(len, 256), 256, 0, s>>>(part, nparts, len, stride, out);
+  reduce_kernel<<<blocks_for(len, 32), 256, 0, s>>>(part, nparts, len, stride, out);
   return cudaGetLastError();
 }
 
@@ -840,7 +1034,7 @@ cudaError_t attn_fwd(const float* QKV, const int32_t* ne, const int32_t* sel, fl
 template <int DH>
 cudaError_t attn_bwd(const float* QKV, const float* P, const float* dO, float* dQKV, long long n, int T, int H,
                      cudaStream_t s) {
-  attn_bwd_kernel<DH><<<blocks_for(n * H * 32, 256), 256, 0, s>>>(QKV, P, dO, dQKV, n, T, H, 1.0f / sqrtf((float)DH));
+  attn_bwd_kernel<DH><<<blocks_for(n * H * 32, 128), 128, 0, s>>>(QKV, P, dO, dQKV, n, T, H, 1.0f / sqrtf((float)DH));
   return cudaGetLastError();
 }
 
@@ -978,7 +1172,7 @@ cudaError_t run(ut_tfm* t, const Call& c, int mode, const HeadArgs& ha_in, float
   const long long plen = 2 * d + (long long)t->n_out * d + t->n_out;
   e = reduce(t->part, kRowWarps, plen, plen, grad + o[idx], s);
   if (e != cudaSuccess) return e;
-  reduce_stats_kernel<<<1, 32, 0, s>>>(t->spart, kRowWarps, 1.0 / (double)c.n, t->stats_d);
+  reduce_stats_kernel<<<1, 256, 0, s>>>(t->spart, kRowWarps, 1.0 / (double)c.n, t->stats_d);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return backward<DJ, DH, TokT>(t, c, grad, s);
