@@ -18,7 +18,7 @@ from typing import Optional
 import numpy as np
 import torch
 
-from . import _abi, lib
+from . import _abi, lib, shard
 
 _vp = ctypes.c_void_p
 
@@ -133,6 +133,21 @@ def gae(reward, value, done, gamma, lam, agent_env=None, stream=None):
     return adv, ret, adv_a
 
 
+def dp_average(grad: torch.Tensor, n_local: int, group=None) -> int:
+    """Data parallelism: every rank holds a gradient of the mean loss over
+    its own n_local samples; afterwards each holds the gradient of the mean
+    over all ranks' samples (the row-weighted average), so identical Adam
+    steps keep the ranks' weights equal.  Returns the total sample count.
+    No-op without an initialised process group of more than one rank."""
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size(group) == 1:
+        return n_local
+    total = int(shard.reduce_sums([n_local], group)[0])
+    shard._weighted_mean_(grad, n_local, total, group)
+    return total
+
+
 @dataclass
 class PPOConfig:
     T: int = 64                 # steps collected per iteration
@@ -154,11 +169,17 @@ class Trainer:
     (its weights copied from the FP32 master after every update), the critic
     reads the true state of each env and keeps its own recurrent embedding
     (zero at reset, carried across the steps of the episode like the
-    agents')."""
+    agents').
 
-    def __init__(self, env, actor_params: np.ndarray, critic_params: np.ndarray, cfg: PPOConfig = PPOConfig()):
+    With a process group of several ranks (one env shard per rank, see
+    ``shard.shard_params``), each rank collects its own batch and every
+    minibatch gradient is averaged across the ranks by sample count before
+    the Adam step (``dp_average``)."""
+
+    def __init__(self, env, actor_params: np.ndarray, critic_params: np.ndarray, cfg: PPOConfig = PPOConfig(),
+                 group=None):
         p = env.params
-        self.env, self.cfg = env, cfg
+        self.env, self.cfg, self.group = env, cfg, group
         self.NA, self.E, self.NS, self.d = env.NA, env.E, env.NS, p.d_model
         T = cfg.T
         self.mb_actor = -(-T * self.NA // cfg.minibatches)
@@ -221,8 +242,11 @@ class Trainer:
         act, logp, adv = self.act.view(T * NA), self.logp.view(T * NA), self.adv_a.view(T * NA)
         ctok = self.ctok[:T].reshape(T * E, self.NS, 8)
         cne, ch, ret = self.cne[:T].reshape(T * E), self.ch[:T].reshape(T * E, self.d), self.ret.view(T * E)
+        import torch.distributed as dist
+
+        rank = dist.get_rank(self.group) if dist.is_available() and dist.is_initialized() else 0
         g = torch.Generator(device="cuda")
-        g.manual_seed(seed)
+        g.manual_seed(shard.rank_seed(seed, rank) & 0x7FFFFFFFFFFFFFFF)
         sa = sc = None
         for ep in range(c.epochs):
             pa = torch.randperm(T * NA, generator=g, device="cuda").to(torch.int32)
@@ -233,10 +257,12 @@ class Trainer:
                 if sel.numel():
                     sa = self.actor.actor_grad(tok, ne, h, act, logp, adv, sel=sel, clip_eps=c.clip_eps,
                                                ent_coef=c.ent_coef, stats=last)
+                    dp_average(self.actor.grad, sel.numel(), self.group)
                     self.actor.adam_step(c.lr_actor, c.beta1, c.beta2, c.eps)
                 sel = pc[k * self.mb_critic:(k + 1) * self.mb_critic]
                 if sel.numel():
                     sc = self.critic.value_grad(ctok, cne, ch, ret, sel=sel, stats=last)
+                    dp_average(self.critic.grad, sel.numel(), self.group)
                     self.critic.adam_step(c.lr_critic, c.beta1, c.beta2, c.eps)
         self.actor.sync_policy(self.env)
         return {"actor": sa, "critic": sc}

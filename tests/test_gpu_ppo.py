@@ -185,16 +185,17 @@ def test_gae_matches_oracle(gamma, lam):
     assert np.array_equal(adv_a.cpu().numpy(), adv.cpu().numpy()[:, agent_env])
 
 
-def _policy_env(n_envs=8, **kw):
-    p = preset("fleet5", n_envs=n_envs).replace(n_particles=64, **kw)
+def _policy_env(n_envs=8, name="fleet5", **kw):
+    p = preset(name, n_envs=n_envs).replace(n_particles=64, **kw)
     env = ut.Env(p)
     prm = synth.policy_params(synth.PolicyDims(p.d_model, p.n_layers, p.n_heads, p.n_actions), seed=53)
     env.set_policy(prm)
     return env, p, prm
 
 
-def test_state_tokens_match_oracle():
-    env, p, _ = _policy_env(n_envs=6, target_depth_max=30.0)
+@pytest.mark.parametrize("name", ["fleet5", "ragged"])
+def test_state_tokens_match_oracle(name):
+    env, p, _ = _policy_env(n_envs=6, name=name, target_depth_max=30.0)
     env.reset(3)
     for _ in range(3):
         env.step()
@@ -208,13 +209,14 @@ def test_state_tokens_match_oracle():
     to = np.concatenate([[0], np.cumsum(t_cnt)])
     arrs = [st[k].double().cpu().numpy() for k in ("ax", "ay", "apsi", "tx", "ty", "tz", "tpsi", "tspeed")]
     ref, rne = oracle.state_tokens_arrays(ao, to, NS, p.feature_scale, p.agent_speed, *arrs)
-    assert np.array_equal(ne.cpu().numpy(), rne)
+    assert np.array_equal(ne.cpu().numpy(), rne) and np.array_equal(rne, a_cnt + t_cnt)
     _close(tok.cpu().numpy(), ref, atol=2e-6, rtol=2e-6)
     assert np.abs(ref[:, :, 2]).max() > 0  # targets at depth
 
 
-def test_snapshot_and_record():
-    env, p, _ = _policy_env(n_envs=5)
+@pytest.mark.parametrize("name", ["fleet5", "ragged"])
+def test_snapshot_and_record(name):
+    env, p, _ = _policy_env(n_envs=5, name=name)
     env.reset(4)
     env.step()
     NA, NS, d = env.NA, env.NS, p.d_model
@@ -285,3 +287,26 @@ def test_trainer_fits_the_value_and_moves_the_policy():
     env.reset(7)
     o0 = env.step()["logits"].clone()
     assert not torch.equal(o0, o1)
+
+
+def test_trainer_on_a_ragged_fleet():
+    """Agents and targets per env vary: per-agent entity counts, the agent
+    -> env advantage map and ragged critic tokens all take part."""
+    env, p, prm = _policy_env(n_envs=24, name="ragged")
+    a_cnt, t_cnt = p.counts()
+    assert len(set(a_cnt.tolist())) > 1 and len(set(t_cnt.tolist())) > 1
+    crit = synth.policy_params(synth.PolicyDims(p.d_model, p.n_layers, p.n_heads, 1), seed=67)
+    tr = ppo.Trainer(env, prm, crit, ppo.PPOConfig(T=8, epochs=1, minibatches=2))
+    st = tr.iteration(3)
+    assert all(np.isfinite(st["actor"])) and all(np.isfinite(st["critic"]))
+    T = tr.cfg.T
+    assert np.array_equal(tr.ne[0].cpu().numpy(), np.repeat(a_cnt + t_cnt, a_cnt))
+    assert np.array_equal(tr.cne[0].cpu().numpy(), a_cnt + t_cnt)
+    # every agent carries its env's advantage
+    adv_a, adv = tr.adv_a.cpu().numpy(), tr.adv.cpu().numpy()
+    assert np.array_equal(adv_a, adv[:, np.repeat(np.arange(p.n_envs), a_cnt)])
+    # the recorded GAE against the oracle's on the recorded rewards, values and episode ends
+    ra, rr = oracle.gae(tr.rew.cpu().numpy(), tr.val.cpu().numpy(), tr.done.cpu().numpy(), tr.cfg.gamma,
+                        tr.cfg.lam)
+    _close(adv, ra, atol=2e-5, rtol=1e-5)
+    assert adv.shape == (T, p.n_envs)
