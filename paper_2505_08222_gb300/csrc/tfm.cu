@@ -27,7 +27,8 @@ namespace ut {
 namespace tfm {
 
 constexpr int kMaxT = 1 + UT_MAX_AGENTS + UT_MAX_TARGETS;  // tokens per sample
-constexpr int kRowBlocks = 304;                             // blocks of the warp-per-row kernels
+constexpr int kRowBlocks = 304;                             // blocks of the head / embedding-gradient kernels
+constexpr int kLnBlocks = 1216;                             // blocks of the LayerNorm kernels
 constexpr int kRowWarps = kRowBlocks * 8;                   // warps writing partial sums
 
 enum { EPI_STORE = 0, EPI_BIAS = 1, EPI_BIAS_RES = 2, EPI_BIAS_GELU = 3, EPI_GELU_GRAD = 4, EPI_PARTIAL = 5 };
@@ -53,6 +54,32 @@ struct Gemm {
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad_f(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+// The epilogues of the GEMM kernels for output (m, n) with accumulator v.
+__device__ __forceinline__ void epi_store(const Gemm& g, long long m, int n, float v) {
+  const long long o = m * g.ldc + n;
+  switch (g.epi) {
+    case EPI_BIAS:
+      g.C[o] = v + g.bias[n];
+      break;
+    case EPI_BIAS_RES:
+      g.C[o] = v + g.bias[n] + g.R[o];
+      break;
+    case EPI_BIAS_GELU:
+      v += g.bias[n];
+      g.C[o] = v;
+      g.C2[o] = gelu_f(v);
+      break;
+    case EPI_GELU_GRAD:
+      g.C[o] = v * gelu_grad_f(g.aux[o]);
+      break;
+    case EPI_PARTIAL:
+      g.C[((long long)blockIdx.z * g.M + m) * g.N + n] = v;
+      break;
+    default:
+      g.C[o] = v;
+  }
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -118,29 +145,7 @@ __global__ void __launch_bounds__(256) sgemm_kernel(Gemm g) {
     for (int j = 0; j < 4; ++j) {
       const int n = n0 + tx * 4 + j;
       if (n >= g.N) continue;
-      float v = acc[i][j];
-      const long long o = m * g.ldc + n;
-      switch (g.epi) {
-        case EPI_BIAS:
-          g.C[o] = v + g.bias[n];
-          break;
-        case EPI_BIAS_RES:
-          g.C[o] = v + g.bias[n] + g.R[o];
-          break;
-        case EPI_BIAS_GELU:
-          v += g.bias[n];
-          g.C[o] = v;
-          g.C2[o] = gelu_f(v);
-          break;
-        case EPI_GELU_GRAD:
-          g.C[o] = v * gelu_grad_f(g.aux[o]);
-          break;
-        case EPI_PARTIAL:
-          g.C[((long long)blockIdx.z * g.M + m) * g.N + n] = v;
-          break;
-        default:
-          g.C[o] = v;
-      }
+      epi_store(g, m, n, acc[i][j]);
     }
   }
 }
@@ -257,29 +262,7 @@ __global__ void __launch_bounds__(256) sgemm128_kernel(Gemm g) {
     for (int j = 0; j < 4; ++j) {
       const int n = n0 + tx * 4 + j;
       if (n >= g.N) continue;
-      float v = acc[i][j];
-      const long long o = m * g.ldc + n;
-      switch (g.epi) {
-        case EPI_BIAS:
-          g.C[o] = v + g.bias[n];
-          break;
-        case EPI_BIAS_RES:
-          g.C[o] = v + g.bias[n] + g.R[o];
-          break;
-        case EPI_BIAS_GELU:
-          v += g.bias[n];
-          g.C[o] = v;
-          g.C2[o] = gelu_f(v);
-          break;
-        case EPI_GELU_GRAD:
-          g.C[o] = v * gelu_grad_f(g.aux[o]);
-          break;
-        case EPI_PARTIAL:
-          g.C[((long long)blockIdx.z * g.M + m) * g.N + n] = v;
-          break;
-        default:
-          g.C[o] = v;
-      }
+      epi_store(g, m, n, acc[i][j]);
     }
   }
 }
@@ -348,8 +331,9 @@ __global__ void ln_fwd_kernel(const float* __restrict__ X, const float* __restri
 }
 
 // LayerNorm backward, one warp per row: out = base + dL/dX from dY (the
-// gradient at the LayerNorm output), and per-warp partial sums of dL/dg
-// (sum dY xh) and dL/db (sum dY) into part[warp][2d].  out may equal base.
+// gradient at the LayerNorm output), and per-block partial sums of dL/dg
+// (sum dY xh) and dL/db (sum dY) into part[block][2d] (blocks of 256
+// threads).  out may equal base.
 template <int DJ>
 __global__ void ln_bwd_kernel(const float* __restrict__ dY, const float* __restrict__ X,
                               const float* __restrict__ stat, const float* __restrict__ gam, const float* base,
@@ -383,10 +367,20 @@ __global__ void ln_bwd_kernel(const float* __restrict__ dY, const float* __restr
       out[o] = base[o] + rstd * (dxh[i] - m1 - xh[i] * m2);
     }
   }
+  // the block's 8 warps combined in warp order: one partial per block
+  __shared__ float red[8][2 * d];
+  const int wl = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < DJ; ++i) {
-    part[w0 * 2 * d + lane + 32 * i] = pg[i];
-    part[w0 * 2 * d + d + lane + 32 * i] = pb[i];
+    red[wl][lane + 32 * i] = pg[i];
+    red[wl][d + lane + 32 * i] = pb[i];
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < 2 * d; j += blockDim.x) {
+    float t = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += red[k][j];
+    part[(long long)blockIdx.x * 2 * d + j] = t;
   }
 }
 
@@ -787,22 +781,22 @@ __global__ void __launch_bounds__(256) colsum_kernel(const float* __restrict__ A
 }
 
 // out[i] = sum over p of part[p * stride + i]: block x sums columns
-// 32x .. 32x+31, thread row g the parts p = g (mod 8) in increasing p, then
-// the 8 row sums in order of g (a fixed association: deterministic).
-__global__ void __launch_bounds__(256) reduce_kernel(const float* __restrict__ part, int nparts, long long len,
-                                                     long long stride, float* __restrict__ out) {
-  __shared__ float red[8][33];
+// 32x .. 32x+31, thread row g the parts p = g (mod 32) in increasing p, then
+// the 32 row sums in order of g (a fixed association: deterministic).
+__global__ void __launch_bounds__(1024) reduce_kernel(const float* __restrict__ part, int nparts, long long len,
+                                                      long long stride, float* __restrict__ out) {
+  __shared__ float red[32][33];
   const int c = threadIdx.x & 31, g = threadIdx.x >> 5;
   const long long i = (long long)blockIdx.x * 32 + c;
   float s = 0.0f;
   if (i < len)
-    for (int p = g; p < nparts; p += 8) s += part[p * stride + i];
+    for (int p = g; p < nparts; p += 32) s += part[p * stride + i];
   red[g][c] = s;
   __syncthreads();
   if (g == 0 && i < len) {
     float t = 0.0f;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) t += red[k][c];
+    for (int k = 0; k < 32; ++k) t += red[k][c];
     out[i] = t;
   }
 }
@@ -979,7 +973,7 @@ Gemm mk(const float* A, long long lda, const float* B, long long ldb, float* C, 
 }
 
 cudaError_t reduce(const float* part, int nparts, long long len, long long stride, float* out, cudaStream_t s) {
-  reduce_kernel<<<blocks_for(len, 32), 256, 0, s>>>(part, nparts, len, stride, out);
+  reduce_kernel<<<blocks_for(len, 32), 1024, 0, s>>>(part, nparts, len, stride, out);
   return cudaGetLastError();
 }
 
@@ -1010,16 +1004,16 @@ cudaError_t wgrad(ut_tfm* t, const float* dOut, int n_o, const float* In, int n_
 
 template <int DJ>
 cudaError_t ln_fwd(const float* X, const float* g, const float* b, float* Y, float* st, long long rows, cudaStream_t s) {
-  ln_fwd_kernel<DJ><<<kRowBlocks, 256, 0, s>>>(X, g, b, Y, st, rows);
+  ln_fwd_kernel<DJ><<<kLnBlocks, 256, 0, s>>>(X, g, b, Y, st, rows);
   return cudaGetLastError();
 }
 
 template <int DJ>
 cudaError_t ln_bwd(ut_tfm* t, const float* dY, const float* X, const float* st, const float* g, const float* base,
                    float* out, float* grad_gb, long long rows, cudaStream_t s) {
-  ln_bwd_kernel<DJ><<<kRowBlocks, 256, 0, s>>>(dY, X, st, g, base, out, t->part, rows);
+  ln_bwd_kernel<DJ><<<kLnBlocks, 256, 0, s>>>(dY, X, st, g, base, out, t->part, rows);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = reduce(t->part, kRowWarps, 2 * 32 * DJ, 2 * 32 * DJ, grad_gb, s);
+  if (e == cudaSuccess) e = reduce(t->part, kLnBlocks, 2 * 32 * DJ, 2 * 32 * DJ, grad_gb, s);
   return e;
 }
 
@@ -1254,6 +1248,7 @@ extern "C" ut_status tfm_create(const ut_tfm_config* cfg, const float* params_ho
   part = std::max(part, (size_t)256 * 4 * d);
   part = std::max(part, (size_t)kRowWarps * (2 * d + (size_t)t->n_out * d + t->n_out));
   part = std::max(part, (size_t)kRowWarps * 9 * d);
+  part = std::max(part, (size_t)kLnBlocks * 2 * d);
   bool ok = true;
   auto A = [&](size_t n) -> float* {
     float* p = (float*)dalloc(t, n * 4);
