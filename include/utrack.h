@@ -598,6 +598,38 @@ ut_status env_state_tokens(ut_env* env, float* tokens_dev, int32_t* n_ent_dev);
 ut_status env_ppo_snapshot(ut_env* env, uint16_t* tokens_dev, int32_t* n_ent_dev, float* h_dev);
 ut_status env_ppo_record(ut_env* env, int32_t* actions_dev, float* logp_dev, float* reward_dev, int32_t* done_dev);
 
+/* Device buffers of one PPO collection of T steps (all on the env's GPU;
+ * NA agents, E envs, NS = A_max + T_max slots, d the agent's d_model, dc the
+ * critic's): tokens [T][NA][NS][8] BF16, n_ent [T][NA], h [T][NA][d],
+ * actions [T][NA], logp [T][NA], reward [T][E], done [T][E] (as
+ * env_ppo_snapshot / env_ppo_record), ctokens [T+1][E][NS][8] FP32 and
+ * cn_ent [T+1][E] (as env_state_tokens), ch [T+2][E][dc] the critic's
+ * recurrent embedding (ch[0] read: the caller sets it, zero at an episode
+ * start; ch[t+1] written from the forward at t), value [T+1][E]. */
+typedef struct ut_ppo_buffers {
+  uint16_t* tokens;
+  int32_t* n_ent;
+  float* h;
+  int32_t* actions;
+  float* logp;
+  float* reward;
+  int32_t* done;
+  float* ctokens;
+  int32_t* cn_ent;
+  float* ch;
+  float* value;
+} ut_ppo_buffers;
+
+/* T collection steps as one CUDA graph (captured on first use, reused while
+ * the arguments and the env's step configuration stay the same): for t = 0 ..
+ * T-1 the critic tokens and forward at t, the snapshot, one env_step with the
+ * transformer agent acting and the record; then the critic at T (the
+ * bootstrap value).  The same kernels and results as the sequence of the
+ * separate calls.  critic: a ut_tfm with n_out 1, FP32 tokens, n_slots = NS
+ * and max_batch >= E.  Enqueued on the env's stream.  Errors: UT_ERR_INVALID,
+ * UT_ERR_STATE (no env_reset or no agent weights), UT_ERR_CUDA. */
+ut_status env_ppo_collect(ut_env* env, ut_tfm* critic, int32_t T, const ut_ppo_buffers* buffers);
+
 #ifdef __cplusplus
 }
 #endif

@@ -96,6 +96,11 @@ class TfmConfig(ctypes.Structure):
                 ("tokens_bf16", ctypes.c_int32), ("reserved", ctypes.c_int32), ("max_batch", ctypes.c_int64)]
 
 
+class PpoBuffers(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("tokens", "n_ent", "h", "actions", "logp", "reward", "done", "ctokens",
+                                              "cn_ent", "ch", "value")]
+
+
 class RolloutStats(ctypes.Structure):
     _fields_ = [("sum_sq_err", ctypes.c_double), ("n_err", ctypes.c_int64), ("rmse", ctypes.c_double),
                 ("reward_sum", ctypes.c_double), ("crash_count", ctypes.c_int64),
@@ -161,6 +166,7 @@ SIGNATURES = {
     "env_state_tokens": (ctypes.c_int, [_vp, _vp, _vp]),
     "env_ppo_snapshot": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "env_ppo_record": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "env_ppo_collect": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.POINTER(PpoBuffers)]),
 }
 
 _lib = None

@@ -366,6 +366,7 @@ void env_destroy(ut_env* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->ppo_exec) cudaGraphExecDestroy(h->ppo_exec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
@@ -443,6 +444,17 @@ cudaError_t enqueue_step(ut_env* h, const int32_t* act, cudaStream_t s) {
   return launch_advance(h->d, s);
 }
 
+
+// The capture stream and fork/join events of a handle, created on first use.
+cudaError_t capture_stream_ensure(ut_env* h) {
+  cudaError_t e = cudaSuccess;
+  if (!h->cap_stream) {
+    e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+  }
+  return e;
+}
 }  // namespace ut
 
 extern "C" {
@@ -495,11 +507,7 @@ ut_status env_metrics(ut_env* h, ut_rollout_stats* out) {
 }
 
 static ut_status graph_ensure(ut_env* h, int32_t T) {
-  if (!h->cap_stream) {
-    UT_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-    UT_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
-    UT_CUDA(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
-  }
+  UT_CUDA(h, ut::capture_stream_ensure(h));
   const int key = T * 16 + (h->policy_ready ? 1 : 0) + 2 * h->est_mode;  // est_mode 0..4
   if (!h->graph_exec || h->graph_key != key || h->graph_variant != h->pf_variant) {
     if (h->graph_exec) {

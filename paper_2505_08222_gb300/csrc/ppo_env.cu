@@ -10,6 +10,9 @@
 #include "../../include/utrack.h"
 #include "env.cuh"
 #include "runtime.cuh"
+#include "tfm.cuh"
+
+#include <vector>
 
 namespace ut {
 namespace {
@@ -53,21 +56,19 @@ __global__ void state_tokens_kernel(EnvDev d, float* __restrict__ tok, int32_t* 
   if (s == 0) n_ent[e] = A + T;
 }
 
-// Entity counts of the agents (A_e + T_e) and their recurrent embedding
-// (BF16) widened to FP32; one thread per agent.
-__global__ void snapshot_kernel(EnvDev d, const uint16_t* __restrict__ h_bf16, int dm, int32_t* __restrict__ n_ent,
-                                float* __restrict__ h_out) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.E) return;
-  const int e = (int)i;
+// Entity counts of the agents (A_e + T_e), one thread per env.
+__global__ void snapshot_nent_kernel(EnvDev d, int32_t* __restrict__ n_ent) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.E) return;
   const int a0 = d.agent_off[e], a1 = d.agent_off[e + 1];
   const int ne = (a1 - a0) + (d.target_off[e + 1] - d.target_off[e]);
-  for (int a = a0; a < a1; ++a) {
-    if (n_ent) n_ent[a] = ne;
-    if (h_out)
-      for (int j = 0; j < dm; ++j)
-        h_out[(long long)a * dm + j] = __uint_as_float((uint32_t)h_bf16[(long long)a * dm + j] << 16);
-  }
+  for (int a = a0; a < a1; ++a) n_ent[a] = ne;
+}
+
+// The agents' recurrent embedding (BF16) widened to FP32, one thread per value.
+__global__ void snapshot_h_kernel(const uint16_t* __restrict__ h_bf16, long long n, float* __restrict__ h_out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) h_out[i] = __uint_as_float((uint32_t)h_bf16[i] << 16);
 }
 
 // Log-probability of each agent's action under its logits (log-softmax in
@@ -87,6 +88,35 @@ __global__ void logp_kernel(const float* __restrict__ logits, const int32_t* __r
 }
 
 inline unsigned blocks(long long n) { return (unsigned)((n + 255) / 256); }
+
+// One collection step t of env_ppo_collect on stream s (t == T: the last
+// critic forward only).
+cudaError_t collect_step(ut_env* h, ut_tfm* critic, const ut_ppo_buffers& b, int t, int T, cudaStream_t s) {
+  const long long E = h->d.E, NA = h->NA, NS = h->d.NS, dm = h->cfg.d_model;
+  const long long dc = tfm_info(critic).d;
+  float* ctok = b.ctokens + t * E * NS * 8;
+  int32_t* cne = b.cn_ent + t * E;
+  state_tokens_kernel<<<blocks(E * NS), 256, 0, s>>>(h->d, ctok, cne);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = tfm_forward_on(critic, ctok, cne, b.ch + t * E * dc, E, b.value + t * E, b.ch + (t + 1) * E * dc, s);
+  if (e != cudaSuccess || t == T) return e;
+  e = cudaMemcpyAsync(b.tokens + t * NA * NS * 8, h->d.obs, (size_t)NA * NS * 8 * 2, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return e;
+  snapshot_nent_kernel<<<blocks(E), 256, 0, s>>>(h->d, b.n_ent + t * NA);
+  snapshot_h_kernel<<<blocks(NA * dm), 256, 0, s>>>(extension_h(h), NA * dm, b.h + t * NA * dm);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = enqueue_step(h, nullptr, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b.actions + t * NA, h->d.actions, (size_t)NA * 4, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return e;
+  logp_kernel<<<blocks(NA), 256, 0, s>>>(extension_logits(h), h->d.actions, h->cfg.n_actions, NA, b.logp + t * NA);
+  e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b.reward + t * E, h->d.reward, (size_t)E * 4, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b.done + t * E, h->d.done, (size_t)E * 4, cudaMemcpyDeviceToDevice, s);
+  return e;
+}
 
 ut_status cuda_fail(ut_env* h, const char* what, cudaError_t e) {
   h->err = std::string(what) + ": " + cudaGetErrorString(e);
@@ -116,8 +146,14 @@ extern "C" ut_status env_ppo_snapshot(ut_env* h, uint16_t* tokens_dev, int32_t* 
   cudaError_t e = cudaSuccess;
   if (tokens_dev)
     e = cudaMemcpyAsync(tokens_dev, h->d.obs, (size_t)h->NA * h->d.NS * 8 * 2, cudaMemcpyDeviceToDevice, h->stream);
-  if (e == cudaSuccess && (n_ent_dev || h_dev)) {
-    snapshot_kernel<<<blocks(h->d.E), 256, 0, h->stream>>>(h->d, hb, h->cfg.d_model, n_ent_dev, h_dev);
+  if (e == cudaSuccess && n_ent_dev) {
+    snapshot_nent_kernel<<<blocks(h->d.E), 256, 0, h->stream>>>(h->d, n_ent_dev);
+    h->launches += 1;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && h_dev) {
+    const long long n = (long long)h->NA * h->cfg.d_model;
+    snapshot_h_kernel<<<blocks(n), 256, 0, h->stream>>>(hb, n, h_dev);
     h->launches += 1;
     e = cudaGetLastError();
   }
@@ -145,4 +181,57 @@ extern "C" ut_status env_ppo_record(ut_env* h, int32_t* actions_dev, float* logp
   if (e == cudaSuccess && done_dev)
     e = cudaMemcpyAsync(done_dev, h->d.done, (size_t)h->d.E * 4, cudaMemcpyDeviceToDevice, h->stream);
   return e == cudaSuccess ? UT_OK : cuda_fail(h, "env_ppo_record", e);
+}
+
+extern "C" ut_status env_ppo_collect(ut_env* h, ut_tfm* critic, int32_t T, const ut_ppo_buffers* b) {
+  if (!h || !critic || !b || T < 1) return UT_ERR_INVALID;
+  if (!b->tokens || !b->n_ent || !b->h || !b->actions || !b->logp || !b->reward || !b->done || !b->ctokens ||
+      !b->cn_ent || !b->ch || !b->value)
+    return UT_ERR_INVALID;
+  if (!h->reset_done || !h->policy_ready || !extension_h(h)) {
+    h->err = "env_ppo_collect: needs env_reset and the transformer agent's weights";
+    return UT_ERR_STATE;
+  }
+  const TfmInfo ci = tfm_info(critic);
+  if (ci.n_out != 1 || ci.tokens_bf16 != 0 || ci.n_slots != h->d.NS || ci.max_batch < h->d.E) {
+    h->err = "env_ppo_collect: the critic needs n_out 1, FP32 tokens, the env's slots and max_batch >= n_envs";
+    return UT_ERR_INVALID;
+  }
+  cudaError_t e = capture_stream_ensure(h);
+  if (e != cudaSuccess) return cuda_fail(h, "env_ppo_collect", e);
+  // the graph is rebuilt when any argument or the step's configuration changes
+  std::vector<uintptr_t> key = {(uintptr_t)critic, (uintptr_t)T, (uintptr_t)h->pf_variant, (uintptr_t)h->est_mode};
+  for (const void* p : {(const void*)b->tokens, (const void*)b->n_ent, (const void*)b->h, (const void*)b->actions,
+                        (const void*)b->logp, (const void*)b->reward, (const void*)b->done, (const void*)b->ctokens,
+                        (const void*)b->cn_ent, (const void*)b->ch, (const void*)b->value})
+    key.push_back((uintptr_t)p);
+  if (!h->ppo_exec || h->ppo_key != key) {
+    if (h->ppo_exec) {
+      cudaGraphExecDestroy(h->ppo_exec);
+      h->ppo_exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    const int64_t launches_before = h->launches;
+    h->capturing = true;
+    e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    cudaError_t ec = cudaSuccess;
+    for (int t = 0; t <= T && e == cudaSuccess && ec == cudaSuccess; ++t) ec = collect_step(h, critic, *b, t, T, h->cap_stream);
+    const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(h->cap_stream, &graph) : e;
+    h->capturing = false;
+    h->launches = launches_before;
+    if (ec != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(h, "env_ppo_collect capture", ec != cudaSuccess ? ec : e2);
+    }
+    e = cudaGraphInstantiate(&h->ppo_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(h, "env_ppo_collect instantiate", e);
+    h->ppo_key = key;
+  }
+  e = cudaEventRecord(h->ev_fork, h->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->cap_stream, h->ev_fork, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(h->ppo_exec, h->cap_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_join, h->cap_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_join, 0);
+  return e == cudaSuccess ? UT_OK : cuda_fail(h, "env_ppo_collect", e);
 }

@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <string>
 #include <vector>
 
@@ -32,6 +33,9 @@ struct ut_env {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   int graph_key = -1, graph_variant = -1;
+  // graph-captured PPO collection (env_ppo_collect), keyed by its arguments
+  cudaGraphExec_t ppo_exec = nullptr;
+  std::vector<uintptr_t> ppo_key;
   // host count of kernels enqueued since the metrics were cleared
   int64_t launches = 0;
   int launches_per_graph = 0;
@@ -52,6 +56,7 @@ namespace ut {
 void* env_alloc(ut_env* h, size_t bytes);
 void env_free_all(ut_env* h);
 cudaError_t enqueue_step(ut_env* h, const int32_t* act, cudaStream_t s);
+cudaError_t capture_stream_ensure(ut_env* h);
 int count_step_kernels(ut_env* h);
 
 // Hooks implemented by the policy / estimator modules.

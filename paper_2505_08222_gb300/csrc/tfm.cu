@@ -22,6 +22,7 @@
 
 #include "../../include/utrack.h"
 #include "common.cuh"
+#include "tfm.cuh"
 
 namespace ut {
 namespace tfm {
@@ -1217,6 +1218,27 @@ bool call_ok(const ut_tfm* t, const void* tok, const int32_t* ne, const float* h
 }  // namespace ut
 
 using namespace ut::tfm;
+
+namespace ut {
+
+TfmInfo tfm_info(const ut_tfm* t) {
+  return TfmInfo{t->d, t->L, t->H, t->n_out, t->NS, t->cfg.tokens_bf16, (long long)t->cfg.max_batch};
+}
+
+cudaError_t tfm_forward_on(ut_tfm* t, const void* tokens, const int32_t* n_ent, const float* h, long long n,
+                           float* out, float* h_out, cudaStream_t s) {
+  HeadArgs ha;
+  std::memset(&ha, 0, sizeof(ha));
+  ha.out = out;
+  ha.h_out = h_out;
+  const cudaStream_t own = t->stream;
+  t->stream = s;
+  const cudaError_t e = dispatch(t, Call{tokens, n_ent, h, nullptr, n}, 0, ha, nullptr);
+  t->stream = own;
+  return e;
+}
+
+}  // namespace ut
 
 extern "C" int64_t tfm_param_count(const ut_tfm_config* cfg) {
   if (!valid_config(cfg)) return -1;

@@ -212,9 +212,23 @@ class Trainer:
             raise TfmError(f"{what}: {_abi.STATUS.get(rc, rc)} {raw.decode() if raw else ''}")
 
     def collect(self, seed: int):
-        """T steps from env_reset(seed): actor inputs, actions, behaviour
-        log-probabilities, rewards, episode ends, critic tokens and values
-        (T + 1 of them: the last bootstraps)."""
+        """T steps from env_reset(seed) as one CUDA graph (env_ppo_collect):
+        actor inputs, actions, behaviour log-probabilities, rewards, episode
+        ends, critic tokens and values (T + 1 of them: the last bootstraps)."""
+        self.env.reset(seed)
+        self.ch[0].zero_()
+        b = self._buffers()
+        self._env_call(lib.env_ppo_collect(self.env.h, self.critic.h, self.cfg.T, ctypes.byref(b)), "env_ppo_collect")
+
+    def _buffers(self):
+        if getattr(self, "_bufs", None) is None:
+            self._bufs = _abi.PpoBuffers(*[t.data_ptr() for t in (self.tok, self.ne, self.h, self.act, self.logp,
+                                                                   self.rew, self.done, self.ctok, self.cne, self.ch,
+                                                                   self.val)])
+        return self._bufs
+
+    def collect_eager(self, seed: int):
+        """The same collection as separate calls, step by step."""
         env, T = self.env, self.cfg.T
         env.reset(seed)
         self.ch[0].zero_()

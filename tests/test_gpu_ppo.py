@@ -310,3 +310,19 @@ def test_trainer_on_a_ragged_fleet():
                         tr.cfg.lam)
     _close(adv, ra, atol=2e-5, rtol=1e-5)
     assert adv.shape == (T, p.n_envs)
+
+
+def test_graph_collection_equals_the_step_by_step_calls():
+    env, p, prm = _policy_env(n_envs=16, name="ragged")
+    crit = synth.policy_params(synth.PolicyDims(p.d_model, p.n_layers, p.n_heads, 1), seed=71)
+    tr = ppo.Trainer(env, prm, crit, ppo.PPOConfig(T=6, epochs=1, minibatches=1))
+    names = ("tok", "ne", "h", "act", "logp", "rew", "done", "ctok", "cne", "ch", "val")
+    tr.collect_eager(9)
+    eager = {k: getattr(tr, k).clone() for k in names}
+    for _ in range(2):  # the captured graph, then its replay
+        for k in names:
+            getattr(tr, k).fill_(-7)
+        tr.collect(9)
+        torch.cuda.synchronize()
+        for k in names:
+            assert torch.equal(getattr(tr, k), eager[k]), k
