@@ -3,7 +3,7 @@ inputs, through the C ABI.
 
 Tolerances (float32 kernel arithmetic against float64):
   positions, headings, ranges, predicted particles: 1e-5 relative, the
-  spec bound for one step from an injected state; relative to
+  required bound for one step from an injected state; relative to
   max(|x|, 100 m) for coordinates (a coordinate is the difference of terms of
   the spawn scale, so near the origin float32 cancellation leaves an
   absolute error of that scale times 1e-7), max(|v|, 1 m/s) for velocities;
@@ -226,8 +226,8 @@ def test_step_parity_from_injected_state(name, n_envs, P, kw):
                                               ("fleet5", 256, 100, 1024, {"shared_filter": 1}),
                                               ("fleet5", 128, 100, 1024, {"pf_ess_num": 8})])
 def test_rollout_rmse_matches_oracle(name, n_envs, T, P, kw):
-    """Mean tracking RMSE of whole rollouts agrees within 2% (north-star
-    bound).  'Mean tracking RMSE' = mean over filters of each filter's RMSE
+    """Mean tracking RMSE of whole rollouts agrees within 2% (the required
+    whole-rollout bound).  'Mean tracking RMSE' = mean over filters of each filter's RMSE
     over the rollout.  Both sides draw the same random numbers, but float32
     and float64 weights place a resampling threshold on different sides of a
     CDF step now and then, after which the two filters are different (equally
