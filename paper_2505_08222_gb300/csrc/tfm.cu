@@ -385,36 +385,52 @@ __global__ void ln_bwd_kernel(const float* __restrict__ dY, const float* __restr
   }
 }
 
-// Self-attention of one (sample, head) per warp, lane t = query token t:
+// Attention work items: pair q = s * H + head.  A warp takes hp = 2 pairs
+// when 2T <= 32 (lanes 0..T-1 the first, T..2T-1 the second), else one.
+__host__ __device__ __forceinline__ int attn_pairs_per_warp(int T) { return 2 * T <= 32 ? 2 : 1; }
+constexpr int kAttnStage = 32;  // staged rows per warp: hp * T <= 32
+
+// Self-attention, lane (slot, t) = query token t of pair q0 + slot:
 // P[s][head][t][u] (zero for masked keys u > n_ent) and O = P V.  The warp
-// first copies the head's K and V rows of its sample to shared memory.
+// first copies its pairs' K and V rows to shared memory.  4 warps per block.
 template <int DH>
-__global__ void __launch_bounds__(256) attn_fwd_kernel(const float* __restrict__ QKV,
+__global__ void __launch_bounds__(128) attn_fwd_kernel(const float* __restrict__ QKV,
                                                        const int32_t* __restrict__ n_ent,
                                                        const int32_t* __restrict__ sel, float* __restrict__ P,
                                                        float* __restrict__ O, long long n, int T, int NS, int H,
                                                        float scale) {
-  __shared__ float sk[8][kMaxT * DH];
-  __shared__ float sv[8][kMaxT * DH];
+  __shared__ float sk[4][kAttnStage * DH];
+  __shared__ float sv[4][kAttnStage * DH];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (w >= n * H) return;  // whole warps leave together
-  const long long s = w / H;
-  const int hh = (int)(w - s * H);
+  const int hp = attn_pairs_per_warp(T);
+  const long long q0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * hp;
+  const long long nq = n * H;
+  if (q0 >= nq) return;  // whole warps leave together
   const int d = DH * H, ld = 3 * d;
+  for (int i = lane; i < hp * T * DH; i += 32) {
+    const int slot = i / (T * DH), r = i - slot * T * DH, u = r / DH, j = r - u * DH;
+    const long long q = q0 + slot;
+    if (q < nq) {
+      const long long s = q / H;
+      const float* base = QKV + s * T * ld + (q - s * H) * DH;
+      sk[wl][i] = base[u * ld + d + j];
+      sv[wl][i] = base[u * ld + 2 * d + j];
+    }
+  }
+  __syncwarp();
+  const int slot = lane / T, t = lane - slot * T;
+  const long long q = q0 + slot;
+  if (slot >= hp || q >= nq) return;
+  const long long s = q / H;
+  const int hh = (int)(q - s * H);
   int ne = n_ent[sel ? (long long)sel[s] : s];
   ne = ne < 0 ? 0 : (ne > NS ? NS : ne);
   const float* base = QKV + s * T * ld + hh * DH;
-  for (int i = lane; i < T * DH; i += 32) {
-    const int u = i / DH, j = i - u * DH;
-    sk[wl][i] = base[u * ld + d + j];
-    sv[wl][i] = base[u * ld + 2 * d + j];
-  }
-  __syncwarp();
-  if (lane >= T) return;
-  float q[DH];
+  const float* K = sk[wl] + slot * T * DH;
+  const float* V = sv[wl] + slot * T * DH;
+  float qv[DH];
 #pragma unroll
-  for (int j = 0; j < DH; ++j) q[j] = base[lane * ld + j];
+  for (int j = 0; j < DH; ++j) qv[j] = base[t * ld + j];
   float sc[kMaxT];
   float mx = -INFINITY;
 #pragma unroll
@@ -423,7 +439,7 @@ __global__ void __launch_bounds__(256) attn_fwd_kernel(const float* __restrict__
     if (u < T && u <= ne) {
       float acc = 0.0f;
 #pragma unroll
-      for (int j = 0; j < DH; ++j) acc = fmaf(q[j], sk[wl][u * DH + j], acc);
+      for (int j = 0; j < DH; ++j) acc = fmaf(qv[j], K[u * DH + j], acc);
       sc[u] = acc * scale;
       mx = fmaxf(mx, sc[u]);
     }
@@ -439,7 +455,7 @@ __global__ void __launch_bounds__(256) attn_fwd_kernel(const float* __restrict__
   float o[DH];
 #pragma unroll
   for (int j = 0; j < DH; ++j) o[j] = 0.0f;
-  float* Pr = P + ((s * H + hh) * T + lane) * T;
+  float* Pr = P + ((s * H + hh) * T + t) * T;
 #pragma unroll
   for (int u = 0; u < kMaxT; ++u) {
     if (u < T) {
@@ -447,12 +463,12 @@ __global__ void __launch_bounds__(256) attn_fwd_kernel(const float* __restrict__
       Pr[u] = p;
       if (u <= ne) {
 #pragma unroll
-        for (int j = 0; j < DH; ++j) o[j] = fmaf(p, sv[wl][u * DH + j], o[j]);
+        for (int j = 0; j < DH; ++j) o[j] = fmaf(p, V[u * DH + j], o[j]);
       }
     }
   }
 #pragma unroll
-  for (int j = 0; j < DH; ++j) O[(s * T + lane) * d + hh * DH + j] = o[j];
+  for (int j = 0; j < DH; ++j) O[(s * T + t) * d + hh * DH + j] = o[j];
 }
 
 // Attention backward of one (sample, head) per warp (4 warps per block): from
@@ -1021,7 +1037,8 @@ cudaError_t ln_bwd(ut_tfm* t, const float* dY, const float* X, const float* st, 
 template <int DH>
 cudaError_t attn_fwd(const float* QKV, const int32_t* ne, const int32_t* sel, float* P, float* O, long long n, int T,
                      int NS, int H, cudaStream_t s) {
-  attn_fwd_kernel<DH><<<blocks_for(n * H * 32, 256), 256, 0, s>>>(QKV, ne, sel, P, O, n, T, NS, H,
+  const long long warps = (n * H + attn_pairs_per_warp(T) - 1) / attn_pairs_per_warp(T);
+  attn_fwd_kernel<DH><<<blocks_for(warps * 32, 128), 128, 0, s>>>(QKV, ne, sel, P, O, n, T, NS, H,
                                                                    1.0f / sqrtf((float)DH));
   return cudaGetLastError();
 }
