@@ -626,8 +626,13 @@ typedef struct ut_ppo_buffers {
  * transformer agent acting and the record; then the critic at T (the
  * bootstrap value).  The same kernels and results as the sequence of the
  * separate calls.  critic: a ut_tfm with n_out 1, FP32 tokens, n_slots = NS
- * and max_batch >= E.  Enqueued on the env's stream.  Errors: UT_ERR_INVALID,
- * UT_ERR_STATE (no env_reset or no agent weights), UT_ERR_CUDA. */
+ * and max_batch >= E; its activation buffers are used by the graph, which
+ * starts after the work already enqueued on the env's stream, so work on the
+ * critic handle must be ordered with that stream (create it on the env's
+ * stream).  The graph reads the weights at run time: later weight updates
+ * (tfm_adam_step, env_set_policy) are seen without a new capture.  Enqueued
+ * on the env's stream.  Errors: UT_ERR_INVALID, UT_ERR_STATE (no env_reset or
+ * no agent weights), UT_ERR_CUDA. */
 ut_status env_ppo_collect(ut_env* env, ut_tfm* critic, int32_t T, const ut_ppo_buffers* buffers);
 
 #ifdef __cplusplus
