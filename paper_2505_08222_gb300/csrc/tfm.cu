@@ -152,30 +152,30 @@ __global__ void __launch_bounds__(256) sgemm_kernel(Gemm g) {
 }
 
 // The same product with a 128 x 64 tile, 8 x 4 outputs per thread, float4
-// global loads and the next K slice prefetched into registers while the
-// current one is multiplied.  Preconditions (checked on the host): the
-// contiguous dimension of each operand is read in aligned float4 (leading
-// dimensions and base addresses multiples of 4 floats; M, N multiples of 4
-// where they are contiguous), and with k-contiguous operands the K range is
-// a multiple of 16.
+// global loads, K staged 32 at a time, the next K slice prefetched into
+// registers while the current one is multiplied.  Preconditions (checked on
+// the host): the contiguous dimension of each operand is read in aligned
+// float4 (leading dimensions and base addresses multiples of 4 floats; M, N
+// multiples of 4 where they are contiguous), and with k-contiguous operands
+// the K range is a multiple of 32.
 template <bool AK, bool BK>
 __global__ void __launch_bounds__(256) sgemm128_kernel(Gemm g) {
-  __shared__ __align__(16) float As[2][16][132];
-  __shared__ __align__(16) float Bs[2][16][68];
+  __shared__ __align__(16) float As[32][132];
+  __shared__ __align__(16) float Bs[32][68];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const long long m0 = (long long)blockIdx.x * 128;
   const int n0 = blockIdx.y * 64;
   const long long kb = (long long)blockIdx.z * g.kchunk;
   const long long ke = kb + g.kchunk < g.K ? kb + g.kchunk : g.K;
-  float4 ra[2], rb;
-  // A slice: 128 (m) x 16 (k) as 512 float4, two per thread
+  float4 ra[4], rb[2];
+  // A slice: 128 (m) x 32 (k) as 1024 float4, four per thread
   auto load_a = [&](long long k0) {
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
+    for (int r = 0; r < 4; ++r) {
       const int i = tid + r * 256;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (AK) {
-        const long long m = m0 + (i >> 2), k = k0 + (i & 3) * 4;
+        const long long m = m0 + (i >> 3), k = k0 + (i & 7) * 4;
         if (m < g.M && k < ke) v = *reinterpret_cast<const float4*>(g.A + m * g.lda + k);
       } else {
         const long long k = k0 + (i >> 5), m = m0 + (i & 31) * 4;
@@ -184,42 +184,50 @@ __global__ void __launch_bounds__(256) sgemm128_kernel(Gemm g) {
       ra[r] = v;
     }
   };
-  // B slice: 16 (k) x 64 (n) as 256 float4, one per thread
+  // B slice: 32 (k) x 64 (n) as 512 float4, two per thread
   auto load_b = [&](long long k0) {
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (BK) {
-      const int n = n0 + (tid >> 2);
-      const long long k = k0 + (tid & 3) * 4;
-      if (n < g.N && k < ke) v = *reinterpret_cast<const float4*>(g.B + (long long)n * g.ldb + k);
-    } else {
-      const long long k = k0 + (tid >> 4);
-      const int n = n0 + (tid & 15) * 4;
-      if (n < g.N && k < ke) v = *reinterpret_cast<const float4*>(g.B + k * g.ldb + n);
-    }
-    rb = v;
-  };
-  auto store = [&](int buf) {
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       const int i = tid + r * 256;
-      if (AK) {
-        const int mm = i >> 2, kk = (i & 3) * 4;
-        As[buf][kk][mm] = ra[r].x;
-        As[buf][kk + 1][mm] = ra[r].y;
-        As[buf][kk + 2][mm] = ra[r].z;
-        As[buf][kk + 3][mm] = ra[r].w;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (BK) {
+        const int n = n0 + (i >> 3);
+        const long long k = k0 + (i & 7) * 4;
+        if (n < g.N && k < ke) v = *reinterpret_cast<const float4*>(g.B + (long long)n * g.ldb + k);
       } else {
-        *reinterpret_cast<float4*>(&As[buf][i >> 5][(i & 31) * 4]) = ra[r];
+        const long long k = k0 + (i >> 4);
+        const int n = n0 + (i & 15) * 4;
+        if (n < g.N && k < ke) v = *reinterpret_cast<const float4*>(g.B + k * g.ldb + n);
+      }
+      rb[r] = v;
+    }
+  };
+  auto store = [&]() {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = tid + r * 256;
+      if (AK) {
+        const int mm = i >> 3, kk = (i & 7) * 4;
+        As[kk][mm] = ra[r].x;
+        As[kk + 1][mm] = ra[r].y;
+        As[kk + 2][mm] = ra[r].z;
+        As[kk + 3][mm] = ra[r].w;
+      } else {
+        *reinterpret_cast<float4*>(&As[i >> 5][(i & 31) * 4]) = ra[r];
       }
     }
-    if (BK) {
-      const int nn = tid >> 2, kk = (tid & 3) * 4;
-      Bs[buf][kk][nn] = rb.x;
-      Bs[buf][kk + 1][nn] = rb.y;
-      Bs[buf][kk + 2][nn] = rb.z;
-      Bs[buf][kk + 3][nn] = rb.w;
-    } else {
-      *reinterpret_cast<float4*>(&Bs[buf][tid >> 4][(tid & 15) * 4]) = rb;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int i = tid + r * 256;
+      if (BK) {
+        const int nn = i >> 3, kk = (i & 7) * 4;
+        Bs[kk][nn] = rb[r].x;
+        Bs[kk + 1][nn] = rb[r].y;
+        Bs[kk + 2][nn] = rb[r].z;
+        Bs[kk + 3][nn] = rb[r].w;
+      } else {
+        *reinterpret_cast<float4*>(&Bs[i >> 4][(i & 15) * 4]) = rb[r];
+      }
     }
   };
   float acc[8][4];
@@ -227,33 +235,34 @@ __global__ void __launch_bounds__(256) sgemm128_kernel(Gemm g) {
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
-  int buf = 0;
   if (kb < ke) {
     load_a(kb);
     load_b(kb);
-    store(0);
+    store();
   }
   __syncthreads();
-  for (long long k0 = kb; k0 < ke; k0 += 16) {
-    const bool more = k0 + 16 < ke;
+  for (long long k0 = kb; k0 < ke; k0 += 32) {
+    const bool more = k0 + 32 < ke;
     if (more) {
-      load_a(k0 + 16);
-      load_b(k0 + 16);
+      load_a(k0 + 32);
+      load_b(k0 + 32);
     }
 #pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 8]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 8 + 4]);
-      const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+    for (int kk = 0; kk < 32; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][ty * 8 + 4]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
       const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
-    if (more) store(buf ^ 1);
-    __syncthreads();
-    buf ^= 1;
+    __syncthreads();  // every thread is done with the slice before it is overwritten
+    if (more) {
+      store();
+      __syncthreads();
+    }
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -959,8 +968,8 @@ cudaError_t gemm(int kind, const Gemm& g, cudaStream_t s) {
   auto al = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
   const bool ak = kind != 2, bk = kind == 0;
   bool fast = al(g.A) && al(g.B) && g.lda % 4 == 0 && g.ldb % 4 == 0;
-  fast = fast && (ak ? (kc % 16 == 0 && g.K % 16 == 0) : g.M % 4 == 0);
-  fast = fast && (bk ? (kc % 16 == 0 && g.K % 16 == 0) : g.N % 4 == 0);
+  fast = fast && (ak ? (kc % 32 == 0 && g.K % 32 == 0) : g.M % 4 == 0);
+  fast = fast && (bk ? (kc % 32 == 0 && g.K % 32 == 0) : g.N % 4 == 0);
   if (fast) {
     dim3 grid2((unsigned)((g.M + 127) / 128), (unsigned)((g.N + 63) / 64), (unsigned)((g.K + kc - 1) / kc));
     if (kind == 0)
