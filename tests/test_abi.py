@@ -153,3 +153,8 @@ def test_training_calls_reject_bad_arguments_before_any_cuda_call(lib):
     assert lib.tfm_forward(None, one, one, one, None, 1, one, None) == 1
     assert lib.tfm_sync_policy(None, None) == 1
     assert lib.env_ppo_record(None, None, None, None, None) == 1
+    bufs = _abi.PpoBuffers()
+    assert lib.env_ppo_collect(None, None, 4, ctypes.byref(bufs)) == 1
+    assert lib.env_ppo_collect(one, one, 0, ctypes.byref(bufs)) == 1  # T < 1
+    assert lib.env_ppo_collect(one, one, 4, None) == 1
+    assert lib.env_ppo_collect(one, one, 4, ctypes.byref(bufs)) == 1  # null buffers
