@@ -21,9 +21,12 @@ from typing import Optional
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = [os.path.join(_HERE, "utrack_oracle.c"), os.path.join(_HERE, "utrack_oracle_nn.c"),
-        os.path.join(_HERE, "utrack_oracle_ppo.c")]
-_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+# UTRACK_ORACLE_DIR points the oracle at another copy of its C sources (the
+# planted-mistake tests build mutated copies there); unset, this directory.
+_SRC_DIR = os.environ.get("UTRACK_ORACLE_DIR") or _HERE
+_SRC = [os.path.join(_SRC_DIR, "utrack_oracle.c"), os.path.join(_SRC_DIR, "utrack_oracle_nn.c"),
+        os.path.join(_SRC_DIR, "utrack_oracle_ppo.c")]
+_LIB_PATH = os.path.join(_SRC_DIR, "_build", "liboracle.so")
 _lib = None
 
 N_SLOTS_FEATURES = 8

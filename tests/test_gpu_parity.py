@@ -77,6 +77,9 @@ def test_resample_indices_bit_exact(P):
         v[rng.integers(0, P)] = 1.0
         w[f] = v.astype(np.float32)
     u64 = rng.integers(0, 2 ** 63, F, dtype=np.int64)
+    # exact ties P Q_i = j W + U0: a zero offset on the uniform (kind 4) and
+    # dyadic (kind 2) filters of the first rows
+    u64[[2, 4, 8, 10]] = 0
     got = ut.pf_resample(torch.from_numpy(w).cuda(), torch.from_numpy(u64).cuda()).cpu().numpy()
     for f in range(F):
         want = oracle.systematic_resample(w[f].astype(np.float64), int(u64[f]) & (2 ** 64 - 1))

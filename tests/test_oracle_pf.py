@@ -35,11 +35,22 @@ def test_predict_closed_form_without_noise_or_measurements():
 
 
 def test_velocity_cap():
+    """Speeds above v_cap (far above, and just above) are cut to v_cap with
+    the direction kept; speeds below it are left unchanged."""
     e = _env(n_envs=1, n_particles=8, pf_accel_sigma=0.0, det_radius=0.0)
-    e.set_arrays(pvx=np.full(e.F * 8, 3.0), pvy=np.full(e.F * 8, 4.0))
+    cap = 1.2 * 1.5
+    speed = np.array([5.0, 1.05 * cap, 1.5 * cap, 0.95 * cap, 0.5 * cap, 0.0, 2.5 * cap, 0.999 * cap])
+    ang = np.linspace(0.3, 5.9, 8)
+    vx = np.tile(speed * np.cos(ang), e.F)
+    vy = np.tile(speed * np.sin(ang), e.F)
+    e.set_arrays(pvx=vx, pvy=vy)
     e.step(np.full(e.NA, 3, np.int32))
-    np.testing.assert_allclose(np.hypot(e.arr["pvx"], e.arr["pvy"]), 1.2 * 1.5, rtol=1e-14)
-    np.testing.assert_allclose(e.arr["pvy"] / e.arr["pvx"], 4.0 / 3.0, rtol=1e-14)
+    got = np.hypot(e.arr["pvx"], e.arr["pvy"])
+    want = np.tile(np.minimum(speed, cap), e.F)
+    np.testing.assert_allclose(got, want, rtol=1e-14, atol=1e-15)
+    moving = np.tile(speed > 0, e.F)
+    np.testing.assert_allclose(np.arctan2(e.arr["pvy"], e.arr["pvx"])[moving],
+                               np.arctan2(vy, vx)[moving], rtol=1e-13, atol=1e-13)
 
 
 def test_weights_brute_force_bayes_p4():
@@ -104,6 +115,13 @@ def test_resample_brute_force_small(P):
         w[rng.integers(0, P)] = 1.0  # max-normalised
         u64 = int(rng.integers(0, 2 ** 63)) * 2 + int(rng.integers(0, 2))
         np.testing.assert_array_equal(oracle.systematic_resample(w, u64), _brute_resample(w, u64))
+    # exact ties P Q_i = j W + U0 (offset 0): uniform weights give the identity
+    # map only under the strict rule C_i > u_j; dyadic weights tie often
+    np.testing.assert_array_equal(oracle.systematic_resample(np.ones(P), 0), np.arange(P))
+    for _ in range(10):
+        w = rng.integers(1, 5, P) / 4.0
+        w[0] = 1.0
+        np.testing.assert_array_equal(oracle.systematic_resample(w, 0), _brute_resample(w, 0))
 
 
 def test_resample_structure():
