@@ -1,5 +1,6 @@
-"""The environment and particle-filter oracle's pins catch plausible
-mistakes: for each planted mistake a copy of the oracle's C sources is made
+"""The pins of the environment, particle-filter and neural-network oracle
+(utrack_oracle.c, utrack_oracle_nn.c) catch plausible mistakes: for each
+planted mistake a copy of the oracle's C sources is made
 with that one edit, the oracle module is pointed at it (UTRACK_ORACLE_DIR)
 in a child process, and the pin tests named for it must fail there; an
 unmodified copy passes the same tests (the control case)."""
@@ -16,6 +17,7 @@ ORACLE = os.path.join(ROOT, "oracle")
 SOURCES = ("utrack_oracle.c", "utrack_oracle_nn.c", "utrack_oracle_ppo.c")
 
 E, P, R = "tests/test_oracle_env.py", "tests/test_oracle_pf.py", "tests/test_oracle_rng.py"
+N = "tests/test_oracle_nn.py"
 
 # name: (file, exact source text, replacement, pin tests that must catch it)
 MUTANTS = {
@@ -44,6 +46,17 @@ MUTANTS = {
     "philox_multiplier": ("utrack_oracle.c", "uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)c0;",
                           "uint64_t prod0 = (uint64_t)0xD2511F55u * (uint64_t)c0;",
                           [R + "::test_philox_is_invertible_round_function"]),
+    # the transformer agent, the estimator MLP and Adam (utrack_oracle_nn.c)
+    "agent_attention_scale_lost": ("utrack_oracle_nn.c", "att[s] = acc / sqrt((double)dh);", "att[s] = acc;",
+                                   [N + "::test_policy_matches_torch_encoder"]),
+    "agent_layernorm_epsilon": ("utrack_oracle_nn.c", "double inv = 1.0 / sqrt(var + 1e-5);",
+                                "double inv = 1.0 / sqrt(var + 1e-3);", [N + "::test_policy_matches_torch_encoder"]),
+    "mlp_gelu_derivative_lost": ("utrack_oracle_nn.c", "dz[j] = da[j] * gelu_grad(z[j]);", "dz[j] = da[j];",
+                                 [N + "::test_mlp_grad_central_differences"]),
+    "huber_slope_sign": ("utrack_oracle_nn.c", "*drho = e > 0.0 ? delta : -delta;", "*drho = delta;",
+                         [N + "::test_mlp_huber_matches_torch_huber_loss"]),
+    "adam_second_moment_decay": ("utrack_oracle_nn.c", "v[i] = beta2 * v[i] + (1.0 - beta2) * grad[i] * grad[i];",
+                                 "v[i] = beta2 * v[i] + (1.0 - beta2) * grad[i];", [N + "::test_adam_matches_torch"]),
 }
 
 
