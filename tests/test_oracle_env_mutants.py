@@ -46,6 +46,23 @@ MUTANTS = {
     "philox_multiplier": ("utrack_oracle.c", "uint64_t prod0 = (uint64_t)0xD2511F53u * (uint64_t)c0;",
                           "uint64_t prod0 = (uint64_t)0xD2511F55u * (uint64_t)c0;",
                           [R + "::test_philox_is_invertible_round_function"]),
+    "ls_normal_equation_factor": ("utrack_oracle.c", "b0 += 0.5 * dx * da;", "b0 += dx * da;",
+                                  ["tests/test_oracle_ls.py::test_exact_static_target_from_noise_free_ranges"]),
+    "ls_solve_sign": ("utrack_oracle.c", "ey = e1y + (a00 * b1 - a01 * b0) / det;",
+                      "ey = e1y + (a00 * b1 + a01 * b0) / det;",
+                      ["tests/test_oracle_ls.py::test_exact_static_target_from_noise_free_ranges"]),
+    "ess_trigger_inverted": ("utrack_oracle.c",
+                             "resample = resample && 16u * s1 * s1 < (uint64_t)c->pf_ess_num * (uint64_t)P * s2;",
+                             "resample = resample && 16u * s1 * s1 > (uint64_t)c->pf_ess_num * (uint64_t)P * s2;",
+                             ["tests/test_oracle_ess.py::test_trigger_is_the_integer_rule_on_the_weights"]),
+    "ess_carried_weights_unshifted": ("utrack_oracle.c",
+                                      "s->pw[(int64_t)f * P + i] = resample ? 0.0 : l[i] - lmax;",
+                                      "s->pw[(int64_t)f * P + i] = resample ? 0.0 : l[i];",
+                                      ["tests/test_oracle_ess.py::test_carried_weights_are_the_product_of_likelihoods"]),
+    "token_kind_flags_swapped": ("utrack_oracle.c", "        t[5] = 1.0;\n        slot++;",
+                                 "        t[4] = 1.0;\n        slot++;", [E + "::test_observation_tokens_structure"]),
+    "estimate_motion_smoothing": ("utrack_oracle.c", "#define OC_VEL_KEEP 0.85", "#define OC_VEL_KEEP 0.8",
+                                  [P + "::test_estimate_motion_features_closed_form"]),
     # the transformer agent, the estimator MLP and Adam (utrack_oracle_nn.c)
     "agent_attention_scale_lost": ("utrack_oracle_nn.c", "att[s] = acc / sqrt((double)dh);", "att[s] = acc;",
                                    [N + "::test_policy_matches_torch_encoder"]),

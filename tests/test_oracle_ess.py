@@ -73,6 +73,11 @@ def test_carried_weights_are_the_product_of_likelihoods():
     w /= w.sum(1, keepdims=True)
     got = out["weight"].reshape(o.F, P)
     np.testing.assert_allclose(got[kept], w[kept], rtol=1e-9, atol=1e-15)
+    # the carried log-weights are log w - max log w: the summed log-likelihoods
+    # shifted to a maximum of exactly 0
+    pw = o.arr["pw"].reshape(o.F, P)
+    np.testing.assert_allclose(pw[kept], (loglik - loglik.max(1, keepdims=True))[kept], rtol=1e-9, atol=1e-9)
+    assert np.all(pw[kept].max(1) == 0.0)
     # the compared filters carried weights through two steps with measurements
     assert kept.sum() >= 10 and (out["meas_n"][kept] > 0).sum() >= 10
 
