@@ -171,10 +171,13 @@ class Trainer:
     (zero at reset, carried across the steps of the episode like the
     agents').
 
-    With a process group of several ranks (one env shard per rank, see
-    ``shard.shard_params``), each rank collects its own batch and every
-    minibatch gradient is averaged across the ranks by sample count before
-    the Adam step (``dp_average``)."""
+    Data parallelism is explicit: given ``group`` (a process group of
+    several ranks, one env shard per rank, see ``shard.shard_params``), each
+    rank collects its own batch and every minibatch gradient is averaged
+    across the group's ranks by sample count before the Adam step
+    (``dp_average``).  With ``group=None`` the trainer is one process, even
+    when torch.distributed is initialised (e.g. one rank of a job that
+    trains alone)."""
 
     def __init__(self, env, actor_params: np.ndarray, critic_params: np.ndarray, cfg: PPOConfig = PPOConfig(),
                  group=None):
@@ -258,7 +261,8 @@ class Trainer:
         cne, ch, ret = self.cne[:T].reshape(T * E), self.ch[:T].reshape(T * E, self.d), self.ret.view(T * E)
         import torch.distributed as dist
 
-        rank = dist.get_rank(self.group) if dist.is_available() and dist.is_initialized() else 0
+        dp = self.group is not None
+        rank = dist.get_rank(self.group) if dp else 0
         g = torch.Generator(device="cuda")
         g.manual_seed(shard.rank_seed(seed, rank) & 0x7FFFFFFFFFFFFFFF)
         sa = sc = None
@@ -271,12 +275,14 @@ class Trainer:
                 if sel.numel():
                     sa = self.actor.actor_grad(tok, ne, h, act, logp, adv, sel=sel, clip_eps=c.clip_eps,
                                                ent_coef=c.ent_coef, stats=last)
-                    dp_average(self.actor.grad, sel.numel(), self.group)
+                    if dp:
+                        dp_average(self.actor.grad, sel.numel(), self.group)
                     self.actor.adam_step(c.lr_actor, c.beta1, c.beta2, c.eps)
                 sel = pc[k * self.mb_critic:(k + 1) * self.mb_critic]
                 if sel.numel():
                     sc = self.critic.value_grad(ctok, cne, ch, ret, sel=sel, stats=last)
-                    dp_average(self.critic.grad, sel.numel(), self.group)
+                    if dp:
+                        dp_average(self.critic.grad, sel.numel(), self.group)
                     self.critic.adam_step(c.lr_critic, c.beta1, c.beta2, c.eps)
         self.actor.sync_policy(self.env)
         return {"actor": sa, "critic": sc}
