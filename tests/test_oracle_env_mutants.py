@@ -63,6 +63,10 @@ MUTANTS = {
                                  "        t[4] = 1.0;\n        slot++;", [E + "::test_observation_tokens_structure"]),
     "estimate_motion_smoothing": ("utrack_oracle.c", "#define OC_VEL_KEEP 0.85", "#define OC_VEL_KEEP 0.8",
                                   [P + "::test_estimate_motion_features_closed_form"]),
+    "critic_token_velocity_sin_cos": ("utrack_oracle_ppo.c",
+                                      "q[3] = agent_speed * cos(apsi[a]); q[4] = agent_speed * sin(apsi[a]);",
+                                      "q[3] = agent_speed * sin(apsi[a]); q[4] = agent_speed * cos(apsi[a]);",
+                                      ["tests/test_oracle_ppo.py::test_state_token_velocities_are_the_next_displacement"]),
     # the transformer agent, the estimator MLP and Adam (utrack_oracle_nn.c)
     "agent_attention_scale_lost": ("utrack_oracle_nn.c", "att[s] = acc / sqrt((double)dh);", "att[s] = acc;",
                                    [N + "::test_policy_matches_torch_encoder"]),

@@ -13,7 +13,8 @@ transformer actor and critic of Sec. III-B.1 / Fig. 3), pinned by:
 * GAE closed forms: lambda = 0 gives the one-step TD error, lambda = 1 and
   gamma = 1 the return to the episode end (bootstrapped at the batch end)
   minus the value, and the backward recursion of the estimator;
-* the critic's state tokens against the state they are built from."""
+* the critic's state tokens against the state they are built from, and their
+  velocities against the next step's displacement (no noise, no turn)."""
 import numpy as np
 import pytest
 
@@ -241,3 +242,20 @@ def test_state_tokens_describe_the_true_state():
             q, i = tok[e, A + k], e * T + k
             np.testing.assert_allclose(q[:3], [a["tx"][i] / S, a["ty"][i] / S, a["tz"][i] / S], rtol=1e-15)
             assert np.hypot(q[3], q[4]) == pytest.approx(a["tspeed"][i], rel=1e-14) and q[7] == 0.0
+
+
+def test_state_token_velocities_are_the_next_displacement():
+    """Without heading noise and target drift, and with every agent steering
+    straight, each entity's next displacement divided by dt is the velocity
+    its token reported."""
+    p = preset("fleet5", n_envs=3).replace(n_particles=16, d_model=0, heading_noise=0.0, target_drift_sigma=0.0)
+    o = oracle.OracleEnv(p, 4)
+    o.reset(0)
+    o.step(o.random_actions(1))
+    tok0, _ = oracle.state_tokens(o)
+    o.step(np.full(o.NA, 3, np.int32))  # the middle rudder angle: no turn
+    tok1, _ = oracle.state_tokens(o)
+    S, dt = p.feature_scale, p.dt
+    vel = (tok1[:, :, :2] - tok0[:, :, :2]) * S / dt
+    np.testing.assert_allclose(vel, tok0[:, :, 3:5], rtol=1e-9, atol=1e-9)
+    assert np.abs(tok0[:, :, 3:5]).max() > 0.1
