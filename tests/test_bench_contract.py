@@ -65,3 +65,8 @@ def test_small_bench_line_has_the_contract_keys():
         assert k in line["e2e"], k
     assert line["gpu_launches"] > 0 and "workload" in line["config"]
     assert 0.0 < line["learned"]["rmse_ratio"] and line["seeds_0_4"]["min"] > 0
+    # the TransfMAPPO update measurement
+    ppo = line["ppo"]
+    assert ppo["value"] > 0 and ppo["ms_per_update"] > 0 and ppo["collect_ms"] > 0
+    assert ppo["roofline"]["bound"] == "alu" and 0.0 < ppo["roofline"]["frac"] < 1.5
+    assert all(v == v for v in ppo["stats_last_minibatch"]["actor"] + ppo["stats_last_minibatch"]["critic"])
