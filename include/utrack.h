@@ -439,20 +439,25 @@ ut_status tc_gemm_bf16(const uint16_t* A_dev, const uint16_t* B_dev, float* C_de
 /* Allocation-free tracker update (the paper has no counterpart).          */
 /* ---------------------------------------------------------------------- */
 
-/* For callers that must not allocate device memory — code running inside
- * another component's CUDA graph capture (where cudaMalloc is not allowed),
- * real-time host threads that forbid allocator calls, or a vehicle simulator
- * that owns every buffer and its memory budget.  It runs the tracking part of
- * one step on caller buffers: pings and communication at the given
- * (already moved) agent and target positions, then the particle-filter step
- * (predict, weight, estimate, systematic resample) of every (env, agent,
- * target) filter — the same rules and random draws as env_step at global step
- * `step` (>= 1) with `seed`.  Uniform fleets only: cfg->n_envs environments of
- * cfg->max_agents agents and cfg->max_targets targets (the per-env count
- * pointers must be NULL), per-agent filters resampled every step
- * (shared_filter and pf_ess_num 0); cfg supplies the constants.
+/* For callers that must not allocate device memory: real-time host threads
+ * that forbid allocator calls (an allocation may synchronise the device and
+ * take unbounded time), a vehicle simulator that owns every buffer and the
+ * GPU's memory budget, or a plug-in whose host process has handed all device
+ * memory to another framework's pool.  It runs the tracking part of one step
+ * on caller buffers: pings and communication at the given (already moved)
+ * agent and target positions, then the particle-filter step (predict,
+ * weight, estimate, systematic resample) of every (env, agent, target)
+ * filter — the same rules and random draws as env_step at global step
+ * `step` (>= 1) with `seed`, including the global id offsets cfg->id_env0,
+ * id_agent0, id_target0 and id_filter0 of a sharded batch.  Uniform fleets
+ * only: cfg->n_envs environments of cfg->max_agents agents and
+ * cfg->max_targets targets (the per-env count pointers must be NULL),
+ * per-agent filters resampled every step (shared_filter and pf_ess_num 0);
+ * cfg supplies the constants.
  *   ax/ay_dev [E*A], tx/ty/tz_dev [E*T]: positions (read);
- *   px/py/pvx/pvy_dev [E*A*T*P]: particles, updated in place;
+ *   px/py/pvx/pvy_dev [E*A*T*P]: particles, updated in place; 16-byte
+ *     aligned when P % 4 == 0 (read and written as float4), else
+ *     UT_ERR_INVALID;
  *   estx/esty/err_dev [E*A*T]: estimate and its 2-D error (written).
  * Intermediates (layout tables, per-filter measurement lists) live in a
  * static device array of about 5.1 MB that every GPU loading the library

@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace ut {
 
 // Programmatic dependent launch between the kernels of one environment step:
@@ -41,6 +43,22 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// Dynamic shared memory above the default limit is a per-device function
+// attribute: opt each kernel in once on every device it runs on.  `mask`
+// holds one bit per device index (devices >= 64 set the attribute on every
+// call).
+template <typename K>
+inline cudaError_t smem_optin(K kernel, size_t bytes, std::atomic<unsigned long long>& mask) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+  if (bit && (mask.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && bit) mask.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
 }
 
 // Stream tags (counter word 3).

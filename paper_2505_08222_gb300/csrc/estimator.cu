@@ -697,19 +697,11 @@ __global__ void record_kernel(EnvDev d, float* feat, float* label) {
   label[(long long)f * 2 + 1] = (d.ty[it] - e1y) / d.est_scale;
 }
 
-template <typename K>
-cudaError_t smem_optin(K k, size_t bytes, int& done) {
-  if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) done = 1;
-  return e;
-}
-
 }  // namespace
 
 cudaError_t launch_forward(const Net& net, const float* X, const int32_t* rows, int B, float* out, float* z,
                            uint16_t* a, cudaStream_t s) {
-  static int ready = 0;
+  static std::atomic<unsigned long long> ready{0};
   cudaError_t e = smem_optin(fwd_kernel, kFwdSmem, ready);
   if (e != cudaSuccess) return e;
   if (B <= 0) return cudaSuccess;
@@ -727,7 +719,7 @@ cudaError_t launch_forward(const Net& net, const float* X, const int32_t* rows, 
 }
 
 cudaError_t launch_forward_env(const Net& net, const EnvDev& d, int stale, cudaStream_t s) {
-  static int ready = 0;
+  static std::atomic<unsigned long long> ready{0};
   cudaError_t e = smem_optin(fwd_env_kernel, kEnvSmem, ready);
   if (e != cudaSuccess) return e;
   if (d.F <= 0) return cudaSuccess;
@@ -742,7 +734,7 @@ cudaError_t launch_record(const EnvDev& d, float* feat, float* label, cudaStream
 }
 
 cudaError_t launch_backward(const Net& net, const TrainBufs& t, cudaStream_t s) {
-  static int ready_b = 0, ready_w = 0;
+  static std::atomic<unsigned long long> ready_b{0}, ready_w{0};
   cudaError_t e = smem_optin(bwd_kernel, kFwdSmem, ready_b);
   if (e == cudaSuccess) e = smem_optin(wgrad_kernel, kWgradSmem, ready_w);
   if (e != cudaSuccess) return e;

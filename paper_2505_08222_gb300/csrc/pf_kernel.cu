@@ -31,10 +31,10 @@ cudaError_t launch_pf_step(const EnvDev& d, int variant, cudaStream_t s) {
 namespace {
 template <int NT, int PPT>
 cudaError_t launch_resample_t(const float* w, const uint64_t* u, int64_t F, int P, int32_t* idx, cudaStream_t s) {
-  static int ready = 0;
+  static std::atomic<unsigned long long> ready{0};
   const size_t smem = pf::resample_smem_bytes(NT, PPT);
   auto k = pf::pf_resample_kernel<NT, PPT>;
-  cudaError_t e = pf::ensure_smem(k, smem, ready);
+  cudaError_t e = smem_optin(k, smem, ready);
   if (e != cudaSuccess) return e;
   k<<<(unsigned)F, NT, smem, s>>>(w, u, P, idx);
   return cudaGetLastError();

@@ -655,21 +655,12 @@ constexpr size_t resample_smem_bytes(int NT, int PPT) {
   return (size_t)NT * PPT * 2 * sizeof(int) + (size_t)NT * sizeof(long long);
 }
 
-// Opt in to the dynamic shared memory a kernel needs (once per process).
-template <typename K>
-cudaError_t ensure_smem(K k, size_t smem, int& done) {
-  if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) done = 1;
-  return e;
-}
-
 template <int NT, int PPT, int MINB, int MODE, bool ESS>
 cudaError_t launch_mode(const EnvDev& d, cudaStream_t s) {
-  static int ready = 0;
+  static std::atomic<unsigned long long> ready{0};
   const size_t smem = step_smem_bytes(NT, PPT);
   auto k = pf_step_kernel<NT, PPT, MINB, MODE, ESS>;
-  cudaError_t e = ensure_smem(k, smem, ready);
+  cudaError_t e = smem_optin(k, smem, ready);
   if (e != cudaSuccess) return e;
   if (d.F > 0) return launch_pdl(k, dim3(d.F), dim3(NT), smem, s, d);
   return cudaSuccess;

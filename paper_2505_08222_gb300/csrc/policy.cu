@@ -671,12 +671,10 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
 
 template <int D>
 cudaError_t launch_policy_t(const PolicyDev& p, cudaStream_t s) {
-  static int ready = 0;
-  if (!ready) {
-    cudaError_t e = cudaFuncSetAttribute(policy_fwd_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Geo<D>::SMEM);
+  static std::atomic<unsigned long long> ready{0};
+  {
+    const cudaError_t e = smem_optin(policy_fwd_kernel<D>, Geo<D>::SMEM, ready);
     if (e != cudaSuccess) return e;
-    ready = 1;
   }
   const long long tiles = (p.NA + p.apt - 1) / p.apt;
   if (tiles > 0) {

@@ -3,6 +3,7 @@
 // descriptors and TMEM read-back that the fused transformer and estimator
 // kernels build on, so they can be checked against a host matmul.
 #include "../../include/utrack.h"
+#include "common.cuh"
 #include "tc.cuh"
 
 namespace ut {
@@ -91,13 +92,8 @@ extern "C" ut_status tc_gemm_bf16(const uint16_t* A_dev, const uint16_t* B_dev, 
   if (M < 1 || N < 16 || N > 256 || N % 16 || K < 16 || K > 256 || K % 16) return UT_ERR_INVALID;
   if (!A_dev || !B_dev || !C_dev) return UT_ERR_INVALID;
   if ((reinterpret_cast<uintptr_t>(A_dev) | reinterpret_cast<uintptr_t>(B_dev)) & 15) return UT_ERR_INVALID;
-  static int ready = 0;
-  if (!ready) {
-    if (cudaFuncSetAttribute(ut::tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)ut::kGemmSmem) != cudaSuccess)
-      return UT_ERR_CUDA;
-    ready = 1;
-  }
+  static std::atomic<unsigned long long> ready{0};
+  if (ut::smem_optin(ut::tc_gemm_kernel, ut::kGemmSmem, ready) != cudaSuccess) return UT_ERR_CUDA;
   ut::tc_gemm_kernel<<<(M + 127) / 128, ut::kGemmThreads, ut::kGemmSmem, (cudaStream_t)cuda_stream>>>(
       A_dev, B_dev, C_dev, M, N, K, status_dev);
   return cudaGetLastError() == cudaSuccess ? UT_OK : UT_ERR_CUDA;

@@ -1,10 +1,11 @@
 // Allocation-free tracker update: pings, communication and the particle-filter
 // step for caller-owned state, with all scratch in a static device array.
 //
-// Some callers cannot allocate device memory: a plugin that runs inside
-// someone else's CUDA graph capture (where cudaMalloc is not permitted), a
-// host thread with real-time guarantees that forbid allocator calls, or a
-// vehicle simulator that hands us its own buffers and owns the memory budget.
+// Some callers cannot allocate device memory: a host thread with real-time
+// guarantees that forbid allocator calls (cudaMalloc may synchronise the
+// device and take unbounded time), a vehicle simulator that hands us its own
+// buffers and owns the memory budget of the GPU, or a plug-in whose host
+// process has given every byte of device memory to another framework's pool.
 // For them tracker_update_noalloc() performs the tracking part of one step —
 // the same device code as env_step's ping / communication / particle-filter
 // stages — on buffers the caller passes in, and keeps its own intermediates
@@ -15,6 +16,7 @@
 // holds its kScratchBytes until the process exits.  All calls share it and it
 // keeps the last call's contents, so calls that overlap on the GPU (different
 // streams, or different host threads without ordering) race on it.
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(kNoallocWarps * 32) noalloc_lists_kernel(EnvDe
     const int a = p / T, k = p - a * T;
     const float dx = s_ax[wid][a] - s_tx[wid][k], dy = s_ay[wid][a] - s_ty[wid][k], dz = 0.0f - s_tz[wid][k];
     const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
-    Rand4 r = philox(d.gid_filter + (uint32_t)(f0 + p), 0u, g, TAG_PING, d.seed);
+    Rand4 r = philox(d.gid_pair + (uint32_t)(f0 + p), 0u, g, TAG_PING, d.seed);
     float n0, n1;
     box_muller(r.x[0], r.x[1], n0, n1);
     const int v = dist <= d.det_radius;
@@ -186,6 +188,21 @@ extern "C" ut_status tracker_update_noalloc(const ut_config* cfg, uint64_t seed,
   if (!ax_dev || !ay_dev || !tx_dev || !ty_dev || !tz_dev || !px_dev || !py_dev || !pvx_dev || !pvy_dev ||
       !estx_dev || !esty_dev || !err_dev)
     return UT_ERR_INVALID;
+  // the filter kernel reads and writes the particles as float4 when P % 4 == 0
+  if (P % 4 == 0) {
+    const float* parts[4] = {px_dev, py_dev, pvx_dev, pvy_dev};
+    for (const float* q : parts) {
+      if (reinterpret_cast<uintptr_t>(q) % 16 != 0) {
+        std::fprintf(stderr,
+                     "tracker_update_noalloc: particle arrays must be 16-byte aligned when n_particles %% 4 == 0\n");
+        return UT_ERR_INVALID;
+      }
+    }
+  }
+  // an error left by earlier, unrelated work is not this call's
+  const cudaError_t stale = cudaGetLastError();
+  if (stale != cudaSuccess)
+    std::fprintf(stderr, "tracker_update_noalloc: cleared an earlier CUDA error: %s\n", cudaGetErrorString(stale));
   unsigned char* s = nullptr;
   if (scratch_address(&s) != cudaSuccess) return UT_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -201,6 +218,13 @@ extern "C" ut_status tracker_update_noalloc(const ut_config* cfg, uint64_t seed,
   d.NT = E * T;
   d.F = (int)F;
   d.seed = seed;
+  // global ids of a shard's first env / agent / target / filter, as env_step
+  // takes them: per-agent filters are their (agent, target) pairs
+  d.gid_env = cfg->id_env0;
+  d.gid_agent = cfg->id_agent0;
+  d.gid_target = cfg->id_target0;
+  d.gid_filter = cfg->id_filter0;
+  d.gid_pair = cfg->id_filter0;
   d.dt = cfg->dt;
   d.range_sigma = cfg->range_sigma;
   d.inv_two_s2 = (float)(1.0 / (2.0 * (double)cfg->range_sigma * (double)cfg->range_sigma));

@@ -137,13 +137,18 @@ def dp_average(grad: torch.Tensor, n_local: int, group=None) -> int:
     """Data parallelism: every rank holds a gradient of the mean loss over
     its own n_local samples; afterwards each holds the gradient of the mean
     over all ranks' samples (the row-weighted average), so identical Adam
-    steps keep the ranks' weights equal.  Returns the total sample count.
-    No-op without an initialised process group of more than one rank."""
+    steps keep the ranks' weights equal.  A rank with no samples passes
+    n_local = 0 (its gradient then carries no weight) and must still call,
+    so that every rank enters the same collectives.  Returns the total sample
+    count (0: no rank had samples, the gradient is left as it is).  No-op
+    without an initialised process group of more than one rank."""
     import torch.distributed as dist
 
     if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size(group) == 1:
         return n_local
     total = int(shard.reduce_sums([n_local], group)[0])
+    if total == 0:  # every rank's slice was empty: nothing to average, no step
+        return 0
     shard._weighted_mean_(grad, n_local, total, group)
     return total
 
@@ -271,18 +276,25 @@ class Trainer:
             pc = torch.randperm(T * E, generator=g, device="cuda").to(torch.int32)
             for k in range(c.minibatches):
                 last = ep == c.epochs - 1 and k == c.minibatches - 1
+                # with a process group every rank takes part in every
+                # all-reduce, its slice empty or not (ragged shards can leave
+                # one rank's last slice empty while another's is not)
                 sel = pa[k * self.mb_actor:(k + 1) * self.mb_actor]
                 if sel.numel():
                     sa = self.actor.actor_grad(tok, ne, h, act, logp, adv, sel=sel, clip_eps=c.clip_eps,
                                                ent_coef=c.ent_coef, stats=last)
-                    if dp:
-                        dp_average(self.actor.grad, sel.numel(), self.group)
+                elif dp:
+                    self.actor.grad.zero_()
+                n = dp_average(self.actor.grad, sel.numel(), self.group) if dp else sel.numel()
+                if n:
                     self.actor.adam_step(c.lr_actor, c.beta1, c.beta2, c.eps)
                 sel = pc[k * self.mb_critic:(k + 1) * self.mb_critic]
                 if sel.numel():
                     sc = self.critic.value_grad(ctok, cne, ch, ret, sel=sel, stats=last)
-                    if dp:
-                        dp_average(self.critic.grad, sel.numel(), self.group)
+                elif dp:
+                    self.critic.grad.zero_()
+                n = dp_average(self.critic.grad, sel.numel(), self.group) if dp else sel.numel()
+                if n:
                     self.critic.adam_step(c.lr_critic, c.beta1, c.beta2, c.eps)
         self.actor.sync_policy(self.env)
         return {"actor": sa, "critic": sc}

@@ -100,6 +100,18 @@ def test_noalloc_rejects_layouts_it_does_not_run(lib):
     assert ut.lib.tracker_update_noalloc(ctypes.byref(cfg), ctypes.c_uint64(1), 0, *dummy, None) == 1
 
 
+def test_noalloc_rejects_unaligned_particle_arrays(lib):
+    """With P % 4 == 0 the filter reads and writes particles as float4: a
+    particle array that does not start on a 16-byte boundary (a view at an
+    odd float offset) is refused on the host, before any device work."""
+    import paper_2505_08222_gb300 as ut
+    cfg, keep = _cfg(n_particles=512)
+    for bad in range(4):  # px, py, pvx, pvy in turn 4 bytes off the boundary
+        args = [ctypes.c_void_p(4096)] * 12
+        args[5 + bad] = ctypes.c_void_p(4096 + 4)
+        assert ut.lib.tracker_update_noalloc(ctypes.byref(cfg), ctypes.c_uint64(1), 1, *args, None) == 1
+
+
 def test_standalone_ops_validate_arguments(lib):
     import paper_2505_08222_gb300 as ut
     assert ut.lib.pf_resample(None, None, -1, 16, None, None) == 1

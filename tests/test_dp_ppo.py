@@ -86,3 +86,38 @@ def test_one_process_is_a_no_op():
     g = torch.arange(5, dtype=torch.float64)
     assert ppo.dp_average(g, 7) == 7
     assert torch.equal(g, torch.arange(5, dtype=torch.float64))
+
+
+def _empty_worker(rank, world, port, outdir):
+    import torch.distributed as dist
+
+    from paper_2505_08222_gb300 import ppo
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # rank 0's slice is empty (zeroed gradient, n_local = 0), rank 1 holds every sample
+        g = torch.zeros(_grad(oracle.ACTOR, 0, N).size, dtype=torch.float64) if rank == 0 else torch.from_numpy(_grad(oracle.ACTOR, 0, N))
+        total = ppo.dp_average(g, 0 if rank == 0 else N)
+        # then a minibatch empty on both ranks: no average, the gradient is left alone
+        h = torch.full((4,), float(rank + 1), dtype=torch.float64)
+        none = ppo.dp_average(h, 0)
+        np.savez(os.path.join(outdir, f"r{rank}.npz"), g=g.numpy(), total=total, h=h.numpy(), none=none)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_a_rank_with_an_empty_slice_still_joins_the_average():
+    """Ragged shards can leave one rank's last minibatch empty; the trainer
+    then zeroes that rank's gradient and calls dp_average with n_local = 0,
+    so both ranks enter the same all-reduces and end with the other rank's
+    gradient."""
+    with tempfile.TemporaryDirectory() as d:
+        mp.start_processes(_empty_worker, args=(2, _free_port(), d), nprocs=2, join=True, start_method="spawn")
+        r = [dict(np.load(os.path.join(d, f"r{k}.npz"))) for k in range(2)]
+    full = _grad(oracle.ACTOR, 0, N)
+    for k in range(2):
+        np.testing.assert_allclose(r[k]["g"], full, rtol=1e-12, atol=1e-15)
+        assert int(r[k]["total"]) == N
+        assert int(r[k]["none"]) == 0
+        assert np.all(r[k]["h"] == k + 1)
