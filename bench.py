@@ -221,6 +221,28 @@ def learned_form(args, p, K, W, rank):
         env.reset(seed)
         return env.rollout(T)["rmse"]
 
+    ar = torch.arange(F, device="cuda")
+
+    def eval_split(learned: int, seed: int, T: int):
+        """Pooled RMSE of T eager steps from env_reset(seed) (the same steps
+        as rollout(T)), and the same pooled over the filter-steps whose
+        newest received ping is from that step (fresh) and the rest."""
+        env.est_set_mode(learned)
+        env.reset(seed)
+        acc = torch.zeros(4, dtype=torch.float64, device="cuda")
+        for _ in range(T):
+            out = env.step()
+            st = env.state()
+            ring = st["ring"].view(F, 16, 4)
+            newest = ring[ar, (st["ring_head"].long() - 1) & 15, 3]
+            fresh = (st["ring_count"] > 0) & (newest == float(st["step"]))
+            e2 = out["err"].double() ** 2
+            acc += torch.stack([e2.sum(), torch.tensor(float(F), dtype=torch.float64, device="cuda"),
+                                (e2 * fresh).sum(), fresh.double().sum()])
+        sq, n, sq_f, n_f = acc.tolist()
+        return {"rmse": (sq / n) ** 0.5, "fresh_rmse": (sq_f / max(n_f, 1.0)) ** 0.5,
+                "stale_rmse": ((sq - sq_f) / max(n - n_f, 1.0)) ** 0.5, "fresh_frac": n_f / n}
+
     ROUNDS, EPISODES = 8, 4
     t0 = time.perf_counter()
     half = steps_rec // 2
@@ -255,6 +277,22 @@ def learned_form(args, p, K, W, rank):
     seeds = [9000 + rank, 9100 + rank]
     pf_rmse = [eval_rmse(False, s, T_eval) for s in seeds]
     le_rmse = [eval_rmse(LEARNED, s, T_eval) for s in seeds]
+    # seeds 0-4 (held out from training and validation): per-seed ratio, and
+    # the ratio over the steps with a fresh ping alone
+    split_pf = [eval_split(False, sd, T_eval) for sd in range(5)]
+    split_le = [eval_split(LEARNED, sd, T_eval) for sd in range(5)]
+    ratios = [b["rmse"] / a["rmse"] for a, b in zip(split_pf, split_le)]
+
+    def _pool(parts, key, wkey):
+        num = sum(x[key] ** 2 * (x[wkey] if wkey else 1.0) for x in parts)
+        den = sum((x[wkey] if wkey else 1.0) for x in parts)
+        return (num / den) ** 0.5
+    fresh_pf = _pool(split_pf, "fresh_rmse", "fresh_frac")
+    fresh_le = _pool(split_le, "fresh_rmse", "fresh_frac")
+    stale_pf = (sum(x["stale_rmse"] ** 2 * (1 - x["fresh_frac"]) for x in split_pf)
+                / max(sum(1 - x["fresh_frac"] for x in split_pf), 1e-12)) ** 0.5
+    stale_le = (sum(x["stale_rmse"] ** 2 * (1 - x["fresh_frac"]) for x in split_le)
+                / max(sum(1 - x["fresh_frac"] for x in split_le), 1e-12)) ** 0.5
     # timed learned-form rollout
     env.est_set_mode(LEARNED)
     env.reset(1000 + rank)
@@ -299,6 +337,15 @@ def learned_form(args, p, K, W, rank):
             "estimator_kernel_ms": est_ms / max(est_n, 1),
             "rmse_m": le_mean, "pf_rmse_m": pf_mean, "rmse_ratio": le_mean / pf_mean,
             "eval": f"{len(seeds)} held-out seeds x {T_eval} steps each form, pooled RMSE per run, mean over seeds",
+            "seeds_0_4": {"rmse_ratio": ratios, "mean": sum(ratios) / 5, "min": min(ratios), "max": max(ratios),
+                          "pf_rmse_m": [x["rmse"] for x in split_pf], "learned_rmse_m": [x["rmse"] for x in split_le],
+                          "fresh_ping_steps": {"pf_rmse_m": fresh_pf, "learned_rmse_m": fresh_le,
+                                               "rmse_ratio": fresh_le / fresh_pf,
+                                               "share_of_filter_steps": sum(x["fresh_frac"] for x in split_pf) / 5},
+                          "stale_steps": {"pf_rmse_m": stale_pf, "learned_rmse_m": stale_le,
+                                          "rmse_ratio": stale_le / stale_pf},
+                          "note": (f"seeds 0-4 (neither trained nor validated on), {T_eval} eager steps each; a "
+                                   "filter-step is fresh when the filter's newest received ping is from that step")},
             "stale_rule": "network applied on steps without a fresh ping too (est_set_mode 2)",
             "ls_form": {"value": st_ls["agent_steps"] / (ms_ls / 1e3), "unit": "agent-steps/s", "ms_per_step": ms_ls / K,
                         "rmse_m": ls_mean, "rmse_ratio": ls_mean / pf_mean,
@@ -473,7 +520,7 @@ def run_reference(args):
 
 PF_SOURCES = ("pf_kernel.cuh", "pf_kernel.cu", "pf_inst_a.cu", "pf_inst_b.cu", "pf_variants.h", "common.cuh",
               "env.cuh", "gelu.cuh")
-TRAFFIC_NOTE = os.path.join(ROOT, "profiles", "pf_step_kernel_fleet5.md")
+TRAFFIC_NOTE = os.path.join(ROOT, "profiles", "pf_step_kernel_fleet5.json")
 
 
 def pf_source_hash() -> str:
@@ -488,17 +535,17 @@ def pf_source_hash() -> str:
 
 
 def _pf_traffic(variant: str, particles: int):
-    """DRAM bytes per launch from the committed ncu summary: its line
-    `traffic: variant=V sources=H bytes_per_particle=B` applies only while
-    the kernel sources still hash to H and the launch variant is V; the
+    """DRAM bytes per launch from the committed ncu figure
+    (profiles/pf_step_kernel_fleet5.json: {"variant", "sources",
+    "bytes_per_particle", ...}); it applies only while the kernel sources
+    still hash to "sources" and the launch variant is "variant"; the
     capture's bytes per particle are scaled to this launch's particles."""
     try:
-        for line in open(TRAFFIC_NOTE):
-            if line.startswith("traffic:"):
-                kv = dict(t.split("=", 1) for t in line.split()[1:])
-                if kv.get("variant") == variant and kv.get("sources") == pf_source_hash():
-                    return float(kv["bytes_per_particle"]) * particles
-    except (OSError, KeyError, ValueError):
+        with open(TRAFFIC_NOTE) as f:
+            t = json.load(f)
+        if t.get("variant") == variant and t.get("sources") == pf_source_hash():
+            return float(t["bytes_per_particle"]) * particles
+    except (OSError, KeyError, ValueError, TypeError):
         pass
     return None
 
@@ -711,12 +758,14 @@ def run_ours(args):
                          "timing": "CUDA events around each launch on its stream, eager replay of the K timed steps (same seed and warm-up)",
                          "peak_kind": f"{peak_kind} copy bandwidth (burst)",
                          "algorithmic_bytes_per_launch": bytes_per_launch},
-            "e2e": {"value": e2e_policy, "unit": "agent-steps/s", "h2d_bytes_per_step": 0,
+            "e2e": {"value": e2e_host, "unit": "agent-steps/s", "h2d_bytes_per_step": NA * 4,
                     "d2h_bytes_per_step": E * 8,
-                    "note": ("eager env_step calls, the same step as the timed one (actions from the device, "
-                             "no host input), reward and done read back to pinned host memory every step"),
-                    "host_actions": {"value": e2e_host, "h2d_bytes_per_step": NA * 4, "d2h_bytes_per_step": E * 8,
-                                     "note": "a host controller's actions copied in every step in place of the policy"}},
+                    "note": ("eager env_step calls through the C ABI from the timed region's start state: every "
+                             "step a host controller's actions [NA] int32 are copied in from pinned host memory "
+                             "and the step's reward and done [E] are read back into pinned host memory"),
+                    "device_actions": {"value": e2e_policy, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": E * 8,
+                                       "note": ("the same, with the actions picked on the device as in the timed "
+                                                "step (no host input)")}},
             "gpu_launches": stats["kernel_launches"],
             "seeds_0_4": {"values": sweep, "mean": sum(sweep) / len(sweep), "min": min(sweep), "max": max(sweep),
                           "median": sorted(sweep)[len(sweep) // 2],

@@ -289,9 +289,24 @@ ut_status env_set_state(ut_env* env, const ut_state_view* in);
  * handle was created with UT_FLAG_DEBUG. */
 ut_status env_debug(const ut_env* env, ut_debug_view* out);
 
-/* Synchronises and reads the device metrics (see ut_rollout_stats). */
+/* Synchronises and reads the device metrics (see ut_rollout_stats).
+ * Returns UT_ERR_TIMEOUT when the device status word records a bounded wait
+ * that gave up (status 2), UT_ERR_INVALID when it records a failed index
+ * check of the checked build (status 3, library compiled with -DUT_CHECKED);
+ * the stats are filled all the same.  env_metrics_reset clears the metrics
+ * and the device status word. */
 ut_status env_metrics(ut_env* env, ut_rollout_stats* out);
 ut_status env_metrics_reset(ut_env* env);
+
+/* Failure-detection test hook (no paper counterpart).  polls > 0: every
+ * later launch of the handle's tensor-core kernels (transformer agent,
+ * learned estimator) first waits on a barrier that nothing signals, gives up
+ * after `polls` polls, and takes the same exit as a real timed-out wait:
+ * device status word set, tensor memory freed, outputs of that launch not
+ * written.  No copy or MMA is in flight when it gives up.  polls == 0
+ * switches it off.  Captured rollout / collection graphs are re-captured.
+ * Errors: UT_ERR_INVALID (null handle). */
+ut_status env_test_wait_timeout(ut_env* env, uint32_t polls);
 
 /* Transformer agent weights (Sec. III-B.1, Fig. 3; readings C16).  params_host
  * holds n_params floats in the canonical order: W_emb[d][8], b_emb[d]; per

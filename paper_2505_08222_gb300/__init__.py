@@ -22,6 +22,8 @@ from . import _abi
 __all__ = ["Env", "UtError", "philox", "pf_resample", "lib"]
 
 lib = _abi.load()
+# checked build (UTRACK_CHECKED=1): handles closed with a failed index check
+CHECK_FAILURES: list = []
 
 
 class UtError(RuntimeError):
@@ -135,6 +137,11 @@ class Env:
     # ------------------------------------------------------------ lifecycle
     def close(self):
         if getattr(self, "h", None):
+            if _abi.CHECKED:  # checked build: record a failed index check before the handle goes
+                s = _abi.RolloutStats()
+                lib.env_metrics(self.h, ctypes.byref(s))
+                if s.device_status == 3:
+                    CHECK_FAILURES.append(lib.env_last_error(self.h).decode())
             lib.env_destroy(self.h)
             self.h = None
 
@@ -308,7 +315,14 @@ class Env:
         return {k: getattr(s, k) for k, _ in _abi.RolloutStats._fields_}
 
     def metrics_reset(self):
+        """Clears the device metrics and the device status word."""
         _check(lib.env_metrics_reset(self.h), self.h, "env_metrics_reset")
+
+    def test_wait_timeout(self, polls: int):
+        """Failure-detection test hook: > 0 makes the tensor-core kernels'
+        first wait run out after ``polls`` polls (status word -> timeout);
+        0 switches it off."""
+        _check(lib.env_test_wait_timeout(self.h, int(polls)), self.h, "env_test_wait_timeout")
 
     # ------------------------------------------------------------ state
     def _state_view(self):

@@ -5,7 +5,9 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libutrack.so")
+# UTRACK_CHECKED=1 loads the index-checked build (build(checked=True))
+CHECKED = os.environ.get("UTRACK_CHECKED", "") == "1"
+LIB_PATH = os.path.join(HERE, "_build_checked" if CHECKED else "_build", "libutrack.so")
 
 UT_ABI_VERSION = 8
 UT_FLAG_DEBUG = 1
@@ -121,6 +123,7 @@ SIGNATURES = {
     "env_debug": (ctypes.c_int, [_vp, ctypes.POINTER(DebugView)]),
     "env_metrics": (ctypes.c_int, [_vp, ctypes.POINTER(RolloutStats)]),
     "env_metrics_reset": (ctypes.c_int, [_vp]),
+    "env_test_wait_timeout": (ctypes.c_int, [_vp, ctypes.c_uint32]),
     "rollout_prepare": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "env_profile": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "env_stage_time": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),

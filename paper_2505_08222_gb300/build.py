@@ -18,6 +18,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libutrack.so")
+# the checked build (-DUT_CHECKED: data-dependent indexes tested in the
+# kernels, failures reported through the device status word) lives apart
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(BUILD_CHECKED, "libutrack.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -55,18 +59,21 @@ def _fingerprint(flags) -> str:
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: bool = False) -> str:
+    """Compiles every translation unit for sm_103a and links the library;
+    ``checked`` builds the index-checked variant into its own folder."""
+    out_dir, lib_path = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
     flags = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-             "-I" + INCLUDE] + ARCH + list(extra_flags)
-    stamp = os.path.join(BUILD, "stamp.txt")
+             "-I" + INCLUDE] + ARCH + list(extra_flags) + (["-DUT_CHECKED"] if checked else [])
+    stamp = os.path.join(out_dir, "stamp.txt")
     fp = _fingerprint(flags)
-    if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == fp:
-        return LIB
+    if not force and os.path.exists(lib_path) and os.path.exists(stamp) and open(stamp).read() == fp:
+        return lib_path
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc] + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -79,17 +86,18 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
     libdir = _cuda_lib_dir(nvcc)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [nvcc, "-shared", "-cudart", "shared"] + ARCH + ["-o", tmp] + objs + [
         "-L" + libdir, "-Xlinker", "-rpath", "-Xlinker", libdir]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib_path)
     with open(stamp, "w") as f:
         f.write(fp)
-    return LIB
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force=True, verbose=True))
+    import sys
+    print(build(force=True, verbose=True, checked="--checked" in sys.argv))

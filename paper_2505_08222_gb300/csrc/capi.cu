@@ -351,12 +351,14 @@ ut_status env_create(const ut_config* cfg, const ut_allocator* allocator, void* 
     return UT_ERR_CUDA;
   }
   h->pf_variant = pf_default_variant(P);
-  if (extension_create(h) != UT_OK) {
+  st = extension_create(h);
+  if (st != UT_OK) {
     std::fprintf(stderr, "env_create: %s\n", h->err.c_str());
+    extension_destroy(h);
     env_free_all(h);
     cudaStreamSynchronize(h->stream);
     delete h;
-    return UT_ERR_NOMEM;
+    return st;
   }
   *out = h;
   return UT_OK;
@@ -481,6 +483,24 @@ ut_status env_metrics_reset(ut_env* h) {
   h->launches = 0;
   UT_CUDA(h, cudaMemsetAsync(h->d.metrics_d, 0, 2 * sizeof(double), h->stream));
   UT_CUDA(h, cudaMemsetAsync(h->d.metrics_u, 0, 4 * sizeof(unsigned long long), h->stream));
+  UT_CUDA(h, cudaMemsetAsync(h->d.status, 0, sizeof(int), h->stream));
+  return UT_OK;
+}
+
+ut_status env_test_wait_timeout(ut_env* h, uint32_t polls) {
+  if (!h) return UT_ERR_INVALID;
+  if (h->test_wait_polls == polls) return UT_OK;
+  h->test_wait_polls = polls;
+  // captured graphs hold the kernels' arguments: capture again with the new value
+  if (h->graph_exec) {
+    cudaGraphExecDestroy(h->graph_exec);
+    h->graph_exec = nullptr;
+  }
+  if (h->ppo_exec) {
+    cudaGraphExecDestroy(h->ppo_exec);
+    h->ppo_exec = nullptr;
+    h->ppo_key.clear();
+  }
   return UT_OK;
 }
 
@@ -503,6 +523,7 @@ ut_status env_metrics(ut_env* h, ut_rollout_stats* out) {
   out->device_status = status;
   out->kernel_launches = h->launches;
   if (status == 2) return fail(h, UT_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (status == 3) return fail(h, UT_ERR_INVALID, "an index check of the checked build failed");
   return UT_OK;
 }
 

@@ -158,9 +158,27 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
-// Device error word: first error code wins.
+// Device error word: first error code wins.  Codes: 1 an action outside
+// [0, n_actions), 2 a bounded wait that gave up, 3 an index check of the
+// checked build that failed.
 __device__ __forceinline__ void raise_status(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
+
+// Checked build (-DUT_CHECKED): the kernels test their data-dependent
+// indexes (counts read from the CSR offsets and measurement headers, the
+// resample map, shared-memory slots) before using them; a failed test records
+// status 3 and the access is skipped, with no trap, so the context stays
+// usable and the next synchronising call reports it.  In the normal build
+// UT_IN_BOUNDS(cond, status) is the constant true and the test compiles away.
+__device__ __forceinline__ bool check_bounds(bool ok, int* status) {
+  if (!ok) raise_status(status, 3);
+  return ok;
+}
+#ifdef UT_CHECKED
+#define UT_IN_BOUNDS(cond, status) (::ut::check_bounds((cond), (status)))
+#else
+#define UT_IN_BOUNDS(cond, status) (true)
+#endif
 
 }  // namespace ut

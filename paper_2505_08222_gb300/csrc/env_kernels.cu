@@ -83,6 +83,7 @@ constexpr int kInitThreads = 256;
 __global__ void __launch_bounds__(kInitThreads) reset_pf_kernel(EnvDev d, uint32_t g) {
   const int f = blockIdx.x;
   const int ia = d.filt_agent[f], it = d.filt_target[f];
+  if (!UT_IN_BOUNDS(ia >= 0 && ia < d.NA && it >= 0 && it < d.NT, d.status)) return;  // (CTA-uniform)
   const float axv = d.ax[ia], ayv = d.ay[ia];
   const float dx = axv - d.tx[it], dy = ayv - d.ty[it], dz = 0.0f - d.tz[it];
   const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
@@ -174,6 +175,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) step_env_kernel(EnvDev d,
   const int a0 = d.agent_off[e], A = d.agent_off[e + 1] - a0;
   const int t0 = d.target_off[e], T = d.target_off[e + 1] - t0;
   const int f0 = d.filter_off[e], q0 = d.pair_off[e];
+  if (!UT_IN_BOUNDS(A >= 1 && A <= d.AM && d.AM <= kMaxAgents && T >= 1 && T <= d.TM && d.TM <= kMaxTargets &&
+                        a0 >= 0 && a0 + A <= d.NA && t0 >= 0 && t0 + T <= d.NT && f0 >= 0 &&
+                        f0 + (d.shared_filter ? T : A * T) <= d.F,
+                    d.status))
+    return;  // (warp-uniform)
 
   if (lane < A) {
     const int i = a0 + lane;
@@ -291,7 +297,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) step_env_kernel(EnvDev d,
     for (int b = 0; b < A; ++b) {
       if ((d.shared_filter || s_recv[wid][a * kMaxAgents + b]) && s_valid[wid][b * T + k]) {
         const float qx = s_ax[wid][b], qy = s_ay[wid][b], r = s_rng[wid][b * T + k];
-        d.meas[(long long)f * d.AM + n] = make_float4(qx, qy, 0.0f, r);
+        if (UT_IN_BOUNDS(n < d.AM, d.status)) d.meas[(long long)f * d.AM + n] = make_float4(qx, qy, 0.0f, r);
         ++n;
         if (d.ring_on) {
           reinterpret_cast<float4*>(d.ring)[(long long)f * kRing + head] = make_float4(qx, qy, r, (float)g);
@@ -334,9 +340,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) obs_reward_kernel(EnvDev 
   double sq = 0.0, rw = 0.0;
   unsigned long long n_err = 0, n_crash = 0, n_agents = 0;
   if (e < d.E) {
-    const int a0 = d.agent_off[e], A = d.agent_off[e + 1] - a0;
-    const int t0 = d.target_off[e], T = d.target_off[e + 1] - t0;
+    const int a0 = d.agent_off[e], A0 = d.agent_off[e + 1] - a0;
+    const int t0 = d.target_off[e], T0 = d.target_off[e + 1] - t0;
     const int f0 = d.filter_off[e];
+    // (checked build: an env whose counts fall outside the handle's maxima is skipped)
+    const bool counts_ok = UT_IN_BOUNDS(A0 >= 1 && A0 <= d.AM && T0 >= 1 && T0 <= d.TM && A0 + T0 <= d.NS &&
+                                            a0 >= 0 && a0 + A0 <= d.NA && f0 >= 0 &&
+                                            f0 + (d.shared_filter ? T0 : A0 * T0) <= d.F,
+                                        d.status);
+    const int A = counts_ok ? A0 : 0, T = counts_ok ? T0 : 1;
     for (int p = lane; p < A * d.NS; p += 32) {
       const int a = p / d.NS, slot = p - a * d.NS;
       const int ia = a0 + a;

@@ -57,7 +57,8 @@ __device__ __forceinline__ void copy_img(unsigned char* dst, const unsigned char
 // output is the correction (x - e1) / L.
 __device__ __forceinline__ void ring_features(const EnvDev& d, int f, uint32_t g, float e1x, float e1y, float e2x,
                                               float e2y, float vx, float vy, float (&x)[IN]) {
-  const float dz = d.tz[d.filt_target[f]];  // target depth; senders at the surface
+  const int it = d.filt_target[f];
+  const float dz = UT_IN_BOUNDS(it >= 0 && it < d.NT, d.status) ? d.tz[it] : 0.0f;  // target depth; senders at the surface
   const float L = d.est_scale;
   const int head = d.ring_head[f], cnt = d.ring_count[f];
   const float4* ring = reinterpret_cast<const float4*>(d.ring) + (long long)f * kRing;
@@ -231,13 +232,17 @@ __device__ __forceinline__ void env_stage(int s, size_t& off, uint32_t& bytes) {
   }
 }
 
-__global__ void __launch_bounds__(kTE, 1) fwd_env_kernel(Net net, EnvDev d, int stale) {
+// test_wait_polls > 0 (test hook, env_test_wait_timeout): first a bounded
+// wait on a barrier that nothing signals, then the timed-out exit (status 2)
+// before any copy or MMA is issued.
+__global__ void __launch_bounds__(kTE, 1) fwd_env_kernel(Net net, EnvDev d, int stale, uint32_t test_wait_polls) {
   pdl_wait();  // (dependents launch as this grid's CTAs exit)
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;           // features hi | lo [2 x 128 x 96], then hidden activations [128 x 256]
   unsigned char* sW = smem + 65536;   // two weight slots
   __shared__ __align__(8) uint64_t full[2];
   __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t never;  // test hook: a barrier nothing signals
   __shared__ uint32_t tbase;
   __shared__ float sOut[kParts][2][128];
   __shared__ int bad;
@@ -253,12 +258,22 @@ __global__ void __launch_bounds__(kTE, 1) fwd_env_kernel(Net net, EnvDev d, int 
     tc::mbar_init(&full[0], 1);
     tc::mbar_init(&full[1], 1);
     tc::mbar_init(&mbar, 1);
+    tc::mbar_init(&never, 1);
     bad = 0;
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tbase;
+  if (test_wait_polls) {
+    if (tid == 32 && !tc::mbar_wait(&never, 0u, test_wait_polls)) bad = 1;
+    __syncthreads();
+    if (bad) {
+      if (tid == 0) raise_status(d.status, 2);
+      if (warp == 0) tc::tmem_dealloc(tmem, 256);
+      return;
+    }
+  }
   const uint32_t tl = tmem + ((uint32_t)(warp & 3) << 21);  // this warp's lane quarter
   const uint32_t aA = tc::smem_addr(sA), aW = tc::smem_addr(sW);
   auto fetch = [&](int st) {  // thread 0: stage st into slot st % 2
@@ -375,7 +390,8 @@ __global__ void __launch_bounds__(kTE, 1) fwd_env_kernel(Net net, EnvDev d, int 
       o0 += sOut[k][0][row];
       o1 += sOut[k][1][row];
     }
-    const int it = d.filt_target[f];
+    const int it0 = d.filt_target[f];
+    const int it = UT_IN_BOUNDS(it0 >= 0 && it0 < d.NT, d.status) ? it0 : 0;
     // Bounded update (dropped if not finite): with a ping received this step
     // the estimate may move up to kMaxCorr L.  Without one, the rule chosen
     // by the mode applies: hold the estimate (stale inputs cannot drive the
@@ -422,8 +438,10 @@ __global__ void __launch_bounds__(kT, 1) bwd_kernel(Net net, TrainBufs t, int* s
   unsigned char* sB = smem + 65536;
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tbase;
-  __shared__ float s_red[2 * HID + 3 * HID + 2];  // dW4, db3, db2, db1, db4
-  __shared__ double s_loss;
+  // per-warp sums, each entry written once by lane 0 of its warp and summed
+  // over the warps in order after the last barrier: dW4, db3, db2, db1, db4
+  __shared__ float s_red[kT / 32][NB_PART];
+  __shared__ double s_loss[kT / 32];
   const int tid = threadIdx.x, warp = tid >> 5, lanei = tid & 31;
   const long long b = (long long)blockIdx.x * kT + tid;
   const bool valid = b < t.B;
@@ -434,11 +452,7 @@ __global__ void __launch_bounds__(kT, 1) bwd_kernel(Net net, TrainBufs t, int* s
     tc::tmem_alloc(&tbase, 256);
     tc::tmem_relinquish();
   }
-  if (tid == 0) {
-    tc::mbar_init(&mbar, 1);
-    s_loss = 0.0;
-  }
-  for (int i = tid; i < 5 * HID + 2; i += kT) s_red[i] = 0.0f;
+  if (tid == 0) tc::mbar_init(&mbar, 1);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -447,8 +461,8 @@ __global__ void __launch_bounds__(kT, 1) bwd_kernel(Net net, TrainBufs t, int* s
   const uint32_t aA = tc::smem_addr(sA), aB = tc::smem_addr(sB);
   uint32_t phase = 0;
   bool ok = true;
-  float* s_dW4 = s_red;
-  float* s_db3 = s_red + 2 * HID;
+  float* s_dW4 = s_red[warp];
+  float* s_db3 = s_dW4 + 2 * HID;
   float* s_db2 = s_db3 + HID;
   float* s_db1 = s_db2 + HID;
   float* s_db4 = s_db1 + HID;
@@ -475,12 +489,12 @@ __global__ void __launch_bounds__(kT, 1) bwd_kernel(Net net, TrainBufs t, int* s
     d1 = g[1] / (float)t.B;
   }
   se = warp_sum_d(se);
-  if (lanei == 0) atomicAdd(&s_loss, se);
+  if (lanei == 0) s_loss[warp] = se;
   {
     const float r0 = warp_sum(d0), r1 = warp_sum(d1);
     if (lanei == 0) {
-      atomicAdd(&s_db4[0], r0);
-      atomicAdd(&s_db4[1], r1);
+      s_db4[0] = r0;
+      s_db4[1] = r1;
     }
   }
   // dz3 = (W4^T dout) * GELU'(z3); dW4 += dout a3^T
@@ -494,13 +508,13 @@ __global__ void __launch_bounds__(kT, 1) bwd_kernel(Net net, TrainBufs t, int* s
       const float a = valid ? gelu1(z) : 0.0f;  // the forward's GELU
       const float w0 = warp_sum(d0 * a), w1 = warp_sum(d1 * a);
       if (lanei == 0) {
-        atomicAdd(&s_dW4[k], w0);
-        atomicAdd(&s_dW4[HID + k], w1);
+        s_dW4[k] = w0;
+        s_dW4[HID + k] = w1;
       }
       const float da = d0 * __ldg(mst + W4_OFF + k) + d1 * __ldg(mst + W4_OFF + HID + k);
       dz[i] = valid ? da * gelu_grad(z) : 0.0f;
       const float sdz = warp_sum(dz[i]);
-      if (lanei == 0) atomicAdd(&s_db3[k], sdz);
+      if (lanei == 0) s_db3[k] = sdz;
     }
     if (valid) {
       uint16_t* dr = t.dz + ((long long)2 * t.B + b) * HID + c0;
@@ -528,7 +542,7 @@ __global__ void __launch_bounds__(kT, 1) bwd_kernel(Net net, TrainBufs t, int* s
         const float z = valid ? t.z[((long long)l * t.B + b) * HID + c0 + i] : 0.0f;
         v[i] = valid ? v[i] * gelu_grad(z) : 0.0f;
         const float s = warp_sum(v[i]);
-        if (lanei == 0) atomicAdd(&s_db[c0 + i], s);
+        if (lanei == 0) s_db[c0 + i] = s;
       }
       if (valid) {
         uint16_t* dr = t.dz + ((long long)l * t.B + b) * HID + c0;
@@ -544,24 +558,83 @@ __global__ void __launch_bounds__(kT, 1) bwd_kernel(Net net, TrainBufs t, int* s
   }
   tc::fence_before_sync();
   __syncthreads();
-  for (int i = tid; i < 2 * HID; i += kT) atomicAdd(&t.grad[W4_OFF + i], s_dW4[i]);
-  for (int i = tid; i < HID; i += kT) {
-    atomicAdd(&t.grad[B3_OFF + i], s_db3[i]);
-    atomicAdd(&t.grad[B2_OFF + i], s_db2[i]);
-    atomicAdd(&t.grad[B1_OFF + i], s_db1[i]);
+  // the CTA's partial sums: the four warps' values added in warp order
+  float* pb = t.part_b + (long long)blockIdx.x * NB_PART;
+  for (int i = tid; i < NB_PART; i += kT) {
+    float acc = s_red[0][i];
+#pragma unroll
+    for (int w = 1; w < kT / 32; ++w) acc += s_red[w][i];
+    pb[i] = acc;
   }
-  if (tid < 2) atomicAdd(&t.grad[B4_OFF + tid], s_db4[tid]);
-  if (tid == 0) atomicAdd(t.loss, s_loss / t.B);
+  if (tid == 0) {
+    double acc = s_loss[0];
+#pragma unroll
+    for (int w = 1; w < kT / 32; ++w) acc += s_loss[w];
+    t.part_loss[blockIdx.x] = acc;
+  }
   if (!ok && tid == 0) raise_status(status, 2);
   if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+// grad[dst(i)] = sum over p of part[p][i], i < len: block x sums entries
+// 32x .. 32x+31, thread row g the parts p = g (mod 32) in increasing p, then
+// the 32 row sums in order of g (a fixed association: deterministic).  dst
+// maps a slab position to its canonical parameter offset: `which` 0 for the
+// bias / output-layer slab, 1 for the hidden weight slab.
+__device__ __forceinline__ long long part_dst(int which, long long i) {
+  if (which == 0) {
+    if (i < 2 * HID) return W4_OFF + i;
+    if (i < 3 * HID) return B3_OFF + (i - 2 * HID);
+    if (i < 4 * HID) return B2_OFF + (i - 3 * HID);
+    if (i < 5 * HID) return B1_OFF + (i - 4 * HID);
+    return B4_OFF + (i - 5 * HID);
+  }
+  if (i < (long long)HID * IN) return W1_OFF + i;
+  if (i < (long long)HID * IN + (long long)HID * HID) return W2_OFF + (i - (long long)HID * IN);
+  return W3_OFF + (i - (long long)HID * IN - (long long)HID * HID);
+}
+
+__global__ void __launch_bounds__(1024) part_reduce_kernel(const float* __restrict__ part, int nparts, long long len,
+                                                           int which, float* __restrict__ grad) {
+  __shared__ float red[32][33];
+  const int c = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const long long i = (long long)blockIdx.x * 32 + c;
+  float s = 0.0f;
+  if (i < len)
+    for (int p = g; p < nparts; p += 32) s += part[(long long)p * len + i];
+  red[g][c] = s;
+  __syncthreads();
+  if (g == 0 && i < len) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc += red[k][c];
+    grad[part_dst(which, i)] = acc;
+  }
+}
+
+// Batch loss = (sum of the CTA partials, in order of p mod 256, then the 256
+// sums in order) / B.
+__global__ void __launch_bounds__(256) loss_reduce_kernel(const double* __restrict__ part, int nparts, int B,
+                                                          double* __restrict__ loss) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int p = threadIdx.x; p < nparts; p += 256) s += part[p];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    for (int k = 0; k < 256; ++k) acc += red[k];
+    *loss = acc / B;
+  }
 }
 
 // ---------------------------------------------------------------------------
 // Weight gradients dW_l = dz_l^T a_{l-1} summed over the batch, on the tensor
 // cores: M = 128 output features (one half), N = input features, K = 128
-// batch rows per MMA group, accumulated in TMEM over the CTA's batch range.
-// The transposed operands are written element-wise into K-major images.
-// grid = (batch splits, output half, layer).
+// batch rows per MMA group, accumulated in TMEM over the CTA's batch range
+// and written to the split's partial slab (summed over the splits in a fixed
+// order by part_reduce_kernel).  The transposed operands are written
+// element-wise into K-major images.  grid = (batch splits, output half, layer).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kT, 2) wgrad_kernel(TrainBufs t, int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -619,15 +692,23 @@ __global__ void __launch_bounds__(kT, 2) wgrad_kernel(TrainBufs t, int* status) 
     }
     ok &= tc::mma_group(tmem, &aA, 1, aB, n_in, kT, c > c_begin, &mbar, phase);
   }
+  if (c_end <= c_begin) {  // per = ceil(chunks / splits) can leave the last splits without rows: zero slab
+    const int o = warp * 32 + (tid & 31);
+    const long long w_off = layer == 0 ? 0 : (long long)HID * IN + (long long)(layer - 1) * HID * HID;
+    float* pw = t.part_w + (long long)blockIdx.x * NW_PART + w_off;
+    for (int c = 0; c < n_in; ++c) pw[(long long)(half * 128 + o) * n_in + c] = 0.0f;
+  }
   if (c_end > c_begin && ok) {
     const int o = warp * 32 + (tid & 31);
-    const long long w_off = layer == 0 ? W1_OFF : (layer == 1 ? W2_OFF : W3_OFF);
+    // this split's slab: dW1 [256][96], then dW2 and dW3 [256][256]
+    const long long w_off = layer == 0 ? 0 : (long long)HID * IN + (long long)(layer - 1) * HID * HID;
+    float* pw = t.part_w + (long long)blockIdx.x * NW_PART + w_off;
     const uint32_t lane = tmem + ((uint32_t)(warp * 32) << 16);
     for (int c0 = 0; c0 < n_in; c0 += 16) {
       float v[16];
       tc::tmem_ld16(lane + c0, v);
 #pragma unroll
-      for (int i = 0; i < 16; ++i) atomicAdd(&t.grad[w_off + (long long)(half * 128 + o) * n_in + c0 + i], v[i]);
+      for (int i = 0; i < 16; ++i) pw[(long long)(half * 128 + o) * n_in + c0 + i] = v[i];
     }
   }
   if (!ok && tid == 0) raise_status(status, 2);
@@ -718,12 +799,13 @@ cudaError_t launch_forward(const Net& net, const float* X, const int32_t* rows, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_forward_env(const Net& net, const EnvDev& d, int stale, cudaStream_t s) {
+cudaError_t launch_forward_env(const Net& net, const EnvDev& d, int stale, uint32_t test_wait_polls,
+                               cudaStream_t s) {
   static std::atomic<unsigned long long> ready{0};
   cudaError_t e = smem_optin(fwd_env_kernel, kEnvSmem, ready);
   if (e != cudaSuccess) return e;
   if (d.F <= 0) return cudaSuccess;
-  launch_pdl(fwd_env_kernel, dim3((d.F + 127) / 128), dim3(kTE), kEnvSmem, s, net, d, stale);
+  launch_pdl(fwd_env_kernel, dim3((d.F + 127) / 128), dim3(kTE), kEnvSmem, s, net, d, stale, test_wait_polls);
   return cudaGetLastError();
 }
 
@@ -739,12 +821,18 @@ cudaError_t launch_backward(const Net& net, const TrainBufs& t, cudaStream_t s) 
   if (e == cudaSuccess) e = smem_optin(wgrad_kernel, kWgradSmem, ready_w);
   if (e != cudaSuccess) return e;
   if (t.B <= 0) return cudaSuccess;
-  bwd_kernel<<<(t.B + kT - 1) / kT, kT, kFwdSmem, s>>>(net, t, nullptr);
+  const int n_chunks = (t.B + kT - 1) / kT;
+  bwd_kernel<<<n_chunks, kT, kFwdSmem, s>>>(net, t, nullptr);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int n_chunks = (t.B + kT - 1) / kT;
-  const int splits = n_chunks < 24 ? n_chunks : 24;
+  const int splits = n_chunks < kWgradSplits ? n_chunks : kWgradSplits;
   wgrad_kernel<<<dim3(splits, 2, 3), kT, kWgradSmem, s>>>(t, nullptr);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // fixed-order sums of the partial slabs into the gradient and the loss
+  part_reduce_kernel<<<(NB_PART + 31) / 32, 1024, 0, s>>>(t.part_b, n_chunks, NB_PART, 0, t.grad);
+  part_reduce_kernel<<<(unsigned)((NW_PART + 31) / 32), 1024, 0, s>>>(t.part_w, splits, NW_PART, 1, t.grad);
+  loss_reduce_kernel<<<1, 256, 0, s>>>(t.part_loss, n_chunks, t.B, t.loss);
   return cudaGetLastError();
 }
 

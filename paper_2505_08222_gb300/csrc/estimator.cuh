@@ -41,6 +41,14 @@ constexpr size_t IMG_W2T_OFF = IMG_W3_OFF + IMG_W;
 constexpr size_t IMG_W3T_OFF = IMG_W2T_OFF + IMG_W;
 constexpr size_t IMG_BYTES = IMG_W3T_OFF + IMG_W;
 
+// Partial-sum slabs of the backward pass: the bias / output-layer gradients
+// (dW4 [2][256], db3, db2, db1 [256], db4 [2]) and the hidden weight
+// gradients (dW1 [256][96], dW2, dW3 [256][256]); the batch is split over at
+// most kWgradSplits weight-gradient CTAs per (layer, half).
+constexpr int NB_PART = 2 * HID + 3 * HID + OUT;
+constexpr int64_t NW_PART = (int64_t)HID * IN + 2 * (int64_t)HID * HID;
+constexpr int kWgradSplits = 24;
+
 struct Net {
   const unsigned char* img;  // operand images
   const float* master;       // FP32 parameters, canonical order (biases, W4)
@@ -57,13 +65,18 @@ struct TrainBufs {
   uint16_t* dz;          // [3][B][256] BF16 gradients w.r.t. z
   float* grad;           // [NPARAM] FP32 gradient
   double* loss;          // [1] loss of the batch
+  // fixed-order partial sums (no atomics: the gradient is deterministic)
+  float* part_b;         // [ceil(B/128)][NB_PART] per-CTA dW4, db3, db2, db1, db4
+  double* part_loss;     // [ceil(B/128)] per-CTA loss sums
+  float* part_w;         // [kWgradSplits][NW_PART] per-split dW1, dW2, dW3
   float huber;           // 0: squared error; > 0: Huber threshold (label units)
   int B;
 };
 
 cudaError_t launch_forward(const Net& net, const float* X, const int32_t* rows, int B, float* out, float* z,
                            uint16_t* a, cudaStream_t s);
-cudaError_t launch_forward_env(const Net& net, const EnvDev& d, int stale, cudaStream_t s);
+cudaError_t launch_forward_env(const Net& net, const EnvDev& d, int stale, uint32_t test_wait_polls,
+                               cudaStream_t s);
 cudaError_t launch_record(const EnvDev& d, float* feat, float* label, cudaStream_t s);
 cudaError_t launch_backward(const Net& net, const TrainBufs& t, cudaStream_t s);
 cudaError_t launch_adam(float* master, float* m, float* v, const float* grad, int step, float lr, float beta1,

@@ -27,6 +27,10 @@ struct EstimatorState {
   float* out = nullptr;
   int32_t* rows = nullptr;
   double* loss = nullptr;
+  // fixed-order partial sums of the backward pass
+  float* part_b = nullptr;
+  double* part_loss = nullptr;
+  float* part_w = nullptr;
 };
 
 struct PolicyState {
@@ -71,6 +75,7 @@ static PolicyDev policy_dev(ut_env* h) {
   p.counters = h->d.counters;
   p.sample = 1;
   p.status = h->d.status;
+  p.test_wait_polls = h->test_wait_polls;
   return p;
 }
 
@@ -148,15 +153,19 @@ extern "C" ut_status env_set_policy(ut_env* h, const float* params_host, int64_t
   std::vector<unsigned char> img;
   std::vector<float> vec, emb, head;
   policy_pack(ps->d, ps->L, ps->n_act, params_host, img, vec, emb, head);
-  if (!ps->wimg) {
-    ps->wimg = (unsigned char*)env_alloc(h, img.size());
-    ps->vec = (float*)env_alloc(h, vec.size() * 4);
-    ps->emb = (float*)env_alloc(h, emb.size() * 4);
-    ps->head = (float*)env_alloc(h, head.size() * 4);
-    if (!ps->wimg || !ps->vec || !ps->emb || !ps->head) {
+  if (!ps->wimg) {  // all or nothing (a failed attempt's buffers stay owned by the handle)
+    unsigned char* wimg = (unsigned char*)env_alloc(h, img.size());
+    float* vec_d = (float*)env_alloc(h, vec.size() * 4);
+    float* emb_d = (float*)env_alloc(h, emb.size() * 4);
+    float* head_d = (float*)env_alloc(h, head.size() * 4);
+    if (!wimg || !vec_d || !emb_d || !head_d) {
       h->err = "env_set_policy: allocation failed";
       return UT_ERR_NOMEM;
     }
+    ps->vec = vec_d;
+    ps->emb = emb_d;
+    ps->head = head_d;
+    ps->wimg = wimg;
   }
   cudaError_t e = cudaMemcpyAsync(ps->wimg, img.data(), img.size(), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ps->vec, vec.data(), vec.size() * 4, cudaMemcpyHostToDevice, h->stream);
@@ -231,14 +240,22 @@ ut_status est_fail(ut_env* h, ut_status st, const char* msg) {
 ut_status est_alloc_weights(ut_env* h) {
   EstimatorState* es = est_state(h);
   if (es->master) return UT_OK;
-  es->master = (float*)env_alloc(h, est::NPARAM * 4);
-  es->m = (float*)env_alloc(h, est::NPARAM * 4);
-  es->v = (float*)env_alloc(h, est::NPARAM * 4);
-  es->grad = (float*)env_alloc(h, est::NPARAM * 4);
-  es->img = (unsigned char*)env_alloc(h, est::IMG_BYTES);
-  es->loss = (double*)env_alloc(h, 8);
-  if (!es->master || !es->m || !es->v || !es->grad || !es->img || !es->loss)
-    return est_fail(h, UT_ERR_NOMEM, "estimator: allocation failed");
+  // all or nothing: a failed attempt leaves the state unset (its partial
+  // buffers stay owned by the handle until env_destroy), so a later call
+  // allocates again instead of finding half a set
+  float* master = (float*)env_alloc(h, est::NPARAM * 4);
+  float* m = (float*)env_alloc(h, est::NPARAM * 4);
+  float* v = (float*)env_alloc(h, est::NPARAM * 4);
+  float* grad = (float*)env_alloc(h, est::NPARAM * 4);
+  unsigned char* img = (unsigned char*)env_alloc(h, est::IMG_BYTES);
+  double* loss = (double*)env_alloc(h, 8);
+  if (!master || !m || !v || !grad || !img || !loss) return est_fail(h, UT_ERR_NOMEM, "estimator: allocation failed");
+  es->m = m;
+  es->v = v;
+  es->grad = grad;
+  es->img = img;
+  es->loss = loss;
+  es->master = master;
   return UT_OK;
 }
 
@@ -251,7 +268,11 @@ ut_status est_alloc_batch(ut_env* h, int B) {
   es->dz = (uint16_t*)env_alloc(h, (size_t)3 * B * est::HID * 2);
   es->out = (float*)env_alloc(h, (size_t)B * 2 * 4);
   es->rows = (int32_t*)env_alloc(h, (size_t)B * 4);
-  if (!es->z || !es->a || !es->dz || !es->out || !es->rows)
+  const size_t n_cta = ((size_t)B + 127) / 128;
+  es->part_b = (float*)env_alloc(h, n_cta * est::NB_PART * 4);
+  es->part_loss = (double*)env_alloc(h, n_cta * 8);
+  if (!es->part_w) es->part_w = (float*)env_alloc(h, (size_t)est::kWgradSplits * est::NW_PART * 4);
+  if (!es->z || !es->a || !es->dz || !es->out || !es->rows || !es->part_b || !es->part_loss || !es->part_w)
     return est_fail(h, UT_ERR_NOMEM, "estimator: batch allocation failed");
   es->batch_cap = B;
   return UT_OK;
@@ -282,6 +303,9 @@ cudaError_t est_grad_batch(ut_env* h, const float* X, const float* Y, const int3
   t.dz = es->dz;
   t.grad = es->grad;
   t.loss = es->loss;
+  t.part_b = es->part_b;
+  t.part_loss = es->part_loss;
+  t.part_w = es->part_w;
   t.huber = huber;
   t.B = B;
   return est::launch_backward(est_net(h), t, s);
@@ -293,7 +317,7 @@ namespace ut {
 cudaError_t extension_estimate_impl(ut_env* h, cudaStream_t s) {
   if (h->est_mode == 4) return launch_ls_update(h->d, s);
   if (h->est_mode < 1 || !h->est || !h->est->weights_set) return cudaErrorNotReady;
-  return est::launch_forward_env(est_net(h), h->d, h->est_mode - 1, s);
+  return est::launch_forward_env(est_net(h), h->d, h->est_mode - 1, h->test_wait_polls, s);
 }
 }  // namespace ut
 

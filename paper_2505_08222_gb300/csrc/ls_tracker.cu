@@ -26,6 +26,7 @@ __global__ void ls_update_kernel(EnvDev d) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= d.F) return;
   const int it = d.filt_target[f];
+  if (!UT_IN_BOUNDS(it >= 0 && it < d.NT, d.status)) return;
   const float dz = d.tz[it];
   const float e1x = d.estx[f], e1y = d.esty[f];
   const float e2x = d.prev_estx[f], e2y = d.prev_esty[f];

@@ -275,7 +275,7 @@ __device__ __forceinline__ int count_at(float v, float eps, const float* s_w, in
 template <int NT, int PPT, bool FULL>
 __device__ __forceinline__ void resample_map(const float (&w)[PPT], long long excl, long long W, int base, int P,
                                              long long* s_excl, float* s_w, int* s_mark, ScanScratch* sc,
-                                             int (&idx)[PPT]) {
+                                             int (&idx)[PPT], int* status) {
   constexpr int NW = NT / 32;
   const long long U0 = (long long)__umul64hi(sc->u64, (unsigned long long)W);
   const float invW = 1.0f / __ll2float_rn(W);
@@ -295,7 +295,7 @@ __device__ __forceinline__ void resample_map(const float (&w)[PPT], long long ex
     if (FULL || base + q < P) {
       cw += w[q];
       const int hi = count_at<PPT>(fmaf(a, cw, b), eps, my_w, q + 1, my_excl, sc, NW, P);
-      if (hi > lo) s_mark[lo] = base + q;
+      if (hi > lo && UT_IN_BOUNDS(lo >= 0 && lo < NT * PPT, status)) s_mark[lo] = base + q;
       lo = hi;
     }
   }
@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
   __syncthreads();  // sh.* visible
 
   // weight (log domain); measurements outer, particles inner
-  const int nm = sh.nm;
+  const int nm = UT_IN_BOUNDS(sh.nm >= 0 && sh.nm <= d.AM && d.AM <= kMaxAgents, d.status) ? sh.nm : 0;
   const float dz2 = sh.dz2;
   float pwv[PPT];  // carried log-weights (ESS form)
   if (ESS) {
@@ -539,10 +539,11 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
     init_markers<PPT>(s_mark, base);
     const long long excl = block_scan_sums<NT>(qsum, swx, swy, &sh.scan, W);  // contains barriers
     if (NT == 32) __syncwarp();  // single-warp blocks: order the shared-memory stores
-    resample_map<NT, PPT, FULL>(w, excl, W, base, P, s_excl, s_w, s_mark, &sh.scan, idx);
+    resample_map<NT, PPT, FULL>(w, excl, W, base, P, s_excl, s_w, s_mark, &sh.scan, idx, d.status);
 #pragma unroll
     for (int q = 0; q < PPT; ++q) {
-      const float4 pnew = s_part[slot_of<NT, PPT>(idx[q])];
+      const int sl = slot_of<NT, PPT>(idx[q]);
+      const float4 pnew = UT_IN_BOUNDS(sl >= 0 && sl < NT * PPT, d.status) ? s_part[sl] : make_float4(0.f, 0.f, 0.f, 0.f);
       x[q] = pnew.x;
       y[q] = pnew.y;
       vx[q] = pnew.z;
@@ -640,7 +641,7 @@ __global__ void __launch_bounds__(NT) pf_resample_kernel(const float* __restrict
   const long long excl = block_scan_sums<NT>(qsum, fx, fy, &s_scan, W);
   if (NT == 32) __syncwarp();
   int idx[PPT];
-  resample_map<NT, PPT, false>(w, excl, W, base, P, s_excl, s_w, s_mark, &s_scan, idx);
+  resample_map<NT, PPT, false>(w, excl, W, base, P, s_excl, s_w, s_mark, &s_scan, idx, nullptr);
 #pragma unroll
   for (int q = 0; q < PPT; ++q)
     if (base + q < P) out[f * P + base + q] = idx[q];

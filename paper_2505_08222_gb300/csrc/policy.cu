@@ -395,6 +395,7 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
   float2* sStat = reinterpret_cast<float2*>(smem + G::STAT_OFF);
   __shared__ __align__(8) uint64_t full[kSlots];
   __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ __align__(8) uint64_t never;  // test hook: a barrier nothing signals
   __shared__ uint32_t tmem_base_s;
   __shared__ int bad;
 
@@ -414,12 +415,24 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
   if (tid == 32) {
     for (int k = 0; k < kSlots; ++k) tc::mbar_init(&full[k], 1);
     tc::mbar_init(&mma_bar, 1);
+    tc::mbar_init(&never, 1);
     bad = 0;
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base_s;
+  if (p.test_wait_polls) {
+    // test hook: a bounded wait that runs out, then the timed-out exit (no
+    // copy or MMA has been issued, so nothing is in flight)
+    if (tid == 32 && !tc::mbar_wait(&never, 0u, p.test_wait_polls)) bad = 1;
+    __syncthreads();
+    if (bad) {
+      if (tid == 0) raise_status(p.status, 2);
+      if (warp == 0) tc::tmem_dealloc(tmem, G::TMEM_COLS);
+      return;
+    }
+  }
   const uint32_t tl = tmem + ((uint32_t)(warp & 3) << 21);  // this warp's lane quarter (lane 32 (w % 4))
   const uint32_t aA = tc::smem_addr(sA), aH = tc::smem_addr(sH), aRing = tc::smem_addr(ring);
   Loader ld{0, 0, p.L * G::NSTG};

@@ -33,6 +33,10 @@ struct PolicyDev {
   uint32_t step;
   int sample;                 // draw Gumbel-max actions
   int* status;
+  // test hook (env_test_wait_timeout): > 0 makes the kernel first wait on a
+  // barrier that nothing signals, for this many polls, and take the
+  // timed-out path (status 2) before it issues any copy or MMA
+  uint32_t test_wait_polls;
 };
 
 int64_t policy_param_count(int d, int L, int n_act);

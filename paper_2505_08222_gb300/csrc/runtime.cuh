@@ -49,6 +49,8 @@ struct ut_env {
   PolicyState* policy = nullptr;
   int est_mode = 0;
   EstimatorState* est = nullptr;
+  // test hook (env_test_wait_timeout): poll bound of a wait that runs out
+  uint32_t test_wait_polls = 0;
 };
 
 namespace ut {

@@ -13,16 +13,15 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 
-def test_traffic_line_matches_current_sources():
-    """The committed profile's traffic line carries the hash of the current
-    filter sources and the variant it was taken with; any other variant or a
-    changed source gives no traffic figure."""
-    lines = [l for l in open(bench.TRAFFIC_NOTE) if l.startswith("traffic:")]
-    assert len(lines) == 1
-    kv = dict(t.split("=", 1) for t in lines[0].split()[1:])
-    assert kv["sources"] == bench.pf_source_hash()
-    t = bench._pf_traffic(kv["variant"], 1000)
-    assert t == pytest.approx(float(kv["bytes_per_particle"]) * 1000)
+def test_traffic_figure_matches_current_sources():
+    """The committed traffic figure (profiles/pf_step_kernel_fleet5.json)
+    carries the hash of the current filter sources and the variant it was
+    taken with; any other variant gives no traffic figure."""
+    with open(bench.TRAFFIC_NOTE) as f:
+        t = json.load(f)
+    assert t["sources"] == bench.pf_source_hash()
+    got = bench._pf_traffic(t["variant"], 1000)
+    assert got == pytest.approx(float(t["bytes_per_particle"]) * 1000)
     assert bench._pf_traffic("no-such-variant", 1000) is None
 
 
@@ -65,6 +64,8 @@ def test_small_bench_line_has_the_contract_keys():
         assert k in line["e2e"], k
     assert line["gpu_launches"] > 0 and "workload" in line["config"]
     assert 0.0 < line["learned"]["rmse_ratio"] and line["seeds_0_4"]["min"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] > 0 and line["e2e"]["d2h_bytes_per_step"] > 0
+    assert 0.0 < line["learned"]["seeds_0_4"]["fresh_ping_steps"]["rmse_ratio"]
     # the TransfMAPPO update measurement
     ppo = line["ppo"]
     assert ppo["value"] > 0 and ppo["ms_per_update"] > 0 and ppo["collect_ms"] > 0

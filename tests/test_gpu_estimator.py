@@ -1,10 +1,13 @@
 """Learned range-only estimator on the GPU against the FP64 oracle.
 
-Forward / gradient tolerance: hidden activations and weights are BF16
-operands (relative rounding 2^-9) with FP32 accumulation; outputs of
-magnitude ~0.3 land within 2e-2 of the FP64 network, gradients within 5 %
-(relative L2 norm per tensor).  Features are FP32 (the first layer splits
-them into BF16 high and low parts), so they match the oracle's to 1e-6."""
+Forward tolerance: hidden activations and weights are BF16 operands (unit
+roundoff 2^-8) with FP32 accumulation; outputs of magnitude ~0.3 land within
+a few 1e-4 of the FP64 network (measured 3.7e-4 at most), and the bound is
+EST_FWD_ATOL = 5e-3.  Gradients are compared element by element against
+a fraction EST_GRAD_FRAC of each tensor's largest entry (tests/parity.py
+derives it from the BF16 roundings of the path).  Features are FP32 (the
+first layer splits them into BF16 high and low parts), so they match the
+oracle's to 1e-6."""
 import numpy as np
 import pytest
 import torch
@@ -19,8 +22,10 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 import paper_2505_08222_gb300 as ut  # noqa: E402
+from parity import EST_GRAD_FRAC, check_elementwise  # noqa: E402
 
 NP = 156930
+EST_FWD_ATOL = 5e-3
 
 
 def _features(n, seed):
@@ -51,7 +56,7 @@ def test_est_forward_matches_oracle():
     got = env.est_forward(torch.from_numpy(X).cuda()).cpu().numpy()
     ref = oracle.mlp_forward(params, X)
     err = np.abs(got - ref)
-    assert np.all(err <= 2e-2 + 2e-2 * np.abs(ref)), float(err.max())
+    assert np.all(err <= EST_FWD_ATOL), float(err.max())
     print(f"est forward: max |d| {err.max():.2e} mean {err.mean():.2e}")
 
 
@@ -65,14 +70,8 @@ def test_est_gradients_match_oracle():
     ref_loss, ref_grad = oracle.mlp_loss_grad(params, X, Y)
     assert abs(loss - ref_loss) <= 2e-2 * ref_loss
     g = grad.cpu().numpy().astype(np.float64)
-    off = 0
-    for name, shape, _ in synth.mlp_shapes():
-        n = int(np.prod(shape))
-        a, b = g[off:off + n], ref_grad[off:off + n]
-        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
-        print(f"grad {name}: relative error {rel:.2e}")
-        assert rel < 5e-2, (name, rel)
-        off += n
+    worst = check_elementwise(g, ref_grad, synth.mlp_shapes(), EST_GRAD_FRAC)
+    print("est gradients, worst |d| / (EST_GRAD_FRAC max|g|) per tensor:", {k: round(v, 3) for k, v in worst.items()})
 
 
 def test_est_huber_gradients_match_oracle():
@@ -90,12 +89,29 @@ def test_est_huber_gradients_match_oracle():
     assert np.mean(r > delta) > 0.2 and np.mean(r < delta) > 0.2
     assert abs(loss - ref_loss) <= 2e-2 * ref_loss
     g = grad.cpu().numpy().astype(np.float64)
-    off = 0
-    for name, shape, _ in synth.mlp_shapes():
-        n = int(np.prod(shape))
-        rel = np.linalg.norm(g[off:off + n] - ref_grad[off:off + n]) / np.linalg.norm(ref_grad[off:off + n])
-        assert rel < 5e-2, (name, rel)
-        off += n
+    worst = check_elementwise(g, ref_grad, synth.mlp_shapes(), EST_GRAD_FRAC)
+    print("est Huber gradients, worst ratio per tensor:", {k: round(v, 3) for k, v in worst.items()})
+
+
+def test_est_gradients_and_training_are_deterministic():
+    """The gradient sums are fixed-order partial sums (no atomics): the same
+    batch gives the same bits, and two training runs from the same weights
+    end with identical weights."""
+    env, _ = _env()
+    params = synth.mlp_params(seed=12, bias_scale=0.1)
+    X = torch.from_numpy(_features(3000, 9)).cuda()
+    Y = torch.from_numpy((np.random.default_rng(10).standard_normal((3000, 2)) * 0.3).astype(np.float32)).cuda()
+    env.est_set_weights(params)
+    l1, g1 = env.est_loss_grad(X, Y, huber=1.0)
+    l2, g2 = env.est_loss_grad(X, Y, huber=1.0)
+    assert l1 == l2 and torch.equal(g1, g2)
+    ends = []
+    for _ in range(2):
+        env.est_set_weights(params)
+        env.est_train(X, Y, steps=30, batch=1024, lr=1e-3, seed=4)
+        ends.append(env.est_get_weights())
+    assert np.array_equal(ends[0], ends[1])
+    assert not np.array_equal(ends[0], params)
 
 
 def test_half_batch_gradients_average_to_full_batch():
@@ -352,11 +368,12 @@ def test_learned_step_matches_oracle(mode):
     """One learned-form step from an injected oracle state, GPU against the
     oracle's learned tracker: with a constant-output network (weights zero,
     output bias exactly representable) the update rule must agree to float32
-    rounding; with a random network to the forward pass's BF16 tolerance
-    (2e-2 + 2e-2 |out| in units of L = 100 m, outputs clamped to 3)."""
+    rounding (1 cm); with a random network within 0.5 m: the BF16 forward
+    moves a correction (units of L = 100 m) by a few 1e-4 of L, measured up to
+    0.1 m, and the bound keeps a factor 5 above that."""
     const = np.zeros(NP, np.float32)
     const[-2:] = (0.5, -4.0)
-    for params, atol in ((const, 1e-2), (synth.mlp_params(seed=21, bias_scale=0.1), 8.0)):
+    for params, atol in ((const, 1e-2), (synth.mlp_params(seed=21, bias_scale=0.1), 0.5)):
         env, p = _env(n_envs=6, det_radius=130.0, comm_drop=0.2)
         env.reset(8)
         o = oracle.OracleEnv(p, 8)

@@ -2,9 +2,11 @@
 FP64 oracle on the same BF16-representable weights and inputs.
 
 Tolerance: activations are rounded to BF16 before every matrix product
-(relative error 2^-9 per operand), accumulations are FP32; over L pre-LN
+(unit roundoff 2^-8 per operand), accumulations are FP32; over L pre-LN
 blocks the logits (magnitude ~1) differ from the FP64 oracle by a few 1e-3
-typically and stay below 3e-2 + 2e-2 |logit|, which the test uses."""
+typically and by at most ~1e-2, so every logit must lie within 2e-2 absolute
+of the oracle's.  The recurrent embedding h is itself stored in BF16 (one
+more rounding of up to 2^-8 |h|), so its bound adds 1e-2 |h|."""
 import numpy as np
 import pytest
 import torch
@@ -20,7 +22,8 @@ if not torch.cuda.is_available():
 
 import paper_2505_08222_gb300 as ut  # noqa: E402
 
-ATOL, RTOL = 3e-2, 2e-2
+ATOL = 2e-2          # logits, absolute
+ATOL_H, RTOL_H = 2e-2, 1e-2  # recurrent embedding (BF16 storage)
 
 
 def _env(name, **kw):
@@ -50,10 +53,12 @@ def test_policy_logits_match_oracle(name, n_agents):
     ref, ref_h = oracle.policy_forward(params, p.d_model, p.n_layers, p.n_heads, tok, n_ent, h, p.n_actions)
     got = logits.cpu().numpy()
     err = np.abs(got - ref)
-    assert np.all(err <= ATOL + RTOL * np.abs(ref)), float(err.max())
     got_h = h_dev.float().cpu().numpy()
-    assert np.all(np.abs(got_h - ref_h) <= ATOL + RTOL * np.abs(ref_h)), float(np.abs(got_h - ref_h).max())
-    print(f"{name}: max |dlogit| {err.max():.2e}, mean {err.mean():.2e}")
+    dh = np.abs(got_h - ref_h)
+    print(f"{name}: max |dlogit| {err.max():.2e}, mean {err.mean():.2e}; "
+          f"h: max |dh| / (ATOL_H + RTOL_H |h|) {np.max(dh / (ATOL_H + RTOL_H * np.abs(ref_h))):.3f}")
+    assert np.all(err <= ATOL), float(err.max())
+    assert np.all(dh <= ATOL_H + RTOL_H * np.abs(ref_h)), float(dh.max())
 
 
 def test_policy_entity_permutation_invariance_on_gpu():
@@ -72,7 +77,7 @@ def test_policy_entity_permutation_invariance_on_gpu():
     # required of nearly every agent and parity-level agreement of all.
     ref, _ = oracle.policy_forward(params, p.d_model, p.n_layers, p.n_heads, tok, n_ent, h, p.n_actions)
     for got in (a, b):
-        assert np.all(np.abs(got - ref) <= ATOL + RTOL * np.abs(ref))
+        assert np.all(np.abs(got - ref) <= ATOL)
     same = np.all(np.abs(a - b) <= 1e-4, axis=1)
     assert same.mean() >= 0.9, same.mean()
 
@@ -103,11 +108,11 @@ def test_env_step_uses_policy_on_reset_observation():
     out = env.step()
     o = oracle.OracleEnv(p, 21)
     o.reset(0)
-    tok = o.obs()
+    tok = synth.round_bf16(o.obs().astype(np.float32))  # the step's tokens are BF16 of the same features
     ref, _ = oracle.policy_forward(params, p.d_model, p.n_layers, p.n_heads, tok, o.n_entities(),
                                    np.zeros((o.NA, p.d_model)), p.n_actions)
     got = out["logits"].cpu().numpy()
-    assert np.all(np.abs(got - ref) <= ATOL + RTOL * np.abs(ref)), float(np.abs(got - ref).max())
+    assert np.all(np.abs(got - ref) <= ATOL), float(np.abs(got - ref).max())
     _, gum = oracle.gumbel_actions(21, 1, got.astype(np.float64))
     a = out["actions"].cpu().numpy()
     noisy = got + gum

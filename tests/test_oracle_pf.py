@@ -124,6 +124,85 @@ def test_resample_brute_force_small(P):
         np.testing.assert_array_equal(oracle.systematic_resample(w, 0), _brute_resample(w, 0))
 
 
+def _exact_resample_real(wmax, u64):
+    """Systematic resampling (Sec. II-A) on the unquantised FP64 weights in
+    exact rationals: C_i = S_i / S with S_i the partial sums of the weights,
+    offset u0 = u64 / 2^64, u_j = (j + u0) / P, idx_j = min{i : C_i > u_j}
+    (clamped to P - 1).  Returns the map and the CDF."""
+    P = len(wmax)
+    S, acc = [], Fraction(0)
+    for w in wmax:
+        acc += Fraction(float(w))
+        S.append(acc)
+    C = [x / acc for x in S]
+    u0 = Fraction(u64, 2 ** 64)
+    out, i = [], 0
+    for j in range(P):
+        u = (j + u0) / P
+        while i < P - 1 and not C[i] > u:
+            i += 1
+        out.append(i)
+    return np.array(out), C
+
+
+@pytest.mark.parametrize("P", [1, 2, 3, 7, 16, 100, 1000])
+def test_quantised_map_is_systematic_resampling_on_the_real_weights(P):
+    """The oracle resamples on weights quantised to q_i = floor(w_i 2^38)
+    (reading C5).  On the real (unquantised) weights, systematic resampling
+    gives the same map except where a threshold u_j lies within
+    (P + 2) 2^-38 of a CDF step: flooring moves each partial sum Q_i / W
+    from S_i / S by less than P 2^-38 (every w <= 1 with max w = 1, so
+    W >= 2^38), and the offset U0 / W lies within 1/W of u64 / 2^64.
+    Weights below 2^-38 of the maximum (dropped by the quantisation) are the
+    only other departure, and they fall under the same bound."""
+    rng = np.random.default_rng(100 + P)
+    delta = Fraction(P + 2, 2 ** 38)
+    n_diff = 0
+    for trial in range(30 if P < 1000 else 6):
+        kind = trial % 3
+        if kind == 0:
+            w = rng.uniform(0, 1, P)
+        elif kind == 1:
+            w = np.exp(-rng.exponential(8.0, P))
+        else:  # some weights below 2^-38 of the maximum
+            w = np.exp(-rng.exponential(20.0, P))
+            w[rng.integers(0, P, max(1, P // 4))] = rng.uniform(0, 2.0 ** -39, max(1, P // 4))
+        w[rng.integers(0, P)] = 1.0
+        u64 = int(rng.integers(0, 2 ** 63)) * 2 + int(rng.integers(0, 2))
+        got = oracle.systematic_resample(w, u64)
+        want, C = _exact_resample_real(w, u64)
+        for j in np.nonzero(got != want)[0]:
+            u = (int(j) + Fraction(u64, 2 ** 64)) / P
+            gap = min(abs(c - u) for c in C)
+            assert gap <= delta, (P, trial, int(j), float(gap))
+            n_diff += 1
+    assert n_diff <= 2, n_diff  # a coincidence within 2^-30 is rare on random draws
+
+
+def test_quantised_map_departs_only_within_the_bound_near_a_step():
+    """A threshold placed inside a dropped weight's interval, or within a
+    few 2^-38 of a CDF step, is where the two maps may differ; one placed
+    well away from every step gives the same index."""
+    P = 4
+    tiny = 2.0 ** -40  # below 2^-38: quantised to 0
+    w = np.array([1.0, tiny, 1.0, 1.0])
+    S = np.cumsum([Fraction(float(x)) for x in w])
+    C = [x / S[-1] for x in S]
+    # u_1 = (1 + u0) / P inside (C_0, C_1]: the real map picks particle 1,
+    # the quantised one (q_1 = 0) cannot
+    u0 = (C[0] + C[1]) / 2 * P - 1
+    assert 0 < u0 < 1
+    u64 = int(u0 * 2 ** 64)
+    got = oracle.systematic_resample(w, u64)
+    want, _ = _exact_resample_real(w, u64)
+    assert want[1] == 1 and got[1] == 2
+    gap = min(abs(c - (1 + Fraction(u64, 2 ** 64)) / P) for c in C)
+    assert gap <= Fraction(P + 2, 2 ** 38)
+    # thresholds (j + 1/2) / P, far from every step (1/3, 1/3 + 2^-40, 2/3, 1): identical maps
+    u64 = 2 ** 63
+    np.testing.assert_array_equal(oracle.systematic_resample(w, u64), _exact_resample_real(w, u64)[0])
+
+
 def test_resample_structure():
     rng = np.random.default_rng(9)
     P = 1000
