@@ -340,10 +340,10 @@ def learned_form(args, p, K, W, rank):
             "seeds_0_4": {"rmse_ratio": ratios, "mean": sum(ratios) / 5, "min": min(ratios), "max": max(ratios),
                           "pf_rmse_m": [x["rmse"] for x in split_pf], "learned_rmse_m": [x["rmse"] for x in split_le],
                           "fresh_ping_steps": {"pf_rmse_m": fresh_pf, "learned_rmse_m": fresh_le,
-                                               "rmse_ratio": fresh_le / fresh_pf,
+                                               "rmse_ratio": fresh_le / fresh_pf if fresh_pf > 0 else None,
                                                "share_of_filter_steps": sum(x["fresh_frac"] for x in split_pf) / 5},
                           "stale_steps": {"pf_rmse_m": stale_pf, "learned_rmse_m": stale_le,
-                                          "rmse_ratio": stale_le / stale_pf},
+                                          "rmse_ratio": stale_le / stale_pf if stale_pf > 0 else None},
                           "note": (f"seeds 0-4 (neither trained nor validated on), {T_eval} eager steps each; a "
                                    "filter-step is fresh when the filter's newest received ping is from that step")},
             "stale_rule": "network applied on steps without a fresh ping too (est_set_mode 2)",

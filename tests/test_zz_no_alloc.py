@@ -81,10 +81,13 @@ def test_noalloc_tracker_matches_the_oracle(P, rank):
     """From an injected state: the oracle steps (move, ping, communicate,
     filter) in FP64; the entry point gets the oracle's moved positions and
     the same pre-step particles (FP32) at the same global step.  Estimates
-    and errors agree within the filter step's tolerance (5 mm); particles
-    agree within 1e-5 relative wherever both sides drew the same measurement
-    lists and resample map (every filter but those with a ping at the
-    detection edge or a threshold within rounding of a CDF step)."""
+    and errors agree within the filter step's tolerance (5 mm).  Resampled
+    particles agree within 1e-5 relative except where a systematic-resampling
+    threshold lies within the FP32 weights' rounding of a CDF step, so that
+    the two sides pick neighbouring particles for that output: with
+    P = 1000 thresholds per filter and weight errors ~1e-5 relative that
+    happens in a few per cent of filters, to one or two of their outputs;
+    more than 99.5 % of all resampled particles must agree."""
     full = preset("fleet5", n_envs=64).replace(n_particles=P, d_model=0, comm_drop=0.2, target_depth_max=30.0)
     p = shard.shard_params(full, rank, 2)
     seed = 5
@@ -110,12 +113,13 @@ def test_noalloc_tracker_matches_the_oracle(P, rank):
         for k in ("estx", "esty"):
             assert np.all(np.abs(est[k].cpu().numpy() - o.arr[k]) < 5e-3), (call, k)
         assert np.all(np.abs(est["err"].cpu().numpy() - ref["err"]) < 5e-3), call
-        same = np.ones(o.F, bool)
+        same = np.ones(o.F * P, bool)
         for k in ("px", "py", "pvx", "pvy"):
             floor = 100.0 if k in ("px", "py") else 1.0
-            ok = rel_close(parts[k].cpu().numpy(), o.arr[k], 1e-5, floor).reshape(o.F, P)
-            same &= ok.all(1)
-        assert same.mean() > 0.98, (call, same.mean())
+            same &= rel_close(parts[k].cpu().numpy(), o.arr[k], 1e-5, floor)
+        print(f"P={P} rank {rank}: {same.mean():.5f} of resampled particles equal to the oracle's; "
+              f"{same.reshape(o.F, P).all(1).mean():.3f} of filters entirely")
+        assert same.mean() > 0.995, (call, same.mean())
 
 
 def test_noalloc_rejects_sizes_beyond_its_static_limit():
