@@ -270,12 +270,30 @@ ut_status env_set_pf_variant(ut_env* env, int32_t variant);
 ut_status env_get_pf_variant(const ut_env* env, int32_t* variant);
 
 /* Autotuner: times `reps` eager steps of every usable particle-filter variant
- * (CUDA events around the filter launches), keeps the fastest, and records it
- * in a process-wide cache keyed by (n_envs, max agents, max targets, P,
- * filters); a later handle with the same key takes the cached choice without
- * timing.  The timed steps advance the environment: call it before
- * env_reset.  Synchronising.  *chosen (optional) receives the variant. */
+ * (CUDA events around the filter launches) and keeps the fastest; then, when
+ * the handle qualifies for the persistent rollout (env_set_rollout_form),
+ * times rollout(reps) in both forms with that variant and keeps the faster
+ * form.  Both choices are recorded in a process-wide cache keyed by (n_envs,
+ * max agents, max targets, P, filters); a later handle with the same key
+ * takes the cached choices without timing.  The timed steps advance the
+ * environment: call env_reset afterwards.  Synchronising.  *chosen
+ * (optional) receives the variant. */
 ut_status env_autotune(ut_env* env, int32_t reps, int32_t* chosen);
+
+/* Rollout form used by rollout(T): 0 replays one captured CUDA graph of T
+ * steps (every configuration); 1 runs one persistent kernel (Sec. III-A.3:
+ * environments are independent, so one CTA advances one environment through
+ * all T steps with block barriers only; an environment with one filter keeps
+ * its particles in registers for the whole rollout).  Form 1 needs the
+ * environment's uniform random actions (no policy set), the particle-filter
+ * tracker (est_set_mode 0), every-step resampling (pf_ess_num 0) and a
+ * filter variant that covers P, else UT_ERR_UNSUPPORTED; when the handle
+ * stops qualifying (a policy or tracker mode set later), rollout() uses the
+ * graph.  With the same filter variant both forms give the same state bit
+ * for bit; the device metrics are the same sums in another order.
+ * env_get_rollout_form reports the form rollout() would use now. */
+ut_status env_set_rollout_form(ut_env* env, int32_t form);
+ut_status env_get_rollout_form(const ut_env* env, int32_t* form);
 
 /* Device views of the state buffers (borrowed).  Synchronises to read the
  * step counters. */

@@ -275,6 +275,16 @@ class Env:
     def est_load(self, path: str):
         _check(lib.est_load(self.h, path.encode()), self.h, "est_load")
 
+    def set_rollout_form(self, form: int):
+        """0: captured CUDA graph of T steps; 1: persistent kernel (random
+        actions and the particle filter only; UtError otherwise)."""
+        _check(lib.env_set_rollout_form(self.h, int(form)), self.h, "env_set_rollout_form")
+
+    def rollout_form(self) -> int:
+        v = ctypes.c_int32()
+        _check(lib.env_get_rollout_form(self.h, ctypes.byref(v)), self.h, "env_get_rollout_form")
+        return v.value
+
     def rollout_prepare(self, T: int):
         _check(lib.rollout_prepare(self.h, T), self.h, "rollout_prepare")
 

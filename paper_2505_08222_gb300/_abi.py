@@ -124,6 +124,8 @@ SIGNATURES = {
     "env_metrics": (ctypes.c_int, [_vp, ctypes.POINTER(RolloutStats)]),
     "env_metrics_reset": (ctypes.c_int, [_vp]),
     "env_test_wait_timeout": (ctypes.c_int, [_vp, ctypes.c_uint32]),
+    "env_set_rollout_form": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "env_get_rollout_form": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32)]),
     "rollout_prepare": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "env_profile": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "env_stage_time": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),

@@ -566,9 +566,23 @@ ut_status rollout_prepare(ut_env* h, int32_t T) {
   return graph_ensure(h, T);
 }
 
+// The persistent kernel runs the step with the environment's random actions
+// and the particle filter: no transformer agent, no learned or LS tracker,
+// every-step resampling, and a filter launch shape that covers P.
+static bool persistent_ok(const ut_env* h) {
+  return !h->policy_ready && h->est_mode == 0 && ut::persistent_supported(h->d, h->pf_variant);
+}
+
 ut_status rollout(ut_env* h, int32_t T, ut_rollout_stats* stats) {
   if (!h || T < 1) return UT_ERR_INVALID;
   if (!h->reset_done) return fail(h, UT_ERR_STATE, "rollout before env_reset");
+  if (h->rollout_form == 1 && persistent_ok(h)) {
+    UT_CUDA(h, env_metrics_reset(h) == UT_OK ? cudaSuccess : cudaErrorUnknown);
+    UT_CUDA(h, ut::launch_rollout_persistent(h->d, h->pf_variant, T, h->stream));
+    h->launches += 2;
+    if (stats) return env_metrics(h, stats);
+    return UT_OK;
+  }
   ut_status st = graph_ensure(h, T);
   if (st != UT_OK) return st;
   UT_CUDA(h, env_metrics_reset(h) == UT_OK ? cudaSuccess : cudaErrorUnknown);
@@ -599,9 +613,43 @@ ut_status env_get_pf_variant(const ut_env* h, int32_t* v) {
   return UT_OK;
 }
 
+ut_status env_set_rollout_form(ut_env* h, int32_t form) {
+  if (!h || form < 0 || form > 1) return UT_ERR_INVALID;
+  if (form == 1 && !persistent_ok(h))
+    return fail(h, UT_ERR_UNSUPPORTED,
+                "persistent rollout: needs random actions (no policy), the particle filter (est_mode 0), "
+                "every-step resampling and a filter launch shape covering P");
+  h->rollout_form = form;
+  return UT_OK;
+}
+
+ut_status env_get_rollout_form(const ut_env* h, int32_t* form) {
+  if (!h || !form) return UT_ERR_INVALID;
+  *form = (h->rollout_form == 1 && persistent_ok(h)) ? 1 : 0;
+  return UT_OK;
+}
+
 namespace {
 std::mutex g_tune_mutex;
-std::map<std::tuple<int, int, int, int, int64_t>, int> g_tune_cache;
+// (E, A_max, T_max, P, filters) -> (filter variant, rollout form)
+std::map<std::tuple<int, int, int, int, int64_t>, std::pair<int, int>> g_tune_cache;
+
+// Device time (ms) of one rollout(T) of the handle in its current form.
+ut_status time_rollout(ut_env* h, int32_t T, float* ms) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  UT_CUDA(h, cudaEventCreate(&a));
+  UT_CUDA(h, cudaEventCreate(&b));
+  UT_CUDA(h, cudaEventRecord(a, h->stream));
+  ut_status st = rollout(h, T, nullptr);
+  if (st == UT_OK) {
+    UT_CUDA(h, cudaEventRecord(b, h->stream));
+    UT_CUDA(h, cudaEventSynchronize(b));
+    UT_CUDA(h, cudaEventElapsedTime(ms, a, b));
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return st;
+}
 }  // namespace
 
 ut_status env_autotune(ut_env* h, int32_t reps, int32_t* chosen) {
@@ -612,8 +660,9 @@ ut_status env_autotune(ut_env* h, int32_t reps, int32_t* chosen) {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      h->pf_variant = it->second;
-      if (chosen) *chosen = it->second;
+      h->pf_variant = it->second.first;
+      h->rollout_form = it->second.second;
+      if (chosen) *chosen = it->second.first;
       return UT_OK;
     }
   }
@@ -641,9 +690,25 @@ ut_status env_autotune(ut_env* h, int32_t reps, int32_t* chosen) {
   h->prof_on = prof_before;
   h->eager_used = 0;
   h->pf_variant = best_v;
+  // the rollout form: the captured graph against the persistent kernel (when
+  // the handle qualifies), each timed over `reps` steps after one warm-up
+  // rollout, with the chosen filter variant
+  int form = 0;
+  if (persistent_ok(h)) {
+    float ms_form[2] = {0.0f, 0.0f};
+    for (int f = 0; f < 2; ++f) {
+      h->rollout_form = f;
+      float warm = 0.0f;
+      ut_status st = time_rollout(h, reps, &warm);
+      if (st == UT_OK) st = time_rollout(h, reps, &ms_form[f]);
+      if (st != UT_OK) return st;
+    }
+    form = ms_form[1] < ms_form[0] ? 1 : 0;
+  }
+  h->rollout_form = form;
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune_cache[key] = best_v;
+    g_tune_cache[key] = std::make_pair(best_v, form);
   }
   if (chosen) *chosen = best_v;
   return UT_OK;

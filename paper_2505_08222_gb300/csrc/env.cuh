@@ -93,5 +93,9 @@ bool pf_variant_valid(int v, int P);
 cudaError_t launch_pf_resample(const float* wmax, const uint64_t* u64, int64_t n_filters, int P, int32_t* idx,
                                cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, uint64_t seed, uint32_t* out, int64_t n, cudaStream_t s);
+// Persistent rollout (rollout_persistent.cu): T steps in one launch, one CTA
+// per environment, random actions, the filter launch shape of `variant`.
+bool persistent_supported(const EnvDev& d, int variant);
+cudaError_t launch_rollout_persistent(const EnvDev& d, int variant, int T, cudaStream_t s);
 
 }  // namespace ut

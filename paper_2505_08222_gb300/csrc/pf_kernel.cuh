@@ -330,12 +330,20 @@ struct Shared {
   int nm;
 };
 
-// MODE 0: any P (scalar loads); 1: P % 4 == 0 (float4 streams); 2: P equal
-// to NT * PPT (float4 streams, no slot is out of range).  ESS: weights carried
-// across steps as log-weights d.pw, resampling only when triggered.
-template <int NT, int PPT, int MINB, int MODE, bool ESS>
-__global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
-  pdl_wait();  // (dependents launch as this grid's CTAs exit: no early trigger in a many-wave kernel)
+// One filter's step by the whole CTA (filter f, global step g): stage the
+// inputs, load the particles (unless RES), predict, weight, estimate sums,
+// resample map and gather, store (unless RES), then thread 0's estimate and
+// history writes.  RES: the particles stay in the registers x, y, vx, vy
+// across calls (thread t holds particles t * PPT .. t * PPT + PPT - 1), as in
+// the persistent rollout; otherwise those arrays are scratch.  MODE 0: any P
+// (scalar loads); 1: P % 4 == 0 (float4 streams); 2: P equal to NT * PPT
+// (float4 streams, no slot is out of range).  ESS: weights carried across
+// steps as log-weights d.pw, resampling only when triggered.  The shared
+// memory is the kernel's: a caller that calls it again must put a block
+// barrier between the calls.
+template <int NT, int PPT, int MODE, bool ESS, bool RES>
+__device__ __forceinline__ void pf_step_body(const EnvDev& d, const int f, const uint32_t g, float (&x)[PPT],
+                                             float (&y)[PPT], float (&vx)[PPT], float (&vy)[PPT]) {
   static_assert(PPT % 4 == 0, "PPT must be a multiple of 4");
   constexpr bool VEC = MODE >= 1, FULL = MODE == 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -346,9 +354,7 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
   __shared__ Shared sh;
 
   const int tid = threadIdx.x;
-  const int f = blockIdx.x;
   const int P = d.P;
-  const uint32_t g = d.counters[0] + 1u;
   const int base = tid * PPT;
   const long long off = (long long)f * P;
 
@@ -380,8 +386,8 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
     sh.scan.u64 = (unsigned long long)r.x[0] | ((unsigned long long)r.x[1] << 32);
   }
 
-  float x[PPT], y[PPT], vx[PPT], vy[PPT];
-  if (VEC) {
+  if (RES) {
+  } else if (VEC) {
 #pragma unroll
     for (int q = 0; q < PPT; q += 4) {
       if (FULL || base + q < P) {
@@ -567,7 +573,8 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
   }
 
   // write back (streaming stores: the state is not reread this step)
-  if (VEC) {
+  if (RES) {
+  } else if (VEC) {
 #pragma unroll
     for (int q = 0; q < PPT; q += 4) {
       if (FULL || base + q < P) {
@@ -613,6 +620,81 @@ __global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
     const float dx = ex - sh.tgt[0], dy = ey - sh.tgt[1];
     d.err[f] = sqrtf(dx * dx + dy * dy);
   }
+}
+
+// Particles of filter f into / out of registers (the persistent rollout's
+// resident form; the same accesses as pf_step_body's).
+template <int NT, int PPT, int MODE>
+__device__ __forceinline__ void load_particles(const EnvDev& d, int f, float (&x)[PPT], float (&y)[PPT],
+                                               float (&vx)[PPT], float (&vy)[PPT]) {
+  constexpr bool VEC = MODE >= 1, FULL = MODE == 2;
+  const int P = d.P;
+  const int base = threadIdx.x * PPT;
+  const long long off = (long long)f * P;
+  if (VEC) {
+#pragma unroll
+    for (int q = 0; q < PPT; q += 4) {
+      if (FULL || base + q < P) {
+        const float4 a = *reinterpret_cast<const float4*>(d.px + off + base + q);
+        const float4 b = *reinterpret_cast<const float4*>(d.py + off + base + q);
+        const float4 c = *reinterpret_cast<const float4*>(d.pvx + off + base + q);
+        const float4 e = *reinterpret_cast<const float4*>(d.pvy + off + base + q);
+        x[q] = a.x; x[q + 1] = a.y; x[q + 2] = a.z; x[q + 3] = a.w;
+        y[q] = b.x; y[q + 1] = b.y; y[q + 2] = b.z; y[q + 3] = b.w;
+        vx[q] = c.x; vx[q + 1] = c.y; vx[q + 2] = c.z; vx[q + 3] = c.w;
+        vy[q] = e.x; vy[q + 1] = e.y; vy[q + 2] = e.z; vy[q + 3] = e.w;
+      } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) x[q + t] = y[q + t] = vx[q + t] = vy[q + t] = 0.0f;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      const bool in = base + q < P;
+      x[q] = in ? d.px[off + base + q] : 0.0f;
+      y[q] = in ? d.py[off + base + q] : 0.0f;
+      vx[q] = in ? d.pvx[off + base + q] : 0.0f;
+      vy[q] = in ? d.pvy[off + base + q] : 0.0f;
+    }
+  }
+}
+
+template <int NT, int PPT, int MODE>
+__device__ __forceinline__ void store_particles(const EnvDev& d, int f, const float (&x)[PPT], const float (&y)[PPT],
+                                                const float (&vx)[PPT], const float (&vy)[PPT]) {
+  constexpr bool VEC = MODE >= 1, FULL = MODE == 2;
+  const int P = d.P;
+  const int base = threadIdx.x * PPT;
+  const long long off = (long long)f * P;
+  if constexpr (VEC) {
+#pragma unroll
+    for (int q = 0; q < PPT; q += 4) {
+      if (FULL || base + q < P) {
+        *reinterpret_cast<float4*>(d.px + off + base + q) = make_float4(x[q], x[q + 1], x[q + 2], x[q + 3]);
+        *reinterpret_cast<float4*>(d.py + off + base + q) = make_float4(y[q], y[q + 1], y[q + 2], y[q + 3]);
+        *reinterpret_cast<float4*>(d.pvx + off + base + q) = make_float4(vx[q], vx[q + 1], vx[q + 2], vx[q + 3]);
+        *reinterpret_cast<float4*>(d.pvy + off + base + q) = make_float4(vy[q], vy[q + 1], vy[q + 2], vy[q + 3]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      if (base + q < P) {
+        d.px[off + base + q] = x[q];
+        d.py[off + base + q] = y[q];
+        d.pvx[off + base + q] = vx[q];
+        d.pvy[off + base + q] = vy[q];
+      }
+    }
+  }
+}
+
+template <int NT, int PPT, int MINB, int MODE, bool ESS>
+__global__ void __launch_bounds__(NT, MINB) pf_step_kernel(EnvDev d) {
+  pdl_wait();  // (dependents launch as this grid's CTAs exit: no early trigger in a many-wave kernel)
+  float x[PPT], y[PPT], vx[PPT], vy[PPT];
+  pf_step_body<NT, PPT, MODE, ESS, false>(d, (int)blockIdx.x, d.counters[0] + 1u, x, y, vx, vy);
 }
 
 // Stand-alone resample map (same device code as the fused step).

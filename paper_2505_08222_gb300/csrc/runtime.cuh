@@ -51,6 +51,9 @@ struct ut_env {
   EstimatorState* est = nullptr;
   // test hook (env_test_wait_timeout): poll bound of a wait that runs out
   uint32_t test_wait_polls = 0;
+  // rollout(): 0 the captured CUDA graph of T steps, 1 the persistent kernel
+  // (when the handle qualifies: random actions, the filter tracker)
+  int rollout_form = 0;
 };
 
 namespace ut {
