@@ -431,7 +431,15 @@ def ppo_update(args, p, rank):
     n_tok = 1 + NS
     fps = ppo_flops_per_sample(d, p.n_layers, n_tok, p.n_actions)
     achieved = fps * tr.mb_actor / (step_ms * 1e-3) / 1e12
-    peak = fp32_simt_peak_tflops(2070.0)
+    tc = bool(getattr(tr.actor, "tensor_cores", False))
+    if tc:  # BF16 GEMM operands on the tensor cores: against the measured bf16 peak
+        peaks, peak_kind = _peaks()
+        peak = peaks["bf16_tflops"]
+        roof_kind = ("tensor", f"{peak_kind} cuBLAS bf16 GEMM (burst); the step also holds FP32 attention, "
+                               "LayerNorm, loss and reduction kernels")
+    else:
+        peak = fp32_simt_peak_tflops(2070.0)
+        roof_kind = ("alu", "derived FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz")
     variant = env.pf_variant_name()
     env.close()
     return {
@@ -439,16 +447,18 @@ def ppo_update(args, p, rank):
         "ms_per_update": update_ms, "collect_ms": collect_ms,
         "iteration_agent_steps_per_s": T * NA / ((collect_ms + update_ms) * 1e-3),
         "T": T, "epochs": 1, "minibatches": 4, "actor_minibatch": tr.mb_actor, "critic_minibatch": tr.mb_critic,
-        "dtype": "f32",
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+        "dtype": "bf16 GEMM operands, f32 accumulation and activations" if tc else "f32",
+        "roofline": {"bound": roof_kind[0], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak,
                      "traffic": None, "scope": "actor PPO gradient step (forward, loss, backward: all kernels)",
-                     "avg_step_ms": step_ms, "flops_per_sample": fps,
-                     "peak_kind": "derived FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz",
+                     "avg_step_ms": step_ms, "flops_per_sample": fps, "peak_kind": roof_kind[1],
                      "timing": "CUDA events around 6 gradient calls on one minibatch"},
         "stats_last_minibatch": stats,
         "filter_variant": variant,
-        "note": ("FP32 transformer training path on CUDA cores; the batch is a real collection (env_reset(1000), "
-                 "T steps with the agent acting, one CUDA graph), the critic fed the true state"),
+        "note": (("linear layers on the tensor cores (BF16 operands, FP32 accumulation), the rest FP32"
+                  if tc else "FP32 transformer training path on CUDA cores")
+                 + "; the batch is a real collection (env_reset(1000), T steps with the agent acting, one CUDA "
+                   "graph), the critic fed the true state"),
     }
 
 

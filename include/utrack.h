@@ -559,6 +559,15 @@ const char* tfm_last_error(const ut_tfm* t);
  * valid until tfm_destroy; writes through it change the network. */
 ut_status tfm_params(ut_tfm* t, float** params_dev);
 
+/* GEMM path of the handle's forward and backward (the dense contractions of
+ * the linear layers): 1 (default) BF16 operands on the tensor cores
+ * (tcgen05.mma, FP32 accumulation in tensor memory; activations stay FP32 in
+ * memory and are rounded to BF16 as they are staged); 0 FP32 on the CUDA
+ * cores.  Attention, LayerNorm, losses and reductions are FP32 either way.
+ * A bounded tensor-core wait that gave up is reported as UT_ERR_TIMEOUT by
+ * the next call that returns statistics.  Errors: UT_ERR_INVALID. */
+ut_status tfm_set_gemm_path(ut_tfm* t, int32_t tensor_cores);
+
 /* Forward of n samples (1 .. max_batch).  Sample s reads batch row
  * b = sel_dev ? sel_dev[s] : s of: tokens_dev [.][n_slots][8] (FP32, or BF16
  * when tokens_bf16), n_ent_dev [.] (clamped to 0 .. n_slots) and h_dev

@@ -159,6 +159,7 @@ SIGNATURES = {
     "tfm_destroy": (None, [_vp]),
     "tfm_last_error": (ctypes.c_char_p, [_vp]),
     "tfm_params": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
+    "tfm_set_gemm_path": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "tfm_forward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp]),
     "tfm_ppo_actor_grad": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp, _vp, ctypes.c_float,
                                           ctypes.c_float, _vp, ctypes.POINTER(ctypes.c_double)]),

@@ -22,6 +22,7 @@
 
 #include "../../include/utrack.h"
 #include "common.cuh"
+#include "tc.cuh"
 #include "tfm.cuh"
 
 namespace ut {
@@ -31,6 +32,7 @@ constexpr int kMaxT = 1 + UT_MAX_AGENTS + UT_MAX_TARGETS;  // tokens per sample
 constexpr int kRowBlocks = 304;                             // blocks of the head / embedding-gradient kernels
 constexpr int kLnBlocks = 1216;                             // blocks of the LayerNorm kernels
 constexpr int kRowWarps = kRowBlocks * 8;                   // warps writing partial sums
+constexpr int kTcSplits = 304;                              // row splits of a tensor-core weight gradient
 
 enum { EPI_STORE = 0, EPI_BIAS = 1, EPI_BIAS_RES = 2, EPI_BIAS_GELU = 3, EPI_GELU_GRAD = 4, EPI_PARTIAL = 5 };
 
@@ -50,6 +52,8 @@ struct Gemm {
   const float* R;      // residual added (EPI_BIAS_RES), ld = ldc
   float* C2;           // GELU of the output (EPI_BIAS_GELU), ld = ldc
   const float* aux;    // pre-activation whose GELU derivative scales the output (EPI_GELU_GRAD), ld = ldc
+  const uint16_t* bimg;  // BF16 image of B for the tensor-core path (kinds 0, 1), or NULL: CUDA cores
+  int* status;           // device status word (a tensor-core wait that gave up)
 };
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
@@ -911,6 +915,16 @@ struct ut_tfm {
   float* part = nullptr;  // partial sums of the parameter gradients
   double *spart = nullptr, *stats_d = nullptr;
   std::vector<int64_t> off;  // canonical tensor offsets
+  // GEMM path: 1 BF16 tensor cores (FP32 accumulation), 0 FP32 CUDA cores
+  int gemm_tc = 1;
+  // BF16 images of the block weights for the tensor-core path, per block l:
+  // Wqkv, Wo, W1, W2 as B of the forward, then their transposes as B of the
+  // input gradient (ImgSpec table on the device, packed once per call)
+  uint16_t* wimg = nullptr;
+  std::vector<int64_t> img_off;  // [L][8] offsets into wimg (elements)
+  int64_t* img_spec = nullptr;   // [L * 8][5] (weight offset, R, C, transpose, image offset)
+  int n_img = 0, img_max = 0;
+  int* status = nullptr;
 };
 
 namespace ut {
@@ -954,12 +968,41 @@ bool valid_config(const ut_tfm_config* c) {
   return c->max_batch >= 1 && c->max_batch <= (1ll << 22);
 }
 
+#include "tfm_tc.cuh"
+
+// Every BF16 weight image of the handle: grid (elements, image).
+__global__ void pack_images_kernel(const float* __restrict__ prm, const int64_t* __restrict__ spec,
+                                   uint16_t* __restrict__ img) {
+  const int64_t* sp = spec + 5 * blockIdx.y;
+  const int R = (int)sp[1], C = (int)sp[2];
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)R * C) return;
+  const int r = (int)(i / C), c = (int)(i % C);
+  const float* W = prm + sp[0];
+  const float v = sp[3] ? W[(long long)c * R + r] : W[(long long)r * C + c];
+  img[sp[4] + img_offset(r, c, R, C) / 2] = f2bf_bits(v);
+}
+
 inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 // kind 0: forward (A row-major, B = W [N][K]); 1: input gradient (A
 // row-major, B = W [K][N]); 2: weight gradient (A and B indexed [k][.]).
 cudaError_t gemm(int kind, const Gemm& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
+  if (kind != 2 && g.bimg && g.K % 32 == 0 && g.N % 32 == 0 && g.lda % 4 == 0 && g.ldc % 4 == 0 &&
+      ((uintptr_t)g.A & 15) == 0 && ((uintptr_t)g.C & 15) == 0 && g.kchunk == g.K) {
+    static std::atomic<unsigned long long> ready{0};
+    cudaError_t e = smem_optin(tc_rows_kernel, kTcSmem, ready);
+    if (e != cudaSuccess) return e;
+    // CTAs loop over the row tiles: about two per SM per column tile
+    const long long tiles = (g.M + 127) / 128;
+    const int n_tiles = (g.N + kTcMaxN - 1) / kTcMaxN;
+    long long ctas = (2 * 152 + n_tiles - 1) / n_tiles;
+    if (ctas > tiles) ctas = tiles;
+    dim3 grid((unsigned)ctas, (unsigned)n_tiles);
+    tc_rows_kernel<<<grid, kTcThreads, kTcSmem, s>>>(g, g.bimg, g.status);
+    return cudaGetLastError();
+  }
   const long long kc = g.kchunk > 0 ? g.kchunk : g.K;
   dim3 grid((unsigned)((g.M + 63) / 64), (unsigned)((g.N + 63) / 64), (unsigned)((g.K + kc - 1) / kc));
   Gemm a = g;
@@ -1007,6 +1050,31 @@ cudaError_t reduce(const float* part, int nparts, long long len, long long strid
 // r, split along the rows into partial slabs summed in order.
 cudaError_t wgrad(ut_tfm* t, const float* dOut, int n_o, const float* In, int n_i, long long rows, float* gW,
                   float* gb, cudaStream_t s) {
+  if (t->gemm_tc && rows > 0) {
+    // tensor cores: (n_o / 128) x (n_i / 256) tiles x row splits, about two
+    // CTAs per SM, each split a multiple of 64 rows
+    static std::atomic<unsigned long long> ready{0};
+    cudaError_t e = smem_optin(tc_wgrad_kernel, kTcSmem, ready);
+    if (e != cudaSuccess) return e;
+    const long long tiles = (long long)((n_o + 127) / 128) * ((n_i + kTcMaxN - 1) / kTcMaxN);
+    long long splits = (kTcSplits + tiles - 1) / tiles;
+    const long long max_split = (rows + kTcChunk - 1) / kTcChunk;
+    if (splits > max_split) splits = max_split;
+    if (splits < 1) splits = 1;
+    long long rc = (rows + splits - 1) / splits;
+    rc = (rc + kTcChunk - 1) / kTcChunk * kTcChunk;
+    splits = (rows + rc - 1) / rc;
+    Gemm g = mk(dOut, n_o, In, n_i, t->part, n_i, n_o, n_i, rows, EPI_PARTIAL);
+    g.kchunk = rc;
+    g.status = t->status;
+    dim3 grid((unsigned)((n_o + 127) / 128), (unsigned)((n_i + kTcMaxN - 1) / kTcMaxN), (unsigned)splits);
+    float* bias_part = t->part + splits * n_o * n_i;
+    tc_wgrad_kernel<<<grid, kTcThreads, kTcSmem, s>>>(g, bias_part, t->status);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = reduce(t->part, (int)splits, (long long)n_o * n_i, (long long)n_o * n_i, gW, s);
+    if (e == cudaSuccess) e = reduce(bias_part, (int)splits, n_o, n_o, gb, s);
+    return e;
+  }
   Gemm g = mk(dOut, n_o, In, n_i, t->part, n_i, n_o, n_i, rows, EPI_PARTIAL);
   const long long tiles = (long long)((n_o + 63) / 64) * ((n_i + 63) / 64);
   long long splits = (608 + tiles - 1) / tiles;
@@ -1073,6 +1141,15 @@ cudaError_t forward(ut_tfm* t, const Call& c, cudaStream_t s) {
   const long long rows = c.n * t->T, MR = t->max_rows;
   const float* w = t->prm;
   const auto& o = t->off;
+  if (t->gemm_tc) {  // the weights' BF16 images for this call
+    pack_images_kernel<<<dim3(blocks_for(t->img_max, 256), (unsigned)t->n_img), 256, 0, s>>>(t->prm, t->img_spec,
+                                                                                            t->wimg);
+    cudaError_t e0 = cudaGetLastError();
+    if (e0 != cudaSuccess) return e0;
+  }
+  auto img = [&](int l, int which) -> const uint16_t* {
+    return t->gemm_tc ? t->wimg + t->img_off[8 * l + which] : nullptr;
+  };
   embed_kernel<TokT><<<blocks_for(rows * d, 256), 256, 0, s>>>((const TokT*)c.tok, c.ne, c.h, c.sel, w + o[0],
                                                               w + o[1], t->X, c.n, t->T, t->NS, d);
   cudaError_t e = cudaGetLastError();
@@ -1094,23 +1171,31 @@ cudaError_t forward(ut_tfm* t, const Call& c, cudaStream_t s) {
     if (e != cudaSuccess) break;
     Gemm g = mk(Y1, d, w + ol[T_WQKV], d, QKV, 3 * d, rows, 3 * d, d, EPI_BIAS);
     g.bias = w + ol[T_BQKV];
+    g.bimg = img(l, 0);
+    g.status = t->status;
     e = gemm(0, g, s);
     if (e == cudaSuccess) e = attn_fwd<DH>(QKV, c.ne, c.sel, P, O, c.n, t->T, t->NS, t->H, s);
     if (e != cudaSuccess) break;
     g = mk(O, d, w + ol[T_WO], d, M, d, rows, d, d, EPI_BIAS_RES);
     g.bias = w + ol[T_BO];
     g.R = Xl;
+    g.bimg = img(l, 1);
+    g.status = t->status;
     e = gemm(0, g, s);
     if (e == cudaSuccess) e = ln_fwd<DJ>(M, w + ol[T_LN2G], w + ol[T_LN2B], Y2, S2, rows, s);
     if (e != cudaSuccess) break;
     g = mk(Y2, d, w + ol[T_W1], d, Z, 4 * d, rows, 4 * d, d, EPI_BIAS_GELU);
     g.bias = w + ol[T_B1];
     g.C2 = G;
+    g.bimg = img(l, 2);
+    g.status = t->status;
     e = gemm(0, g, s);
     if (e != cudaSuccess) break;
     g = mk(G, 4 * d, w + ol[T_W2], 4 * d, Xn, d, rows, d, 4 * d, EPI_BIAS_RES);
     g.bias = w + ol[T_B2];
     g.R = M;
+    g.bimg = img(l, 3);
+    g.status = t->status;
     e = gemm(0, g, s);
   }
   return e;
@@ -1123,6 +1208,12 @@ cudaError_t backward(ut_tfm* t, const Call& c, float* grad, cudaStream_t s) {
   const float* w = t->prm;
   const auto& o = t->off;
   cudaError_t e = cudaSuccess;
+  // input-gradient GEMM of block l with the transposed image `which` (4..7)
+  auto dgemm = [&](int l, int which, Gemm g) {
+    g.bimg = t->gemm_tc ? t->wimg + t->img_off[8 * l + which] : nullptr;
+    g.status = t->status;
+    return gemm(1, g, s);
+  };
   for (int l = t->L - 1; l >= 0 && e == cudaSuccess; --l) {
     const int64_t* ol = o.data() + 2 + 12 * l;
     const float* Xl = t->X + l * MR * d;
@@ -1139,16 +1230,16 @@ cudaError_t backward(ut_tfm* t, const Call& c, float* grad, cudaStream_t s) {
     // feed-forward sub-block: X' = M + W2 gelu(W1 LN2(M) + b1) + b2
     Gemm g = mk(t->dX, d, w + ol[T_W2], 4 * d, t->dBig, 4 * d, rows, 4 * d, d, EPI_GELU_GRAD);
     g.aux = Z;
-    e = gemm(1, g, s);
+    e = dgemm(l, 7, g);
     if (e == cudaSuccess) e = wgrad(t, t->dX, d, G, 4 * d, rows, grad + ol[T_W2], grad + ol[T_B2], s);
-    if (e == cudaSuccess) e = gemm(1, mk(t->dBig, 4 * d, w + ol[T_W1], d, t->dY, d, rows, d, 4 * d, EPI_STORE), s);
+    if (e == cudaSuccess) e = dgemm(l, 6, mk(t->dBig, 4 * d, w + ol[T_W1], d, t->dY, d, rows, d, 4 * d, EPI_STORE));
     if (e == cudaSuccess) e = wgrad(t, t->dBig, 4 * d, Y2, d, rows, grad + ol[T_W1], grad + ol[T_B1], s);
     if (e == cudaSuccess) e = ln_bwd<DJ>(t, t->dY, M, S2, w + ol[T_LN2G], t->dX, t->dM, grad + ol[T_LN2G], rows, s);
     // attention sub-block: M = X + Wo attn(LN1(X)) + bo
-    if (e == cudaSuccess) e = gemm(1, mk(t->dM, d, w + ol[T_WO], d, t->dO, d, rows, d, d, EPI_STORE), s);
+    if (e == cudaSuccess) e = dgemm(l, 5, mk(t->dM, d, w + ol[T_WO], d, t->dO, d, rows, d, d, EPI_STORE));
     if (e == cudaSuccess) e = wgrad(t, t->dM, d, O, d, rows, grad + ol[T_WO], grad + ol[T_BO], s);
     if (e == cudaSuccess) e = attn_bwd<DH>(QKV, P, t->dO, t->dBig, c.n, t->T, t->H, s);
-    if (e == cudaSuccess) e = gemm(1, mk(t->dBig, 3 * d, w + ol[T_WQKV], d, t->dY, d, rows, d, 3 * d, EPI_STORE), s);
+    if (e == cudaSuccess) e = dgemm(l, 4, mk(t->dBig, 3 * d, w + ol[T_WQKV], d, t->dY, d, rows, d, 3 * d, EPI_STORE));
     if (e == cudaSuccess) e = wgrad(t, t->dBig, 3 * d, Y1, d, rows, grad + ol[T_WQKV], grad + ol[T_BQKV], s);
     if (e == cudaSuccess) e = ln_bwd<DJ>(t, t->dY, Xl, S1, w + ol[T_LN1G], t->dM, t->dX, grad + ol[T_LN1G], rows, s);
   }
@@ -1297,6 +1388,7 @@ extern "C" ut_status tfm_create(const ut_tfm_config* cfg, const float* params_ho
   part = std::max(part, (size_t)kRowWarps * (2 * d + (size_t)t->n_out * d + t->n_out));
   part = std::max(part, (size_t)kRowWarps * 9 * d);
   part = std::max(part, (size_t)kLnBlocks * 2 * d);
+  part = std::max(part, (size_t)kTcSplits * (4 * d * d + 4 * d));  // tensor-core weight- and bias-gradient slabs
   bool ok = true;
   auto A = [&](size_t n) -> float* {
     float* p = (float*)dalloc(t, n * 4);
@@ -1326,11 +1418,40 @@ extern "C" ut_status tfm_create(const ut_tfm_config* cfg, const float* params_ho
   t->spart = (double*)dalloc(t, (size_t)kRowWarps * 4 * 8);
   t->stats_d = (double*)dalloc(t, 4 * 8);
   ok = ok && t->spart && t->stats_d;
+  // weight images: per block, B of the forward for Wqkv [3d][d], Wo [d][d],
+  // W1 [4d][d], W2 [d][4d], then B of the input gradient (their transposes)
+  std::vector<int64_t> spec;
+  int64_t img_total = 0;
+  t->img_max = 0;
+  for (int l = 0; l < t->L; ++l) {
+    const int64_t* ol = t->off.data() + 2 + 12 * l;
+    const int64_t woff[4] = {ol[T_WQKV], ol[T_WO], ol[T_W1], ol[T_W2]};
+    const int rows_w[4] = {3 * t->d, t->d, 4 * t->d, t->d}, cols_w[4] = {t->d, t->d, t->d, 4 * t->d};
+    for (int tr = 0; tr < 2; ++tr)
+      for (int k = 0; k < 4; ++k) {
+        const int R = tr ? cols_w[k] : rows_w[k], C = tr ? rows_w[k] : cols_w[k];
+        // each 256-row block holds C columns of 256 rows (the last block padded)
+        const int64_t n = (int64_t)((R + kTcMaxN - 1) / kTcMaxN) * kTcMaxN * C;
+        t->img_off.push_back(img_total);
+        spec.insert(spec.end(), {woff[k], (int64_t)R, (int64_t)C, (int64_t)tr, img_total});
+        img_total += n;
+        t->img_max = std::max(t->img_max, R * C);
+      }
+  }
+  t->n_img = 8 * t->L;
+  t->wimg = (uint16_t*)dalloc(t, (size_t)img_total * 2);
+  t->img_spec = (int64_t*)dalloc(t, spec.size() * 8);
+  t->status = (int*)dalloc(t, 4);
+  ok = ok && t->wimg && t->img_spec && t->status;
   if (!ok) {
     tfm_destroy(t);
     return UT_ERR_NOMEM;
   }
   cudaError_t e = cudaMemcpyAsync(t->prm, params_host, (size_t)n_params * 4, cudaMemcpyHostToDevice, t->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(t->img_spec, spec.data(), spec.size() * 8, cudaMemcpyHostToDevice, t->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->wimg, 0, (size_t)img_total * 2, t->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(t->status, 0, 4, t->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(t->am, 0, (size_t)n_params * 4, t->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(t->av, 0, (size_t)n_params * 4, t->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(t->stream);
@@ -1372,9 +1493,19 @@ extern "C" ut_status tfm_forward(ut_tfm* t, const void* tokens_dev, const int32_
 
 static ut_status finish_stats(ut_tfm* t, double* stats_host, const char* name) {
   if (!stats_host) return UT_OK;
+  int status = 0;
   cudaError_t e = cudaMemcpyAsync(stats_host, t->stats_d, 4 * 8, cudaMemcpyDeviceToHost, t->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&status, t->status, 4, cudaMemcpyDeviceToHost, t->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(t->stream);
-  return e == cudaSuccess ? UT_OK : fail(t, UT_ERR_CUDA, std::string(name) + ": " + cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(t, UT_ERR_CUDA, std::string(name) + ": " + cudaGetErrorString(e));
+  if (status == 2) return fail(t, UT_ERR_TIMEOUT, std::string(name) + ": a bounded tensor-core wait gave up");
+  return UT_OK;
+}
+
+extern "C" ut_status tfm_set_gemm_path(ut_tfm* t, int32_t tensor_cores) {
+  if (!t || (tensor_cores != 0 && tensor_cores != 1)) return UT_ERR_INVALID;
+  t->gemm_tc = tensor_cores;
+  return UT_OK;
 }
 
 extern "C" ut_status tfm_ppo_actor_grad(ut_tfm* t, const void* tokens_dev, const int32_t* n_ent_dev,

@@ -37,7 +37,7 @@ class Tfm:
     ``max_batch`` samples."""
 
     def __init__(self, params: np.ndarray, d_model: int, n_layers: int, n_heads: int, n_out: int, n_slots: int,
-                 max_batch: int, tokens_bf16: bool, stream: Optional[int] = None):
+                 max_batch: int, tokens_bf16: bool, stream: Optional[int] = None, tensor_cores: bool = True):
         c = _abi.TfmConfig(_abi.UT_ABI_VERSION, d_model, n_layers, n_heads, n_out, n_slots, int(tokens_bf16), 0,
                            max_batch)
         self.cfg = c
@@ -54,6 +54,13 @@ class Tfm:
         self.h = h
         self.d, self.n_out, self.n_slots = d_model, n_out, n_slots
         self.grad = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        self.set_gemm_path(tensor_cores)
+
+    def set_gemm_path(self, tensor_cores: bool):
+        """True: the linear layers' GEMMs on the tensor cores (BF16 operands,
+        FP32 accumulation); False: FP32 on the CUDA cores."""
+        self._check(lib.tfm_set_gemm_path(self.h, 1 if tensor_cores else 0), "tfm_set_gemm_path")
+        self.tensor_cores = bool(tensor_cores)
 
     def _check(self, rc, what, handle=True):
         if rc != 0:

@@ -69,5 +69,5 @@ def test_small_bench_line_has_the_contract_keys():
     # the TransfMAPPO update measurement
     ppo = line["ppo"]
     assert ppo["value"] > 0 and ppo["ms_per_update"] > 0 and ppo["collect_ms"] > 0
-    assert ppo["roofline"]["bound"] == "alu" and 0.0 < ppo["roofline"]["frac"] < 1.5
+    assert ppo["roofline"]["bound"] in ("tensor", "alu") and 0.0 < ppo["roofline"]["frac"] < 1.5
     assert all(v == v for v in ppo["stats_last_minibatch"]["actor"] + ppo["stats_last_minibatch"]["critic"])
