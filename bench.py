@@ -722,7 +722,7 @@ def run_ours(args):
     # roofline of the transformer agent (it dominates the large workload): its
     # forward over this batch's tokens through the stand-alone entry (the same
     # device code as the step's), CUDA events over K launches on the stream;
-    # algorithmic tensor FLOPs 2 * 128 * 12 d^2 L per 128-row tile
+    # algorithmic FLOPs of the real tokens (below)
     pol_roof = None
     if policy_on:
         tok = env.step(None)["obs"].view(torch.bfloat16)
@@ -742,11 +742,19 @@ def run_ours(args):
         pol_ms = e0.elapsed_time(e1) / K
         apt = 128 // (1 + p.max_agents + p.max_targets)
         tiles = -(-NA // apt)
-        flops = tiles * 2 * 128 * 12 * p.d_model ** 2 * p.n_layers
+        # algorithmic FLOPs of the real tokens (an agent of env e has 1 + A_e + T_e):
+        # the block GEMMs 2 * 12 d^2 per token per layer, attention 4 n_tok^2 d per
+        # agent per layer (QK^T and PV); the padded rows of the 128-row tiles are
+        # not counted
+        n_tok = (1 + a_cnt + t_cnt).astype(np.int64)
+        tok_rows = int((a_cnt * n_tok).sum())
+        attn = int((a_cnt * n_tok * n_tok).sum()) * 4 * p.d_model * p.n_layers
+        flops = tok_rows * 2 * 12 * p.d_model ** 2 * p.n_layers + attn
         pol_tf = flops / (pol_ms / 1e3) / 1e12
         pol_roof = {"bound": "tensor", "achieved": pol_tf, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                     "frac": pol_tf / peaks["bf16_tflops"], "traffic": None, "kernel": "policy_fwd_kernel",
                     "avg_launch_ms": pol_ms, "launches": K, "tiles": tiles, "flops_per_launch": flops,
+                    "flops": "real tokens only: 24 d^2 L per token + 4 n_tok^2 d L per agent (attention)",
                     "peak_kind": f"{peak_kind} cuBLAS bf16 GEMM (burst)",
                     "timing": "CUDA events over K stand-alone launches on the batch's tokens"}
 

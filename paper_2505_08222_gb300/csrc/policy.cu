@@ -79,8 +79,14 @@ struct Geo {
   static constexpr uint32_t COL_Q = 0, COL_K = D, COL_V = 2 * D;
   static constexpr uint32_t COL_S = D;             // O-projection / W1 chunk (after K, V are drained)
   static constexpr uint32_t COL_ACC = 0;           // FFN output (after Q is consumed)
+  // pipelined FFN (d = 128): the W1 MMA of chunk c + 1 runs while the CUDA
+  // cores take GELU of chunk c, so the hidden chunk has two TMEM column
+  // blocks (COL_S, COL_S + 128) and two BF16 images in the K/V region
+  static constexpr bool PIPE = D == 128;
   static_assert(KV_BYTES >= (size_t)128 * 128 * 2, "hidden chunk must fit in the K/V region");
   static_assert(COL_S + 128 <= TMEM_COLS && 3 * D <= (int)TMEM_COLS, "TMEM plan");
+  static_assert(!PIPE || (NC >= 2 && COL_S + 256 <= TMEM_COLS && KV_BYTES >= (size_t)2 * 128 * 128 * 2),
+                "pipelined FFN plan");
   static_assert(SLOT % 16 == 0 && IMG_W2 <= SLOT, "bulk copies are 16-byte multiples");
 };
 
@@ -111,8 +117,26 @@ __device__ __forceinline__ void stage_image(int s, size_t& off, uint32_t& bytes)
     off = (size_t)i * G::IMG_DD;
     bytes = (uint32_t)G::IMG_DD;
   } else {
-    const int c = (i - 4) >> 1;
-    if (((i - 4) & 1) == 0) {
+    // FFN chunks in the order the MMAs consume them: W1_0, W2_0, W1_1, ...;
+    // with the pipelined FFN (G::PIPE) W1 of the next chunk comes before W2
+    // of the current one: W1_0, W1_1, W2_0, W1_2, W2_1, ..., W2_{NC-1}
+    const int j = i - 4;
+    bool w1;
+    int c;
+    if (!G::PIPE) {
+      w1 = (j & 1) == 0;
+      c = j >> 1;
+    } else if (j == 0) {
+      w1 = true;
+      c = 0;
+    } else if (j == 2 * G::NC - 1) {
+      w1 = false;
+      c = G::NC - 1;
+    } else {
+      w1 = (j & 1) == 1;
+      c = w1 ? (j + 1) >> 1 : (j - 2) >> 1;
+    }
+    if (w1) {
       off = G::OFF_W1 + (size_t)c * G::IMG_W1;
       bytes = (uint32_t)G::IMG_W1;
     } else {
@@ -164,13 +188,13 @@ __device__ __forceinline__ void publish() {
   tc::fence_after_sync();
 }
 
-// LayerNorm of a row whose NS column parts live in NS threads (t, t + 128,
-// ...): each part's mean and centred sum of squares are combined (pairwise
-// update of Chan et al. for equal counts), then this thread writes its part
-// of the normalised row into the BF16 A operand.  Contains a block barrier.
+// LayerNorm statistics of a row whose NS column parts live in NS threads
+// (t, t + 128, ...): each part's mean and centred sum of squares are combined
+// (pairwise update of Chan et al. for equal counts).  Contains a block
+// barrier.
 template <int D>
-__device__ __forceinline__ void ln_part_to_a(const float (&x)[Geo<D>::COLS], const float* g, const float* b,
-                                             unsigned char* sA, float2* sStat, int row, int part) {
+__device__ __forceinline__ void ln_part_stats(const float (&x)[Geo<D>::COLS], float2* sStat, int row, int part,
+                                              float& mean_out, float& inv_out) {
   constexpr int NS = Geo<D>::NS, COLS = Geo<D>::COLS;
   float s = 0.0f;
 #pragma unroll
@@ -200,7 +224,18 @@ __device__ __forceinline__ void ln_part_to_a(const float (&x)[Geo<D>::COLS], con
     dev = fmaf(dl, dl, dev);
   }
   m2 = fmaf(dev, (float)COLS, m2);
-  const float inv = rsqrtf(m2 * (1.0f / D) + kLnEps);
+  mean_out = mean;
+  inv_out = rsqrtf(m2 * (1.0f / D) + kLnEps);
+}
+
+// LayerNorm of the row (ln_part_stats), this thread's part of the
+// normalised row written into the BF16 A operand.  Contains a block barrier.
+template <int D>
+__device__ __forceinline__ void ln_part_to_a(const float (&x)[Geo<D>::COLS], const float* g, const float* b,
+                                             unsigned char* sA, float2* sStat, int row, int part) {
+  constexpr int COLS = Geo<D>::COLS;
+  float mean, inv;
+  ln_part_stats<D>(x, sStat, row, part, mean, inv);
   const int c_lo = part * COLS;
 #pragma unroll
   for (int c0 = 0; c0 < COLS; c0 += 8) {
@@ -395,6 +430,7 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
   float2* sStat = reinterpret_cast<float2*>(smem + G::STAT_OFF);
   __shared__ __align__(8) uint64_t full[kSlots];
   __shared__ __align__(8) uint64_t mma_bar;
+  __shared__ __align__(8) uint64_t bar[4];  // further MMA groups in flight at the same time
   __shared__ __align__(8) uint64_t never;  // test hook: a barrier nothing signals
   __shared__ uint32_t tmem_base_s;
   __shared__ int bad;
@@ -415,6 +451,7 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
   if (tid == 32) {
     for (int k = 0; k < kSlots; ++k) tc::mbar_init(&full[k], 1);
     tc::mbar_init(&mma_bar, 1);
+    for (int k = 0; k < 4; ++k) tc::mbar_init(&bar[k], 1);
     tc::mbar_init(&never, 1);
     bad = 0;
   }
@@ -437,7 +474,7 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
   const uint32_t aA = tc::smem_addr(sA), aH = tc::smem_addr(sH), aRing = tc::smem_addr(ring);
   Loader ld{0, 0, p.L * G::NSTG};
   if (tid == 0) pump<D>(ld, p.wimg, ring, full);
-  uint32_t mphase = 0;
+  uint32_t mphase = 0, phases = 0;  // bit k: parity of bar[k]
   bool ok = true;  // every bounded wait of this thread succeeded
   int s = 0;       // global weight stage
 
@@ -457,6 +494,21 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
     }
   };
   auto slot_addr = [&](int stage) { return aRing + (uint32_t)((stage % kSlots) * G::SLOT); };
+  // Every thread: wait for the group committed to bar[k].  A barrier gets
+  // its next commit only after a block barrier that follows every thread's
+  // wait, so that no thread can miss a phase.
+  auto wait_bar = [&](int k) {
+    ok &= tc::mbar_wait(&bar[k], (phases >> k) & 1u, kPolls);
+    phases ^= 1u << k;
+  };
+  // Thread 0: every stage issued so far has completed; refill the ring.
+  auto release = [&]() {
+    tc::fence_after_sync();
+    if (tid == 0) {
+      ld.done = s;
+      pump<D>(ld, p.wimg, ring, full);
+    }
+  };
 
   // ---- token rows ----------------------------------------------------------
   float x[COLS];
@@ -507,19 +559,26 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
     // ---- attention sub-block: Q, K, V in one MMA group ----
     ln_part_to_a<D>(x, ln1g, ln1b, sA, sStat, row, part);  // its barrier also publishes `vec`
     publish();
+    // K, V and Q as three groups, each drained as it completes: K and V
+    // while the later MMAs run, Q last since it replaces the LayerNorm output
+    // that all three read in the A image
     if (tid == 0) {
       wait_images(3);
-      issue_mma(tmem + G::COL_Q, aA, slot_addr(s), D, D, false);
       issue_mma(tmem + G::COL_K, aA, slot_addr(s + 1), D, D, false);
+      tc::mma_commit(&bar[0]);
       issue_mma(tmem + G::COL_V, aA, slot_addr(s + 2), D, D, false);
+      tc::mma_commit(&bar[1]);
+      issue_mma(tmem + G::COL_Q, aA, slot_addr(s), D, D, false);
       tc::mma_commit(&mma_bar);
     }
-    wait_mma(3);
     // Q (+ bias, times log2(e) / 4 for a base-2 softmax), K and V (+ bias) ->
-    // K-major BF16 images, this thread's part of the columns; Q replaces the
-    // LayerNorm output in the A image (the QKV group has completed)
+    // K-major BF16 images, this thread's part of the columns
 #pragma unroll 1
-    for (int qkv = 0; qkv < 3; ++qkv) {
+    for (int j = 0; j < 3; ++j) {
+      const int qkv = j == 2 ? 0 : j + 1;
+      if (j < 2) wait_bar(j);
+      if (j == 2) wait_mma(3);  // (releases the three weight images)
+      tc::fence_after_sync();
       const float* bias = qkv == 0 ? bq : (qkv == 1 ? bk : bv);
       const float scale = qkv == 0 ? 0.25f * 1.44269504088896341f : 1.0f;  // 1 / sqrt(16), log2(e)
       unsigned char* dst = qkv == 0 ? sA : (qkv == 1 ? sK : sV);
@@ -568,6 +627,75 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
 
     // ---- feed-forward sub-block ----
     ln_part_to_a<D>(x, ln2g, ln2b, sA, sStat, row, part);
+    if constexpr (G::PIPE) {
+      // Software-pipelined over the hidden chunks: the tensor cores run W2 of
+      // chunk c - 1 during the first half of GELU_c and W1 of chunk c + 1
+      // during the second half.  The chunk's pre-activations alternate
+      // between two TMEM column blocks and its GELU output between two BF16
+      // images; W1_c commits to bar[c & 1], W2_c to bar[2 + (c & 1)], and both
+      // are waited for at the top of a later chunk, when the MMAs have long
+      // completed.
+      publish();
+      if (tid == 0) {
+        wait_images(1);
+        issue_mma(tmem + G::COL_S, aA, slot_addr(s), 128, D, false);
+        tc::mma_commit(&bar[0]);
+      }
+      ++s;
+#pragma unroll 1
+      for (int c = 0; c < G::NC; ++c) {
+        const uint32_t col_cur = G::COL_S + (uint32_t)(c & 1) * 128u, col_nxt = G::COL_S + (uint32_t)((c + 1) & 1) * 128u;
+        unsigned char* hcur = sH + (size_t)(c & 1) * 128 * 128 * 2;
+        // W1_c complete (block c & 1 holds its output) and W2_{c-2} complete
+        // (its operand image c & 1 is free)
+        wait_bar(c & 1);
+        if (c >= 2) wait_bar(2 + (c & 1));
+        release();
+        if (c > 0) {
+          if (tid == 0) {
+            wait_images(1);
+            issue_mma(tmem + G::COL_ACC, tc::smem_addr(sH + (size_t)((c - 1) & 1) * 128 * 128 * 2), slot_addr(s), D,
+                      128, c > 1);
+            tc::mma_commit(&bar[2 + ((c - 1) & 1)]);
+          }
+          ++s;
+        }
+        // GELU of this thread's hidden units of chunk c -> BF16 operand, in
+        // two halves with W1_{c+1} issued between them
+#pragma unroll 1
+        for (int c0 = 0; c0 < G::HCOLS; c0 += 16) {
+          if (c0 == G::HCOLS / 2 && c + 1 < G::NC) {
+            if (tid == 0) {
+              wait_images(1);
+              issue_mma(tmem + col_nxt, aA, slot_addr(s), 128, D, false);
+              tc::mma_commit(&bar[(c + 1) & 1]);
+            }
+            ++s;
+          }
+          float v[16];
+          const int hc = part * G::HCOLS + c0;
+          tc::tmem_ld16(tl + col_cur + hc, v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] += b1[c * 128 + hc + i];
+#pragma unroll
+          for (int i = 0; i < 16; i += 2) gelu2(v[i], v[i + 1]);
+          store8(hcur, row, hc, 128, v);
+          store8(hcur, row, hc + 8, 128, v + 8);
+        }
+        publish();  // H_c visible to the tensor cores, block c & 1 read
+      }
+      // W2 of the last chunk; then W2_{NC-2} and W2_{NC-1} complete
+      if (tid == 0) {
+        wait_images(1);
+        issue_mma(tmem + G::COL_ACC, tc::smem_addr(sH + (size_t)((G::NC - 1) & 1) * 128 * 128 * 2), slot_addr(s), D,
+                  128, true);
+        tc::mma_commit(&bar[2 + ((G::NC - 1) & 1)]);
+      }
+      ++s;
+      wait_bar(2 + ((G::NC - 2) & 1));
+      wait_bar(2 + ((G::NC - 1) & 1));
+      release();
+    } else {
 #pragma unroll 1
     for (int c = 0; c < G::NC; ++c) {
       publish();
@@ -598,6 +726,7 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
       }
       wait_mma(1);
     }
+    }
 #pragma unroll
     for (int c0 = 0; c0 < COLS; c0 += 16) {
       float v[16];
@@ -608,65 +737,87 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
   }
 
   // ---- head on the recurrent token ----------------------------------------
-  // The recurrent rows' X goes to shared memory (the K/V region is free once
-  // the last MMA has completed); one thread per (agent, action) computes a
-  // logit, then one thread per agent draws the action.
-  float* sXr = reinterpret_cast<float*>(smem + G::KV_OFF);
-  float* sLog = sXr + p.apt * D;
+  // LN_f of the recurrent rows (statistics combined across the row's column
+  // parts) goes to shared memory (the K/V region is free once the last MMA
+  // has completed); then one warp per agent forms the logits (lanes split the
+  // columns, warp sums) and draws the action (one lane per action, warp
+  // argmax with the lowest index among equal maxima).
+  float* sY = reinterpret_cast<float*>(smem + G::KV_OFF);  // [apt][D]
   if (!ok) atomicExch(&bad, 1);
-  if (agent_ok && tok == 0) {
-    uint16_t* hp = p.h + ag * D + c_lo;
+  {
+    float mean, inv;
+    ln_part_stats<D>(x, sStat, row, part, mean, inv);
+    if (agent_ok && tok == 0) {
+      uint16_t* hp = p.h + ag * D + c_lo;
 #pragma unroll
-    for (int c0 = 0; c0 < COLS; c0 += 16) {
-      float v[16];
+      for (int c0 = 0; c0 < COLS; c0 += 16) {
+        float v[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        v[i] = x[c0 + i];
-        sXr[slot * D + c_lo + c0 + i] = v[i];
+        for (int i = 0; i < 16; ++i) {
+          v[i] = x[c0 + i];
+          sY[slot * D + c_lo + c0 + i] =
+              fmaf((x[c0 + i] - mean) * inv, __ldg(p.lnf_g + c_lo + c0 + i), __ldg(p.lnf_b + c_lo + c0 + i));
+        }
+        store16_bf(hp + c0, v);
       }
-      store16_bf(hp + c0, v);
     }
   }
   __syncthreads();
   const bool good = bad == 0;
-  const int n_act = p.n_act;
-  for (int t = tid; t < p.apt * n_act; t += kThreads) {
-    const int sl = t / n_act, j = t - sl * n_act;
+#pragma unroll 1
+  for (int sl = warp; sl < p.apt && good; sl += kThreads / 32) {
+    const int lane = tid & 31, n_act = p.n_act;
     const long long a2 = (long long)blockIdx.x * p.apt + sl;
-    float acc = 0.0f;
-    if (a2 < p.NA && good) {
-      const float* xr = sXr + sl * D;
-      float mu = 0.0f;
-      for (int c = 0; c < D; ++c) mu += xr[c];
-      mu *= (1.0f / D);
-      float var = 0.0f;
-      for (int c = 0; c < D; ++c) var = fmaf(xr[c] - mu, xr[c] - mu, var);
-      const float inv = rsqrtf(var * (1.0f / D) + kLnEps);
-      acc = __ldg(p.head_b + j);
-      const float* w = p.head_w + j * D;
-      for (int c = 0; c < D; ++c)
-        acc = fmaf(__ldg(w + c), fmaf((xr[c] - mu) * inv, __ldg(p.lnf_g + c), __ldg(p.lnf_b + c)), acc);
-      p.logits[a2 * n_act + j] = acc;
-    }
-    sLog[t] = acc;
-  }
-  __syncthreads();
-  if (p.sample && good && tid < p.apt) {
-    const long long a2 = (long long)blockIdx.x * p.apt + tid;
-    if (a2 < p.NA) {
-      const uint32_t g = p.counters ? p.counters[0] + 1u : p.step;
-      float best = -INFINITY;
-      int arg = 0;
-      for (int j = 0; j < n_act; ++j) {
-        Rand4 r = philox(p.gid_agent + (uint32_t)a2, (uint32_t)(j >> 2), g, TAG_GUMBEL, p.seed);
-        const float gum = -logf(-logf(unif_mid(r.x[j & 3])));
-        const float z = sLog[tid * n_act + j] + gum;
-        if (z > best) {
-          best = z;
-          arg = j;
+    if (a2 < p.NA) {  // (warp-uniform)
+      float y[D / 32];
+#pragma unroll
+      for (int i = 0; i < D / 32; ++i) y[i] = sY[sl * D + lane + 32 * i];
+      float mine = 0.0f;  // lane j: logit of action j
+      for (int j0 = 0; j0 < n_act; j0 += 8) {
+        float acc[8];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          acc[jj] = 0.0f;
+          if (j0 + jj < n_act) {
+            const float* w = p.head_w + (size_t)(j0 + jj) * D + lane;
+#pragma unroll
+            for (int i = 0; i < D / 32; ++i) acc[jj] = fmaf(__ldg(w + 32 * i), y[i], acc[jj]);
+          }
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) acc[jj] += __shfl_xor_sync(0xffffffffu, acc[jj], o);
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+          if (lane == j0 + jj) mine = acc[jj];
       }
-      p.actions[a2] = arg;
+      if (lane < n_act) {
+        mine += __ldg(p.head_b + lane);
+        p.logits[a2 * n_act + lane] = mine;
+      }
+      if (p.sample) {
+        float z = -INFINITY;
+        int arg = lane;
+        if (lane < n_act) {
+          const uint32_t g = p.counters ? p.counters[0] + 1u : p.step;
+          const Rand4 r = philox(p.gid_agent + (uint32_t)a2, (uint32_t)(lane >> 2), g, TAG_GUMBEL, p.seed);
+          const int q = lane & 3;
+          const uint32_t u = q == 0 ? r.x[0] : (q == 1 ? r.x[1] : (q == 2 ? r.x[2] : r.x[3]));
+          z = mine - logf(-logf(unif_mid(u)));
+          if (!(z == z)) z = -INFINITY;  // a NaN never wins
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float oz = __shfl_xor_sync(0xffffffffu, z, o);
+          const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+          if (oz > z || (oz == z && oa < arg)) {
+            z = oz;
+            arg = oa;
+          }
+        }
+        if (lane == 0) p.actions[a2] = arg;
+      }
     }
   }
 
@@ -689,6 +840,7 @@ cudaError_t launch_policy_t(const PolicyDev& p, cudaStream_t s) {
     const cudaError_t e = smem_optin(policy_fwd_kernel<D>, Geo<D>::SMEM, ready);
     if (e != cudaSuccess) return e;
   }
+  if (p.n_act < 1 || p.n_act > 32 || p.apt < 1) return cudaErrorInvalidValue;  // (a lane per action)
   const long long tiles = (p.NA + p.apt - 1) / p.apt;
   if (tiles > 0) {
     const cudaError_t e =
