@@ -2,19 +2,24 @@
 //
 // Each agent's tokens are its recurrent embedding h followed by its entity
 // vectors (self, teammates, targets; observation tokens of Sec. III-A.2).
-// Agents are packed R = 1 + max entities rows apart into 128-row tiles.  One
-// CTA of 128 NS threads owns a tile (NS = 2 column parts for d = 64, 4 for
-// d = 128): thread t works on row t % 128 and on column part t / 128 of that
-// row, keeping its part of the residual stream X in registers from start to
-// end:
+// A 128-row tile holds apt = 128 / R agents of R = 1 + S tokens (S entity
+// slots): for R <= 16 agent a's tokens in rows R a .. R a + R - 1, recurrent
+// token first; for R = 17 the entity tokens of agent a in rows S a ..
+// S a + S - 1 and the recurrent tokens of all agents after them (rows
+// S apt + a), so that each agent's entity queries fill one 16-row MMA tile.
+// One CTA of 128 P threads owns a
+// tile (P = 2 column parts for d = 64, 4 for d = 128): thread t works on row
+// t % 128 and on column part t / 128 of that row, keeping its part of the
+// residual stream X in registers from start to end:
 //
 //   X = [h ; W_emb tok + b_emb]                         (CUDA cores, FP32)
 //   per block l:   Y = LN1(X) -> BF16 operand A
 //                  Q, K, V = Y Wq^T, Y Wk^T, Y Wv^T      (three tcgen05.mma
 //                      groups issued together, FP32 in TMEM)
 //                  O = softmax(Q K^T / 4) V per head, within the agent's
-//                      valid tokens                      (warp-level MMAs, one
-//                      warp per agent and head)
+//                      valid tokens                      (warp-level MMAs, a
+//                      warp per (agent, head); with 17 tokens the recurrent
+//                      queries per (head, 4 agents))
 //                  X += O Wo^T + bo                      (tcgen05.mma)
 //                  X += W2 GELU(W1 LN2(X) + b1) + b2      (tcgen05.mma, hidden
 //                      units in chunks of 128 accumulated in TMEM)
@@ -42,7 +47,7 @@ namespace ut {
 namespace {
 
 constexpr int kSlots = 3;                                  // weight ring depth
-static_assert(1 + UT_MAX_AGENTS + UT_MAX_TARGETS <= 32, "attention tiles cover at most 32 rows per agent");
+static_assert(UT_MAX_AGENTS + UT_MAX_TARGETS <= 16, "an agent's entity queries fit one 16-row MMA tile");
 constexpr float kLnEps = 1e-5f;
 constexpr uint32_t kPolls = 1u << 22;                      // bounded mbarrier waits
 
@@ -309,9 +314,257 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-// One (agent, head) on the calling warp: the agent's rows r0 .. r0 + R - 1,
-// keys r0 .. r0 + nt - 1 valid; writes O_h into the agent's rows of aO (the
-// same K-major image as Q).  MT = 16-row tiles covering R.
+// Attention of one head within each agent's valid tokens, split row layout
+// (agents of 17 tokens, one more than an MMA tile): the entity tokens of agent
+// a are rows NS a .. NS a + NS - 1, its recurrent token is row RB + a
+// (RB = NS apt: the recurrent rows of all agents follow the entity rows).  The valid keys of agent a are its recurrent row
+// and the entity rows NS a + c, c < n_ent(a).  O overwrites Q in the query
+// rows and the head's columns; the tasks of one head write disjoint rows and
+// read other rows of Q only as queries whose results they discard.
+
+// Entity queries of agent a, head h: one 16-row m-tile from NS a against the
+// 16 entity-key rows from NS a and against the 8-key tile holding the
+// agent's recurrent key (keys of other agents in those tiles masked).
+__device__ __forceinline__ void attend_entity(uint32_t aQ, uint32_t aK, uint32_t aV, int a, int NS, int RB, int n_ent,
+                                              int h) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3, mi = lane >> 3, rr = lane & 7;
+  const int r0 = NS * a;
+  const int kr0 = RB + (a & ~15);  // the 16 recurrent rows holding the agent's
+  const bool hi = (a & 8) != 0;    // its 8-key tile within them
+  const int kc = a & 7;            // its column within that tile
+  uint32_t qa[4], kb[4], kr[4], vb[4], vr[4];
+  ldsm_x4(kmajor_row(aQ, min(r0 + rr + (mi & 1) * 8, 127), 16 * h + (mi >> 1) * 8), qa);
+  ldsm_x4(kmajor_row(aK, min(r0 + rr + (mi >> 1) * 8, 127), 16 * h + (mi & 1) * 8), kb);
+  ldsm_x4(kmajor_row(aK, min(kr0 + rr + (mi >> 1) * 8, 127), 16 * h + (mi & 1) * 8), kr);
+  ldsm_x4_t(kmajor_row(aV, min(r0 + rr + (mi & 1) * 8, 127), 16 * h + (mi >> 1) * 8), vb);
+  ldsm_x4_t(kmajor_row(aV, min(kr0 + rr + (mi & 1) * 8, 127), 16 * h + (mi >> 1) * 8), vr);
+  float s1[2][4], s2[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    s1[0][i] = 0.0f;
+    s1[1][i] = 0.0f;
+    s2[i] = 0.0f;
+  }
+  mma16816(s1[0], qa, kb[0], kb[1]);
+  mma16816(s1[1], qa, kb[2], kb[3]);
+  mma16816(s2, qa, hi ? kr[2] : kr[0], hi ? kr[3] : kr[1]);
+  // softmax along each query row (base-2: Q carries the log2(e) factor);
+  // the recurrent key is valid in every row, so each row max is finite
+  float inv[2];
+#pragma unroll
+  for (int hr = 0; hr < 2; ++hr) {
+    float mx = -INFINITY;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+#pragma unroll
+      for (int n = 0; n < 2; ++n) {
+        const float v = 8 * n + 2 * tig + j < n_ent ? s1[n][2 * hr + j] : -INFINITY;
+        s1[n][2 * hr + j] = v;
+        mx = fmaxf(mx, v);
+      }
+      const float v = 2 * tig + j == kc ? s2[2 * hr + j] : -INFINITY;
+      s2[2 * hr + j] = v;
+      mx = fmaxf(mx, v);
+    }
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+    float sum = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+#pragma unroll
+      for (int n = 0; n < 2; ++n) {
+        const float e = ex2_approx(s1[n][2 * hr + j] - mx);
+        s1[n][2 * hr + j] = e;
+        sum += e;
+      }
+      const float e = ex2_approx(s2[2 * hr + j] - mx);
+      s2[2 * hr + j] = e;
+      sum += e;
+    }
+    sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+    sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+    inv[hr] = 1.0f / sum;
+  }
+  // O = P V over the 16 entity keys, then over the 16 recurrent keys (P is
+  // zero there but in the agent's column)
+  float o[2][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    o[0][i] = 0.0f;
+    o[1][i] = 0.0f;
+  }
+  const uint32_t pa[4] = {pack_bf2(s1[0][0], s1[0][1]), pack_bf2(s1[0][2], s1[0][3]), pack_bf2(s1[1][0], s1[1][1]),
+                          pack_bf2(s1[1][2], s1[1][3])};
+  mma16816(o[0], pa, vb[0], vb[1]);
+  mma16816(o[1], pa, vb[2], vb[3]);
+  const uint32_t p01 = pack_bf2(s2[0], s2[1]), p23 = pack_bf2(s2[2], s2[3]);
+  const uint32_t pb[4] = {hi ? 0u : p01, hi ? 0u : p23, hi ? p01 : 0u, hi ? p23 : 0u};
+  mma16816(o[0], pb, vr[0], vr[1]);
+  mma16816(o[1], pb, vr[2], vr[3]);
+  __syncwarp();
+  // normalised O into the agent's entity rows (other rows of the m-tile
+  // belong to the next agent or to the recurrent block)
+#pragma unroll
+  for (int hr = 0; hr < 2; ++hr) {
+    const int rl = g + 8 * hr;
+    if (rl < NS) {
+#pragma unroll
+      for (int dn = 0; dn < 2; ++dn) {
+        const int k = 16 * h + 8 * dn + 2 * tig;
+        const uint32_t w = pack_bf2(o[dn][2 * hr] * inv[hr], o[dn][2 * hr + 1] * inv[hr]);
+        asm volatile("st.shared.b32 [%0], %1;" ::"r"(kmajor_row(aQ, r0 + rl, k) + (uint32_t)((k & 7) * 2)), "r"(w)
+                     : "memory");
+      }
+    }
+  }
+}
+
+// Recurrent queries of agents a0 .. a0 + na - 1, head h (all within one
+// block of 16 recurrent rows): the m-tile is that block of Q rows; each
+// agent's 16 entity-key rows give a 16 x 16 score tile of which only the
+// agent's own row is kept, and the block's 16 recurrent keys give one more
+// tile of which only the diagonal is kept.  O = P V accumulates one product
+// per agent (P nonzero in the agent's row only) plus the diagonal one.
+__device__ __forceinline__ void attend_recurrent(uint32_t aQ, uint32_t aK, uint32_t aV, int a0, int na, int NS,
+                                                 int RB, const int* nent, int h) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3, mi = lane >> 3, rr = lane & 7;
+  const int base = a0 & ~15, rb16 = RB + base;
+  uint32_t qa[4], kr[4], vr[4];
+  ldsm_x4(kmajor_row(aQ, min(rb16 + rr + (mi & 1) * 8, 127), 16 * h + (mi >> 1) * 8), qa);
+  ldsm_x4(kmajor_row(aK, min(rb16 + rr + (mi >> 1) * 8, 127), 16 * h + (mi & 1) * 8), kr);
+  ldsm_x4_t(kmajor_row(aV, min(rb16 + rr + (mi & 1) * 8, 127), 16 * h + (mi >> 1) * 8), vr);
+  // this thread's rows g + 8 hr are the recurrent rows of agents base + g + 8 hr
+  bool mine[2];
+  int ne[2];
+#pragma unroll
+  for (int hr = 0; hr < 2; ++hr) {
+    const int a = base + g + 8 * hr;
+    mine[hr] = a >= a0 && a < a0 + na;
+    ne[hr] = mine[hr] ? nent[a] : 0;
+  }
+  // e[hr][2 n + j]: entity key 8 n + 2 tig + j of row hr's agent; er[hr]: its
+  // recurrent key (column g of n-tile hr, held by the lane with 2 tig + j = g)
+  float e[2][4], er[2];
+  {
+    float sr[2][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      sr[0][i] = 0.0f;
+      sr[1][i] = 0.0f;
+      e[0][i] = -INFINITY;
+      e[1][i] = -INFINITY;
+    }
+    mma16816(sr[0], qa, kr[0], kr[1]);
+    mma16816(sr[1], qa, kr[2], kr[3]);
+#pragma unroll
+    for (int hr = 0; hr < 2; ++hr) {
+      er[hr] = -INFINITY;
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        if (2 * tig + j == g && mine[hr]) er[hr] = sr[hr][2 * hr + j];
+    }
+  }
+#pragma unroll 1
+  for (int al = 0; al < na; ++al) {
+    const int a = a0 + al, ra = a - base, ha = ra >> 3, ga = ra & 7;
+    uint32_t kb[4];
+    ldsm_x4(kmajor_row(aK, min(NS * a + rr + (mi >> 1) * 8, 127), 16 * h + (mi & 1) * 8), kb);
+    float sa[2][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      sa[0][i] = 0.0f;
+      sa[1][i] = 0.0f;
+    }
+    mma16816(sa[0], qa, kb[0], kb[1]);
+    mma16816(sa[1], qa, kb[2], kb[3]);
+    if (g == ga) {
+      if (ha == 0) {
+        e[0][0] = sa[0][0];
+        e[0][1] = sa[0][1];
+        e[0][2] = sa[1][0];
+        e[0][3] = sa[1][1];
+      } else {
+        e[1][0] = sa[0][2];
+        e[1][1] = sa[0][3];
+        e[1][2] = sa[1][2];
+        e[1][3] = sa[1][3];
+      }
+    }
+  }
+  // softmax along each row (rows of agents outside the group get P = 0)
+  float pr[2], inv[2];
+#pragma unroll
+  for (int hr = 0; hr < 2; ++hr) {
+    float mx = er[hr];
+#pragma unroll
+    for (int n = 0; n < 2; ++n)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const float v = 8 * n + 2 * tig + j < ne[hr] ? e[hr][2 * n + j] : -INFINITY;
+        e[hr][2 * n + j] = v;
+        mx = fmaxf(mx, v);
+      }
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+    if (!mine[hr]) mx = 0.0f;  // (every score of such a row is -inf)
+    float sum = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      e[hr][i] = ex2_approx(e[hr][i] - mx);
+      sum += e[hr][i];
+    }
+    pr[hr] = ex2_approx(er[hr] - mx);
+    sum += pr[hr];
+    sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+    sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+    inv[hr] = mine[hr] ? 1.0f / sum : 0.0f;
+  }
+  float o[2][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    o[0][i] = 0.0f;
+    o[1][i] = 0.0f;
+  }
+#pragma unroll 1
+  for (int al = 0; al < na; ++al) {
+    const int a = a0 + al, ra = a - base, ha = ra >> 3, ga = ra & 7;
+    uint32_t vb[4];
+    ldsm_x4_t(kmajor_row(aV, min(NS * a + rr + (mi & 1) * 8, 127), 16 * h + (mi >> 1) * 8), vb);
+    const bool r_lo = g == ga && ha == 0, r_hi = g == ga && ha == 1;
+    const uint32_t pa[4] = {r_lo ? pack_bf2(e[0][0], e[0][1]) : 0u, r_hi ? pack_bf2(e[1][0], e[1][1]) : 0u,
+                            r_lo ? pack_bf2(e[0][2], e[0][3]) : 0u, r_hi ? pack_bf2(e[1][2], e[1][3]) : 0u};
+    mma16816(o[0], pa, vb[0], vb[1]);
+    mma16816(o[1], pa, vb[2], vb[3]);
+  }
+  {
+    // the recurrent keys: row g's is column g (keys 0-7), row g + 8's is
+    // column g + 8 (keys 8-15)
+    const uint32_t pd[4] = {pack_bf2(2 * tig == g ? pr[0] : 0.0f, 2 * tig + 1 == g ? pr[0] : 0.0f), 0u, 0u,
+                            pack_bf2(2 * tig == g ? pr[1] : 0.0f, 2 * tig + 1 == g ? pr[1] : 0.0f)};
+    mma16816(o[0], pd, vr[0], vr[1]);
+    mma16816(o[1], pd, vr[2], vr[3]);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int hr = 0; hr < 2; ++hr) {
+    if (mine[hr]) {
+      const int row = rb16 + g + 8 * hr;
+#pragma unroll
+      for (int dn = 0; dn < 2; ++dn) {
+        const int k = 16 * h + 8 * dn + 2 * tig;
+        const uint32_t w = pack_bf2(o[dn][2 * hr] * inv[hr], o[dn][2 * hr + 1] * inv[hr]);
+        asm volatile("st.shared.b32 [%0], %1;" ::"r"(kmajor_row(aQ, row, k) + (uint32_t)((k & 7) * 2)), "r"(w)
+                     : "memory");
+      }
+    }
+  }
+}
+
+// Contiguous row layout (agents of at most 16 tokens): agent a's tokens are
+// rows r0 = R a .. r0 + R - 1, the recurrent token first.  One (agent, head)
+// on the calling warp: keys r0 .. r0 + nt - 1 valid; writes O_h into the
+// agent's rows of aO (the same K-major image as Q).  MT = 16-row tiles
+// covering R.
 template <int MT>
 __device__ __forceinline__ void attend_warp(uint32_t aQ, uint32_t aK, uint32_t aV, int r0, int R, int nt, int h) {
   const int lane = threadIdx.x & 31, g = lane >> 2, tig = lane & 3;
@@ -434,15 +687,26 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
   __shared__ __align__(8) uint64_t never;  // test hook: a barrier nothing signals
   __shared__ uint32_t tmem_base_s;
   __shared__ int bad;
+  __shared__ int s_nent[64];  // entity tokens in use per agent of the tile
 
   const int tid = threadIdx.x, warp = tid >> 5;
   const int row = tid & 127, part = tid >> 7;
   const int c_lo = part * COLS;
-  const int slot = row / p.R, tok = row - slot * p.R;
+  // row layout: agents of at most 16 tokens contiguous (slot * R + tok);
+  // longer ones split: entity rows slot * NS + (tok - 1), then the recurrent
+  // rows (tok 0) at NS * apt + slot; rows past those are padding (slot >= apt)
+  const bool split = p.R > 16;
+  const int rb = p.NS * p.apt;
+  const int slot = split ? (row < rb ? row / p.NS : row - rb) : row / p.R;
+  const int tok = split ? (row < rb ? 1 + row - slot * p.NS : 0) : row - slot * p.R;
   const long long ag = (long long)blockIdx.x * p.apt + slot;
   const bool agent_ok = slot < p.apt && ag < p.NA;
   const int n_tok = agent_ok ? 1 + min(max(p.n_ent[ag], 0), p.NS) : 0;
   const bool row_ok = tok < n_tok;
+  if (tid < p.apt) {
+    const long long a2 = (long long)blockIdx.x * p.apt + tid;
+    s_nent[tid] = a2 < p.NA ? min(max(p.n_ent[a2], 0), p.NS) : 0;
+  }
 
   if (warp == 0) {
     tc::tmem_alloc(&tmem_base_s, G::TMEM_COLS);
@@ -594,20 +858,28 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
       }
     }
     __syncthreads();  // Q, K, V of every row visible
-    // softmax attention per (agent, head) on warp-level MMAs; O overwrites Q
-    // in the agent's rows and the head's columns
+    // softmax attention on warp-level MMAs, one task per warp at a time:
+    // contiguous layout: (agent, head); split layout: (head, group of 4
+    // agents) for the recurrent queries, then (agent, head) for the entity
+    // queries; O overwrites Q in the query rows
     {
       const uint32_t aK = tc::smem_addr(sK), aV = tc::smem_addr(sV);
+      const int n_rec = split ? ((p.apt + 3) >> 2) * G::H : 0, n_tasks = n_rec + p.apt * G::H;
+      const long long left = p.NA - (long long)blockIdx.x * p.apt;  // agents of this tile and beyond
 #pragma unroll 1
-      for (int task = warp; task < p.apt * G::H; task += kThreads / 32) {
-        const int a = task / G::H, h = task - a * G::H;
-        const long long ag2 = (long long)blockIdx.x * p.apt + a;
-        if (ag2 >= p.NA) continue;  // warp-uniform
-        const int nt = 1 + min(max(p.n_ent[ag2], 0), p.NS);
-        if (p.R <= 16)
-          attend_warp<1>(aA, aK, aV, a * p.R, p.R, nt, h);
-        else
-          attend_warp<2>(aA, aK, aV, a * p.R, p.R, nt, h);
+      for (int task = warp; task < n_tasks; task += kThreads / 32) {  // (warp-uniform)
+        if (task < n_rec) {
+          const int gi = task / G::H, h = task - gi * G::H, a0 = 4 * gi;
+          const int na = (int)min((long long)min(4, p.apt - a0), left - a0);
+          if (na > 0) attend_recurrent(aA, aK, aV, a0, na, p.NS, rb, s_nent, h);
+        } else {
+          const int t2 = task - n_rec, a = t2 / G::H, h = t2 - a * G::H;
+          if (a >= left) continue;
+          if (split)
+            attend_entity(aA, aK, aV, a, p.NS, rb, s_nent[a], h);
+          else
+            attend_warp<1>(aA, aK, aV, a * p.R, p.R, 1 + s_nent[a], h);
+        }
       }
     }
     publish();
@@ -840,7 +1112,10 @@ cudaError_t launch_policy_t(const PolicyDev& p, cudaStream_t s) {
     const cudaError_t e = smem_optin(policy_fwd_kernel<D>, Geo<D>::SMEM, ready);
     if (e != cudaSuccess) return e;
   }
-  if (p.n_act < 1 || p.n_act > 32 || p.apt < 1) return cudaErrorInvalidValue;  // (a lane per action)
+  // (a lane per action; the row layouts need R = 1 + NS and R apt <= 128)
+  if (p.n_act < 1 || p.n_act > 32 || p.NS < 1 || p.NS > 16 || p.R != 1 + p.NS || p.apt < 1 || p.apt > 64 ||
+      p.R * p.apt > 128)
+    return cudaErrorInvalidValue;
   const long long tiles = (p.NA + p.apt - 1) / p.apt;
   if (tiles > 0) {
     const cudaError_t e =
