@@ -529,7 +529,7 @@ def run_reference(args):
 
 
 PF_SOURCES = ("pf_kernel.cuh", "pf_kernel.cu", "pf_inst_a.cu", "pf_inst_b.cu", "pf_variants.h", "common.cuh",
-              "env.cuh", "gelu.cuh")
+              "env.cuh", "f32x2.cuh")
 TRAFFIC_NOTE = os.path.join(ROOT, "profiles", "pf_step_kernel_fleet5.json")
 
 

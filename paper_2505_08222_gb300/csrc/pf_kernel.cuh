@@ -30,7 +30,7 @@
 #pragma once
 
 #include "env.cuh"
-#include "gelu.cuh"
+#include "f32x2.cuh"
 
 namespace ut {
 namespace pf {
@@ -42,13 +42,6 @@ __device__ __forceinline__ void cp_async4(float* dst_smem, const float* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(a), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// Packed FP32 pair add (gelu.cuh has the pack, unpack, fma and mul forms).
-__device__ __forceinline__ unsigned long long f2add(unsigned long long a, unsigned long long b) {
-  unsigned long long r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
 
 __device__ __forceinline__ float sqrt_approx(float x) {
   float y;
