@@ -745,16 +745,22 @@ def run_ours(args):
         # algorithmic FLOPs of the real tokens (an agent of env e has 1 + A_e + T_e):
         # the block GEMMs 2 * 12 d^2 per token per layer, attention 4 n_tok^2 d per
         # agent per layer (QK^T and PV); the padded rows of the 128-row tiles are
-        # not counted
+        # not counted.  With 17-token agents the kernel skips the last block's
+        # entity queries (only the recurrent row reaches the head): that block's
+        # attention counts 4 n_tok d per agent
         n_tok = (1 + a_cnt + t_cnt).astype(np.int64)
         tok_rows = int((a_cnt * n_tok).sum())
-        attn = int((a_cnt * n_tok * n_tok).sum()) * 4 * p.d_model * p.n_layers
+        split = 1 + p.max_agents + p.max_targets > 16
+        attn = int((a_cnt * n_tok * n_tok).sum()) * 4 * p.d_model * (p.n_layers - 1 if split else p.n_layers)
+        if split:
+            attn += int((a_cnt * n_tok).sum()) * 4 * p.d_model
         flops = tok_rows * 2 * 12 * p.d_model ** 2 * p.n_layers + attn
         pol_tf = flops / (pol_ms / 1e3) / 1e12
         pol_roof = {"bound": "tensor", "achieved": pol_tf, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                     "frac": pol_tf / peaks["bf16_tflops"], "traffic": None, "kernel": "policy_fwd_kernel",
                     "avg_launch_ms": pol_ms, "launches": K, "tiles": tiles, "flops_per_launch": flops,
-                    "flops": "real tokens only: 24 d^2 L per token + 4 n_tok^2 d L per agent (attention)",
+                    "flops": ("real tokens only: 24 d^2 L per token + 4 n_tok^2 d per agent and block "
+                              "(attention; the last block's recurrent query alone with 17-token agents)"),
                     "peak_kind": f"{peak_kind} cuBLAS bf16 GEMM (burst)",
                     "timing": "CUDA events over K stand-alone launches on the batch's tokens"}
 

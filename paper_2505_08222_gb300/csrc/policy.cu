@@ -864,7 +864,11 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
     // queries; O overwrites Q in the query rows
     {
       const uint32_t aK = tc::smem_addr(sK), aV = tc::smem_addr(sV);
-      const int n_rec = split ? ((p.apt + 3) >> 2) * G::H : 0, n_tasks = n_rec + p.apt * G::H;
+      // (split layout, last block: only the recurrent rows reach the head and
+      // the next h, so the entity queries' outputs are never read and their
+      // tasks are skipped; the keys and values of every token still enter)
+      const int n_rec = split ? ((p.apt + 3) >> 2) * G::H : 0;
+      const int n_tasks = n_rec + (split && l == p.L - 1 ? 0 : p.apt * G::H);
       const long long left = p.NA - (long long)blockIdx.x * p.apt;  // agents of this tile and beyond
 #pragma unroll 1
       for (int task = warp; task < n_tasks; task += kThreads / 32) {  // (warp-uniform)
