@@ -419,8 +419,8 @@ __device__ __forceinline__ void attend_entity(uint32_t aQ, uint32_t aK, uint32_t
   }
 }
 
-// Recurrent queries of agents a0 .. a0 + na - 1, head h (all within one
-// block of 16 recurrent rows): the m-tile is that block of Q rows; each
+// Recurrent queries of agents a0 .. a0 + na - 1 (na <= 4), head h (all within
+// one block of 16 recurrent rows): the m-tile is that block of Q rows; each
 // agent's 16 entity-key rows give a 16 x 16 score tile of which only the
 // agent's own row is kept, and the block's 16 recurrent keys give one more
 // tile of which only the diagonal is kept.  O = P V accumulates one product
@@ -464,8 +464,9 @@ __device__ __forceinline__ void attend_recurrent(uint32_t aQ, uint32_t aK, uint3
         if (2 * tig + j == g && mine[hr]) er[hr] = sr[hr][2 * hr + j];
     }
   }
-#pragma unroll 1
-  for (int al = 0; al < na; ++al) {
+#pragma unroll
+  for (int al = 0; al < 4; ++al) {  // (na <= 4; unrolled so that the agents' loads and MMAs overlap)
+    if (al >= na) break;
     const int a = a0 + al, ra = a - base, ha = ra >> 3, ga = ra & 7;
     uint32_t kb[4];
     ldsm_x4(kmajor_row(aK, min(NS * a + rr + (mi >> 1) * 8, 127), 16 * h + (mi & 1) * 8), kb);
@@ -525,8 +526,9 @@ __device__ __forceinline__ void attend_recurrent(uint32_t aQ, uint32_t aK, uint3
     o[0][i] = 0.0f;
     o[1][i] = 0.0f;
   }
-#pragma unroll 1
-  for (int al = 0; al < na; ++al) {
+#pragma unroll
+  for (int al = 0; al < 4; ++al) {
+    if (al >= na) break;
     const int a = a0 + al, ra = a - base, ha = ra >> 3, ga = ra & 7;
     uint32_t vb[4];
     ldsm_x4_t(kmajor_row(aV, min(NS * a + rr + (mi & 1) * 8, 127), 16 * h + (mi >> 1) * 8), vb);
