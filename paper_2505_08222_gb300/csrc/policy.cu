@@ -88,6 +88,10 @@ struct Geo {
   // cores take GELU of chunk c, so the hidden chunk has two TMEM column
   // blocks (COL_S, COL_S + 128) and two BF16 images in the K/V region
   static constexpr bool PIPE = D == 128;
+  // LayerNorm outputs (the A operand of the Q/K/V and W1 MMAs) in TMEM, two
+  // BF16 per 32-bit column: D / 2 columns after V and after the hidden blocks
+  static constexpr uint32_t COL_A = (3 * D > (int)COL_S + (PIPE ? 256 : 128)) ? 3 * D : COL_S + (PIPE ? 256 : 128);
+  static_assert(COL_A + D / 2 <= TMEM_COLS, "TMEM plan: LayerNorm operand");
   static_assert(KV_BYTES >= (size_t)128 * 128 * 2, "hidden chunk must fit in the K/V region");
   static_assert(COL_S + 128 <= TMEM_COLS && 3 * D <= (int)TMEM_COLS, "TMEM plan");
   static_assert(!PIPE || (NC >= 2 && COL_S + 256 <= TMEM_COLS && KV_BYTES >= (size_t)2 * 128 * 128 * 2),
@@ -184,6 +188,17 @@ __device__ __forceinline__ void issue_mma(uint32_t d_tmem, uint32_t a_addr, uint
   }
 }
 
+// acc[128 x N] (+)= A[128 x K] * B[N x K]^T with A in TMEM (columns a_tmem ..,
+// K / 2 of them), issued by the calling thread.
+__device__ __forceinline__ void issue_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint32_t b_addr, int N, int K,
+                                             bool accumulate) {
+  const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)N);
+  for (int k = 0; k < K / 16; ++k) {
+    const uint64_t bd = tc::smem_desc(b_addr + k * 2 * N * 16, N * 16, 128);
+    tc::mma_bf16_ts(d_tmem, a_tmem + (uint32_t)(k * 8), bd, idesc, (accumulate || k > 0) ? 1u : 0u);
+  }
+}
+
 // Make every thread's shared-memory operand writes (and TMEM reads) visible
 // before thread 0 issues the next MMA group.
 __device__ __forceinline__ void publish() {
@@ -191,6 +206,26 @@ __device__ __forceinline__ void publish() {
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
+}
+
+// The per-row epilogue items of this thread: (part p, k) is the 16 columns
+// p * W + 16 k .. + 15 of its row (W = the part's width, NIT = W / 16).  Warp 0
+// holds the thread that issues the MMAs, which blocks while the tensor pipe
+// takes them, so it takes no items: its items (part 0) go round-robin, from
+// `rot` on, to the other warps of its TMEM lane quarter (4, 8, ..), which
+// run on the same SM sub-partition; each sub-partition keeps the same work.
+template <int NP, int NIT, typename F>
+__device__ __forceinline__ void for_items(int warp, int part, int rot, F&& f) {
+  if (warp != 0) {
+#pragma unroll 1
+    for (int k = 0; k < NIT; ++k) f(part, k);
+  }
+  if (NP > 1 && warp != 0 && (warp & 3) == 0) {
+    const int h = warp >> 2;  // 1 .. NP - 1
+#pragma unroll 1
+    for (int k = 0; k < NIT; ++k)
+      if (1 + (k + rot) % (NP - 1) == h) f(0, k);
+  }
 }
 
 // LayerNorm statistics of a row whose NS column parts live in NS threads
@@ -233,22 +268,28 @@ __device__ __forceinline__ void ln_part_stats(const float (&x)[Geo<D>::COLS], fl
   inv_out = rsqrtf(m2 * (1.0f / D) + kLnEps);
 }
 
-// LayerNorm of the row (ln_part_stats), this thread's part of the
-// normalised row written into the BF16 A operand.  Contains a block barrier.
+// LayerNorm of the row (ln_part_stats), this thread's part of the normalised
+// row written as BF16 pairs into the row's TMEM lane (the A operand of the
+// next MMAs, columns taddr .. taddr + COLS / 2 - 1 of this warp's lane
+// quarter), then the wait for the stores.  Contains a block barrier.
 template <int D>
-__device__ __forceinline__ void ln_part_to_a(const float (&x)[Geo<D>::COLS], const float* g, const float* b,
-                                             unsigned char* sA, float2* sStat, int row, int part) {
+__device__ __forceinline__ void ln_part_to_tmem(const float (&x)[Geo<D>::COLS], const float* g, const float* b,
+                                                uint32_t taddr, float2* sStat, int row, int part) {
   constexpr int COLS = Geo<D>::COLS;
+  static_assert(COLS % 32 == 0, "whole 16-column TMEM stores");
   float mean, inv;
   ln_part_stats<D>(x, sStat, row, part, mean, inv);
   const int c_lo = part * COLS;
 #pragma unroll
-  for (int c0 = 0; c0 < COLS; c0 += 8) {
-    float v[8];
+  for (int c0 = 0; c0 < COLS; c0 += 32) {
+    uint32_t w[16];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = fmaf((x[c0 + i] - mean) * inv, g[c_lo + c0 + i], b[c_lo + c0 + i]);
-    store8(sA, row, c_lo + c0, 128, v);
+    for (int i = 0; i < 16; ++i)
+      w[i] = pack_bf2(fmaf((x[c0 + 2 * i] - mean) * inv, g[c_lo + c0 + 2 * i], b[c_lo + c0 + 2 * i]),
+                      fmaf((x[c0 + 2 * i + 1] - mean) * inv, g[c_lo + c0 + 2 * i + 1], b[c_lo + c0 + 2 * i + 1]));
+    tc::tmem_st16(taddr + (uint32_t)(c0 / 2), w);
   }
+  tc::tmem_wait_st();
 }
 
 // 16 BF16 values (two 16-byte words) -> FP32.
@@ -822,42 +863,40 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
     const float *ln1g = vec, *ln1b = vec + D, *bq = vec + 2 * D, *bk = vec + 3 * D, *bv = vec + 4 * D;
     const float *bo = vec + 5 * D, *ln2g = vec + 6 * D, *ln2b = vec + 7 * D, *b1 = vec + 8 * D, *b2 = vec + 12 * D;
 
-    // ---- attention sub-block: Q, K, V in one MMA group ----
-    ln_part_to_a<D>(x, ln1g, ln1b, sA, sStat, row, part);  // its barrier also publishes `vec`
+    // ---- attention sub-block: the LayerNorm output in TMEM is the A
+    // operand of Q, K and V (three MMA groups, each drained as it completes
+    // while the later ones run) ----
+    ln_part_to_tmem<D>(x, ln1g, ln1b, tl + G::COL_A + (uint32_t)(c_lo / 2), sStat, row, part);  // (publishes `vec`)
     publish();
-    // K, V and Q as three groups, each drained as it completes: K and V
-    // while the later MMAs run, Q last since it replaces the LayerNorm output
-    // that all three read in the A image
     if (tid == 0) {
       wait_images(3);
-      issue_mma(tmem + G::COL_K, aA, slot_addr(s + 1), D, D, false);
+      issue_mma_ts(tmem + G::COL_Q, tmem + G::COL_A, slot_addr(s), D, D, false);
       tc::mma_commit(&bar[0]);
-      issue_mma(tmem + G::COL_V, aA, slot_addr(s + 2), D, D, false);
+      issue_mma_ts(tmem + G::COL_K, tmem + G::COL_A, slot_addr(s + 1), D, D, false);
       tc::mma_commit(&bar[1]);
-      issue_mma(tmem + G::COL_Q, aA, slot_addr(s), D, D, false);
+      issue_mma_ts(tmem + G::COL_V, tmem + G::COL_A, slot_addr(s + 2), D, D, false);
       tc::mma_commit(&mma_bar);
     }
     // Q (+ bias, times log2(e) / 4 for a base-2 softmax), K and V (+ bias) ->
     // K-major BF16 images, this thread's part of the columns
 #pragma unroll 1
-    for (int j = 0; j < 3; ++j) {
-      const int qkv = j == 2 ? 0 : j + 1;
-      if (j < 2) wait_bar(j);
-      if (j == 2) wait_mma(3);  // (releases the three weight images)
+    for (int qkv = 0; qkv < 3; ++qkv) {
+      if (qkv < 2) wait_bar(qkv);
+      if (qkv == 2) wait_mma(3);  // (releases the three weight images)
       tc::fence_after_sync();
       const float* bias = qkv == 0 ? bq : (qkv == 1 ? bk : bv);
       const float scale = qkv == 0 ? 0.25f * 1.44269504088896341f : 1.0f;  // 1 / sqrt(16), log2(e)
       unsigned char* dst = qkv == 0 ? sA : (qkv == 1 ? sK : sV);
       const uint32_t col = qkv == 0 ? G::COL_Q : (qkv == 1 ? G::COL_K : G::COL_V);
-#pragma unroll 1
-      for (int c0 = 0; c0 < COLS; c0 += 16) {
+      for_items<G::NS, COLS / 16>(warp, part, qkv * (COLS / 16), [&](int pp, int k) {
+        const int cc = pp * COLS + 16 * k;
         float v[16];
-        tc::tmem_ld16(tl + col + c_lo + c0, v);
+        tc::tmem_ld16(tl + col + cc, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = (v[i] + bias[c_lo + c0 + i]) * scale;
-        store8(dst, row, c_lo + c0, 128, v);
-        store8(dst, row, c_lo + c0 + 8, 128, v + 8);
-      }
+        for (int i = 0; i < 16; ++i) v[i] = (v[i] + bias[cc + i]) * scale;
+        store8(dst, row, cc, 128, v);
+        store8(dst, row, cc + 8, 128, v + 8);
+      });
     }
     __syncthreads();  // Q, K, V of every row visible
     // softmax attention on warp-level MMAs, one task per warp at a time:
@@ -904,11 +943,10 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
     }
 
     // ---- feed-forward sub-block ----
-    ln_part_to_a<D>(x, ln2g, ln2b, sA, sStat, row, part);
+    ln_part_to_tmem<D>(x, ln2g, ln2b, tl + G::COL_A + (uint32_t)(c_lo / 2), sStat, row, part);
     if constexpr (G::PIPE) {
       // Software-pipelined over the hidden chunks: the tensor cores run W2 of
-      // chunk c - 1 during the first half of GELU_c and W1 of chunk c + 1
-      // during the second half.  The chunk's pre-activations alternate
+      // chunk c - 1 and W1 of chunk c + 1 during GELU_c.  The chunk's pre-activations alternate
       // between two TMEM column blocks and its GELU output between two BF16
       // images; W1_c commits to bar[c & 1], W2_c to bar[2 + (c & 1)], and both
       // are waited for at the top of a later chunk, when the MMAs have long
@@ -916,7 +954,7 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
       publish();
       if (tid == 0) {
         wait_images(1);
-        issue_mma(tmem + G::COL_S, aA, slot_addr(s), 128, D, false);
+        issue_mma_ts(tmem + G::COL_S, tmem + G::COL_A, slot_addr(s), 128, D, false);
         tc::mma_commit(&bar[0]);
       }
       ++s;
@@ -938,20 +976,18 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
           }
           ++s;
         }
-        // GELU of this thread's hidden units of chunk c -> BF16 operand, in
-        // two halves with W1_{c+1} issued between them
-#pragma unroll 1
-        for (int c0 = 0; c0 < G::HCOLS; c0 += 16) {
-          if (c0 == G::HCOLS / 2 && c + 1 < G::NC) {
-            if (tid == 0) {
-              wait_images(1);
-              issue_mma(tmem + col_nxt, aA, slot_addr(s), 128, D, false);
-              tc::mma_commit(&bar[(c + 1) & 1]);
-            }
-            ++s;
+        if (c + 1 < G::NC) {  // (warp 0 takes no GELU items: its thread 0 issues W1_{c+1} now)
+          if (tid == 0) {
+            wait_images(1);
+            issue_mma_ts(tmem + col_nxt, tmem + G::COL_A, slot_addr(s), 128, D, false);
+            tc::mma_commit(&bar[(c + 1) & 1]);
           }
+          ++s;
+        }
+        // GELU of this thread's hidden units of chunk c -> BF16 operand
+        for_items<G::NS, G::HCOLS / 16>(warp, part, c * (G::HCOLS / 16), [&](int pp, int k) {
+          const int hc = pp * G::HCOLS + 16 * k;
           float v[16];
-          const int hc = part * G::HCOLS + c0;
           tc::tmem_ld16(tl + col_cur + hc, v);
 #pragma unroll
           for (int i = 0; i < 16; ++i) v[i] += b1[c * 128 + hc + i];
@@ -959,7 +995,7 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
           for (int i = 0; i < 16; i += 2) gelu2(v[i], v[i + 1]);
           store8(hcur, row, hc, 128, v);
           store8(hcur, row, hc + 8, 128, v + 8);
-        }
+        });
         publish();  // H_c visible to the tensor cores, block c & 1 read
       }
       // W2 of the last chunk; then W2_{NC-2} and W2_{NC-1} complete
@@ -979,15 +1015,14 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
       publish();
       if (tid == 0) {
         wait_images(1);
-        issue_mma(tmem + G::COL_S, aA, slot_addr(s), 128, D, false);
+        issue_mma_ts(tmem + G::COL_S, tmem + G::COL_A, slot_addr(s), 128, D, false);
         tc::mma_commit(&mma_bar);
       }
       wait_mma(1);
       // GELU of this thread's hidden units of the chunk -> BF16 operand
-#pragma unroll 1
-      for (int c0 = 0; c0 < G::HCOLS; c0 += 16) {
+      for_items<G::NS, G::HCOLS / 16>(warp, part, c * (G::HCOLS / 16), [&](int pp, int k) {
+        const int hc = pp * G::HCOLS + 16 * k;
         float v[16];
-        const int hc = part * G::HCOLS + c0;
         tc::tmem_ld16(tl + G::COL_S + hc, v);
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] += b1[c * 128 + hc + i];
@@ -995,7 +1030,7 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
         for (int i = 0; i < 16; i += 2) gelu2(v[i], v[i + 1]);
         store8(sH, row, hc, 128, v);
         store8(sH, row, hc + 8, 128, v + 8);
-      }
+      });
       publish();
       if (tid == 0) {
         wait_images(1);
