@@ -209,18 +209,22 @@ __device__ __forceinline__ void publish() {
 }
 
 // The per-row epilogue items of this thread: (part p, k) is the 16 columns
-// p * W + 16 k .. + 15 of its row (W = the part's width, NIT = W / 16).  Warp 0
+// p * W + 16 k .. + 15 of its row (W = the part's width, NIT = W / 16); f
+// takes one item, f2 the pair k, k + 1 (the thread's own items).  Warp 0
 // holds the thread that issues the MMAs, which blocks while the tensor pipe
-// takes them, so it takes no items: its items (part 0) go round-robin, from
-// `rot` on, to the other warps of its TMEM lane quarter (4, 8, ..), which
-// run on the same SM sub-partition; each sub-partition keeps the same work.
-template <int NP, int NIT, typename F>
-__device__ __forceinline__ void for_items(int warp, int part, int rot, F&& f) {
-  if (warp != 0) {
+// takes them, so with four column parts it takes no items: its items (part 0)
+// go round-robin, from `rot` on, to the other warps of its TMEM lane quarter
+// (4, 8, 12), which run on the same SM sub-partition; each sub-partition keeps
+// the same work.
+template <int NP, int NIT, typename F, typename F2>
+__device__ __forceinline__ void for_items(int warp, int part, int rot, F&& f, F2&& f2) {
+  static_assert(NIT % 2 == 0, "own items in pairs");
+  constexpr bool kOffload = NP >= 4;  // (with one helper warp, its doubled items cost more than the issue)
+  if (!kOffload || warp != 0) {  // own items two at a time
 #pragma unroll 1
-    for (int k = 0; k < NIT; ++k) f(part, k);
+    for (int k = 0; k < NIT; k += 2) f2(part, k);
   }
-  if (NP > 1 && warp != 0 && (warp & 3) == 0) {
+  if (kOffload && warp != 0 && (warp & 3) == 0) {
     const int h = warp >> 2;  // 1 .. NP - 1
 #pragma unroll 1
     for (int k = 0; k < NIT; ++k)
@@ -888,15 +892,26 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
       const float scale = qkv == 0 ? 0.25f * 1.44269504088896341f : 1.0f;  // 1 / sqrt(16), log2(e)
       unsigned char* dst = qkv == 0 ? sA : (qkv == 1 ? sK : sV);
       const uint32_t col = qkv == 0 ? G::COL_Q : (qkv == 1 ? G::COL_K : G::COL_V);
-      for_items<G::NS, COLS / 16>(warp, part, qkv * (COLS / 16), [&](int pp, int k) {
-        const int cc = pp * COLS + 16 * k;
-        float v[16];
-        tc::tmem_ld16(tl + col + cc, v);
+      for_items<G::NS, COLS / 16>(
+          warp, part, qkv * (COLS / 16),
+          [&](int pp, int k) {
+            const int cc = pp * COLS + 16 * k;
+            float v[16];
+            tc::tmem_ld16(tl + col + cc, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = (v[i] + bias[cc + i]) * scale;
-        store8(dst, row, cc, 128, v);
-        store8(dst, row, cc + 8, 128, v + 8);
-      });
+            for (int i = 0; i < 16; ++i) v[i] = (v[i] + bias[cc + i]) * scale;
+            store8(dst, row, cc, 128, v);
+            store8(dst, row, cc + 8, 128, v + 8);
+          },
+          [&](int pp, int k) {
+            const int cc = pp * COLS + 16 * k;
+            float v[32];
+            tc::tmem_ld32(tl + col + cc, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = (v[i] + bias[cc + i]) * scale;
+#pragma unroll
+            for (int i = 0; i < 32; i += 8) store8(dst, row, cc + i, 128, v + i);
+          });
     }
     __syncthreads();  // Q, K, V of every row visible
     // softmax attention on warp-level MMAs, one task per warp at a time:
@@ -985,17 +1000,33 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
           ++s;
         }
         // GELU of this thread's hidden units of chunk c -> BF16 operand
-        for_items<G::NS, G::HCOLS / 16>(warp, part, c * (G::HCOLS / 16), [&](int pp, int k) {
-          const int hc = pp * G::HCOLS + 16 * k;
-          float v[16];
-          tc::tmem_ld16(tl + col_cur + hc, v);
+        for_items<G::NS, G::HCOLS / 16>(
+            warp, part, c * (G::HCOLS / 16),
+            [&](int pp, int k) {
+              const int hc = pp * G::HCOLS + 16 * k;
+              float v[16];
+              tc::tmem_ld16(tl + col_cur + hc, v);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] += b1[c * 128 + hc + i];
+              for (int i = 0; i < 16; ++i) v[i] += b1[c * 128 + hc + i];
 #pragma unroll
-          for (int i = 0; i < 16; i += 2) gelu2(v[i], v[i + 1]);
-          store8(hcur, row, hc, 128, v);
-          store8(hcur, row, hc + 8, 128, v + 8);
-        });
+              for (int i = 0; i < 16; i += 2) gelu2(v[i], v[i + 1]);
+              store8(hcur, row, hc, 128, v);
+              store8(hcur, row, hc + 8, 128, v + 8);
+            },
+            [&](int pp, int k) {  // (one item at a time: 32 live values cost more than the second wait)
+#pragma unroll 1
+              for (int kk = k; kk < k + 2; ++kk) {
+                const int hc = pp * G::HCOLS + 16 * kk;
+                float v[16];
+                tc::tmem_ld16(tl + col_cur + hc, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] += b1[c * 128 + hc + i];
+#pragma unroll
+                for (int i = 0; i < 16; i += 2) gelu2(v[i], v[i + 1]);
+                store8(hcur, row, hc, 128, v);
+                store8(hcur, row, hc + 8, 128, v + 8);
+              }
+            });
         publish();  // H_c visible to the tensor cores, block c & 1 read
       }
       // W2 of the last chunk; then W2_{NC-2} and W2_{NC-1} complete
@@ -1020,17 +1051,33 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
       }
       wait_mma(1);
       // GELU of this thread's hidden units of the chunk -> BF16 operand
-      for_items<G::NS, G::HCOLS / 16>(warp, part, c * (G::HCOLS / 16), [&](int pp, int k) {
-        const int hc = pp * G::HCOLS + 16 * k;
-        float v[16];
-        tc::tmem_ld16(tl + G::COL_S + hc, v);
+      for_items<G::NS, G::HCOLS / 16>(
+          warp, part, c * (G::HCOLS / 16),
+          [&](int pp, int k) {
+            const int hc = pp * G::HCOLS + 16 * k;
+            float v[16];
+            tc::tmem_ld16(tl + G::COL_S + hc, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] += b1[c * 128 + hc + i];
+            for (int i = 0; i < 16; ++i) v[i] += b1[c * 128 + hc + i];
 #pragma unroll
-        for (int i = 0; i < 16; i += 2) gelu2(v[i], v[i + 1]);
-        store8(sH, row, hc, 128, v);
-        store8(sH, row, hc + 8, 128, v + 8);
-      });
+            for (int i = 0; i < 16; i += 2) gelu2(v[i], v[i + 1]);
+            store8(sH, row, hc, 128, v);
+            store8(sH, row, hc + 8, 128, v + 8);
+          },
+          [&](int pp, int k) {
+#pragma unroll 1
+            for (int kk = k; kk < k + 2; ++kk) {
+              const int hc = pp * G::HCOLS + 16 * kk;
+              float v[16];
+              tc::tmem_ld16(tl + G::COL_S + hc, v);
+#pragma unroll
+              for (int i = 0; i < 16; ++i) v[i] += b1[c * 128 + hc + i];
+#pragma unroll
+              for (int i = 0; i < 16; i += 2) gelu2(v[i], v[i + 1]);
+              store8(sH, row, hc, 128, v);
+              store8(sH, row, hc + 8, 128, v + 8);
+            }
+          });
       publish();
       if (tid == 0) {
         wait_images(1);
