@@ -27,8 +27,8 @@ constexpr size_t kFwdSmem = 65536 + 65536;
 constexpr size_t kWgradSmem = 32768 + 65536;
 
 // Derivative of erf-GELU for the backward pass: Phi(x) + x phi(x).  (The
-// forward passes evaluate GELU with the A&S 7.1.26 erfc of gelu.cuh, within
-// 5e-7 of the erf form.)
+// forward passes evaluate GELU with gelu.cuh's form, within 5.4e-6 of the
+// erf form.)
 __device__ __forceinline__ float gelu_grad(float x) {
   return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
 }
@@ -208,8 +208,8 @@ __global__ void __launch_bounds__(kT, 1) fwd_kernel(FwdArgs p) {
 // ---------------------------------------------------------------------------
 // Estimator step in the environment (learned form): one CTA of 512 threads
 // per 128 filters, thread = filter row x one of 4 column parts.  Part 0
-// builds the row's features; the hidden-layer epilogues (bias, erf-GELU with
-// erf from Abramowitz & Stegun 7.1.26 in packed pairs, BF16 operand) split
+// builds the row's features; the hidden-layer epilogues (bias, erf-GELU of
+// gelu.cuh in packed pairs, BF16 operand) split
 // the 256 hidden units 4 ways; the weight images (N-halves
 // of W1, W2, W3) stream through two shared-memory slots by the bulk-copy
 // engine, so the next layer's weights arrive during the current epilogue.
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(kTE, 1) fwd_env_kernel(Net net, EnvDev d, int 
 #pragma unroll
       for (int i = 0; i < 16; ++i) av[i] = v[i] + __ldg(bias + c0 + i);
 #pragma unroll
-      for (int i = 0; i < 16; i += 2) gelu2(av[i], av[i + 1]);  // A&S 7.1.26 erf-GELU, packed pairs
+      for (int i = 0; i < 16; i += 2) gelu2(av[i], av[i + 1]);  // erf-GELU, packed pairs
       if (l < 2) {
         store8(sA, row, c0, 128, av);
         store8(sA, row, c0 + 8, 128, av + 8);
