@@ -566,6 +566,127 @@ __global__ void __launch_bounds__(128) attn_bwd_kernel(const float* __restrict__
   }
 }
 
+// m16n8k8 TF32 MMA on FP32 registers (operands rounded to TF32 first, FP32
+// accumulation).  Fragments (g = lane / 4, t = lane % 4): A a0 (g, t),
+// a1 (g + 8, t), a2 (g, t + 4), a3 (g + 8, t + 4); B b0 (k t, n g),
+// b1 (k t + 4, n g); C c0 (g, 2t), c1 (g, 2t + 1), c2 (g + 8, 2t),
+// c3 (g + 8, 2t + 1).
+__device__ __forceinline__ uint32_t tf32r(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void mma_tf32(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+constexpr int kAttLd = 20;  // floats per staged 16-wide row (conflict-free fragment loads)
+
+// C[16 x 16] (+)= A B over k = 16 from staged [16][kAttLd] tiles: A(r, k) =
+// TA ? a[k][r] : a[r][k], B(k, n) = TB ? b[n][k] : b[k][n].  c[j] holds the
+// n-tile of columns 8 j .. 8 j + 7.
+template <bool TA, bool TB>
+__device__ __forceinline__ void mma16x16(float (&c)[2][4], const float* a, const float* b, int g, int t) {
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) {
+    const int k0 = 8 * kk + t, k1 = k0 + 4;
+    const uint32_t a0 = tf32r(TA ? a[k0 * kAttLd + g] : a[g * kAttLd + k0]);
+    const uint32_t a1 = tf32r(TA ? a[k0 * kAttLd + g + 8] : a[(g + 8) * kAttLd + k0]);
+    const uint32_t a2 = tf32r(TA ? a[k1 * kAttLd + g] : a[g * kAttLd + k1]);
+    const uint32_t a3 = tf32r(TA ? a[k1 * kAttLd + g + 8] : a[(g + 8) * kAttLd + k1]);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int nn = 8 * j + g;
+      const uint32_t b0 = tf32r(TB ? b[nn * kAttLd + k0] : b[k0 * kAttLd + nn]);
+      const uint32_t b1 = tf32r(TB ? b[nn * kAttLd + k1] : b[k1 * kAttLd + nn]);
+      mma_tf32(c[j], a0, a1, a2, a3, b0, b1);
+    }
+  }
+}
+
+// Attention backward on the tensor cores (tensor-core path; T <= 16, head
+// dimension 16), one (sample, head) per warp, 4 warps per block: the
+// products of attn_bwd_kernel, dP = dO V^T, dQ = dS K, dK = dS^T Q,
+// dV = P^T dO, as m16n8k8 TF32 MMAs over the tokens padded to 16 (padded
+// rows and columns staged as zeros), and dS = P (dP - rowsum(P dP)) scale on
+// the accumulator fragments (a row lives in the 4 lanes of a quad).
+__global__ void __launch_bounds__(128) attn_bwd_mma_kernel(const float* __restrict__ QKV, const float* __restrict__ P,
+                                                           const float* __restrict__ dO, float* __restrict__ dQKV,
+                                                           long long n, int T, int H, float scale) {
+  __shared__ float sm[4][6][16 * kAttLd];  // Q, K, V, dO, P, dS of each warp
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= n * H) return;  // whole warps leave together
+  const long long s = w / H;
+  const int hh = (int)(w - s * H);
+  const int d = 16 * H, ld = 3 * d;
+  float *sQ = sm[wl][0], *sK = sm[wl][1], *sV = sm[wl][2], *sG = sm[wl][3], *sP = sm[wl][4], *sS = sm[wl][5];
+  const float* Pb = P + (s * H + hh) * T * T;
+  for (int i = lane; i < 256; i += 32) {
+    const int u = i >> 4, j = i & 15;
+    const bool in = u < T;
+    const float* base = QKV + (s * T + u) * ld + hh * 16;
+    sQ[u * kAttLd + j] = in ? base[j] : 0.0f;
+    sK[u * kAttLd + j] = in ? base[d + j] : 0.0f;
+    sV[u * kAttLd + j] = in ? base[2 * d + j] : 0.0f;
+    sG[u * kAttLd + j] = in ? dO[(s * T + u) * d + hh * 16 + j] : 0.0f;
+    sP[u * kAttLd + j] = (in && j < T) ? Pb[u * T + j] : 0.0f;
+  }
+  __syncwarp();
+  // dP = dO V^T
+  float dp[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+  mma16x16<false, true>(dp, sG, sV, g, t);
+  // dS = P (dP - rowsum(P dP)) scale (rows g and g + 8 of this quad)
+  float pv[2][4], r0 = 0.0f, r1 = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int c = 8 * j + 2 * t;
+    pv[j][0] = sP[g * kAttLd + c];
+    pv[j][1] = sP[g * kAttLd + c + 1];
+    pv[j][2] = sP[(g + 8) * kAttLd + c];
+    pv[j][3] = sP[(g + 8) * kAttLd + c + 1];
+    r0 = fmaf(pv[j][0], dp[j][0], fmaf(pv[j][1], dp[j][1], r0));
+    r1 = fmaf(pv[j][2], dp[j][2], fmaf(pv[j][3], dp[j][3], r1));
+  }
+  r0 += __shfl_xor_sync(0xffffffffu, r0, 1);
+  r0 += __shfl_xor_sync(0xffffffffu, r0, 2);
+  r1 += __shfl_xor_sync(0xffffffffu, r1, 1);
+  r1 += __shfl_xor_sync(0xffffffffu, r1, 2);
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int c = 8 * j + 2 * t;
+    sS[g * kAttLd + c] = pv[j][0] * (dp[j][0] - r0) * scale;
+    sS[g * kAttLd + c + 1] = pv[j][1] * (dp[j][1] - r0) * scale;
+    sS[(g + 8) * kAttLd + c] = pv[j][2] * (dp[j][2] - r1) * scale;
+    sS[(g + 8) * kAttLd + c + 1] = pv[j][3] * (dp[j][3] - r1) * scale;
+  }
+  __syncwarp();
+  float dq[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+  float dk[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+  float dv[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+  mma16x16<false, false>(dq, sS, sK, g, t);  // dQ = dS K
+  mma16x16<true, false>(dk, sS, sQ, g, t);   // dK = dS^T Q
+  mma16x16<true, false>(dv, sP, sG, g, t);   // dV = P^T dO
+  float* out = dQKV + s * T * ld + hh * 16;
+#pragma unroll
+  for (int hr = 0; hr < 2; ++hr) {
+    const int row = g + 8 * hr;
+    if (row < T) {
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int c = 8 * j + 2 * t;
+        *reinterpret_cast<float2*>(out + row * ld + c) = make_float2(dq[j][2 * hr], dq[j][2 * hr + 1]);
+        *reinterpret_cast<float2*>(out + row * ld + d + c) = make_float2(dk[j][2 * hr], dk[j][2 * hr + 1]);
+        *reinterpret_cast<float2*>(out + row * ld + 2 * d + c) = make_float2(dv[j][2 * hr], dv[j][2 * hr + 1]);
+      }
+    }
+  }
+}
+
 struct HeadArgs {
   const float* XL;  // [rows][d] residual stream after the last block
   long long n;
@@ -1122,8 +1243,11 @@ cudaError_t attn_fwd(const float* QKV, const int32_t* ne, const int32_t* sel, fl
 
 template <int DH>
 cudaError_t attn_bwd(const float* QKV, const float* P, const float* dO, float* dQKV, long long n, int T, int H,
-                     cudaStream_t s) {
-  attn_bwd_kernel<DH><<<blocks_for(n * H * 32, 128), 128, 0, s>>>(QKV, P, dO, dQKV, n, T, H, 1.0f / sqrtf((float)DH));
+                     bool mma, cudaStream_t s) {
+  if (mma && DH == 16 && T <= 16)
+    attn_bwd_mma_kernel<<<blocks_for(n * H * 32, 128), 128, 0, s>>>(QKV, P, dO, dQKV, n, T, H, 1.0f / sqrtf((float)DH));
+  else
+    attn_bwd_kernel<DH><<<blocks_for(n * H * 32, 128), 128, 0, s>>>(QKV, P, dO, dQKV, n, T, H, 1.0f / sqrtf((float)DH));
   return cudaGetLastError();
 }
 
@@ -1238,7 +1362,7 @@ cudaError_t backward(ut_tfm* t, const Call& c, float* grad, cudaStream_t s) {
     // attention sub-block: M = X + Wo attn(LN1(X)) + bo
     if (e == cudaSuccess) e = dgemm(l, 5, mk(t->dM, d, w + ol[T_WO], d, t->dO, d, rows, d, d, EPI_STORE));
     if (e == cudaSuccess) e = wgrad(t, t->dM, d, O, d, rows, grad + ol[T_WO], grad + ol[T_BO], s);
-    if (e == cudaSuccess) e = attn_bwd<DH>(QKV, P, t->dO, t->dBig, c.n, t->T, t->H, s);
+    if (e == cudaSuccess) e = attn_bwd<DH>(QKV, P, t->dO, t->dBig, c.n, t->T, t->H, t->gemm_tc != 0, s);
     if (e == cudaSuccess) e = dgemm(l, 4, mk(t->dBig, 3 * d, w + ol[T_WQKV], d, t->dY, d, rows, d, 3 * d, EPI_STORE));
     if (e == cudaSuccess) e = wgrad(t, t->dBig, 3 * d, Y1, d, rows, grad + ol[T_WQKV], grad + ol[T_BQKV], s);
     if (e == cudaSuccess) e = ln_bwd<DJ>(t, t->dY, Xl, S1, w + ol[T_LN1G], t->dM, t->dX, grad + ol[T_LN1G], rows, s);
