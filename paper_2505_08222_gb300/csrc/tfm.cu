@@ -608,6 +608,94 @@ __device__ __forceinline__ void mma16x16(float (&c)[2][4], const float* a, const
   }
 }
 
+// Attention forward on the tensor cores (tensor-core path; T <= 16, head
+// dimension 16), one (sample, head) per warp, 4 warps per block: S = Q K^T
+// as m16n8k8 TF32 MMAs over the tokens padded to 16, the masked softmax on
+// the accumulator fragments (keys u <= n_ent of the sample, a row in the 4
+// lanes of a quad), P written out (zero at masked keys) and staged, then
+// O = P V.
+__global__ void __launch_bounds__(128) attn_fwd_mma_kernel(const float* __restrict__ QKV,
+                                                           const int32_t* __restrict__ n_ent,
+                                                           const int32_t* __restrict__ sel, float* __restrict__ P,
+                                                           float* __restrict__ O, long long n, int T, int NS, int H,
+                                                           float scale) {
+  __shared__ float sm[4][4][16 * kAttLd];  // Q, K, V, P of each warp
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= n * H) return;  // whole warps leave together
+  const long long s = w / H;
+  const int hh = (int)(w - s * H);
+  const int d = 16 * H, ld = 3 * d;
+  int ne = n_ent[sel ? (long long)sel[s] : s];
+  ne = ne < 0 ? 0 : (ne > NS ? NS : ne);
+  float *sQ = sm[wl][0], *sK = sm[wl][1], *sV = sm[wl][2], *sP = sm[wl][3];
+  for (int i = lane; i < 256; i += 32) {
+    const int u = i >> 4, j = i & 15;
+    const bool in = u < T;
+    const float* base = QKV + (s * T + u) * ld + hh * 16;
+    sQ[u * kAttLd + j] = in ? base[j] : 0.0f;
+    sK[u * kAttLd + j] = in ? base[d + j] : 0.0f;
+    sV[u * kAttLd + j] = in ? base[2 * d + j] : 0.0f;
+  }
+  __syncwarp();
+  float sc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+  mma16x16<false, true>(sc, sQ, sK, g, t);  // S = Q K^T
+  float* Pb = P + (s * H + hh) * T * T;
+#pragma unroll
+  for (int hr = 0; hr < 2; ++hr) {
+    const int row = g + 8 * hr;
+    float mx = -INFINITY;
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int col = 8 * j + 2 * t + e;
+        const float v = (col < T && col <= ne) ? sc[j][2 * hr + e] * scale : -INFINITY;
+        sc[j][2 * hr + e] = v;
+        mx = fmaxf(mx, v);
+      }
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+    float z = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const float x = sc[j][2 * hr + e];
+        const float ex = x == -INFINITY ? 0.0f : __expf(x - mx);
+        sc[j][2 * hr + e] = ex;
+        z += ex;
+      }
+    z += __shfl_xor_sync(0xffffffffu, z, 1);
+    z += __shfl_xor_sync(0xffffffffu, z, 2);
+    const float iz = 1.0f / z;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int col = 8 * j + 2 * t;
+      const float p0 = sc[j][2 * hr] * iz, p1 = sc[j][2 * hr + 1] * iz;
+      sP[row * kAttLd + col] = p0;
+      sP[row * kAttLd + col + 1] = p1;
+      if (row < T) {
+        if (col < T) Pb[row * T + col] = p0;
+        if (col + 1 < T) Pb[row * T + col + 1] = p1;
+      }
+    }
+  }
+  __syncwarp();
+  float o[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+  mma16x16<false, false>(o, sP, sV, g, t);  // O = P V
+#pragma unroll
+  for (int hr = 0; hr < 2; ++hr) {
+    const int row = g + 8 * hr;
+    if (row < T) {
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        *reinterpret_cast<float2*>(O + (s * T + row) * d + hh * 16 + 8 * j + 2 * t) =
+            make_float2(o[j][2 * hr], o[j][2 * hr + 1]);
+    }
+  }
+}
+
 // Attention backward on the tensor cores (tensor-core path; T <= 16, head
 // dimension 16), one (sample, head) per warp, 4 warps per block: the
 // products of attn_bwd_kernel, dP = dO V^T, dQ = dS K, dK = dS^T Q,
@@ -1234,7 +1322,12 @@ cudaError_t ln_bwd(ut_tfm* t, const float* dY, const float* X, const float* st, 
 
 template <int DH>
 cudaError_t attn_fwd(const float* QKV, const int32_t* ne, const int32_t* sel, float* P, float* O, long long n, int T,
-                     int NS, int H, cudaStream_t s) {
+                     int NS, int H, bool mma, cudaStream_t s) {
+  if (mma && DH == 16 && T <= 16) {
+    attn_fwd_mma_kernel<<<blocks_for(n * H * 32, 128), 128, 0, s>>>(QKV, ne, sel, P, O, n, T, NS, H,
+                                                                     1.0f / sqrtf((float)DH));
+    return cudaGetLastError();
+  }
   const long long warps = (n * H + attn_pairs_per_warp(T) - 1) / attn_pairs_per_warp(T);
   attn_fwd_kernel<DH><<<blocks_for(warps * 32, 128), 128, 0, s>>>(QKV, ne, sel, P, O, n, T, NS, H,
                                                                    1.0f / sqrtf((float)DH));
@@ -1298,7 +1391,7 @@ cudaError_t forward(ut_tfm* t, const Call& c, cudaStream_t s) {
     g.bimg = img(l, 0);
     g.status = t->status;
     e = gemm(0, g, s);
-    if (e == cudaSuccess) e = attn_fwd<DH>(QKV, c.ne, c.sel, P, O, c.n, t->T, t->NS, t->H, s);
+    if (e == cudaSuccess) e = attn_fwd<DH>(QKV, c.ne, c.sel, P, O, c.n, t->T, t->NS, t->H, t->gemm_tc != 0, s);
     if (e != cudaSuccess) break;
     g = mk(O, d, w + ol[T_WO], d, M, d, rows, d, d, EPI_BIAS_RES);
     g.bias = w + ol[T_BO];
