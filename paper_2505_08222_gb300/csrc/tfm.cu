@@ -282,32 +282,40 @@ __global__ void __launch_bounds__(256) sgemm128_kernel(Gemm g) {
 }
 
 // Embedding of the entity tokens; token 0 of each sample is its recurrent
-// embedding.  One thread per output value.
+// embedding.  One warp per token row (lanes over the d outputs, the row's 8
+// token features read once), 8 rows per block.
 template <typename TokT>
 __global__ void embed_kernel(const TokT* __restrict__ tok, const int32_t* __restrict__ n_ent,
                              const float* __restrict__ h, const int32_t* __restrict__ sel,
                              const float* __restrict__ W, const float* __restrict__ b, float* __restrict__ X,
                              long long n, int T, int NS, int d) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n * T * d) return;
-  const int j = (int)(i % d);
-  const long long row = i / d;
+  const int lane = threadIdx.x & 31;
+  const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= n * T) return;  // whole warps leave together
   const long long s = row / T;
   const int t = (int)(row - s * T);
   const long long bs = sel ? (long long)sel[s] : s;
+  float* x = X + row * d;
   if (t == 0) {
-    X[i] = h[bs * d + j];
+    for (int j = lane; j < d; j += 32) x[j] = h[bs * d + j];
     return;
   }
   int ne = n_ent[bs];
   ne = ne < 0 ? 0 : (ne > NS ? NS : ne);
-  float acc = b[j];
-  if (t <= ne) {
-    const TokT* q = tok + (bs * NS + (t - 1)) * 8;
+  float q[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc = fmaf(W[j * 8 + k], (float)q[k], acc);
+  for (int k = 0; k < 8; ++k) q[k] = 0.0f;
+  if (t <= ne) {
+    const TokT* qt = tok + (bs * NS + (t - 1)) * 8;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) q[k] = (float)qt[k];
   }
-  X[i] = acc;
+  for (int j = lane; j < d; j += 32) {
+    float acc = b[j];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc = fmaf(W[j * 8 + k], q[k], acc);
+    x[j] = acc;
+  }
 }
 
 // LayerNorm forward, one warp per row: Y = (X - mean) rstd g + b and the row's
@@ -1367,7 +1375,7 @@ cudaError_t forward(ut_tfm* t, const Call& c, cudaStream_t s) {
   auto img = [&](int l, int which) -> const uint16_t* {
     return t->gemm_tc ? t->wimg + t->img_off[8 * l + which] : nullptr;
   };
-  embed_kernel<TokT><<<blocks_for(rows * d, 256), 256, 0, s>>>((const TokT*)c.tok, c.ne, c.h, c.sel, w + o[0],
+  embed_kernel<TokT><<<blocks_for(rows * 32, 256), 256, 0, s>>>((const TokT*)c.tok, c.ne, c.h, c.sel, w + o[0],
                                                               w + o[1], t->X, c.n, t->T, t->NS, d);
   cudaError_t e = cudaGetLastError();
   for (int l = 0; l < t->L && e == cudaSuccess; ++l) {
