@@ -282,39 +282,52 @@ __global__ void __launch_bounds__(256) sgemm128_kernel(Gemm g) {
 }
 
 // Embedding of the entity tokens; token 0 of each sample is its recurrent
-// embedding.  One warp per token row (lanes over the d outputs, the row's 8
-// token features read once), 8 rows per block.
-template <typename TokT>
-__global__ void embed_kernel(const TokT* __restrict__ tok, const int32_t* __restrict__ n_ent,
-                             const float* __restrict__ h, const int32_t* __restrict__ sel,
-                             const float* __restrict__ W, const float* __restrict__ b, float* __restrict__ X,
-                             long long n, int T, int NS, int d) {
+// embedding.  Warps loop over token rows (lane: outputs lane + 32 i, its
+// rows of W and its biases held in registers; a row's 8 token features read
+// once).
+template <typename TokT, int DJ>
+__global__ void __launch_bounds__(256) embed_kernel(const TokT* __restrict__ tok, const int32_t* __restrict__ n_ent,
+                                                    const float* __restrict__ h, const int32_t* __restrict__ sel,
+                                                    const float* __restrict__ W, const float* __restrict__ b,
+                                                    float* __restrict__ X, long long n, int T, int NS) {
+  constexpr int d = 32 * DJ;
   const int lane = threadIdx.x & 31;
-  const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (row >= n * T) return;  // whole warps leave together
-  const long long s = row / T;
-  const int t = (int)(row - s * T);
-  const long long bs = sel ? (long long)sel[s] : s;
-  float* x = X + row * d;
-  if (t == 0) {
-    for (int j = lane; j < d; j += 32) x[j] = h[bs * d + j];
-    return;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  float wr[DJ][8], br[DJ];
+#pragma unroll
+  for (int i = 0; i < DJ; ++i) {
+    br[i] = b[lane + 32 * i];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) wr[i][k] = W[(lane + 32 * i) * 8 + k];
   }
-  int ne = n_ent[bs];
-  ne = ne < 0 ? 0 : (ne > NS ? NS : ne);
-  float q[8];
+  for (long long row = w0; row < n * T; row += nw) {
+    const long long s = row / T;
+    const int t = (int)(row - s * T);
+    const long long bs = sel ? (long long)sel[s] : s;
+    float* x = X + row * d;
+    if (t == 0) {
 #pragma unroll
-  for (int k = 0; k < 8; ++k) q[k] = 0.0f;
-  if (t <= ne) {
-    const TokT* qt = tok + (bs * NS + (t - 1)) * 8;
+      for (int i = 0; i < DJ; ++i) x[lane + 32 * i] = h[bs * d + lane + 32 * i];
+      continue;
+    }
+    int ne = n_ent[bs];
+    ne = ne < 0 ? 0 : (ne > NS ? NS : ne);
+    float q[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) q[k] = (float)qt[k];
-  }
-  for (int j = lane; j < d; j += 32) {
-    float acc = b[j];
+    for (int k = 0; k < 8; ++k) q[k] = 0.0f;
+    if (t <= ne) {
+      const TokT* qt = tok + (bs * NS + (t - 1)) * 8;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc = fmaf(W[j * 8 + k], q[k], acc);
-    x[j] = acc;
+      for (int k = 0; k < 8; ++k) q[k] = (float)qt[k];
+    }
+#pragma unroll
+    for (int i = 0; i < DJ; ++i) {
+      float acc = br[i];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc = fmaf(wr[i][k], q[k], acc);
+      x[lane + 32 * i] = acc;
+    }
   }
 }
 
@@ -1375,8 +1388,18 @@ cudaError_t forward(ut_tfm* t, const Call& c, cudaStream_t s) {
   auto img = [&](int l, int which) -> const uint16_t* {
     return t->gemm_tc ? t->wimg + t->img_off[8 * l + which] : nullptr;
   };
-  embed_kernel<TokT><<<blocks_for(rows * 32, 256), 256, 0, s>>>((const TokT*)c.tok, c.ne, c.h, c.sel, w + o[0],
-                                                              w + o[1], t->X, c.n, t->T, t->NS, d);
+  {
+    const unsigned blocks = (unsigned)std::min<long long>((rows + 7) / 8, 152LL * 16);
+    const TokT* tk = (const TokT*)c.tok;
+    if (d == 32)
+      embed_kernel<TokT, 1><<<blocks, 256, 0, s>>>(tk, c.ne, c.h, c.sel, w + o[0], w + o[1], t->X, c.n, t->T, t->NS);
+    else if (d == 64)
+      embed_kernel<TokT, 2><<<blocks, 256, 0, s>>>(tk, c.ne, c.h, c.sel, w + o[0], w + o[1], t->X, c.n, t->T, t->NS);
+    else if (d == 96)
+      embed_kernel<TokT, 3><<<blocks, 256, 0, s>>>(tk, c.ne, c.h, c.sel, w + o[0], w + o[1], t->X, c.n, t->T, t->NS);
+    else
+      embed_kernel<TokT, 4><<<blocks, 256, 0, s>>>(tk, c.ne, c.h, c.sel, w + o[0], w + o[1], t->X, c.n, t->T, t->NS);
+  }
   cudaError_t e = cudaGetLastError();
   for (int l = 0; l < t->L && e == cudaSuccess; ++l) {
     const int64_t* ol = o.data() + 2 + 12 * l;
