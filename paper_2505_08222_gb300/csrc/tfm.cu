@@ -1224,13 +1224,16 @@ cudaError_t gemm(int kind, const Gemm& g, cudaStream_t s) {
     static std::atomic<unsigned long long> ready{0};
     cudaError_t e = smem_optin(tc_rows_kernel, kTcSmem, ready);
     if (e != cudaSuccess) return e;
-    // CTAs loop over the row tiles: about two per SM per column tile
+    // CTAs loop over the row tiles: about as many per SM per column tile as
+    // fit (three for N <= 128, two for the wider products)
+    const size_t smem = tc_rows_smem(g.N);
+    const int per_sm = smem <= 72 * 1024 ? 3 : 2;
     const long long tiles = (g.M + 127) / 128;
     const int n_tiles = (g.N + kTcMaxN - 1) / kTcMaxN;
-    long long ctas = (2 * 152 + n_tiles - 1) / n_tiles;
+    long long ctas = (per_sm * 152 + n_tiles - 1) / n_tiles;
     if (ctas > tiles) ctas = tiles;
     dim3 grid((unsigned)ctas, (unsigned)n_tiles);
-    tc_rows_kernel<<<grid, kTcThreads, kTcSmem, s>>>(g, g.bimg, g.status);
+    tc_rows_kernel<<<grid, kTcThreads, smem, s>>>(g, g.bimg, g.status);
     return cudaGetLastError();
   }
   const long long kc = g.kchunk > 0 ? g.kchunk : g.K;

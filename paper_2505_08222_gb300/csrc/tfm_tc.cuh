@@ -87,6 +87,15 @@ __device__ __forceinline__ void epi_store4(const Gemm& g, long long m, int n, fl
 
 constexpr int kTcEpiLd = 68;  // floats per row of the epilogue staging tile (64 + 4: conflict-free)
 
+// Shared memory of tc_rows_kernel for outputs N wide: two A stages and two B
+// stages sized for min(N, 256) rows, at least the epilogue staging tile
+// (which overlays them); narrow products fit three CTAs per SM.
+inline size_t tc_rows_smem(int N) {
+  const size_t stages = 2 * kTcStageA + 2 * (size_t)std::min(kTcMaxN, N) * kTcChunk * 2;
+  const size_t epi = (size_t)128 * kTcEpiLd * 4;
+  return stages > epi ? stages : epi;
+}
+
 // Kinds 0 / 1: C[m][n] = sum_k A[m][k] B(n, k) + epilogue, A FP32 row-major
 // (lda), B the image of `R` = g.N rows by `C` = g.K columns.  Grid (CTAs
 // looping over the row tiles of 128, column tiles of 256): each CTA keeps
@@ -94,7 +103,7 @@ constexpr int kTcEpiLd = 68;  // floats per row of the epilogue staging tile (64
 // chunks are staged two deep (the A loads of a chunk all issued before its
 // conversion), then the accumulator goes through shared memory so that the
 // epilogue reads and writes whole rows (coalesced float4 accesses).
-__global__ void __launch_bounds__(kTcThreads, 2) tc_rows_kernel(Gemm g, const uint16_t* __restrict__ bimg,
+__global__ void __launch_bounds__(kTcThreads, 3) tc_rows_kernel(Gemm g, const uint16_t* __restrict__ bimg,
                                                                 int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;                   // [2][128 x 64] BF16
@@ -121,6 +130,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_rows_kernel(Gemm g, const ui
   const uint32_t tmem = tbase;
   const uint16_t* bblk = bimg + (size_t)blockIdx.y * kTcMaxN * K;  // this column tile's image block
   const int nchunks = (K + kTcChunk - 1) / kTcChunk;
+  const size_t b_stage = (size_t)min(kTcMaxN, g.N) * kTcChunk * 2;  // B stage bytes (tc_rows_smem)
   const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)Nt);
   const long long tiles = (g.M + 127) / 128;
   uint32_t phase[2] = {0u, 0u};
@@ -137,7 +147,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_rows_kernel(Gemm g, const ui
         tc::fence_after_sync();
       }
       unsigned char* a = sA + s * kTcStageA;
-      unsigned char* b = sB + s * kTcStageB;
+      unsigned char* b = sB + (size_t)s * b_stage;
       // A: unit = (row, 8-column group), consecutive threads on consecutive
       // rows of one group (conflict-free 16-byte stores); all of a thread's
       // loads are issued before the first conversion
