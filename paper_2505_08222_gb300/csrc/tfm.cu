@@ -32,7 +32,7 @@ constexpr int kMaxT = 1 + UT_MAX_AGENTS + UT_MAX_TARGETS;  // tokens per sample
 constexpr int kRowBlocks = 304;                             // blocks of the head / embedding-gradient kernels
 constexpr int kLnBlocks = 1216;                             // blocks of the LayerNorm kernels
 constexpr int kRowWarps = kRowBlocks * 8;                   // warps writing partial sums
-constexpr int kTcSplits = 304;                              // row splits of a tensor-core weight gradient
+constexpr int kTcSplitsMax = 3 * 152;                       // row splits of a tensor-core weight gradient (at most)
 
 enum { EPI_STORE = 0, EPI_BIAS = 1, EPI_BIAS_RES = 2, EPI_BIAS_GELU = 3, EPI_GELU_GRAD = 4, EPI_PARTIAL = 5 };
 
@@ -1284,13 +1284,16 @@ cudaError_t reduce(const float* part, int nparts, long long len, long long strid
 cudaError_t wgrad(ut_tfm* t, const float* dOut, int n_o, const float* In, int n_i, long long rows, float* gW,
                   float* gb, cudaStream_t s) {
   if (t->gemm_tc && rows > 0) {
-    // tensor cores: (n_o / 128) x (n_i / 256) tiles x row splits, about two
-    // CTAs per SM, each split a multiple of 64 rows
+    // tensor cores: (n_o / 128) x (n_i / 256) tiles x row splits, about as
+    // many CTAs per SM as fit (three for n_i <= 128, else two), each split a
+    // multiple of 64 rows
     static std::atomic<unsigned long long> ready{0};
     cudaError_t e = smem_optin(tc_wgrad_kernel, kTcSmem, ready);
     if (e != cudaSuccess) return e;
+    const size_t smem = tc_wgrad_smem(n_i);
+    const int per_sm = smem <= 72 * 1024 ? 3 : 2;
     const long long tiles = (long long)((n_o + 127) / 128) * ((n_i + kTcMaxN - 1) / kTcMaxN);
-    long long splits = (kTcSplits + tiles - 1) / tiles;
+    long long splits = (per_sm * 152 + tiles - 1) / tiles;
     const long long max_split = (rows + kTcChunk - 1) / kTcChunk;
     if (splits > max_split) splits = max_split;
     if (splits < 1) splits = 1;
@@ -1302,7 +1305,7 @@ cudaError_t wgrad(ut_tfm* t, const float* dOut, int n_o, const float* In, int n_
     g.status = t->status;
     dim3 grid((unsigned)((n_o + 127) / 128), (unsigned)((n_i + kTcMaxN - 1) / kTcMaxN), (unsigned)splits);
     float* bias_part = t->part + splits * n_o * n_i;
-    tc_wgrad_kernel<<<grid, kTcThreads, kTcSmem, s>>>(g, bias_part, t->status);
+    tc_wgrad_kernel<<<grid, kTcThreads, smem, s>>>(g, bias_part, t->status);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = reduce(t->part, (int)splits, (long long)n_o * n_i, (long long)n_o * n_i, gW, s);
     if (e == cudaSuccess) e = reduce(bias_part, (int)splits, n_o, n_o, gb, s);
@@ -1639,7 +1642,7 @@ extern "C" ut_status tfm_create(const ut_tfm_config* cfg, const float* params_ho
   part = std::max(part, (size_t)kRowWarps * (2 * d + (size_t)t->n_out * d + t->n_out));
   part = std::max(part, (size_t)kRowWarps * 9 * d);
   part = std::max(part, (size_t)kLnBlocks * 2 * d);
-  part = std::max(part, (size_t)kTcSplits * (4 * d * d + 4 * d));  // tensor-core weight- and bias-gradient slabs
+  part = std::max(part, (size_t)kTcSplitsMax * (4 * d * d + 4 * d));  // tensor-core weight- and bias-gradient slabs
   bool ok = true;
   auto A = [&](size_t n) -> float* {
     float* p = (float*)dalloc(t, n * 4);

@@ -87,6 +87,12 @@ __device__ __forceinline__ void epi_store4(const Gemm& g, long long m, int n, fl
 
 constexpr int kTcEpiLd = 68;  // floats per row of the epilogue staging tile (64 + 4: conflict-free)
 
+// Shared memory of tc_wgrad_kernel for inputs n_i wide: two A stages and two
+// B stages of min(n_i rounded up to 32, 256) rows.
+inline size_t tc_wgrad_smem(int n_i) {
+  return 2 * kTcStageA + 2 * (size_t)std::min(kTcMaxN, (n_i + 31) / 32 * 32) * kTcChunk * 2;
+}
+
 // Shared memory of tc_rows_kernel for outputs N wide: two A stages and two B
 // stages sized for min(N, 256) rows, at least the epilogue staging tile
 // (which overlays them); narrow products fit three CTAs per SM.
@@ -260,7 +266,7 @@ __global__ void __launch_bounds__(kTcThreads, 3) tc_rows_kernel(Gemm g, const ui
 // g.K = rows, g.kchunk = rows per split; part is g.C [splits][n_o][n_i].
 // The bias gradient's partial sums sum_m dOut[m][n] (FP32, fixed order) go to
 // bias_part [splits][n_o].
-__global__ void __launch_bounds__(kTcThreads, 2) tc_wgrad_kernel(Gemm g, float* __restrict__ bias_part, int* status) {
+__global__ void __launch_bounds__(kTcThreads, 3) tc_wgrad_kernel(Gemm g, float* __restrict__ bias_part, int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;                   // [2][128 x 64] BF16: (n, m)
   unsigned char* sB = smem + 2 * kTcStageA;   // [2][256 x 64] BF16: (k, m)
@@ -271,6 +277,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_wgrad_kernel(Gemm g, float* 
   const int nb0 = blockIdx.x * 128, kb0 = blockIdx.y * kTcMaxN;
   const int Nt = min(kTcMaxN, n_i - kb0);
   const int Ntp = (Nt + 31) / 32 * 32;  // B rows staged (a multiple of 32; rows past n_i are zero)
+  const size_t b_stage = (size_t)min(kTcMaxN, (n_i + 31) / 32 * 32) * kTcChunk * 2;  // (tc_wgrad_smem)
   const long long r0 = (long long)blockIdx.z * g.kchunk;
   const long long r1 = min(g.K, r0 + g.kchunk);
   const uint32_t ncols = tc_cols(Ntp);
@@ -301,7 +308,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_wgrad_kernel(Gemm g, float* 
       tc::fence_after_sync();
     }
     unsigned char* a = sA + s * kTcStageA;
-    unsigned char* b = sB + s * kTcStageB;
+    unsigned char* b = sB + (size_t)s * b_stage;
     // transposed staging: warp w takes rows m0 + 8 w .. + 7 of the chunk, in
     // blocks of 32 consecutive columns (row loads coalesced across the warp);
     // each lane packs its column's 8 rows into one 16-byte core row.  A
