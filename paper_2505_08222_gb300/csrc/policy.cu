@@ -97,6 +97,7 @@ struct Geo {
   static_assert(!PIPE || (NC >= 2 && COL_S + 256 <= TMEM_COLS && KV_BYTES >= (size_t)2 * 128 * 128 * 2),
                 "pipelined FFN plan");
   static_assert(SLOT % 16 == 0 && IMG_W2 <= SLOT, "bulk copies are 16-byte multiples");
+  static_assert(VEC % 4 == 0 && VEC_OFF % 16 == 0, "16-byte copies of the per-layer vectors");
 };
 
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
@@ -198,6 +199,14 @@ __device__ __forceinline__ void issue_mma_ts(uint32_t d_tmem, uint32_t a_tmem, u
     tc::mma_bf16_ts(d_tmem, a_tmem + (uint32_t)(k * 8), bd, idesc, (accumulate || k > 0) ? 1u : 0u);
   }
 }
+
+// 16-byte asynchronous global -> shared copy; commit of the calling thread's
+// copies as a group, and the wait for all of them.
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_addr(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Make every thread's shared-memory operand writes (and TMEM reads) visible
 // before thread 0 issues the next MMA group.
@@ -821,6 +830,18 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
     }
   };
 
+  // The per-layer vectors (LayerNorm gains and offsets, biases) arrive by
+  // asynchronous copies into the double buffer, layer 0's now and layer
+  // l + 1's during layer l's attention; each thread waits for its own copies
+  // at the top of the layer, and the LayerNorm's barrier publishes them.
+  auto prefetch_vec = [&](int l) {
+    float* dst = sVec + (l & 1) * G::VEC;
+    const float* src = p.vec + (size_t)l * G::VEC;
+    for (int i = tid; i < G::VEC / 4; i += kThreads) cp_async16(dst + 4 * i, src + 4 * i);
+    cp_async_commit();
+  };
+  prefetch_vec(0);
+
   // ---- token rows ----------------------------------------------------------
   float x[COLS];
   if (row_ok && tok == 0) {
@@ -860,10 +881,7 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
   // gave up only marks the result invalid.
   for (int l = 0; l < p.L; ++l) {
     float* vec = sVec + (l & 1) * G::VEC;  // double-buffered: the previous layer may still read its copy
-    {
-      const float4* src = reinterpret_cast<const float4*>(p.vec + (size_t)l * G::VEC);
-      for (int i = tid; i < G::VEC / 4; i += kThreads) reinterpret_cast<float4*>(vec)[i] = __ldg(src + i);
-    }
+    cp_async_wait_all();
     const float *ln1g = vec, *ln1b = vec + D, *bq = vec + 2 * D, *bk = vec + 3 * D, *bv = vec + 4 * D;
     const float *bo = vec + 5 * D, *ln2g = vec + 6 * D, *ln2b = vec + 7 * D, *b1 = vec + 8 * D, *b2 = vec + 12 * D;
 
@@ -942,6 +960,7 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
         }
       }
     }
+    if (l + 1 < p.L) prefetch_vec(l + 1);  // (buffer (l + 1) & 1 was last read in layer l - 1)
     publish();
     if (tid == 0) {
       wait_images(1);
