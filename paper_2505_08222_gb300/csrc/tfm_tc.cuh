@@ -85,37 +85,41 @@ __device__ __forceinline__ void epi_store4(const Gemm& g, long long m, int n, fl
   *reinterpret_cast<float4*>(g.C + o) = r;
 }
 
-constexpr int kTcEpiLd = 68;  // floats per row of the epilogue staging tile (64 + 4: conflict-free)
-
 // Shared memory of tc_wgrad_kernel for inputs n_i wide: two A stages and two
 // B stages of min(n_i rounded up to 32, 256) rows.
 inline size_t tc_wgrad_smem(int n_i) {
   return 2 * kTcStageA + 2 * (size_t)std::min(kTcMaxN, (n_i + 31) / 32 * 32) * kTcChunk * 2;
 }
 
-// Shared memory of tc_rows_kernel for outputs N wide: two A stages and two B
-// stages sized for min(N, 256) rows, at least the epilogue staging tile
-// (which overlays them); narrow products fit three CTAs per SM.
+// Shared memory of tc_rows_kernel for outputs N wide: two A stages (the
+// epilogue's staging tile overlays them) and two B stages sized for
+// min(N, 256) rows; narrow products fit three CTAs per SM.
 inline size_t tc_rows_smem(int N) {
-  const size_t stages = 2 * kTcStageA + 2 * (size_t)std::min(kTcMaxN, N) * kTcChunk * 2;
-  const size_t epi = (size_t)128 * kTcEpiLd * 4;
-  return stages > epi ? stages : epi;
+  return 2 * kTcStageA + 2 * (size_t)std::min(kTcMaxN, N) * kTcChunk * 2;
 }
 
 // Kinds 0 / 1: C[m][n] = sum_k A[m][k] B(n, k) + epilogue, A FP32 row-major
 // (lda), B the image of `R` = g.N rows by `C` = g.K columns.  Grid (CTAs
 // looping over the row tiles of 128, column tiles of 256): each CTA keeps
-// its tensor memory and barriers across its row tiles.  Per tile, the K
-// chunks are staged two deep (the A loads of a chunk all issued before its
-// conversion), then the accumulator goes through shared memory so that the
-// epilogue reads and writes whole rows (coalesced float4 accesses).
+// its tensor memory and barriers across its row tiles.  The K chunks are
+// staged two deep.  A chunk's B (a contiguous range of the image) arrives by
+// one bulk copy; with K <= 128 the B chunks stay resident across row tiles.
+// A is loaded into registers a chunk ahead (the next chunk's loads, of this
+// tile or the next, are issued as soon as the current chunk is converted,
+// so they are in flight during its MMAs and the epilogue), rounded to BF16
+// and written K-major.  The accumulator goes through a staging tile over the
+// A stages (rows of 64 floats, 16-byte chunks XOR-swizzled by row) so that
+// the epilogue reads and writes whole rows (coalesced float4 accesses).
+__device__ __forceinline__ int epi_pos(int row, int c4) { return row * 64 + ((c4 ^ (row & 15)) << 2); }
+
 __global__ void __launch_bounds__(kTcThreads, 3) tc_rows_kernel(Gemm g, const uint16_t* __restrict__ bimg,
                                                                 int* status) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* sA = smem;                   // [2][128 x 64] BF16
-  unsigned char* sB = smem + 2 * kTcStageA;   // [2][256 x 64] BF16
-  float* sE = reinterpret_cast<float*>(smem);  // epilogue staging [128][kTcEpiLd] (after the tile's MMAs)
+  unsigned char* sA = smem;                    // [2][128 x 64] BF16
+  unsigned char* sB = smem + 2 * kTcStageA;    // [2][min(N, 256) x 64] BF16
+  float* sE = reinterpret_cast<float*>(smem);  // epilogue staging [128][64] over the A stages
   __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t bfull[2];
   __shared__ uint32_t tbase;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n0 = blockIdx.y * kTcMaxN;
@@ -126,9 +130,11 @@ __global__ void __launch_bounds__(kTcThreads, 3) tc_rows_kernel(Gemm g, const ui
     tc::tmem_alloc(&tbase, ncols);
     tc::tmem_relinquish();
   }
-  if (tid == 0) {
-    tc::mbar_init(&mbar[0], 1);
-    tc::mbar_init(&mbar[1], 1);
+  if (tid == 32) {
+    for (int k = 0; k < 2; ++k) {
+      tc::mbar_init(&mbar[k], 1);
+      tc::mbar_init(&bfull[k], 1);
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -136,72 +142,83 @@ __global__ void __launch_bounds__(kTcThreads, 3) tc_rows_kernel(Gemm g, const ui
   const uint32_t tmem = tbase;
   const uint16_t* bblk = bimg + (size_t)blockIdx.y * kTcMaxN * K;  // this column tile's image block
   const int nchunks = (K + kTcChunk - 1) / kTcChunk;
+  const bool b_resident = nchunks <= 2;  // chunk c of every tile uses stage c (or both, for one chunk)
   const size_t b_stage = (size_t)min(kTcMaxN, g.N) * kTcChunk * 2;  // B stage bytes (tc_rows_smem)
   const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)Nt);
   const long long tiles = (g.M + 127) / 128;
-  uint32_t phase[2] = {0u, 0u};
+  uint32_t phase = 0u, bphase = 0u, bpend = 0u;  // per stage s: bit s
   bool ok = true;
   int q_used = 0;  // chunks committed so far (the stage ring runs across tiles)
+
+  // A of (row tile m0, chunk at k0): unit = (row, 8-column group), 2 or 4 per
+  // thread, in registers until stage_a
+  float4 xa[4][2];
+  auto load_a = [&](long long m0, int k0) {
+    const int units = 128 * (min(kTcChunk, K - k0) >> 3);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int u = tid + i * kTcThreads;
+      const int row = u & 127, grp = u >> 7;
+      xa[i][0] = xa[i][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (u < units && m0 + row < g.M) {
+        const float4* src = reinterpret_cast<const float4*>(g.A + (m0 + row) * g.lda + k0 + grp * 8);
+        xa[i][0] = __ldg(src);
+        xa[i][1] = __ldg(src + 1);
+      }
+    }
+  };
+  // consecutive threads on consecutive rows of one group: conflict-free
+  // 16-byte stores
+  auto stage_a = [&](unsigned char* a, int kc) {
+    const int units = 128 * (kc >> 3);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int u = tid + i * kTcThreads;
+      if (u < units) {
+        const int row = u & 127, grp = u >> 7;
+        const uint4 p = make_uint4(pack_bf2(xa[i][0].x, xa[i][0].y), pack_bf2(xa[i][0].z, xa[i][0].w),
+                                   pack_bf2(xa[i][1].x, xa[i][1].y), pack_bf2(xa[i][1].z, xa[i][1].w));
+        *reinterpret_cast<uint4*>(a + tc::kmajor_offset(row, grp * 8, 128)) = p;
+      }
+    }
+  };
+
+  if ((long long)blockIdx.x < tiles) load_a((long long)blockIdx.x * 128, 0);
   for (long long mt = blockIdx.x; mt < tiles; mt += gridDim.x) {
     const long long m0 = mt * 128;
     for (int c = 0; c < nchunks; ++c, ++q_used) {
       const int s = q_used & 1;
       const int k0 = c * kTcChunk, kc = min(kTcChunk, K - k0);
       if (q_used >= 2 && c >= 2) {  // this tile's MMAs two chunks back read this stage
-        ok &= tc::mbar_wait(&mbar[s], phase[s], kTcPolls);
-        phase[s] ^= 1u;
+        ok &= tc::mbar_wait(&mbar[s], (phase >> s) & 1u, kTcPolls);
+        phase ^= 1u << s;
         tc::fence_after_sync();
       }
       unsigned char* a = sA + s * kTcStageA;
       unsigned char* b = sB + (size_t)s * b_stage;
-      // A: unit = (row, 8-column group), consecutive threads on consecutive
-      // rows of one group (conflict-free 16-byte stores); all of a thread's
-      // loads are issued before the first conversion
-      {
-        const int units = 128 * (kc >> 3);  // 512 or 1024: 2 or 4 per thread
-        float4 x[4][2];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int u = tid + i * kTcThreads;
-          const int row = u & 127, grp = u >> 7;
-          x[i][0] = x[i][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (u < units && m0 + row < g.M) {
-            const float4* src = reinterpret_cast<const float4*>(g.A + (m0 + row) * g.lda + k0 + grp * 8);
-            x[i][0] = __ldg(src);
-            x[i][1] = __ldg(src + 1);
-          }
-        }
-        // B: the chunk is one contiguous range of the image (<= 8 x 16 B per thread)
-        const uint4* bsrc = reinterpret_cast<const uint4*>(bblk + (size_t)k0 * Nt);
-        const int n16 = Nt * kc / 8;
-        uint4 y[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int u = tid + i * kTcThreads;
-          y[i] = u < n16 ? __ldg(bsrc + u) : make_uint4(0u, 0u, 0u, 0u);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int u = tid + i * kTcThreads;
-          if (u < units) {
-            const int row = u & 127, grp = u >> 7;
-            const uint4 p = make_uint4(pack_bf2(x[i][0].x, x[i][0].y), pack_bf2(x[i][0].z, x[i][0].w),
-                                       pack_bf2(x[i][1].x, x[i][1].y), pack_bf2(x[i][1].z, x[i][1].w));
-            *reinterpret_cast<uint4*>(a + tc::kmajor_offset(row, grp * 8, 128)) = p;
-          }
-        }
-        uint4* bdst = reinterpret_cast<uint4*>(b);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int u = tid + i * kTcThreads;
-          if (u < n16) bdst[u] = y[i];
-        }
+      const bool b_new = !b_resident || q_used < 2;
+      if (b_new && tid == 0) {  // the stage is free: its last MMA has completed
+        const uint32_t bytes = (uint32_t)(Nt * kc * 2);
+        tc::mbar_expect_tx(&bfull[s], bytes);
+        tc::bulk_g2s(b, bblk + (size_t)k0 * Nt, bytes, &bfull[s]);
       }
+      stage_a(a, kc);
+      // the next chunk's A: in flight during this chunk's MMAs (and epilogue)
+      if (c + 1 < nchunks)
+        load_a(m0, k0 + kTcChunk);
+      else if (mt + gridDim.x < tiles)
+        load_a(m0 + (long long)gridDim.x * 128, 0);
       tc::fence_async_smem();
       tc::fence_before_sync();
       __syncthreads();
       tc::fence_after_sync();
       if (tid == 0) {
+        if (b_new) {
+          if (tc::mbar_wait(&bfull[s], (bphase >> s) & 1u, kTcPolls))
+            bphase ^= 1u << s;
+          else
+            ok = false, bpend |= 1u << s;
+        }
         const uint32_t aa = tc::smem_addr(a), bb = tc::smem_addr(b);
         for (int j = 0; j < kc / 16; ++j) {
           const uint64_t ad = tc::smem_desc(aa + j * 2 * 128 * 16, 128 * 16, 128);
@@ -214,8 +231,8 @@ __global__ void __launch_bounds__(kTcThreads, 3) tc_rows_kernel(Gemm g, const ui
     // this tile's last (up to two) chunks: their MMAs are done
     for (int c = max(0, nchunks - 2); c < nchunks; ++c) {
       const int s = (q_used - nchunks + c) & 1;
-      ok &= tc::mbar_wait(&mbar[s], phase[s], kTcPolls);
-      phase[s] ^= 1u;
+      ok &= tc::mbar_wait(&mbar[s], (phase >> s) & 1u, kTcPolls);
+      phase ^= 1u << s;
     }
     tc::fence_after_sync();
     ok = __syncthreads_and(ok);  // (the tensor-memory loads below are warp-collective)
@@ -228,14 +245,15 @@ __global__ void __launch_bounds__(kTcThreads, 3) tc_rows_kernel(Gemm g, const ui
     for (int c0 = 0; c0 < Nt; c0 += 64) {
       const int cw = min(64, Nt - c0);  // 32 or 64
       if (half * 32 < cw) {
-        float v[16], w[16];
-        tc::tmem_ld16(lane_addr + c0 + half * 32, v);
-        tc::tmem_ld16(lane_addr + c0 + half * 32 + 16, w);
-        float* dst = sE + (q * 32 + lane) * kTcEpiLd + half * 32;
+        const int row = q * 32 + lane;
 #pragma unroll
-        for (int j = 0; j < 16; j += 4) {
-          *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-          *reinterpret_cast<float4*>(dst + 16 + j) = make_float4(w[j], w[j + 1], w[j + 2], w[j + 3]);
+        for (int h = 0; h < 2; ++h) {
+          float v[16];
+          tc::tmem_ld16(lane_addr + c0 + half * 32 + h * 16, v);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            *reinterpret_cast<float4*>(sE + epi_pos(row, half * 8 + h * 4 + j)) =
+                make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
         }
       }
       tc::fence_before_sync();
@@ -246,13 +264,18 @@ __global__ void __launch_bounds__(kTcThreads, 3) tc_rows_kernel(Gemm g, const ui
         const int row = u / per_row, c4 = u - row * per_row;
         const long long m = m0 + row;
         if (m < g.M) {
-          const float4 v = *reinterpret_cast<const float4*>(sE + row * kTcEpiLd + c4 * 4);
+          const float4 v = *reinterpret_cast<const float4*>(sE + epi_pos(row, c4));
           epi_store4(g, m, n0 + c0 + c4 * 4, v);
         }
       }
-      __syncthreads();  // the staging tile is free again
+      __syncthreads();  // the staging tile (the A stages) is free again
     }
   }
+  // (a B copy whose wait gave up may still be landing: wait for it, bounded,
+  // before the CTA exits)
+  if (bpend != 0u)
+    for (int k = 0; k < 2; ++k)
+      if ((bpend >> k) & 1u) tc::mbar_wait(&bfull[k], (bphase >> k) & 1u, kTcPolls);
   if (!ok && tid == 0) raise_status(status, 2);
   tc::fence_before_sync();
   __syncthreads();
