@@ -629,170 +629,254 @@ __device__ __forceinline__ void mma16x16(float (&c)[2][4], const float* a, const
   }
 }
 
+// Per-warp staging of one (sample, head) item: rows u = lane / 4 + 8 r
+// (r = 0, 1) of the item's 16-wide Q, K, V slices (and dO in the backward),
+// quarter lane % 4 of each row, as float4; rows u >= T are zero.  The warps
+// are persistent: the next item's slices are loaded into registers while the
+// current item is computed from shared memory.
+struct AttRows {
+  float4 q[2], k[2], v[2];
+};
+__device__ __forceinline__ void att_fetch(AttRows& r, const float* __restrict__ QKV, long long s, int hh, int T, int d,
+                                          int lane) {
+  const int u0 = lane >> 2, j4 = lane & 3;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int u = u0 + 8 * i;
+    r.q[i] = r.k[i] = r.v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (u < T) {
+      const float4* base = reinterpret_cast<const float4*>(QKV + (s * T + u) * 3 * d + hh * 16) + j4;
+      r.q[i] = __ldg(base);
+      r.k[i] = __ldg(base + d / 4);
+      r.v[i] = __ldg(base + d / 2);
+    }
+  }
+}
+__device__ __forceinline__ void att_stage(const float4 (&x)[2], float* dst, int lane) {
+  const int u0 = lane >> 2, j4 = lane & 3;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) *reinterpret_cast<float4*>(dst + (u0 + 8 * i) * kAttLd + 4 * j4) = x[i];
+}
+
+// Resident blocks of 128 threads for a persistent attention kernel: as many
+// as fit on the device at once (at least one per SM).
+template <typename K>
+inline long long att_capacity(K kernel) {
+  int dev = 0, b = 0, m = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, 128, 0) != cudaSuccess) {
+    (void)cudaGetLastError();
+    b = 1, m = 152;
+  }
+  return (long long)(b > 0 ? b : 1) * (m > 0 ? m : 152);
+}
+template <typename K>
+inline long long att_grid(K kernel, long long items) {
+  static const long long cap = att_capacity(kernel);  // (initialised once, thread-safe)
+  const long long need = (items + 3) / 4;
+  return need < cap ? need : cap;
+}
+
 // Attention forward on the tensor cores (tensor-core path; T <= 16, head
-// dimension 16), one (sample, head) per warp, 4 warps per block: S = Q K^T
-// as m16n8k8 TF32 MMAs over the tokens padded to 16, the masked softmax on
-// the accumulator fragments (keys u <= n_ent of the sample, a row in the 4
-// lanes of a quad), P written out (zero at masked keys) and staged, then
-// O = P V.
-__global__ void __launch_bounds__(128) attn_fwd_mma_kernel(const float* __restrict__ QKV,
+// dimension 16), one (sample, head) item per warp at a time, persistent warps
+// (4 per block) over the items: S = Q K^T as m16n8k8 TF32 MMAs over the
+// tokens padded to 16, the masked softmax on the accumulator fragments (keys
+// u <= n_ent of the sample, a row in the 4 lanes of a quad), P written out
+// (zero at masked keys) and staged, then O = P V.
+__global__ void __launch_bounds__(128, 8) attn_fwd_mma_kernel(const float* __restrict__ QKV,
                                                            const int32_t* __restrict__ n_ent,
                                                            const int32_t* __restrict__ sel, float* __restrict__ P,
                                                            float* __restrict__ O, long long n, int T, int NS, int H,
                                                            float scale) {
-  __shared__ float sm[4][4][16 * kAttLd];  // Q, K, V, P of each warp
+  __shared__ __align__(16) float sm[4][4][16 * kAttLd];  // Q, K, V, P of each warp
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (w >= n * H) return;  // whole warps leave together
-  const long long s = w / H;
-  const int hh = (int)(w - s * H);
-  const int d = 16 * H, ld = 3 * d;
-  int ne = n_ent[sel ? (long long)sel[s] : s];
-  ne = ne < 0 ? 0 : (ne > NS ? NS : ne);
+  const int d = 16 * H;
+  const long long items = n * H, stride = (long long)gridDim.x * 4;
   float *sQ = sm[wl][0], *sK = sm[wl][1], *sV = sm[wl][2], *sP = sm[wl][3];
-  for (int i = lane; i < 256; i += 32) {
-    const int u = i >> 4, j = i & 15;
-    const bool in = u < T;
-    const float* base = QKV + (s * T + u) * ld + hh * 16;
-    sQ[u * kAttLd + j] = in ? base[j] : 0.0f;
-    sK[u * kAttLd + j] = in ? base[d + j] : 0.0f;
-    sV[u * kAttLd + j] = in ? base[2 * d + j] : 0.0f;
-  }
-  __syncwarp();
-  float sc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-  mma16x16<false, true>(sc, sQ, sK, g, t);  // S = Q K^T
-  float* Pb = P + (s * H + hh) * T * T;
+  long long w = (long long)blockIdx.x * 4 + wl;
+  AttRows r;
+  int ne_next = 0;
+  auto fetch = [&](long long wi) {
+    const long long s = wi / H;
+    att_fetch(r, QKV, s, (int)(wi - s * H), T, d, lane);
+    ne_next = __ldg(n_ent + (sel ? (long long)__ldg(sel + s) : s));
+  };
+  if (w < items) fetch(w);
+  for (; w < items; w += stride) {
+    const long long s = w / H;
+    const int hh = (int)(w - s * H);
+    att_stage(r.q, sQ, lane);
+    att_stage(r.k, sK, lane);
+    att_stage(r.v, sV, lane);
+    const int ne = ne_next < 0 ? 0 : (ne_next > NS ? NS : ne_next);
+    if (w + stride < items) fetch(w + stride);  // in flight during this item
+    __syncwarp();
+    float sc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    mma16x16<false, true>(sc, sQ, sK, g, t);  // S = Q K^T
+    float* Pb = P + (s * H + hh) * T * T;
 #pragma unroll
-  for (int hr = 0; hr < 2; ++hr) {
-    const int row = g + 8 * hr;
-    float mx = -INFINITY;
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int col = 8 * j + 2 * t + e;
-        const float v = (col < T && col <= ne) ? sc[j][2 * hr + e] * scale : -INFINITY;
-        sc[j][2 * hr + e] = v;
-        mx = fmaxf(mx, v);
-      }
-    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-    float z = 0.0f;
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const float x = sc[j][2 * hr + e];
-        const float ex = x == -INFINITY ? 0.0f : __expf(x - mx);
-        sc[j][2 * hr + e] = ex;
-        z += ex;
-      }
-    z += __shfl_xor_sync(0xffffffffu, z, 1);
-    z += __shfl_xor_sync(0xffffffffu, z, 2);
-    const float iz = 1.0f / z;
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int col = 8 * j + 2 * t;
-      const float p0 = sc[j][2 * hr] * iz, p1 = sc[j][2 * hr + 1] * iz;
-      sP[row * kAttLd + col] = p0;
-      sP[row * kAttLd + col + 1] = p1;
-      if (row < T) {
-        if (col < T) Pb[row * T + col] = p0;
-        if (col + 1 < T) Pb[row * T + col + 1] = p1;
-      }
-    }
-  }
-  __syncwarp();
-  float o[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-  mma16x16<false, false>(o, sP, sV, g, t);  // O = P V
-#pragma unroll
-  for (int hr = 0; hr < 2; ++hr) {
-    const int row = g + 8 * hr;
-    if (row < T) {
+    for (int hr = 0; hr < 2; ++hr) {
+      const int row = g + 8 * hr;
+      float mx = -INFINITY;
 #pragma unroll
       for (int j = 0; j < 2; ++j)
-        *reinterpret_cast<float2*>(O + (s * T + row) * d + hh * 16 + 8 * j + 2 * t) =
-            make_float2(o[j][2 * hr], o[j][2 * hr + 1]);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int col = 8 * j + 2 * t + e;
+          const float v = (col < T && col <= ne) ? sc[j][2 * hr + e] * scale : -INFINITY;
+          sc[j][2 * hr + e] = v;
+          mx = fmaxf(mx, v);
+        }
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+      float z = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const float x = sc[j][2 * hr + e];
+          const float ex = x == -INFINITY ? 0.0f : __expf(x - mx);
+          sc[j][2 * hr + e] = ex;
+          z += ex;
+        }
+      z += __shfl_xor_sync(0xffffffffu, z, 1);
+      z += __shfl_xor_sync(0xffffffffu, z, 2);
+      const float iz = 1.0f / z;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int col = 8 * j + 2 * t;
+        const float p0 = sc[j][2 * hr] * iz, p1 = sc[j][2 * hr + 1] * iz;
+        sP[row * kAttLd + col] = p0;
+        sP[row * kAttLd + col + 1] = p1;
+        if (row < T) {
+          if (col < T) Pb[row * T + col] = p0;
+          if (col + 1 < T) Pb[row * T + col + 1] = p1;
+        }
+      }
     }
+    __syncwarp();
+    float o[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    mma16x16<false, false>(o, sP, sV, g, t);  // O = P V
+#pragma unroll
+    for (int hr = 0; hr < 2; ++hr) {
+      const int row = g + 8 * hr;
+      if (row < T) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+          *reinterpret_cast<float2*>(O + (s * T + row) * d + hh * 16 + 8 * j + 2 * t) =
+              make_float2(o[j][2 * hr], o[j][2 * hr + 1]);
+      }
+    }
+    __syncwarp();  // the staged tiles are read before the next item overwrites them
   }
 }
 
 // Attention backward on the tensor cores (tensor-core path; T <= 16, head
-// dimension 16), one (sample, head) per warp, 4 warps per block: the
-// products of attn_bwd_kernel, dP = dO V^T, dQ = dS K, dK = dS^T Q,
-// dV = P^T dO, as m16n8k8 TF32 MMAs over the tokens padded to 16 (padded
-// rows and columns staged as zeros), and dS = P (dP - rowsum(P dP)) scale on
-// the accumulator fragments (a row lives in the 4 lanes of a quad).
-__global__ void __launch_bounds__(128) attn_bwd_mma_kernel(const float* __restrict__ QKV, const float* __restrict__ P,
+// dimension 16), one (sample, head) item per warp at a time, persistent warps
+// (4 per block): the products of attn_bwd_kernel, dP = dO V^T, dQ = dS K,
+// dK = dS^T Q, dV = P^T dO, as m16n8k8 TF32 MMAs over the tokens padded to
+// 16 (padded rows and columns staged as zeros), and
+// dS = P (dP - rowsum(P dP)) scale on the accumulator fragments (a row lives
+// in the 4 lanes of a quad).  dS is staged over V (V is read only by dP).
+__global__ void __launch_bounds__(128, 6) attn_bwd_mma_kernel(const float* __restrict__ QKV, const float* __restrict__ P,
                                                            const float* __restrict__ dO, float* __restrict__ dQKV,
                                                            long long n, int T, int H, float scale) {
-  __shared__ float sm[4][6][16 * kAttLd];  // Q, K, V, dO, P, dS of each warp
+  __shared__ __align__(16) float sm[4][5][16 * kAttLd];  // Q, K, V then dS, dO, P of each warp
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (w >= n * H) return;  // whole warps leave together
-  const long long s = w / H;
-  const int hh = (int)(w - s * H);
   const int d = 16 * H, ld = 3 * d;
-  float *sQ = sm[wl][0], *sK = sm[wl][1], *sV = sm[wl][2], *sG = sm[wl][3], *sP = sm[wl][4], *sS = sm[wl][5];
-  const float* Pb = P + (s * H + hh) * T * T;
-  for (int i = lane; i < 256; i += 32) {
-    const int u = i >> 4, j = i & 15;
-    const bool in = u < T;
-    const float* base = QKV + (s * T + u) * ld + hh * 16;
-    sQ[u * kAttLd + j] = in ? base[j] : 0.0f;
-    sK[u * kAttLd + j] = in ? base[d + j] : 0.0f;
-    sV[u * kAttLd + j] = in ? base[2 * d + j] : 0.0f;
-    sG[u * kAttLd + j] = in ? dO[(s * T + u) * d + hh * 16 + j] : 0.0f;
-    sP[u * kAttLd + j] = (in && j < T) ? Pb[u * T + j] : 0.0f;
+  const long long items = n * H, stride = (long long)gridDim.x * 4;
+  float *sQ = sm[wl][0], *sK = sm[wl][1], *sV = sm[wl][2], *sS = sm[wl][2], *sG = sm[wl][3], *sP = sm[wl][4];
+  // P of an item: T * T contiguous floats, element e = lane + 32 i at
+  // (e / T, e % T) of the staged tile; the padding stays zero
+  int pofs[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int e = lane + 32 * i;
+    pofs[i] = e < T * T ? (e / T) * kAttLd + e % T : -1;
   }
-  __syncwarp();
-  // dP = dO V^T
-  float dp[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-  mma16x16<false, true>(dp, sG, sV, g, t);
-  // dS = P (dP - rowsum(P dP)) scale (rows g and g + 8 of this quad)
-  float pv[2][4], r0 = 0.0f, r1 = 0.0f;
+  for (int i = lane; i < 16 * kAttLd; i += 32) sP[i] = 0.0f;
+  long long w = (long long)blockIdx.x * 4 + wl;
+  AttRows r;
+  float4 rg[2];
+  float rp[4];
+  auto fetch = [&](long long wi) {
+    const long long s = wi / H;
+    const int hh = (int)(wi - s * H);
+    att_fetch(r, QKV, s, hh, T, d, lane);
+    const int u0 = lane >> 2, j4 = lane & 3;
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    const int c = 8 * j + 2 * t;
-    pv[j][0] = sP[g * kAttLd + c];
-    pv[j][1] = sP[g * kAttLd + c + 1];
-    pv[j][2] = sP[(g + 8) * kAttLd + c];
-    pv[j][3] = sP[(g + 8) * kAttLd + c + 1];
-    r0 = fmaf(pv[j][0], dp[j][0], fmaf(pv[j][1], dp[j][1], r0));
-    r1 = fmaf(pv[j][2], dp[j][2], fmaf(pv[j][3], dp[j][3], r1));
-  }
-  r0 += __shfl_xor_sync(0xffffffffu, r0, 1);
-  r0 += __shfl_xor_sync(0xffffffffu, r0, 2);
-  r1 += __shfl_xor_sync(0xffffffffu, r1, 1);
-  r1 += __shfl_xor_sync(0xffffffffu, r1, 2);
+    for (int i = 0; i < 2; ++i) {
+      const int u = u0 + 8 * i;
+      rg[i] = u < T ? __ldg(reinterpret_cast<const float4*>(dO + (s * T + u) * d + hh * 16) + j4)
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float* Pb = P + (s * H + hh) * T * T;
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    const int c = 8 * j + 2 * t;
-    sS[g * kAttLd + c] = pv[j][0] * (dp[j][0] - r0) * scale;
-    sS[g * kAttLd + c + 1] = pv[j][1] * (dp[j][1] - r0) * scale;
-    sS[(g + 8) * kAttLd + c] = pv[j][2] * (dp[j][2] - r1) * scale;
-    sS[(g + 8) * kAttLd + c + 1] = pv[j][3] * (dp[j][3] - r1) * scale;
-  }
-  __syncwarp();
-  float dq[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-  float dk[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-  float dv[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-  mma16x16<false, false>(dq, sS, sK, g, t);  // dQ = dS K
-  mma16x16<true, false>(dk, sS, sQ, g, t);   // dK = dS^T Q
-  mma16x16<true, false>(dv, sP, sG, g, t);   // dV = P^T dO
-  float* out = dQKV + s * T * ld + hh * 16;
+    for (int i = 0; i < 4; ++i) rp[i] = pofs[i] >= 0 ? __ldg(Pb + lane + 32 * i) : 0.0f;
+  };
+  if (w < items) fetch(w);
+  for (; w < items; w += stride) {
+    const long long s = w / H;
+    const int hh = (int)(w - s * H);
+    att_stage(r.q, sQ, lane);
+    att_stage(r.k, sK, lane);
+    att_stage(r.v, sV, lane);
+    att_stage(rg, sG, lane);
 #pragma unroll
-  for (int hr = 0; hr < 2; ++hr) {
-    const int row = g + 8 * hr;
-    if (row < T) {
+    for (int i = 0; i < 4; ++i)
+      if (pofs[i] >= 0) sP[pofs[i]] = rp[i];
+    if (w + stride < items) fetch(w + stride);  // in flight during this item
+    __syncwarp();
+    // dP = dO V^T
+    float dp[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    mma16x16<false, true>(dp, sG, sV, g, t);
+    // dS = P (dP - rowsum(P dP)) scale (rows g and g + 8 of this quad)
+    float pv[2][4], r0 = 0.0f, r1 = 0.0f;
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const int c = 8 * j + 2 * t;
-        *reinterpret_cast<float2*>(out + row * ld + c) = make_float2(dq[j][2 * hr], dq[j][2 * hr + 1]);
-        *reinterpret_cast<float2*>(out + row * ld + d + c) = make_float2(dk[j][2 * hr], dk[j][2 * hr + 1]);
-        *reinterpret_cast<float2*>(out + row * ld + 2 * d + c) = make_float2(dv[j][2 * hr], dv[j][2 * hr + 1]);
+    for (int j = 0; j < 2; ++j) {
+      const int c = 8 * j + 2 * t;
+      pv[j][0] = sP[g * kAttLd + c];
+      pv[j][1] = sP[g * kAttLd + c + 1];
+      pv[j][2] = sP[(g + 8) * kAttLd + c];
+      pv[j][3] = sP[(g + 8) * kAttLd + c + 1];
+      r0 = fmaf(pv[j][0], dp[j][0], fmaf(pv[j][1], dp[j][1], r0));
+      r1 = fmaf(pv[j][2], dp[j][2], fmaf(pv[j][3], dp[j][3], r1));
+    }
+    r0 += __shfl_xor_sync(0xffffffffu, r0, 1);
+    r0 += __shfl_xor_sync(0xffffffffu, r0, 2);
+    r1 += __shfl_xor_sync(0xffffffffu, r1, 1);
+    r1 += __shfl_xor_sync(0xffffffffu, r1, 2);
+    __syncwarp();  // every lane's V fragments are read: dS goes over V
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int c = 8 * j + 2 * t;
+      sS[g * kAttLd + c] = pv[j][0] * (dp[j][0] - r0) * scale;
+      sS[g * kAttLd + c + 1] = pv[j][1] * (dp[j][1] - r0) * scale;
+      sS[(g + 8) * kAttLd + c] = pv[j][2] * (dp[j][2] - r1) * scale;
+      sS[(g + 8) * kAttLd + c + 1] = pv[j][3] * (dp[j][3] - r1) * scale;
+    }
+    __syncwarp();
+    float dq[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    float dk[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    float dv[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    mma16x16<false, false>(dq, sS, sK, g, t);  // dQ = dS K
+    mma16x16<true, false>(dk, sS, sQ, g, t);   // dK = dS^T Q
+    mma16x16<true, false>(dv, sP, sG, g, t);   // dV = P^T dO
+    float* out = dQKV + s * T * ld + hh * 16;
+#pragma unroll
+    for (int hr = 0; hr < 2; ++hr) {
+      const int row = g + 8 * hr;
+      if (row < T) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int c = 8 * j + 2 * t;
+          *reinterpret_cast<float2*>(out + row * ld + c) = make_float2(dq[j][2 * hr], dq[j][2 * hr + 1]);
+          *reinterpret_cast<float2*>(out + row * ld + d + c) = make_float2(dk[j][2 * hr], dk[j][2 * hr + 1]);
+          *reinterpret_cast<float2*>(out + row * ld + 2 * d + c) = make_float2(dv[j][2 * hr], dv[j][2 * hr + 1]);
+        }
       }
     }
+    __syncwarp();  // the staged tiles are read before the next item overwrites them
   }
 }
 
@@ -1350,9 +1434,10 @@ cudaError_t ln_bwd(ut_tfm* t, const float* dY, const float* X, const float* st, 
 template <int DH>
 cudaError_t attn_fwd(const float* QKV, const int32_t* ne, const int32_t* sel, float* P, float* O, long long n, int T,
                      int NS, int H, bool mma, cudaStream_t s) {
-  if (mma && DH == 16 && T <= 16) {
-    attn_fwd_mma_kernel<<<blocks_for(n * H * 32, 128), 128, 0, s>>>(QKV, ne, sel, P, O, n, T, NS, H,
-                                                                     1.0f / sqrtf((float)DH));
+  if (n <= 0) return cudaSuccess;
+  if (mma && DH == 16 && T <= 16 && ((uintptr_t)QKV & 15) == 0) {
+    const long long grid = att_grid(attn_fwd_mma_kernel, n * H);
+    attn_fwd_mma_kernel<<<(unsigned)grid, 128, 0, s>>>(QKV, ne, sel, P, O, n, T, NS, H, 1.0f / sqrtf((float)DH));
     return cudaGetLastError();
   }
   const long long warps = (n * H + attn_pairs_per_warp(T) - 1) / attn_pairs_per_warp(T);
@@ -1364,8 +1449,10 @@ cudaError_t attn_fwd(const float* QKV, const int32_t* ne, const int32_t* sel, fl
 template <int DH>
 cudaError_t attn_bwd(const float* QKV, const float* P, const float* dO, float* dQKV, long long n, int T, int H,
                      bool mma, cudaStream_t s) {
-  if (mma && DH == 16 && T <= 16)
-    attn_bwd_mma_kernel<<<blocks_for(n * H * 32, 128), 128, 0, s>>>(QKV, P, dO, dQKV, n, T, H, 1.0f / sqrtf((float)DH));
+  if (n <= 0) return cudaSuccess;
+  if (mma && DH == 16 && T <= 16 && ((uintptr_t)QKV & 15) == 0 && ((uintptr_t)dO & 15) == 0)
+    attn_bwd_mma_kernel<<<(unsigned)att_grid(attn_bwd_mma_kernel, n * H), 128, 0, s>>>(QKV, P, dO, dQKV, n, T, H,
+                                                                                       1.0f / sqrtf((float)DH));
   else
     attn_bwd_kernel<DH><<<blocks_for(n * H * 32, 128), 128, 0, s>>>(QKV, P, dO, dQKV, n, T, H, 1.0f / sqrtf((float)DH));
   return cudaGetLastError();
