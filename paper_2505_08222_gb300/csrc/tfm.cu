@@ -341,12 +341,23 @@ __global__ void ln_fwd_kernel(const float* __restrict__ X, const float* __restri
   const int lane = threadIdx.x & 31;
   const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  float gj[DJ], bj[DJ], xn[DJ];
+#pragma unroll
+  for (int i = 0; i < DJ; ++i) {
+    gj[i] = gam[lane + 32 * i];
+    bj[i] = bet[lane + 32 * i];
+    xn[i] = w0 < rows ? X[w0 * d + lane + 32 * i] : 0.0f;
+  }
   for (long long r = w0; r < rows; r += nw) {
     float x[DJ], s = 0.0f;
 #pragma unroll
     for (int i = 0; i < DJ; ++i) {
-      x[i] = X[r * d + lane + 32 * i];
+      x[i] = xn[i];
       s += x[i];
+    }
+    if (r + nw < rows) {  // the warp's next row: in flight during this one
+#pragma unroll
+      for (int i = 0; i < DJ; ++i) xn[i] = X[(r + nw) * d + lane + 32 * i];
     }
     const float mean = warp_sum(s) * (1.0f / d);
     float v = 0.0f;
@@ -354,10 +365,7 @@ __global__ void ln_fwd_kernel(const float* __restrict__ X, const float* __restri
     for (int i = 0; i < DJ; ++i) v += (x[i] - mean) * (x[i] - mean);
     const float rstd = 1.0f / sqrtf(warp_sum(v) * (1.0f / d) + 1e-5f);
 #pragma unroll
-    for (int i = 0; i < DJ; ++i) {
-      const int j = lane + 32 * i;
-      Y[r * d + j] = (x[i] - mean) * rstd * gam[j] + bet[j];
-    }
+    for (int i = 0; i < DJ; ++i) Y[r * d + lane + 32 * i] = (x[i] - mean) * rstd * gj[i] + bj[i];
     if (lane == 0) {
       stat[2 * r] = mean;
       stat[2 * r + 1] = rstd;
@@ -377,30 +385,46 @@ __global__ void ln_bwd_kernel(const float* __restrict__ dY, const float* __restr
   const int lane = threadIdx.x & 31;
   const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  float pg[DJ], pb[DJ];
-#pragma unroll
-  for (int i = 0; i < DJ; ++i) pg[i] = pb[i] = 0.0f;
-  for (long long r = w0; r < rows; r += nw) {
-    const float mean = stat[2 * r], rstd = stat[2 * r + 1];
-    float xh[DJ], dxh[DJ], m1 = 0.0f, m2 = 0.0f;
+  float pg[DJ], pb[DJ], gj[DJ];
+  // the warp's next row (dY, X, base, statistics): in flight during the
+  // current one
+  float dyn[DJ], xn[DJ], bn[DJ], mn = 0.0f, rn = 0.0f;
+  auto fetch = [&](long long r) {
 #pragma unroll
     for (int i = 0; i < DJ; ++i) {
-      const int j = lane + 32 * i;
-      const float dy = dY[r * d + j];
-      xh[i] = (X[r * d + j] - mean) * rstd;
-      dxh[i] = dy * gam[j];
+      const long long o = r * d + lane + 32 * i;
+      dyn[i] = dY[o];
+      xn[i] = X[o];
+      bn[i] = base[o];
+    }
+    mn = stat[2 * r];
+    rn = stat[2 * r + 1];
+  };
+#pragma unroll
+  for (int i = 0; i < DJ; ++i) {
+    pg[i] = pb[i] = 0.0f;
+    gj[i] = gam[lane + 32 * i];
+  }
+  if (w0 < rows) fetch(w0);
+  for (long long r = w0; r < rows; r += nw) {
+    const float mean = mn, rstd = rn;
+    float xh[DJ], dxh[DJ], bs[DJ], m1 = 0.0f, m2 = 0.0f;
+#pragma unroll
+    for (int i = 0; i < DJ; ++i) {
+      const float dy = dyn[i];
+      xh[i] = (xn[i] - mean) * rstd;
+      bs[i] = bn[i];
+      dxh[i] = dy * gj[i];
       pg[i] = fmaf(dy, xh[i], pg[i]);
       pb[i] += dy;
       m1 += dxh[i];
       m2 = fmaf(dxh[i], xh[i], m2);
     }
+    if (r + nw < rows) fetch(r + nw);
     m1 = warp_sum(m1) * (1.0f / d);
     m2 = warp_sum(m2) * (1.0f / d);
 #pragma unroll
-    for (int i = 0; i < DJ; ++i) {
-      const long long o = r * d + lane + 32 * i;
-      out[o] = base[o] + rstd * (dxh[i] - m1 - xh[i] * m2);
-    }
+    for (int i = 0; i < DJ; ++i) out[r * d + lane + 32 * i] = bs[i] + rstd * (dxh[i] - m1 - xh[i] * m2);
   }
   // the block's 8 warps combined in warp order: one partial per block
   __shared__ float red[8][2 * d];
@@ -660,11 +684,13 @@ __device__ __forceinline__ void att_stage(const float4 (&x)[2], float* dst, int 
 
 // Resident blocks of 128 threads for a persistent attention kernel: as many
 // as fit on the device at once (at least one per SM).
+// Blocks of `threads` threads of `kernel` resident on the device at once (at
+// least one per SM), for the persistent and grid-stride kernels.
 template <typename K>
-inline long long att_capacity(K kernel) {
+inline long long resident_blocks(K kernel, int threads) {
   int dev = 0, b = 0, m = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, 128, 0) != cudaSuccess) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, 0) != cudaSuccess) {
     (void)cudaGetLastError();
     b = 1, m = 152;
   }
@@ -672,7 +698,7 @@ inline long long att_capacity(K kernel) {
 }
 template <typename K>
 inline long long att_grid(K kernel, long long items) {
-  static const long long cap = att_capacity(kernel);  // (initialised once, thread-safe)
+  static const long long cap = resident_blocks(kernel, 128);  // (initialised once, thread-safe)
   const long long need = (items + 3) / 4;
   return need < cap ? need : cap;
 }
@@ -1416,18 +1442,22 @@ cudaError_t wgrad(ut_tfm* t, const float* dOut, int n_o, const float* In, int n_
   return e;
 }
 
+// The LayerNorm kernels loop over rows (grid stride): at most kLnBlocks
+// blocks, no more than are resident at once.
 template <int DJ>
 cudaError_t ln_fwd(const float* X, const float* g, const float* b, float* Y, float* st, long long rows, cudaStream_t s) {
-  ln_fwd_kernel<DJ><<<kLnBlocks, 256, 0, s>>>(X, g, b, Y, st, rows);
+  static const int nblk = (int)std::min<long long>(kLnBlocks, resident_blocks(ln_fwd_kernel<DJ>, 256));
+  ln_fwd_kernel<DJ><<<nblk, 256, 0, s>>>(X, g, b, Y, st, rows);
   return cudaGetLastError();
 }
 
 template <int DJ>
 cudaError_t ln_bwd(ut_tfm* t, const float* dY, const float* X, const float* st, const float* g, const float* base,
                    float* out, float* grad_gb, long long rows, cudaStream_t s) {
-  ln_bwd_kernel<DJ><<<kLnBlocks, 256, 0, s>>>(dY, X, st, g, base, out, t->part, rows);
+  static const int nblk = (int)std::min<long long>(kLnBlocks, resident_blocks(ln_bwd_kernel<DJ>, 256));
+  ln_bwd_kernel<DJ><<<nblk, 256, 0, s>>>(dY, X, st, g, base, out, t->part, rows);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = reduce(t->part, kLnBlocks, 2 * 32 * DJ, 2 * 32 * DJ, grad_gb, s);
+  if (e == cudaSuccess) e = reduce(t->part, nblk, 2 * 32 * DJ, 2 * 32 * DJ, grad_gb, s);
   return e;
 }
 
