@@ -140,6 +140,14 @@ __device__ __forceinline__ uint16_t f2bf_bits(float v) {
   return *reinterpret_cast<uint16_t*>(&b);
 }
 __device__ __forceinline__ float bf_bits2f(uint16_t v) { return __uint_as_float(((uint32_t)v) << 16); }
+// Two FP32 values rounded to BF16 (nearest even, as f2bf_bits) and packed,
+// lo in the low half: one cvt.rn.bf16x2.f32, whose first source goes to the
+// upper half.
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
 
 // Warp reductions.
 __device__ __forceinline__ float warp_sum(float v) {

@@ -230,10 +230,10 @@ __device__ __forceinline__ void obs_reward_warp(const EnvDev& d, int e, int afte
         v[5] = 1.0f;
       }
       uint4 packed;
-      packed.x = (uint32_t)f2bf_bits(v[0]) | ((uint32_t)f2bf_bits(v[1]) << 16);
-      packed.y = (uint32_t)f2bf_bits(v[2]) | ((uint32_t)f2bf_bits(v[3]) << 16);
-      packed.z = (uint32_t)f2bf_bits(v[4]) | ((uint32_t)f2bf_bits(v[5]) << 16);
-      packed.w = (uint32_t)f2bf_bits(v[6]) | ((uint32_t)f2bf_bits(v[7]) << 16);
+      packed.x = bf16x2_bits(v[0], v[1]);
+      packed.y = bf16x2_bits(v[2], v[3]);
+      packed.z = bf16x2_bits(v[4], v[5]);
+      packed.w = bf16x2_bits(v[6], v[7]);
       reinterpret_cast<uint4*>(d.obs)[(long long)ia * d.NS + slot] = packed;
     }
     if (!after_reset) {

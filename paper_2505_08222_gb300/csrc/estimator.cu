@@ -35,10 +35,10 @@ __device__ __forceinline__ float gelu_grad(float x) {
 
 __device__ __forceinline__ void store8(unsigned char* img, int row, int k0, int rows, const float* v) {
   uint4 p;
-  p.x = (uint32_t)f2bf_bits(v[0]) | ((uint32_t)f2bf_bits(v[1]) << 16);
-  p.y = (uint32_t)f2bf_bits(v[2]) | ((uint32_t)f2bf_bits(v[3]) << 16);
-  p.z = (uint32_t)f2bf_bits(v[4]) | ((uint32_t)f2bf_bits(v[5]) << 16);
-  p.w = (uint32_t)f2bf_bits(v[6]) | ((uint32_t)f2bf_bits(v[7]) << 16);
+  p.x = bf16x2_bits(v[0], v[1]);
+  p.y = bf16x2_bits(v[2], v[3]);
+  p.z = bf16x2_bits(v[4], v[5]);
+  p.w = bf16x2_bits(v[6], v[7]);
   *reinterpret_cast<uint4*>(img + tc::kmajor_offset(row, k0, rows)) = p;
 }
 
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kT, 1) fwd_kernel(FwdArgs p) {
         for (int i = 0; i < 16; i += 4) *reinterpret_cast<float4*>(zr + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
 #pragma unroll
         for (int i = 0; i < 16; i += 2)
-          *reinterpret_cast<uint32_t*>(ar + i) = (uint32_t)f2bf_bits(av[i]) | ((uint32_t)f2bf_bits(av[i + 1]) << 16);
+          *reinterpret_cast<uint32_t*>(ar + i) = bf16x2_bits(av[i], av[i + 1]);
       }
       if (l < 2) {
         store8(sA, tid, c0, 128, av);
@@ -520,7 +520,7 @@ __global__ void __launch_bounds__(kT, 1) bwd_kernel(Net net, TrainBufs t, int* s
       uint16_t* dr = t.dz + ((long long)2 * t.B + b) * HID + c0;
 #pragma unroll
       for (int i = 0; i < 16; i += 2)
-        *reinterpret_cast<uint32_t*>(dr + i) = (uint32_t)f2bf_bits(dz[i]) | ((uint32_t)f2bf_bits(dz[i + 1]) << 16);
+        *reinterpret_cast<uint32_t*>(dr + i) = bf16x2_bits(dz[i], dz[i + 1]);
     }
     store8(sA, tid, c0, 128, dz);
     store8(sA, tid, c0 + 8, 128, dz + 8);
@@ -548,7 +548,7 @@ __global__ void __launch_bounds__(kT, 1) bwd_kernel(Net net, TrainBufs t, int* s
         uint16_t* dr = t.dz + ((long long)l * t.B + b) * HID + c0;
 #pragma unroll
         for (int i = 0; i < 16; i += 2)
-          *reinterpret_cast<uint32_t*>(dr + i) = (uint32_t)f2bf_bits(v[i]) | ((uint32_t)f2bf_bits(v[i + 1]) << 16);
+          *reinterpret_cast<uint32_t*>(dr + i) = bf16x2_bits(v[i], v[i + 1]);
       }
       if (l == 1) {
         store8(sA, tid, c0, 128, v);

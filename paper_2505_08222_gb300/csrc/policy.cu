@@ -41,6 +41,7 @@
 #include "policy.cuh"
 #include "runtime.cuh"
 #include "gelu.cuh"
+#include "f32x2.cuh"
 #include "tc.cuh"
 
 namespace ut {
@@ -103,8 +104,26 @@ struct Geo {
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
-__device__ __forceinline__ uint32_t pack_bf2(float a, float b) {
-  return (uint32_t)f2bf_bits(a) | ((uint32_t)f2bf_bits(b) << 16);
+__device__ __forceinline__ uint32_t pack_bf2(float a, float b) { return bf16x2_bits(a, b); }
+
+// Element-wise epilogue steps on packed FP32 pairs (each lane rounded like
+// the scalar operation): v = (v + b) s over N values; v += b; x += v + b.
+template <int N>
+__device__ __forceinline__ void bias_scale2(float* v, const float* b, float s) {
+  const unsigned long long S = f2pk(s, s);
+#pragma unroll
+  for (int i = 0; i < N; i += 2) f2upk(f2mul(f2add(f2pk(v[i], v[i + 1]), f2pk(b[i], b[i + 1])), S), v[i], v[i + 1]);
+}
+template <int N>
+__device__ __forceinline__ void bias_add2(float* v, const float* b) {
+#pragma unroll
+  for (int i = 0; i < N; i += 2) f2upk(f2add(f2pk(v[i], v[i + 1]), f2pk(b[i], b[i + 1])), v[i], v[i + 1]);
+}
+template <int N>
+__device__ __forceinline__ void residual_add2(float* x, const float* v, const float* b) {
+#pragma unroll
+  for (int i = 0; i < N; i += 2)
+    f2upk(f2add(f2pk(x[i], x[i + 1]), f2add(f2pk(v[i], v[i + 1]), f2pk(b[i], b[i + 1]))), x[i], x[i + 1]);
 }
 
 // Store 8 consecutive K values of `row` into a K-major operand image.
@@ -293,13 +312,19 @@ __device__ __forceinline__ void ln_part_to_tmem(const float (&x)[Geo<D>::COLS], 
   float mean, inv;
   ln_part_stats<D>(x, sStat, row, part, mean, inv);
   const int c_lo = part * COLS;
+  const unsigned long long NM = f2pk(-mean, -mean), INV = f2pk(inv, inv);
 #pragma unroll
   for (int c0 = 0; c0 < COLS; c0 += 32) {
     uint32_t w[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i)
-      w[i] = pack_bf2(fmaf((x[c0 + 2 * i] - mean) * inv, g[c_lo + c0 + 2 * i], b[c_lo + c0 + 2 * i]),
-                      fmaf((x[c0 + 2 * i + 1] - mean) * inv, g[c_lo + c0 + 2 * i + 1], b[c_lo + c0 + 2 * i + 1]));
+    for (int i = 0; i < 16; ++i) {  // (x - mean) inv g + b on packed pairs
+      const int c = c_lo + c0 + 2 * i;
+      float y0, y1;
+      f2upk(f2fma(f2mul(f2add(f2pk(x[c0 + 2 * i], x[c0 + 2 * i + 1]), NM), INV), f2pk(g[c], g[c + 1]),
+                  f2pk(b[c], b[c + 1])),
+            y0, y1);
+      w[i] = pack_bf2(y0, y1);
+    }
     tc::tmem_st16(taddr + (uint32_t)(c0 / 2), w);
   }
   tc::tmem_wait_st();
@@ -916,8 +941,7 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
             const int cc = pp * COLS + 16 * k;
             float v[16];
             tc::tmem_ld16(tl + col + cc, v);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = (v[i] + bias[cc + i]) * scale;
+            bias_scale2<16>(v, bias + cc, scale);
             store8(dst, row, cc, 128, v);
             store8(dst, row, cc + 8, 128, v + 8);
           },
@@ -925,8 +949,7 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
             const int cc = pp * COLS + 16 * k;
             float v[32];
             tc::tmem_ld32(tl + col + cc, v);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = (v[i] + bias[cc + i]) * scale;
+            bias_scale2<32>(v, bias + cc, scale);
 #pragma unroll
             for (int i = 0; i < 32; i += 8) store8(dst, row, cc + i, 128, v + i);
           });
@@ -972,8 +995,7 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
     for (int c0 = 0; c0 < COLS; c0 += 16) {
       float v[16];
       tc::tmem_ld16(tl + G::COL_S + c_lo + c0, v);
-#pragma unroll
-      for (int i = 0; i < 16; ++i) x[c0 + i] += v[i] + bo[c_lo + c0 + i];
+      residual_add2<16>(x + c0, v, bo + c_lo + c0);
     }
 
     // ---- feed-forward sub-block ----
@@ -1025,8 +1047,7 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
               const int hc = pp * G::HCOLS + 16 * k;
               float v[16];
               tc::tmem_ld16(tl + col_cur + hc, v);
-#pragma unroll
-              for (int i = 0; i < 16; ++i) v[i] += b1[c * 128 + hc + i];
+              bias_add2<16>(v, b1 + c * 128 + hc);
 #pragma unroll
               for (int i = 0; i < 16; i += 2) gelu2(v[i], v[i + 1]);
               store8(hcur, row, hc, 128, v);
@@ -1038,8 +1059,7 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
                 const int hc = pp * G::HCOLS + 16 * kk;
                 float v[16];
                 tc::tmem_ld16(tl + col_cur + hc, v);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] += b1[c * 128 + hc + i];
+                bias_add2<16>(v, b1 + c * 128 + hc);
 #pragma unroll
                 for (int i = 0; i < 16; i += 2) gelu2(v[i], v[i + 1]);
                 store8(hcur, row, hc, 128, v);
@@ -1076,8 +1096,7 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
             const int hc = pp * G::HCOLS + 16 * k;
             float v[16];
             tc::tmem_ld16(tl + G::COL_S + hc, v);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] += b1[c * 128 + hc + i];
+            bias_add2<16>(v, b1 + c * 128 + hc);
 #pragma unroll
             for (int i = 0; i < 16; i += 2) gelu2(v[i], v[i + 1]);
             store8(sH, row, hc, 128, v);
@@ -1089,8 +1108,7 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
               const int hc = pp * G::HCOLS + 16 * kk;
               float v[16];
               tc::tmem_ld16(tl + G::COL_S + hc, v);
-#pragma unroll
-              for (int i = 0; i < 16; ++i) v[i] += b1[c * 128 + hc + i];
+              bias_add2<16>(v, b1 + c * 128 + hc);
 #pragma unroll
               for (int i = 0; i < 16; i += 2) gelu2(v[i], v[i + 1]);
               store8(sH, row, hc, 128, v);
@@ -1110,8 +1128,7 @@ __global__ void __launch_bounds__(Geo<D>::THREADS, D == 64 ? 2 : 1) policy_fwd_k
     for (int c0 = 0; c0 < COLS; c0 += 16) {
       float v[16];
       tc::tmem_ld16(tl + G::COL_ACC + c_lo + c0, v);
-#pragma unroll
-      for (int i = 0; i < 16; ++i) x[c0 + i] += v[i] + b2[c_lo + c0 + i];
+      residual_add2<16>(x + c0, v, b2 + c_lo + c0);
     }
   }
 

@@ -47,9 +47,7 @@ __host__ __device__ inline size_t img_offset(int r, int c, int R, int C) {
   return (size_t)blk * kTcMaxN * C * 2 + (size_t)(c >> 3) * rows * 16 + (size_t)rr * 16 + (size_t)(c & 7) * 2;
 }
 
-__device__ __forceinline__ uint32_t pack_bf2(float lo, float hi) {
-  return (uint32_t)f2bf_bits(lo) | ((uint32_t)f2bf_bits(hi) << 16);
-}
+__device__ __forceinline__ uint32_t pack_bf2(float lo, float hi) { return bf16x2_bits(lo, hi); }
 
 // The epilogue of four consecutive outputs (m, n .. n + 3) (float4 form of
 // epi_store; ldc, n multiples of 4).
