@@ -3,9 +3,11 @@
 Q(a) approximates Phi(-a) e^(a^2 / 2) = erfc(a / sqrt 2) e^(a^2 / 2) / 2 on
 [0, 4] (a smooth, slowly varying function: the Gaussian factor is taken out);
 degree 8, least squares on the relative error, reweighted towards minimax.
-Prints the FP32 coefficients (constant term first) and the largest absolute
-GELU error of the FP32 evaluation order used on the device, against FP64
-erf, over [-12, 12] and a normal sample.  Run: python gelu_fit.py
+Prints the FP32 coefficients (constant term first; gelu.cuh holds them
+negated and evaluates -Q, then relu(x) + (|x| e) (-Q) in one fma, which
+rounds exactly as the subtraction below) and the largest absolute GELU error
+of that FP32 evaluation order, against FP64 erf, over [-12, 12] and a normal
+sample.  Run: python gelu_fit.py
 """
 import numpy as np
 from scipy.special import erf, erfc
