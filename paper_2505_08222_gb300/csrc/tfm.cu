@@ -682,20 +682,22 @@ __device__ __forceinline__ void att_stage(const float4 (&x)[2], float* dst, int 
   for (int i = 0; i < 2; ++i) *reinterpret_cast<float4*>(dst + (u0 + 8 * i) * kAttLd + 4 * j4) = x[i];
 }
 
-// Resident blocks of 128 threads for a persistent attention kernel: as many
-// as fit on the device at once (at least one per SM).
 // Blocks of `threads` threads of `kernel` resident on the device at once (at
 // least one per SM), for the persistent and grid-stride kernels.
 template <typename K>
 inline long long resident_blocks(K kernel, int threads) {
   int dev = 0, b = 0, m = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, 0) != cudaSuccess) {
     (void)cudaGetLastError();
     b = 1, m = 152;
   }
   return (long long)(b > 0 ? b : 1) * (m > 0 ? m : 152);
 }
+
+// Grid of a persistent attention kernel (4 items per block at a time): the
+// resident blocks, or fewer when there are fewer items.
 template <typename K>
 inline long long att_grid(K kernel, long long items) {
   static const long long cap = resident_blocks(kernel, 128);  // (initialised once, thread-safe)
@@ -709,11 +711,10 @@ inline long long att_grid(K kernel, long long items) {
 // tokens padded to 16, the masked softmax on the accumulator fragments (keys
 // u <= n_ent of the sample, a row in the 4 lanes of a quad), P written out
 // (zero at masked keys) and staged, then O = P V.
-__global__ void __launch_bounds__(128, 8) attn_fwd_mma_kernel(const float* __restrict__ QKV,
-                                                           const int32_t* __restrict__ n_ent,
-                                                           const int32_t* __restrict__ sel, float* __restrict__ P,
-                                                           float* __restrict__ O, long long n, int T, int NS, int H,
-                                                           float scale) {
+__global__ void __launch_bounds__(128, 8)
+    attn_fwd_mma_kernel(const float* __restrict__ QKV, const int32_t* __restrict__ n_ent,
+                        const int32_t* __restrict__ sel, float* __restrict__ P, float* __restrict__ O, long long n,
+                        int T, int NS, int H, float scale) {
   __shared__ __align__(16) float sm[4][4][16 * kAttLd];  // Q, K, V, P of each warp
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
   const int d = 16 * H;
@@ -804,9 +805,9 @@ __global__ void __launch_bounds__(128, 8) attn_fwd_mma_kernel(const float* __res
 // 16 (padded rows and columns staged as zeros), and
 // dS = P (dP - rowsum(P dP)) scale on the accumulator fragments (a row lives
 // in the 4 lanes of a quad).  dS is staged over V (V is read only by dP).
-__global__ void __launch_bounds__(128, 6) attn_bwd_mma_kernel(const float* __restrict__ QKV, const float* __restrict__ P,
-                                                           const float* __restrict__ dO, float* __restrict__ dQKV,
-                                                           long long n, int T, int H, float scale) {
+__global__ void __launch_bounds__(128, 6)
+    attn_bwd_mma_kernel(const float* __restrict__ QKV, const float* __restrict__ P, const float* __restrict__ dO,
+                        float* __restrict__ dQKV, long long n, int T, int H, float scale) {
   __shared__ __align__(16) float sm[4][5][16 * kAttLd];  // Q, K, V then dS, dO, P of each warp
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
   const int d = 16 * H, ld = 3 * d;
