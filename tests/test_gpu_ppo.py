@@ -153,6 +153,39 @@ def test_actor_gradient_matches_oracle(case, tc):
     print(f"{case} tc={tc}: worst per-tensor gradient error {worst:.2e}; loss {st[0]:.5f} vs {loss:.5f}")
 
 
+ATTN_EDGES = {
+    # the tensor-core attention kernels' edges (head width 16): 16 tokens
+    # (no padded row), 2 tokens (14 padded rows), two samples (fewer items
+    # than warps)
+    "t16": (32, 1, 2, 5, 15, True, 37),
+    "t2": (64, 1, 4, 7, 1, True, 45),
+    "two_samples": (64, 2, 4, 7, 10, True, 2),
+}
+
+
+@pytest.mark.parametrize("case", list(ATTN_EDGES))
+def test_tensor_core_attention_edges_match_oracle(case):
+    """Forward outputs and the actor gradient on the tensor-core path (the
+    attention on mma.sync) at token counts 16 and 2 and with two samples."""
+    d, L, H, no, NS, bf, n = ATTN_EDGES[case]
+    prm = synth.policy_params(synth.PolicyDims(d, L, H, no), seed=53)
+    net = ppo.Tfm(prm, d, L, H, no, NS, n, bf, tensor_cores=True)
+    tok, ne, h, tok_d, ne_d, h_d = _inputs(n, NS, d, 54, bf)
+    h_out = torch.empty_like(h_d)
+    out = net.forward(tok_d, ne_d, h_d, h_out=h_out).cpu().numpy()
+    ref, ref_h = oracle.tfm_forward(prm, d, L, H, no, tok, ne, h)
+    e1 = _close_tc(out, ref, True)
+    _close_tc(h_out.cpu().numpy(), ref_h, True)
+    act, logp_old, adv = _ppo_args(prm, d, L, H, no, tok, ne, h, 55)
+    st = net.actor_grad(tok_d, ne_d, h_d, torch.from_numpy(act).cuda(), torch.from_numpy(logp_old).cuda(),
+                        torch.from_numpy(adv).cuda(), clip_eps=0.2, ent_coef=0.01)
+    loss, g, rst = oracle.tfm_loss_grad(prm, d, L, H, no, oracle.ACTOR, tok, ne, h, act, logp_old, adv, 0.2, 0.01)
+    worst = _grad_close(net.grad.cpu().numpy(), g, synth.policy_shapes(synth.PolicyDims(d, L, H, no)),
+                        tol=_tol(True)["grad"])
+    np.testing.assert_allclose(st[:2], rst[:2], rtol=2e-2, atol=2e-3)
+    print(f"{case}: max |dout| {e1:.2e}, worst per-tensor gradient error {worst:.2e}")
+
+
 @pytest.mark.parametrize("tc", [False, True])
 def test_value_gradient_matches_oracle(tc):
     d, L, H, no, NS, bf, n = CASES["critic64"]
